@@ -1,0 +1,181 @@
+/*
+ * hsf.h -- C ABI of a GB300 (sm_103a) library for joint-cutting Hybrid
+ * Schroedinger-Feynman (HSF) simulation of quantum circuits.
+ *
+ * Method (Herzog, Burgholzer, Ufrecht, Scherer, Wille, "Joint Cutting for Hybrid
+ * Schroedinger-Feynman Simulation of Quantum Circuits"):
+ *   - Sec. II-B: the qubits are split horizontally after qubit l; half a holds
+ *     qubits l+1..n-1 (the left / most significant Kronecker factor), half b holds
+ *     qubits 0..l.
+ *   - Sec. III-A / IV-A: the gates crossing the cut are grouped into blocks; each
+ *     block unitary A is multiplied out and Schmidt-decomposed,
+ *     A = sum_m sigma_m X_m (x) Y_m (eq. equ-schmidt-decompostion-res), via the SVD
+ *     of the relabelled matrix A~_{(i^b j^b),(i^a j^a)} (eq. eq-svd).
+ *   - Sec. II-B: a path chooses one Schmidt term per block; for each path both
+ *     half circuits are simulated from |0...0> and the amplitudes are the sum over
+ *     paths of the products psi_a^p(x_a) psi_b^p(x_b) ("Kronecker product ... and
+ *     adding up all contributions").
+ *
+ * Conventions (Sec. II-A): bit q of a basis index / bitstring is qubit q; the
+ * amplitude index is x = x_a * 2^{n_b} + x_b.  A gate on the ordered qubits
+ * (q[0], q[1], ...) has its matrix index in Kronecker order with q[0] the most
+ * significant factor (CNOT with the control listed first is P0 (x) I + P1 (x) X,
+ * Example 2).  Rotations: RX/RY/RZ(t) = exp(-i t P/2), RZZ(t) = exp(-i t Z(x)Z/2).
+ *
+ * Paths are numbered in mixed radix over the blocks in the order they are listed
+ * (block 0 is the most significant digit).  The listed order must be compatible with
+ * the circuit's dependencies (a block that depends on another is listed after it).
+ *
+ * Errors: every entry point returns an hsf_status; nothing is thrown across the
+ * ABI.  hsf_last_error() returns a human-readable message for the calling thread's
+ * last failure.  All device work is ordered on the caller's stream; only hsf_plan
+ * synchronises (it reads back the Schmidt ranks).
+ */
+#ifndef HSF_H
+#define HSF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum hsf_status {
+  HSF_OK = 0,
+  HSF_EINVAL = 1,    /* bad argument: gate, qubit, cut, size, pointer, mode      */
+  HSF_EBLOCK = 2,    /* crossing gate not in exactly one block, non-convex block,
+                        block without a crossing gate, or blocks listed out of
+                        dependency order                                          */
+  HSF_ERANK = 3,     /* path count above max_paths / 2^62, block too large         */
+  HSF_ENOMEM = 4,    /* workspace too small or host allocation failed            */
+  HSF_ECUDA = 5,     /* a CUDA runtime call failed (message has the CUDA error)   */
+  HSF_ETIMEOUT = 6,  /* a bounded device-side wait expired                       */
+  HSF_ENUMERIC = 7,  /* NaN / Inf detected                                       */
+  HSF_ENOTSUP = 8    /* combination not supported by this build                  */
+} hsf_status;
+
+typedef enum hsf_gate_kind {
+  HSF_GATE_MATRIX = 0, /* explicit 2^nq x 2^nq unitary in `mat`, nq in 1..3        */
+  HSF_GATE_H = 1, HSF_GATE_X = 2, HSF_GATE_Y = 3, HSF_GATE_Z = 4,
+  HSF_GATE_S = 5, HSF_GATE_T = 6,
+  HSF_GATE_RX = 7, HSF_GATE_RY = 8, HSF_GATE_RZ = 9,
+  HSF_GATE_CX = 10, HSF_GATE_CZ = 11, HSF_GATE_SWAP = 12, HSF_GATE_ISWAP = 13,
+  HSF_GATE_RZZ = 14
+} hsf_gate_kind;
+
+/* One gate.  `mat` (HSF_GATE_MATRIX only) points to host memory holding the
+ * 2^nq x 2^nq complex128 matrix, row-major, re/im interleaved; it is copied by
+ * hsf_plan.  `param_id` >= 0 ties the angle to entry param_id of a shared angle
+ * vector (gradients, angle overrides); -1 keeps `param`. */
+typedef struct hsf_gate {
+  int32_t kind;
+  int32_t nq;
+  int32_t q[4];
+  double param;
+  int32_t param_id;
+  int32_t reserved;
+  const double *mat;
+} hsf_gate;
+
+typedef struct hsf_circuit {
+  int32_t n;              /* qubits, 2..62                                        */
+  int32_t num_gates;
+  const hsf_gate *gates;  /* host array of num_gates gates, in circuit order       */
+} hsf_circuit;
+
+/* Blocks in CSR form: block k holds gate indices gate_idx[offsets[k] .. offsets[k+1]).
+ * Every gate crossing the cut must be in exactly one block; a block may also hold
+ * gates of one side (they are multiplied into the block).  Singleton blocks give
+ * the standard per-gate cut. */
+typedef struct hsf_blocks {
+  int32_t num_blocks;
+  const int32_t *offsets;   /* num_blocks + 1 entries, host memory */
+  const int32_t *gate_idx;  /* host memory                         */
+} hsf_blocks;
+
+typedef enum hsf_precision { HSF_PREC_C64 = 0, HSF_PREC_C128 = 1 } hsf_precision;
+
+/* Path-GEMM arithmetic for full / window output. */
+typedef enum hsf_gemm_mode {
+  HSF_GEMM_FP32 = 0,     /* CUDA-core FP32 products, FP32 accumulate            */
+  HSF_GEMM_BF16X3 = 1,   /* tensor cores: split-BF16 (hi*hi + hi*lo + lo*hi)    */
+  HSF_GEMM_TF32X3 = 2,   /* tensor cores: split-TF32 (3 products)               */
+  HSF_GEMM_TF32 = 3      /* tensor cores: one TF32 product (reported only)      */
+} hsf_gemm_mode;
+
+typedef struct hsf_plan_opts {
+  int32_t precision;       /* hsf_precision of the half states                      */
+  int32_t gemm_mode;       /* hsf_gemm_mode for full / window output                */
+  double rank_tol;         /* keep sigma_m > rank_tol * sigma_0; <= 0 means 1e-12   */
+  uint64_t max_paths;      /* 0 means 2^40                                          */
+  int32_t tile_bits;       /* 0 = automatic                                         */
+  int32_t flags;           /* HSF_FLAG_* below                                       */
+  const double *angles;    /* optional host array: angle of param_id j is angles[j] */
+  int32_t num_angles;
+  int32_t reserved;
+} hsf_plan_opts;
+
+#define HSF_FLAG_NO_LIGHTCONE 1   /* keep circuit order: no hoisting of gates that
+                                     commute with later Schmidt factors             */
+#define HSF_FLAG_NO_LEAF_CONTRACT 2 /* always materialise leaf half states         */
+
+typedef struct hsf_plan hsf_plan;
+
+typedef struct hsf_plan_info {
+  int32_t n, n_a, n_b;
+  int32_t num_blocks;
+  uint64_t num_paths;       /* product of the Schmidt ranks                         */
+  int32_t precision;
+  int32_t max_rank;
+  int64_t tree_nodes;       /* half-state simulations per side with prefix reuse    */
+  int64_t num_launches;     /* sweep launches per side for one full run             */
+} hsf_plan_info;
+
+/* Plan a circuit: validates the circuit, cut and blocks, multiplies every block and
+ * Schmidt-decomposes it on the current CUDA device in FP64 (one-sided Jacobi SVD),
+ * reads back the ranks (synchronous), and builds the per-level gate programs.
+ * cut_l: the cut lies between qubit cut_l and cut_l+1 (Table II "cut pos."),
+ * 0 <= cut_l <= n-2.  opts may be NULL (defaults).  On success *out owns all
+ * plan-time device tables; release it with hsf_plan_destroy. */
+hsf_status hsf_plan_create(const hsf_circuit *circuit, int32_t cut_l,
+                           const hsf_blocks *blocks, const hsf_plan_opts *opts,
+                           hsf_plan **out);
+
+hsf_status hsf_plan_get_info(const hsf_plan *plan, hsf_plan_info *info);
+
+/* Singular values (descending, only the kept ones) and rank of block k; copies at
+ * most cap values into sigma (host). */
+hsf_status hsf_plan_get_sigma(const hsf_plan *plan, int32_t block, double *sigma,
+                              int32_t cap, int32_t *rank);
+
+void hsf_plan_destroy(hsf_plan *plan);
+
+/* Device workspace (bytes) that hsf_run needs for the given output request:
+ * num_bitstrings > 0 selects bitstring output, else window > 0 selects the first
+ * `window` amplitudes, else all 2^n amplitudes.  The library sizes its breadth
+ * (paths in flight) to fit `budget_bytes` when it is nonzero. */
+hsf_status hsf_workspace_size(const hsf_plan *plan, size_t num_bitstrings,
+                              uint64_t window, size_t budget_bytes, size_t *bytes);
+
+/* Amplitudes by HSF path sum over paths [path_begin, path_end) (both 0 = all).
+ *   bitstrings: device array of num uint64 (bit q = qubit q), or NULL.
+ *   window:     with bitstrings == NULL: the first `window` amplitudes (0 = all 2^n).
+ *   out:        device array of complex128 (re, im interleaved), one per amplitude.
+ *   workspace:  device buffer of at least hsf_workspace_size(...) bytes, 256-byte
+ *               aligned, caller-owned.  stream: cudaStream_t (NULL = legacy default).
+ * The per-path products are formed in the plan's state precision and summed across
+ * path chunks in FP64 with Neumaier compensation. */
+hsf_status hsf_run(hsf_plan *plan, const uint64_t *bitstrings, size_t num,
+                   uint64_t window, uint64_t path_begin, uint64_t path_end,
+                   void *out, void *workspace, size_t workspace_bytes, void *stream);
+
+const char *hsf_last_error(void);
+
+/* Library version string. */
+const char *hsf_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HSF_H */

@@ -1,0 +1,101 @@
+// Internal declarations shared by the host planner (C++) and the CUDA kernels.
+// Nothing here is part of the public C ABI (include/hsf.h).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+namespace hsf {
+
+// ---------------------------------------------------------------------------
+// Gate programs of the half-state sweep kernel.
+// A program is a list of ops applied in order to one tile of a half state.  A tile
+// holds 2^t amplitudes: the storage bits in `active_mask` vary inside the tile, the
+// other storage bits are fixed per tile.
+// ---------------------------------------------------------------------------
+enum : int32_t { OP_DENSE = 0, OP_DIAG = 1 };
+constexpr int32_t kFixedBit = 64;   // pos >= kFixedBit: storage bit (pos - 64) outside the tile
+
+struct DevOp {
+  int32_t type;          // OP_DENSE: 2^nq x 2^nq matrix; OP_DIAG: 2^nq phases
+  int32_t nq;            // 1..3
+  int32_t pos[3];        // tile bit of each operand qubit, pos[0] = matrix MSB
+  int32_t mat;           // offset (complex elements) into the program's matrix pool
+  int32_t digit_stride;  // > 0: matrix = pool[mat + digit * digit_stride] (Schmidt factor)
+  int32_t pad;
+};
+
+// One launch of the sweep kernel: all tiles of all nodes of one tree level, one pass.
+struct SweepArgs {
+  const DevOp *ops;
+  int32_t num_ops;
+  int32_t h;             // half-state qubits
+  const void *mats;      // float2 / double2 pool
+  const void *src;       // parent level buffer (read_parent) or == dst
+  void *dst;             // this level's buffer, node-major, 2^h amplitudes per node
+  uint64_t active_mask;  // storage bits inside a tile
+  int32_t t;             // popcount(active_mask)
+  int32_t radix;         // Schmidt rank of this level's block (1 at the root)
+  int64_t node_lo;       // level-global index of the first node held in dst
+  int64_t parent_lo;     // level-global index of the first node held in src
+  int64_t num_nodes;
+  int32_t tiles_per_node;
+  int32_t read_parent;   // 1: tile is loaded from node/radix in src
+  int32_t init_zero;     // 1: tile starts from |0...0>
+  int32_t pad;
+};
+
+// Path accumulation over leaf half states (bitstring output).
+struct GatherArgs {
+  const void *A;         // a-side leaves [paths][2^ha]
+  const void *B;         // b-side leaves [paths][2^hb]
+  int64_t num_paths;
+  int32_t ha, hb;
+  const uint64_t *bits;  // bitstrings (bit q = qubit q)
+  int64_t S;
+  int32_t paths_per_group;
+  int32_t num_groups;
+  double *partial;       // [num_groups][S][2]
+};
+
+// Window / full output: C[i][j] = sum_p A[p][i] * B[p][j], i < M, j < N.
+struct WindowArgs {
+  const void *A;
+  const void *B;
+  int64_t num_paths;
+  int32_t ha, hb;
+  int64_t M, N;          // rows (x_a) and columns (x_b) of the window rectangle
+  uint64_t window;       // amplitudes kept: index x_a * 2^hb + x_b < window
+  double *out;           // complex128 accumulator (re, im)
+  double *comp;          // Neumaier compensation (re, im)
+};
+
+struct BlockSvdArgs {
+  // inputs
+  int32_t num_blocks;
+  const int32_t *block_k;        // [num_blocks] total qubits k, k_a, k_b packed as 3 ints
+  const int32_t *gate_begin;     // [num_blocks + 1] into gate descriptors
+  const int32_t *gate_desc;      // per gate: nq, pos0, pos1, pos2, mat offset (5 ints)
+  const double *gate_mats;       // complex128 pool (re, im)
+  double rank_tol;
+  int32_t max_sweeps;
+  // outputs
+  double *sigma;                 // [num_blocks][64]
+  int32_t *rank;                 // [num_blocks]
+  double *xf;                    // [num_blocks][64][64][2]  X'_m (scaled by sqrt sigma)
+  double *yf;                    // [num_blocks][64][64][2]  Y'_m
+  int32_t *sweeps_used;          // [num_blocks]
+};
+
+cudaError_t launch_sweep(const SweepArgs &a, int precision, cudaStream_t st);
+cudaError_t launch_gather_dot(const GatherArgs &a, int precision, cudaStream_t st);
+cudaError_t launch_reduce_partials(const double *partial, int32_t num_groups, int64_t S,
+                                   double *out, double *comp, cudaStream_t st);
+cudaError_t launch_window(const WindowArgs &a, int precision, cudaStream_t st);
+cudaError_t launch_finalize(double *out, const double *comp, int64_t count, cudaStream_t st);
+cudaError_t launch_zero(double *p, int64_t count, cudaStream_t st);
+cudaError_t launch_block_svd(const BlockSvdArgs &a, cudaStream_t st);
+
+}  // namespace hsf

@@ -1,0 +1,252 @@
+"""Thin ctypes binding of libhsf (include/hsf.h): argument marshalling only.
+
+Every numerical step runs in the library's CUDA kernels.  The functions keep the C
+names (``hsf_plan_create``, ``hsf_run``, ...); ``Plan`` is a small owner object that
+frees the native plan and caches a device workspace allocated through PyTorch.
+
+The library is loaded from this package directory; if it is missing the import of
+this module raises (there is no fallback path).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libhsf.so")
+
+HSF_OK = 0
+STATUS = {0: "HSF_OK", 1: "HSF_EINVAL", 2: "HSF_EBLOCK", 3: "HSF_ERANK", 4: "HSF_ENOMEM",
+          5: "HSF_ECUDA", 6: "HSF_ETIMEOUT", 7: "HSF_ENUMERIC", 8: "HSF_ENOTSUP"}
+KIND = {"matrix": 0, "h": 1, "x": 2, "y": 3, "z": 4, "s": 5, "t": 6, "rx": 7, "ry": 8, "rz": 9,
+        "cx": 10, "cz": 11, "swap": 12, "iswap": 13, "rzz": 14}
+PREC = {"c64": 0, "c128": 1}
+GEMM = {"fp32": 0, "bf16x3": 1, "tf32x3": 2, "tf32": 3}
+FLAG_NO_LIGHTCONE = 1
+FLAG_NO_LEAF_CONTRACT = 2
+
+
+class HsfError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class hsf_gate(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("nq", ctypes.c_int32), ("q", ctypes.c_int32 * 4),
+                ("param", ctypes.c_double), ("param_id", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("mat", ctypes.POINTER(ctypes.c_double))]
+
+
+class hsf_circuit(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("num_gates", ctypes.c_int32),
+                ("gates", ctypes.POINTER(hsf_gate))]
+
+
+class hsf_blocks(ctypes.Structure):
+    _fields_ = [("num_blocks", ctypes.c_int32), ("offsets", ctypes.POINTER(ctypes.c_int32)),
+                ("gate_idx", ctypes.POINTER(ctypes.c_int32))]
+
+
+class hsf_plan_opts(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int32), ("gemm_mode", ctypes.c_int32),
+                ("rank_tol", ctypes.c_double), ("max_paths", ctypes.c_uint64),
+                ("tile_bits", ctypes.c_int32), ("flags", ctypes.c_int32),
+                ("angles", ctypes.POINTER(ctypes.c_double)), ("num_angles", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+class hsf_plan_info(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("n_a", ctypes.c_int32), ("n_b", ctypes.c_int32),
+                ("num_blocks", ctypes.c_int32), ("num_paths", ctypes.c_uint64),
+                ("precision", ctypes.c_int32), ("max_rank", ctypes.c_int32),
+                ("tree_nodes", ctypes.c_int64), ("num_launches", ctypes.c_int64)]
+
+
+# symbol -> (restype, argtypes); also the list the load test checks against the header
+SIGNATURES = {
+    "hsf_plan_create": (ctypes.c_int, [ctypes.POINTER(hsf_circuit), ctypes.c_int32,
+                                       ctypes.POINTER(hsf_blocks), ctypes.POINTER(hsf_plan_opts),
+                                       ctypes.POINTER(ctypes.c_void_p)]),
+    "hsf_plan_get_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(hsf_plan_info)]),
+    "hsf_plan_get_sigma": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32,
+                                          ctypes.POINTER(ctypes.c_double), ctypes.c_int32,
+                                          ctypes.POINTER(ctypes.c_int32)]),
+    "hsf_plan_destroy": (None, [ctypes.c_void_p]),
+    "hsf_workspace_size": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_size_t, ctypes.c_uint64,
+                                          ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]),
+    "hsf_run": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_uint64,
+                               ctypes.c_uint64, ctypes.c_uint64, ctypes.c_void_p, ctypes.c_void_p,
+                               ctypes.c_size_t, ctypes.c_void_p]),
+    "hsf_last_error": (ctypes.c_char_p, []),
+    "hsf_version": (ctypes.c_char_p, []),
+}
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load libhsf.so (raises OSError if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise OSError(f"{path} not found: build it with `python -m paper_2502_06959_gb300.build`")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(code: int):
+    if code != HSF_OK:
+        raise HsfError(code, load_library().hsf_last_error().decode())
+
+
+def _marshal(n: int, gates, blocks: Sequence[Sequence[int]]):
+    arr = (hsf_gate * max(1, len(gates)))()
+    keep = []
+    for i, g in enumerate(gates):
+        e = arr[i]
+        e.kind = KIND[g.kind]
+        e.nq = len(g.qubits)
+        for j, q in enumerate(g.qubits):
+            e.q[j] = int(q)
+        e.param = float(g.param)
+        e.param_id = int(g.param_id)
+        if g.kind == "matrix":
+            m = np.ascontiguousarray(np.asarray(g.matrix, dtype=np.complex128)).view(np.float64)
+            keep.append(m)
+            e.mat = m.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    circ = hsf_circuit(n, len(gates), arr)
+    offs = np.zeros(len(blocks) + 1, dtype=np.int32)
+    idx = []
+    for b, blk in enumerate(blocks):
+        idx.extend(int(x) for x in blk)
+        offs[b + 1] = len(idx)
+    idx = np.asarray(idx if idx else [0], dtype=np.int32)
+    keep += [offs, idx, arr]
+    bl = hsf_blocks(len(blocks), offs.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                    idx.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)))
+    return circ, bl, keep
+
+
+def hsf_plan_create(n: int, gates, cut: int, blocks, precision: str = "c64", gemm: str = "fp32",
+                    rank_tol: float = 0.0, max_paths: int = 0, tile_bits: int = 0, flags: int = 0,
+                    angles: Optional[Sequence[float]] = None) -> int:
+    lib = load_library()
+    circ, bl, keep = _marshal(n, gates, blocks)
+    opts = hsf_plan_opts()
+    opts.precision = PREC[precision]
+    opts.gemm_mode = GEMM[gemm]
+    opts.rank_tol = rank_tol
+    opts.max_paths = max_paths
+    opts.tile_bits = tile_bits
+    opts.flags = flags
+    if angles is not None:
+        ang = np.ascontiguousarray(angles, dtype=np.float64)
+        keep.append(ang)
+        opts.angles = ang.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        opts.num_angles = ang.size
+    out = ctypes.c_void_p()
+    _check(lib.hsf_plan_create(ctypes.byref(circ), cut, ctypes.byref(bl), ctypes.byref(opts),
+                               ctypes.byref(out)))
+    return out.value
+
+
+def hsf_plan_get_info(plan: int) -> dict:
+    info = hsf_plan_info()
+    _check(load_library().hsf_plan_get_info(plan, ctypes.byref(info)))
+    return {f: getattr(info, f) for f, _ in hsf_plan_info._fields_}
+
+
+def hsf_plan_get_sigma(plan: int, block: int) -> np.ndarray:
+    buf = (ctypes.c_double * 64)()
+    rank = ctypes.c_int32()
+    _check(load_library().hsf_plan_get_sigma(plan, block, buf, 64, ctypes.byref(rank)))
+    return np.array(buf[:rank.value])
+
+
+def hsf_plan_destroy(plan: int) -> None:
+    if plan:
+        load_library().hsf_plan_destroy(plan)
+
+
+def hsf_workspace_size(plan: int, num_bitstrings: int = 0, window: int = 0, budget: int = 0) -> int:
+    out = ctypes.c_size_t()
+    _check(load_library().hsf_workspace_size(plan, num_bitstrings, window, budget, ctypes.byref(out)))
+    return out.value
+
+
+def hsf_run(plan: int, bitstrings_ptr: int, num: int, window: int, path_begin: int, path_end: int,
+            out_ptr: int, workspace_ptr: int, workspace_bytes: int, stream: int = 0) -> None:
+    _check(load_library().hsf_run(plan, bitstrings_ptr or None, num, window, path_begin, path_end,
+                                  out_ptr, workspace_ptr, workspace_bytes, stream or None))
+
+
+def hsf_version() -> str:
+    return load_library().hsf_version().decode()
+
+
+class Plan:
+    """Owner of a native plan plus a cached PyTorch workspace.
+
+    ``run`` returns a complex128 CUDA tensor with the requested amplitudes."""
+
+    def __init__(self, n: int, gates, cut: int, blocks, **opts):
+        self.n = n
+        self.cut = cut
+        self.handle = hsf_plan_create(n, gates, cut, blocks, **opts)
+        self.info = hsf_plan_get_info(self.handle)
+        self._ws = None
+
+    @classmethod
+    def from_problem(cls, problem, **opts):
+        return cls(problem.n, problem.gates, problem.cut, problem.blocks, **opts)
+
+    def sigma(self, block: int) -> np.ndarray:
+        return hsf_plan_get_sigma(self.handle, block)
+
+    def workspace(self, num_bitstrings: int = 0, window: int = 0, budget: int = 0):
+        import torch
+        if budget == 0:
+            free, _ = torch.cuda.mem_get_info()
+            budget = int(free * 0.6)
+        need = hsf_workspace_size(self.handle, num_bitstrings, window, budget)
+        if self._ws is None or self._ws.numel() < need:
+            self._ws = None
+            self._ws = torch.empty(need, dtype=torch.uint8, device="cuda")
+        return self._ws
+
+    def run(self, bitstrings=None, window: int = 0, path_range=(0, 0), out=None, stream=None,
+            budget: int = 0):
+        import torch
+        num = 0 if bitstrings is None else int(bitstrings.numel())
+        if bitstrings is not None and num == 0:
+            return torch.empty(0, dtype=torch.complex128, device="cuda")
+        count = num if num else (window if window else (1 << self.n))
+        if out is None:
+            out = torch.empty(count, dtype=torch.complex128, device="cuda")
+        ws = self.workspace(num, window, budget)
+        st = stream if stream is not None else torch.cuda.current_stream()
+        hsf_run(self.handle, bitstrings.data_ptr() if num else 0, num, window,
+                int(path_range[0]), int(path_range[1]), out.data_ptr(), ws.data_ptr(), ws.numel(),
+                st.cuda_stream)
+        return out
+
+    def close(self):
+        if self.handle:
+            hsf_plan_destroy(self.handle)
+            self.handle = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

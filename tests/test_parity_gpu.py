@@ -1,0 +1,252 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
+
+Tolerances: the half states and per-path products run in the plan's precision; the
+cross-path sum is FP64.  complex128 plans must match within 1e-12 (max abs); complex64
+plans within the FP32 bound 1e-5 (max abs) and, so that the bound keeps meaning at
+large n where amplitudes are ~2^{-n/2}, also within 1e-4 of the largest reference
+amplitude (FP32 unit round-off 6e-8 times a few hundred gates, with margin).
+"""
+import numpy as np
+import pytest
+
+import oracle.hsf_oracle as O
+from paper_2502_06959_gb300 import workloads as W
+from paper_2502_06959_gb300.workloads import Gate
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    from paper_2502_06959_gb300 import build
+    build.build()
+    from paper_2502_06959_gb300 import hsf
+    hsf.load_library()
+
+
+def H():
+    from paper_2502_06959_gb300 import hsf
+    return hsf
+
+
+def check(got, ref, prec):
+    err = float(np.max(np.abs(got - ref))) if ref.size else 0.0
+    if prec == "c128":
+        assert err <= 1e-12, err
+    else:
+        scale = float(np.max(np.abs(ref))) if ref.size else 1.0
+        assert err <= 1e-5, err
+        assert err <= 1e-4 * scale, (err, scale)
+    return err
+
+
+def gpu_amps(pr, prec="c64", bitstrings=None, window=0, path_range=(0, 0), blocks=None, **opts):
+    import torch
+    plan = H().Plan(pr.n, pr.gates, pr.cut, pr.blocks if blocks is None else blocks,
+                    precision=prec, **opts)
+    bs = None
+    if bitstrings is not None:
+        bs = torch.from_numpy(np.asarray(bitstrings, dtype=np.uint64).view(np.int64)).cuda()
+    out = plan.run(bs, window=window, path_range=path_range)
+    torch.cuda.synchronize()
+    res = out.cpu().numpy()
+    info = plan.info
+    plan.close()
+    return res, info
+
+
+@pytest.mark.parametrize("prec", ["c128", "c64"])
+def test_c1_all_amplitudes(prec):
+    pr = W.workload_c1()
+    ref = O.schrodinger(pr.n, pr.gates)
+    got, info = gpu_amps(pr, prec)
+    assert info["num_paths"] == 4
+    check(got, ref, prec)
+
+
+@pytest.mark.parametrize("prec", ["c128", "c64"])
+def test_c1_plain_cut_equals_joint(prec):
+    pr = W.workload_c1()
+    plain = W.singleton_blocks(pr.n, pr.gates, pr.cut)
+    got, info = gpu_amps(pr, prec, blocks=plain)
+    assert info["num_paths"] == 64
+    check(got, O.schrodinger(pr.n, pr.gates), prec)
+
+
+def _sigma_cases():
+    cases = []
+    c1 = W.workload_c1()
+    cases.append((c1, c1.blocks))
+    c2 = W.workload_c2(layers=6, num_blocks=2, num_bitstrings=0)
+    cases.append((c2, c2.blocks))
+    c4 = W.workload_c4(n=12)
+    cases.append((c4, c4.blocks))
+    rng = np.random.default_rng(7)
+    for ka, kb in ((2, 2), (3, 3), (1, 3), (3, 1), (2, 1)):
+        n = ka + kb
+        gates = []
+        for d in range(8):
+            for q in range(n):
+                gates.append(Gate("matrix", (q,), matrix=W.haar_u2(rng)))
+            for q in range(n - 1):
+                gates.append(Gate("cz", (q + 1, q)))
+        cases.append((W.Problem(n, gates, kb - 1, [list(range(len(gates)))]), None))
+    return cases
+
+
+def test_block_svd_matches_lapack():
+    for pr, blocks in _sigma_cases():
+        blocks = pr.blocks if blocks is None else blocks
+        dec = O.decompose_blocks(pr.n, pr.gates, pr.cut, blocks)
+        plan = H().Plan(pr.n, pr.gates, pr.cut, blocks, precision="c128")
+        for k, d in enumerate(dec):
+            s = plan.sigma(k)
+            assert len(s) == len(d["sigma"])
+            assert np.max(np.abs(s - d["sigma"])) < 1e-13
+            assert abs(np.sum(s ** 2) - (1 << len(d["qubits"]))) < 1e-11
+        plan.close()
+
+
+def test_cascade_and_closed_form_ranks():
+    for kind in ("cx", "cz", "rzz", "swap"):
+        gates = [Gate(kind, (3, t), param=0.9) for t in (2, 1, 0)] if kind != "swap" else [Gate("swap", (1, 0))]
+        n = 4 if kind != "swap" else 2
+        cut = 2 if kind != "swap" else 0
+        plan = H().Plan(n, gates, cut, [list(range(len(gates)))], precision="c128")
+        s = plan.sigma(0)
+        if kind == "swap":
+            assert np.allclose(s, [1, 1, 1, 1], atol=1e-14)
+        else:
+            assert len(s) == 2
+        plan.close()
+
+
+@pytest.mark.parametrize("seed", range(8))
+@pytest.mark.parametrize("prec", ["c128", "c64"])
+def test_random_circuits_all_gate_kinds(seed, prec):
+    rng = np.random.default_rng(1000 + seed)
+    n = int(rng.integers(4, 11))
+    cut = int(rng.integers(0, n - 1))
+    gates = W.random_circuit(n, 40, seed)
+    # group crossing gates: consecutive crossing gates sharing a qubit pair become one
+    # block when that keeps the block convex, else singletons
+    blocks = W.singleton_blocks(n, gates, cut)
+    ref = O.schrodinger(n, gates)
+    pr = W.Problem(n, gates, cut, blocks)
+    got, _ = gpu_amps(pr, prec)
+    check(got, ref, prec)
+
+
+@pytest.mark.parametrize("tile_bits", [3, 4, 5])
+@pytest.mark.parametrize("prec", ["c128", "c64"])
+def test_multi_pass_tiles(tile_bits, prec):
+    pr = W.random_brickwork(14, 6, 6, block_after=(2, 4), block_kind="mixed", block_len=3, seed=77)
+    ref = O.schrodinger(pr.n, pr.gates)
+    got, _ = gpu_amps(pr, prec, tile_bits=tile_bits)
+    check(got, ref, prec)
+
+
+@pytest.mark.parametrize("prec", ["c128", "c64"])
+def test_bitstrings_windows_and_path_ranges(prec):
+    pr = W.random_brickwork(12, 5, 6, block_after=(1, 3, 5), block_kind="mixed", block_len=3, seed=5)
+    ref = O.schrodinger(pr.n, pr.gates)
+    rng = np.random.default_rng(3)
+    bs = W.random_bitstrings(rng, pr.n, 333)
+    got, info = gpu_amps(pr, prec, bitstrings=bs)
+    check(got, ref[bs.astype(np.int64)], prec)
+    for w in (1, 63, 64, 65, 1000):
+        got, _ = gpu_amps(pr, prec, window=w)
+        check(got, ref[:w], prec)
+    P = info["num_paths"]
+    for (a, b) in ((0, 1), (1, 7), (5, P), (P - 1, P)):
+        want, _ = O.hsf_amplitudes(pr.n, pr.gates, pr.cut, pr.blocks, bitstrings=bs, path_range=(a, b))
+        got, _ = gpu_amps(pr, prec, bitstrings=bs, path_range=(a, b))
+        check(got, want, prec)
+
+
+@pytest.mark.parametrize("prec", ["c128", "c64"])
+def test_light_cone_order_and_chunking_do_not_change_results(prec):
+    from paper_2502_06959_gb300 import hsf
+    import torch
+    pr = W.random_brickwork(12, 5, 8, block_after=(2, 4, 6), block_kind="rzz", block_len=3, seed=8)
+    ref = O.schrodinger(pr.n, pr.gates)
+    got, _ = gpu_amps(pr, prec, flags=hsf.FLAG_NO_LIGHTCONE)
+    check(got, ref, prec)
+    got, _ = gpu_amps(pr, prec)
+    check(got, ref, prec)
+    # a tight workspace budget forces several path chunks
+    plan = hsf.Plan(pr.n, pr.gates, pr.cut, pr.blocks, precision=prec)
+    full = hsf.hsf_workspace_size(plan.handle, 0, 0, 0)
+    budget = full
+    while True:                      # the smallest budget that still holds one chunk
+        try:
+            need = hsf.hsf_workspace_size(plan.handle, 0, 0, budget // 2)
+        except hsf.HsfError:
+            break
+        budget = need
+    assert budget < full
+    out = plan.run(None, budget=budget)
+    torch.cuda.synchronize()
+    check(out.cpu().numpy(), ref, prec)
+    plan.close()
+
+
+def test_edge_cases():
+    # no crossing gate: one path; gates only on one side; minimal n; cut at either end
+    cases = [
+        W.Problem(2, [Gate("h", (1,)), Gate("cx", (1, 0))], 0, [[1]]),             # Example 1
+        W.Problem(3, [Gate("h", (0,)), Gate("x", (2,))], 0, []),
+        W.Problem(5, [], 2, []),
+        W.Problem(6, W.random_circuit(6, 20, 4, kinds=["matrix", "rzz", "cx"]), 4, None),
+        W.Problem(6, W.random_circuit(6, 20, 5, kinds=["matrix", "rzz", "cx"]), 0, None),
+    ]
+    for pr in cases:
+        if pr.blocks is None:
+            pr.blocks = W.singleton_blocks(pr.n, pr.gates, pr.cut)
+        ref = O.schrodinger(pr.n, pr.gates)
+        for prec in ("c128", "c64"):
+            got, _ = gpu_amps(pr, prec)
+            check(got, ref, prec)
+    # Example 1 exactly
+    got, _ = gpu_amps(cases[0], "c128")
+    assert np.max(np.abs(got - np.array([1, 0, 0, 1]) / np.sqrt(2))) < 1e-15
+    # a zero-length bitstring request and an empty path range give empty / zero output
+    got, _ = gpu_amps(cases[3], "c64", bitstrings=np.zeros(0, dtype=np.uint64))
+    assert got.size == 0
+    got, _ = gpu_amps(cases[3], "c64", bitstrings=np.arange(5, dtype=np.uint64), path_range=(2, 2))
+    assert np.all(got == 0)
+
+
+def test_c4_qaoa_bitstrings():
+    pr = W.workload_c4()
+    want, info = O.hsf_amplitudes(pr.n, pr.gates, pr.cut, pr.blocks, bitstrings=pr.bitstrings)
+    assert info["num_paths"] == 256
+    got, ginfo = gpu_amps(pr, "c64", bitstrings=pr.bitstrings)
+    assert ginfo["num_paths"] == 256
+    check(got, want, "c64")
+
+
+def test_c2_reduced_full_width():
+    """n = 30 (15|15) with the C2 generator, 2 blocks and 6 layers (16 paths):
+    every amplitude of 4096 bitstrings against the oracle's full path sum."""
+    pr = W.workload_c2(num_blocks=2, layers=6)
+    want, info = O.hsf_amplitudes(pr.n, pr.gates, pr.cut, pr.blocks, bitstrings=pr.bitstrings)
+    assert info["num_paths"] == 16
+    got, _ = gpu_amps(pr, "c64", bitstrings=pr.bitstrings)
+    check(got, want, "c64")
+
+
+@pytest.mark.parametrize("path_range", [(0, 48), (40000, 40016), (65536 - 16, 65536)])
+def test_c2_full_size_sampled_paths(path_range):
+    """The full n = 30 workload (8 blocks, 20 layers, 4^8 paths) in the launch
+    configuration the benchmark times, restricted to a range of paths that the
+    oracle sums one path at a time."""
+    pr = W.workload_c2()
+    want, info = O.hsf_amplitudes(pr.n, pr.gates, pr.cut, pr.blocks, bitstrings=pr.bitstrings,
+                                  path_range=path_range)
+    assert info["num_paths"] == 4 ** 8
+    got, ginfo = gpu_amps(pr, "c64", bitstrings=pr.bitstrings, path_range=path_range)
+    assert ginfo["num_paths"] == 4 ** 8
+    check(got, want, "c64")
