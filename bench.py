@@ -1,0 +1,384 @@
+#!/usr/bin/env python
+"""Benchmark of joint-cut HSF simulation on one GB300 (or N, one process per GPU).
+
+Workload (default): n = 30 qubits split 15|15, 20 layers of Haar U(2) with CZ
+brickwork inside each half, 8 jointly cut blocks of 4 RZZ (+ interleaved U(2)) on the
+qubit pair (14, 15) -> 4^8 = 65536 paths (2^32 with per-gate cuts); amplitudes of 4096
+seeded bitstrings, complex64 half states, FP64 cross-path sums.
+
+A step is the whole hot path for one circuit: plan (validation, block products and
+FP64 Schmidt SVD on the GPU, gate programs) + run (all paths' half-state sweeps and
+the path sum) through the C ABI.  The metric is circuits per second.
+
+Multi-GPU: each rank simulates its own circuit (seed + rank); there is no collective
+on the data path ("scaling": "weak").
+
+--impl reference times the FP64 CPU oracle on the host cores over a bounded sample
+of paths of the same workload and reports the extrapolated circuits per second.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "HSF circuits/s (n=30 joint cut, 4096 bitstrings)"
+UNIT = "circuits/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="c64", choices=["c64", "c128"])
+    ap.add_argument("--no-extras", action="store_true", help="skip plain-cut and CPU baseline legs")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU-baseline sample time")
+    return ap.parse_args()
+
+
+def workload(rank: int = 0):
+    from paper_2502_06959_gb300 import workloads as W
+    return W.workload_c2(seed=2 + rank)
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d.get("hbm_gbs", 6800.0), d.get("bf16_tflops", 1900.0), d.get("sm_max_mhz", 2070.0), "measured"
+    return 6800.0, 1900.0, 2070.0, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle leg (the only place bench.py runs oracle/)
+# ---------------------------------------------------------------------------
+def _oracle_slice(args):
+    n, gates, cut, blocks, bits, a, b = args
+    import oracle.hsf_oracle as O
+    out, _ = O.hsf_amplitudes(n, gates, cut, blocks, bitstrings=bits, path_range=(a, b))
+    return out
+
+
+def oracle_sample(pr, paths_per_core: int, cores: int, start: int = 0):
+    """Oracle path sum over [start, start + cores*paths_per_core) on `cores` spawned
+    processes; returns (amplitudes, seconds, paths)."""
+    import multiprocessing as mp
+    total = cores * paths_per_core
+    jobs = [(pr.n, pr.gates, pr.cut, pr.blocks, pr.bitstrings, start + i * paths_per_core,
+             start + (i + 1) * paths_per_core) for i in range(cores)]
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(cores) as pool:
+        pool.map(_oracle_slice, jobs[:1])            # start-up outside the timing
+        t0 = time.perf_counter()
+        parts = pool.map(_oracle_slice, jobs)
+        dt = time.perf_counter() - t0
+    return np.sum(parts, axis=0), dt, total
+
+
+def cpu_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def calibrate_paths_per_core(pr, target_s: float, cores: int):
+    _, dt, tot = oracle_sample(pr, 1, cores)
+    per_path_core = dt                        # seconds for one path on each core
+    return max(1, int(target_s / max(per_path_core, 1e-3)))
+
+
+def run_reference(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    pr = workload(0)
+    cores = cpu_cores()
+    from paper_2502_06959_gb300.workloads import Problem  # noqa: F401  (inputs only)
+    P = 4 ** 8
+    per_step_target = max(2.0, 120.0 / max(1, args.steps + args.warmup))
+    ppc = calibrate_paths_per_core(pr, per_step_target, cores)
+    times = []
+    for i in range(args.warmup + args.steps):
+        _, dt, tot = oracle_sample(pr, ppc, cores, start=(i * cores * ppc) % P)
+        if i >= args.warmup:
+            times.append(dt / tot)          # seconds per path
+    sec_per_path = statistics.mean(times)
+    value = 1.0 / (sec_per_path * P)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec_per_path * P * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128",
+        "data": "synthetic",
+        "config": {"workload": "n30_15x15_20layers_8blocks_4096bitstrings", "paths": P,
+                   "bitstrings": 4096, "sample_paths_per_step": ppc * cores},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"{ppc * cores} of {P} paths per step, extrapolated"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    from paper_2502_06959_gb300 import hsf
+    hsf.load_library()
+    pr = workload(rank)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    bits_np = pr.bitstrings.astype(np.uint64)
+    bits = torch.from_numpy(bits_np.view(np.int64)).to(dev)
+    S = bits.numel()
+    out = torch.empty(S, dtype=torch.complex128, device=dev)
+    stream = torch.cuda.current_stream()
+
+    # workspace sized once for this circuit
+    plan0 = hsf.Plan.from_problem(pr, precision=args.precision)
+    info = dict(plan0.info)
+    free, _ = torch.cuda.mem_get_info()
+    ws_bytes = hsf.hsf_workspace_size(plan0.handle, S, 0, int(free * 0.7))
+    ws = torch.empty(ws_bytes, dtype=torch.uint8, device=dev)
+
+    def step(plan_each=True):
+        if plan_each:
+            h = hsf.hsf_plan_create(pr.n, pr.gates, pr.cut, pr.blocks, precision=args.precision)
+        else:
+            h = plan0.handle
+        hsf.hsf_run(h, bits.data_ptr(), S, 0, 0, 0, out.data_ptr(), ws.data_ptr(), ws_bytes,
+                    stream.cuda_stream)
+        return h
+
+    def sync_all():
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+
+    handles = []
+    for _ in range(args.warmup):
+        handles.append(step())
+    torch.cuda.synchronize()
+    for h in handles:
+        hsf.hsf_plan_destroy(h)
+    handles = []
+
+    # ---- timed region: K full steps (plan + run) ----
+    hsf.hsf_set_profiling(True)
+    sync_all()
+    l0 = hsf.hsf_launch_count()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(dev.index) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            handles.append(step())
+        e1.record(stream)
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    launches = hsf.hsf_launch_count() - l0
+    kstats = {}
+    for h in handles:
+        st = hsf.hsf_profile_collect(h)
+        for k, v in st.items():
+            acc = kstats.setdefault(k, dict(launches=0, ms=0.0, bytes=0.0, flops=0.0))
+            for f in acc:
+                acc[f] += v[f]
+    hsf.hsf_set_profiling(False)
+    for h in handles:
+        hsf.hsf_plan_destroy(h)
+    ms_t = torch.tensor([ms], device=dev)
+    if dist:
+        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
+    ms = float(ms_t.item())
+    value = args.steps * world / (ms / 1e3)
+
+    # ---- run only (plan reused) ----
+    sync_all()
+    e0.record(stream)
+    for _ in range(args.steps):
+        step(plan_each=False)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_run = e0.elapsed_time(e1)
+
+    # ---- end to end through the C ABI with host buffers ----
+    hbits = torch.from_numpy(bits_np.view(np.int64)).pin_memory()
+    hout = torch.empty(S, dtype=torch.complex128).pin_memory()
+    dbits = torch.empty_like(bits)
+    sync_all()
+    e0.record(stream)
+    for _ in range(args.steps):
+        dbits.copy_(hbits, non_blocking=True)
+        h = hsf.hsf_plan_create(pr.n, pr.gates, pr.cut, pr.blocks, precision=args.precision)
+        hsf.hsf_run(h, dbits.data_ptr(), S, 0, 0, 0, out.data_ptr(), ws.data_ptr(), ws_bytes,
+                    stream.cuda_stream)
+        hout.copy_(out, non_blocking=True)
+        handles.append(h)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_e2e = e0.elapsed_time(e1)
+    for h in handles[args.steps:]:
+        hsf.hsf_plan_destroy(h)
+    e2e_t = torch.tensor([ms_e2e], device=dev)
+    if dist:
+        dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
+    e2e_value = args.steps * world / (float(e2e_t.item()) / 1e3)
+
+    hbm_peak, bf16_peak, sm_max, peak_src = peaks()
+    sw = kstats.get("sweep", {})
+    sweep_ms = sw.get("ms", 0.0)
+    nl = max(1, sw.get("launches", 1))
+    sweep_gbs = sw.get("bytes", 0.0) / (sweep_ms / 1e3) / 1e9 if sweep_ms else 0.0
+    sweep_tflops = sw.get("flops", 0.0) / (sweep_ms / 1e3) / 1e12 if sweep_ms else 0.0
+    fp32_peak_tflops = 152 * 128 * 2 * sm_max * 1e6 / 1e12
+    total_kernel_ms = sum(v["ms"] for v in kstats.values())
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
+        "config": {"workload": "n30_15x15_20layers_8blocks_4096bitstrings", "n": pr.n, "cut": pr.cut,
+                   "paths": int(info["num_paths"]), "tree_nodes_per_side": int(info["tree_nodes"]),
+                   "bitstrings": S, "blocks": len(pr.blocks),
+                   "l2": "working set (half-state buffers) >> L2, no flush needed",
+                   "step": "plan (host + FP64 SVD kernel) + run (all paths)"},
+        "gpu_launches": int(launches),
+        "run_only": {"value": args.steps / (ms_run / 1e3), "unit": UNIT, "ms_per_step": ms_run / args.steps},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(S * 8),
+                "d2h_bytes_per_step": int(S * 16)},
+        "roofline": {"bound": "hbm", "kernel": "sweep", "achieved": sweep_gbs, "peak": hbm_peak,
+                     "unit": "GB/s", "frac": sweep_gbs / hbm_peak if hbm_peak else None,
+                     "traffic": None, "peak_source": peak_src,
+                     "avg_launch_ms": sweep_ms / nl, "launches": int(sw.get("launches", 0)),
+                     "alu_tflops": sweep_tflops, "alu_peak_tflops": fp32_peak_tflops,
+                     "alu_frac": sweep_tflops / fp32_peak_tflops},
+        "kernels": {k: {"launches": int(v["launches"]), "ms": v["ms"],
+                        "share": v["ms"] / total_kernel_ms if total_kernel_ms else 0.0}
+                    for k, v in kstats.items() if v["launches"]},
+        "clocks": clk.summary(),
+    }
+
+    if rank == 0 and not args.no_extras:
+        # joint vs plain cut: the same circuit with one block per crossing gate (2^32
+        # paths) timed on a fixed path budget and extrapolated
+        from paper_2502_06959_gb300 import workloads as W
+        plain_blocks = W.singleton_blocks(pr.n, pr.gates, pr.cut)
+        pp = hsf.Plan(pr.n, pr.gates, pr.cut, plain_blocks, precision=args.precision)
+        budget_paths = 1 << 16
+        pp.run(bits, path_range=(0, budget_paths))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        pp.run(bits, path_range=(0, budget_paths))
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        plain_paths = int(pp.info["num_paths"])
+        est = plain_paths * dt / budget_paths
+        line["plain_cut"] = {"paths": plain_paths, "sample_paths": budget_paths,
+                             "paths_per_s": budget_paths / dt, "est_seconds": est,
+                             "joint_speedup_vs_plain": est / (ms / 1e3 / args.steps)}
+        pp.close()
+        # CPU oracle baseline on a bounded sample, and the error of the same paths
+        cores = cpu_cores()
+        ppc = calibrate_paths_per_core(pr, args.cpu_seconds, cores)
+        ref, dt, tot = oracle_sample(pr, ppc, cores, start=0)
+        P = int(info["num_paths"])
+        cpu_value = tot / dt / P
+        got = plan0.run(bits, path_range=(0, tot)).cpu().numpy()
+        err = float(np.max(np.abs(got - ref)))
+        line["cpu_baseline"] = {"value": cpu_value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                "sample": f"paths [0, {tot}) of {P} on {cores} spawned processes, "
+                                          f"{dt:.1f} s, extrapolated to the full path count"}
+        line["err_vs_fp64"] = {"max_abs": err, "max_ref": float(np.max(np.abs(ref))),
+                               "paths": tot, "precision": args.precision}
+    plan0.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -172,6 +172,33 @@ hsf_status hsf_run(hsf_plan *plan, const uint64_t *bitstrings, size_t num,
 
 const char *hsf_last_error(void);
 
+/* Per-kernel timing for roofline reporting.  With profiling on, every kernel that
+ * hsf_run launches is bracketed by CUDA events on the caller's stream and tagged
+ * with its algorithmic bytes and flops; hsf_profile_collect waits for the events,
+ * adds them up per kernel kind (HSF_KERNEL_*) into stats[0..cap) and clears the
+ * plan's record.  Profiling is off by default; it is a process-wide switch. */
+typedef enum hsf_kernel_kind {
+  HSF_KERNEL_SWEEP = 0,      /* half-state gate sweeps                       */
+  HSF_KERNEL_GATHER = 1,     /* bitstring gather-dot over paths              */
+  HSF_KERNEL_REDUCE = 2,     /* FP64 compensated cross-chunk sums            */
+  HSF_KERNEL_WINDOW = 3,     /* window / full path GEMM                      */
+  HSF_KERNEL_OTHER = 4,      /* zero-fill, finalize                          */
+  HSF_NUM_KERNEL_KINDS = 8
+} hsf_kernel_kind;
+
+typedef struct hsf_kernel_stat {
+  int64_t launches;
+  double ms;                 /* summed event-timed duration                  */
+  double bytes;              /* algorithmic DRAM bytes (read + write)        */
+  double flops;              /* algorithmic floating-point operations        */
+} hsf_kernel_stat;
+
+void hsf_set_profiling(int32_t on);
+hsf_status hsf_profile_collect(hsf_plan *plan, hsf_kernel_stat *stats, int32_t cap);
+
+/* Number of CUDA kernels this library has launched in the process so far. */
+uint64_t hsf_launch_count(void);
+
 /* Library version string. */
 const char *hsf_version(void);
 

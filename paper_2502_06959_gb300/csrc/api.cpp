@@ -17,6 +17,7 @@
 // sized to the workspace); each level is one sweep launch per pass and side; the
 // leaves are accumulated by gather_dot (bitstrings) or window (full output).
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -36,6 +37,8 @@ using namespace hsf;
 namespace {
 
 thread_local std::string g_err;
+std::atomic<uint64_t> g_launches{0};
+std::atomic<int> g_profiling{0};
 
 hsf_status fail(hsf_status code, const char *fmt, ...) {
   char buf[1024];
@@ -447,6 +450,7 @@ hsf_status decompose_blocks(hsf_plan &p) {
   a.yf = (double *)(d + o_y);
   a.sweeps_used = (int32_t *)(d + o_sw);
   CUDA_TRY(launch_block_svd(a, 0));
+  g_launches++;
   CUDA_TRY(cudaDeviceSynchronize());
   std::vector<double> sig((size_t)B * 64), xf(nf), yf(nf);
   std::vector<int32_t> rank(B);
@@ -630,9 +634,58 @@ bool choose_layout(const hsf_plan &p, size_t num_bits, uint64_t window, size_t b
   return false;
 }
 
+// Launch one kernel (fn) and, with profiling on, bracket it with events on `st`.
+template <typename F>
+hsf_status launch(hsf_plan &p, int kind, double bytes, double flops, cudaStream_t st, F fn) {
+  if (!g_profiling.load()) {
+    CUDA_TRY(fn());
+    g_launches++;
+    return HSF_OK;
+  }
+  hsf_plan::ProfRec r{kind, nullptr, nullptr, bytes, flops};
+  CUDA_TRY(cudaEventCreate(&r.e0));
+  CUDA_TRY(cudaEventCreate(&r.e1));
+  CUDA_TRY(cudaEventRecord(r.e0, st));
+  CUDA_TRY(fn());
+  g_launches++;
+  CUDA_TRY(cudaEventRecord(r.e1, st));
+  p.prof.push_back(r);
+  return HSF_OK;
+}
+
+#define LAUNCH(kind, bytes, flops, call)                                                 \
+  do {                                                                                   \
+    hsf_status s_ = launch(*p, kind, bytes, flops, st, [&]() { return (call); });        \
+    if (s_ != HSF_OK) return s_;                                                         \
+  } while (0)
+
 }  // namespace
 
 extern "C" {
+
+void hsf_set_profiling(int32_t on) { g_profiling.store(on ? 1 : 0); }
+
+uint64_t hsf_launch_count(void) { return g_launches.load(); }
+
+hsf_status hsf_profile_collect(hsf_plan *p, hsf_kernel_stat *stats, int32_t cap) {
+  if (!p || (!stats && cap > 0)) return fail(HSF_EINVAL, "NULL argument");
+  for (int i = 0; i < cap; ++i) stats[i] = hsf_kernel_stat{0, 0.0, 0.0, 0.0};
+  for (auto &r : p->prof) {
+    float ms = 0.f;
+    CUDA_TRY(cudaEventSynchronize(r.e1));
+    CUDA_TRY(cudaEventElapsedTime(&ms, r.e0, r.e1));
+    if (r.kind < cap) {
+      stats[r.kind].launches += 1;
+      stats[r.kind].ms += ms;
+      stats[r.kind].bytes += r.bytes;
+      stats[r.kind].flops += r.flops;
+    }
+    cudaEventDestroy(r.e0);
+    cudaEventDestroy(r.e1);
+  }
+  p->prof.clear();
+  return HSF_OK;
+}
 
 const char *hsf_last_error(void) { return g_err.c_str(); }
 const char *hsf_version(void) { return "hsf-gb300 0.1 (sm_103a)"; }
@@ -704,6 +757,7 @@ hsf_status hsf_plan_get_sigma(const hsf_plan *p, int32_t block, double *sigma, i
 
 void hsf_plan_destroy(hsf_plan *p) {
   if (!p) return;
+  for (auto &r : p->prof) { cudaEventDestroy(r.e0); cudaEventDestroy(r.e1); }
   if (p->dev_table) cudaFree(p->dev_table);
   delete p;
 }
@@ -739,8 +793,9 @@ hsf_status hsf_run(hsf_plan *p, const uint64_t *bits, size_t num, uint64_t windo
   double *outd = (double *)out;
   double *comp = (double *)(ws + L.off_comp);
   const uint64_t count = num > 0 ? num : (window ? window : (1ull << p->n));
-  CUDA_TRY(launch_zero(outd, (int64_t)(2 * count), st));
-  CUDA_TRY(launch_zero(comp, (int64_t)(2 * count), st));
+  const double csz = p->precision == HSF_PREC_C64 ? 8.0 : 16.0;
+  LAUNCH(HSF_KERNEL_OTHER, 16.0 * count, 0.0, launch_zero(outd, (int64_t)(2 * count), st));
+  LAUNCH(HSF_KERNEL_OTHER, 16.0 * count, 0.0, launch_zero(comp, (int64_t)(2 * count), st));
   const int B = (int)p->blocks.size();
   const uint64_t C = L.chunk;
   for (uint64_t a0 = (path_begin / C) * C; a0 < path_end; a0 += C) {
@@ -774,7 +829,10 @@ hsf_status hsf_run(hsf_plan *p, const uint64_t *bits, size_t num, uint64_t windo
           a.parent_lo = prev_lo;
           a.num_nodes = hi - lo;
           a.tiles_per_node = 1 << (sd.h - ps.t);
-          CUDA_TRY(launch_sweep(a, p->precision, st));
+          const double amps = (double)a.num_nodes * (double)(1ull << sd.h);
+          double fl = 0.0;
+          for (const OpH &op : ps.ops) fl += amps * (op.type == OP_DENSE ? 8.0 * (1 << op.nq) : 6.0);
+          LAUNCH(HSF_KERNEL_SWEEP, 2.0 * amps * csz, fl, launch_sweep(a, p->precision, st));
         }
         prev_lo = lo;
         if (k == B) leaf[s] = dst;
@@ -793,8 +851,10 @@ hsf_status hsf_run(hsf_plan *p, const uint64_t *bits, size_t num, uint64_t windo
       g.paths_per_group = L.ppg;
       g.num_groups = (int32_t)((np + L.ppg - 1) / L.ppg);
       g.partial = (double *)(ws + L.off_partial);
-      CUDA_TRY(launch_gather_dot(g, p->precision, st));
-      CUDA_TRY(launch_reduce_partials(g.partial, g.num_groups, g.S, outd, comp, st));
+      LAUNCH(HSF_KERNEL_GATHER, (double)np * g.S * 2.0 * csz + 16.0 * g.num_groups * g.S,
+             8.0 * (double)np * g.S, launch_gather_dot(g, p->precision, st));
+      LAUNCH(HSF_KERNEL_REDUCE, 16.0 * g.num_groups * g.S + 64.0 * g.S, 0.0,
+             launch_reduce_partials(g.partial, g.num_groups, g.S, outd, comp, st));
     } else {
       WindowArgs w{};
       w.A = leaf[0];
@@ -808,10 +868,11 @@ hsf_status hsf_run(hsf_plan *p, const uint64_t *bits, size_t num, uint64_t windo
       w.N = (int64_t)std::min<uint64_t>(count, nbw);
       w.out = outd;
       w.comp = comp;
-      CUDA_TRY(launch_window(w, p->precision, st));
+      LAUNCH(HSF_KERNEL_WINDOW, (double)np * (w.M + w.N) * csz + 64.0 * w.M * w.N,
+             8.0 * (double)np * w.M * w.N, launch_window(w, p->precision, st));
     }
   }
-  CUDA_TRY(launch_finalize(outd, comp, (int64_t)(2 * count), st));
+  LAUNCH(HSF_KERNEL_OTHER, 48.0 * count, 0.0, launch_finalize(outd, comp, (int64_t)(2 * count), st));
   return HSF_OK;
 }
 

@@ -80,4 +80,6 @@ struct hsf_plan {
   size_t dev_table_bytes = 0;
   int64_t tree_nodes = 0;
   int64_t launches = 0;
+  struct ProfRec { int kind; cudaEvent_t e0, e1; double bytes, flops; };
+  std::vector<ProfRec> prof;
 };

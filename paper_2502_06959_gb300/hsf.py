@@ -82,8 +82,19 @@ SIGNATURES = {
                                ctypes.c_uint64, ctypes.c_uint64, ctypes.c_void_p, ctypes.c_void_p,
                                ctypes.c_size_t, ctypes.c_void_p]),
     "hsf_last_error": (ctypes.c_char_p, []),
+    "hsf_set_profiling": (None, [ctypes.c_int32]),
+    "hsf_profile_collect": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32]),
+    "hsf_launch_count": (ctypes.c_uint64, []),
     "hsf_version": (ctypes.c_char_p, []),
 }
+
+KERNEL_KINDS = ("sweep", "gather", "reduce", "window", "other")
+
+
+class hsf_kernel_stat(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_int64), ("ms", ctypes.c_double), ("bytes", ctypes.c_double),
+                ("flops", ctypes.c_double)]
+
 
 _lib = None
 
@@ -188,6 +199,21 @@ def hsf_run(plan: int, bitstrings_ptr: int, num: int, window: int, path_begin: i
             out_ptr: int, workspace_ptr: int, workspace_bytes: int, stream: int = 0) -> None:
     _check(load_library().hsf_run(plan, bitstrings_ptr or None, num, window, path_begin, path_end,
                                   out_ptr, workspace_ptr, workspace_bytes, stream or None))
+
+
+def hsf_set_profiling(on: bool) -> None:
+    load_library().hsf_set_profiling(1 if on else 0)
+
+
+def hsf_profile_collect(plan: int) -> dict:
+    arr = (hsf_kernel_stat * 8)()
+    _check(load_library().hsf_profile_collect(plan, arr, 8))
+    return {k: dict(launches=arr[i].launches, ms=arr[i].ms, bytes=arr[i].bytes, flops=arr[i].flops)
+            for i, k in enumerate(KERNEL_KINDS)}
+
+
+def hsf_launch_count() -> int:
+    return int(load_library().hsf_launch_count())
 
 
 def hsf_version() -> str:
