@@ -119,6 +119,8 @@ typedef struct hsf_plan_opts {
 #define HSF_FLAG_NO_LIGHTCONE 1   /* keep circuit order: no hoisting of gates that
                                      commute with later Schmidt factors             */
 #define HSF_FLAG_NO_LEAF_CONTRACT 2 /* always materialise leaf half states         */
+#define HSF_FLAG_NO_REGISTER_SWEEP 4 /* sweep with one shared-memory pass per op     */
+#define HSF_FLAG_IDENTITY_STORAGE 8  /* store local qubit q at storage bit q          */
 
 typedef struct hsf_plan hsf_plan;
 
@@ -130,6 +132,9 @@ typedef struct hsf_plan_info {
   int32_t max_rank;
   int64_t tree_nodes;       /* half-state simulations per side with prefix reuse    */
   int64_t num_launches;     /* sweep launches per side for one full run             */
+  int32_t leaf_bits;        /* > 0: bitstring runs contract the leaf level directly,
+                               its program spans this many low storage bits          */
+  int32_t reserved;
 } hsf_plan_info;
 
 /* Plan a circuit: validates the circuit, cut and blocks, multiplies every block and
@@ -182,7 +187,8 @@ typedef enum hsf_kernel_kind {
   HSF_KERNEL_GATHER = 1,     /* bitstring gather-dot over paths              */
   HSF_KERNEL_REDUCE = 2,     /* FP64 compensated cross-chunk sums            */
   HSF_KERNEL_WINDOW = 3,     /* window / full path GEMM                      */
-  HSF_KERNEL_OTHER = 4,      /* zero-fill, finalize                          */
+  HSF_KERNEL_OTHER = 4,      /* zero-fill, index maps, finalize              */
+  HSF_KERNEL_LEAF = 5,       /* leaf level contracted at the bitstrings      */
   HSF_NUM_KERNEL_KINDS = 8
 } hsf_kernel_kind;
 

@@ -36,9 +36,7 @@ __global__ void gather_dot_kernel(GatherArgs a) {
   const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int g = blockIdx.y;
   if (s >= a.S) return;
-  const uint64_t x = a.bits[s];
-  const uint64_t xb = x & ((1ull << a.hb) - 1ull);
-  const uint64_t xa = (x >> a.hb) & ((1ull << a.ha) - 1ull);
+  const uint64_t xa = a.ia[s], xb = a.ib[s];
   const C *A = reinterpret_cast<const C *>(a.A);
   const C *B = reinterpret_cast<const C *>(a.B);
   const int64_t p0 = (int64_t)g * a.paths_per_group;
@@ -91,8 +89,8 @@ __global__ void __launch_bounds__(256) window_kernel(WindowArgs a) {
       C va, vb;
       va.x = va.y = vb.x = vb.y = R(0);
       if (p < a.num_paths) {
-        if (i0 + cc < a.M) va = A[((uint64_t)p << a.ha) + (uint64_t)(i0 + cc)];
-        if (j0 + cc < a.N) vb = B[((uint64_t)p << a.hb) + (uint64_t)(j0 + cc)];
+        if (i0 + cc < a.M) va = A[((uint64_t)p << a.ha) + a.row_index[i0 + cc]];
+        if (j0 + cc < a.N) vb = B[((uint64_t)p << a.hb) + a.col_index[j0 + cc]];
       }
       As[kk][cc] = va;
       Bs[kk][cc] = vb;
@@ -124,6 +122,100 @@ __global__ void __launch_bounds__(256) window_kernel(WindowArgs a) {
     a.comp[2 * idx] = cr;
     a.comp[2 * idx + 1] = ci;
   }
+}
+
+// Leaf contraction.  Thread = bitstring s; it walks a group of parent nodes and, for
+// each, reads the 2^C amplitudes of both parents around x_a(s) / x_b(s) (contiguous:
+// the leaf level only touches the C lowest storage bits), applies row x(s) of every
+// leaf operator L_m and accumulates sum_m (L^a_m phi_a)(x_a) (L^b_m phi_b)(x_b).
+template <typename R, int CB>
+__global__ void __launch_bounds__(128) leaf_contract_kernel(LeafArgs a) {
+  using C = typename CT<R>::T;
+  constexpr int D = 1 << CB;
+  constexpr int LD = D + 1;                    // padded row stride (bank spread)
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C *La = reinterpret_cast<C *>(smem_raw);
+  C *Lb = La + a.r * D * LD;
+  const C *gLa = reinterpret_cast<const C *>(a.La), *gLb = reinterpret_cast<const C *>(a.Lb);
+  for (int e = threadIdx.x; e < a.r * D * D; e += blockDim.x) {
+    const int row = e / D, col = e % D;        // row runs over (m, row)
+    La[row * LD + col] = gLa[e];
+    Lb[row * LD + col] = gLb[e];
+  }
+  __syncthreads();
+  const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= a.S) return;
+  const int g = blockIdx.y;
+  const uint64_t ia = a.ia[s], ib = a.ib[s];
+  const int ra = (int)(ia & (D - 1)), rb = (int)(ib & (D - 1));
+  const uint64_t ba = ia - ra, bb = ib - rb;
+  const int64_t j0 = (int64_t)g * a.parents_per_group;
+  const int64_t j1 = min(a.num_parents, j0 + a.parents_per_group);
+  R accr = R(0), acci = R(0);
+  for (int64_t j = j0; j < j1; ++j) {
+    const int mlo = j == 0 ? a.m_first : 0;
+    const int mhi = j == a.num_parents - 1 ? a.m_last : a.r;
+    C x[D];
+    const C *pa = reinterpret_cast<const C *>(a.Pa) + ((uint64_t)j << a.ha) + ba;
+#pragma unroll
+    for (int k = 0; k < D; ++k) x[k] = pa[k];
+    C va[8];
+#pragma unroll
+    for (int m = 0; m < 8; ++m) {
+      va[m].x = va[m].y = R(0);
+      if (m < a.r) {
+        const C *row = La + (m * D + ra) * LD;
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+          const C l = row[k];
+          va[m].x = fma(l.x, x[k].x, fma(-l.y, x[k].y, va[m].x));
+          va[m].y = fma(l.x, x[k].y, fma(l.y, x[k].x, va[m].y));
+        }
+      }
+    }
+    const C *pb = reinterpret_cast<const C *>(a.Pb) + ((uint64_t)j << a.hb) + bb;
+#pragma unroll
+    for (int k = 0; k < D; ++k) x[k] = pb[k];
+#pragma unroll
+    for (int m = 0; m < 8; ++m) {
+      if (m < mlo || m >= mhi) continue;
+      const C *row = Lb + (m * D + rb) * LD;
+      R vr = R(0), vi = R(0);
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        const C l = row[k];
+        vr = fma(l.x, x[k].x, fma(-l.y, x[k].y, vr));
+        vi = fma(l.x, x[k].y, fma(l.y, x[k].x, vi));
+      }
+      accr = fma(va[m].x, vr, fma(-va[m].y, vi, accr));
+      acci = fma(va[m].x, vi, fma(va[m].y, vr, acci));
+    }
+  }
+  double *dst = a.partial + 2 * ((int64_t)g * a.S + s);
+  dst[0] = (double)accr;
+  dst[1] = (double)acci;
+}
+
+__global__ void index_prep_kernel(IndexArgs a) {
+  const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= a.S) return;
+  const uint64_t x = a.bits[s];
+  uint64_t ia = 0, ib = 0;
+  for (int q = 0; q < a.hb; ++q)
+    if ((x >> q) & 1ull) ib |= 1ull << a.store_b[q];
+  for (int q = 0; q < a.ha; ++q)
+    if ((x >> (a.nb + q)) & 1ull) ia |= 1ull << a.store_a[q];
+  a.ia[s] = ia;
+  a.ib[s] = ib;
+}
+
+__global__ void range_index_kernel(uint64_t *dst, int64_t count, PermArgs perm) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= count) return;
+  uint64_t r = 0;
+  for (int q = 0; q < perm.h; ++q)
+    if (((uint64_t)i >> q) & 1ull) r |= 1ull << perm.store[q];
+  dst[i] = r;
 }
 
 __global__ void finalize_kernel(double *out, const double *comp, int64_t count) {
@@ -162,6 +254,46 @@ cudaError_t launch_window(const WindowArgs &a, int precision, cudaStream_t st) {
     window_kernel<float><<<grid, 256, 0, st>>>(a);
   else
     window_kernel<double><<<grid, 256, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t leaf_dispatch(const LeafArgs &a, cudaStream_t st) {
+  using C = typename CT<R>::T;
+  dim3 grid((unsigned)((a.S + 127) / 128), (unsigned)a.num_groups);
+  const int D = 1 << a.c;
+  const size_t smem = (size_t)2 * a.r * D * (D + 1) * sizeof(C);
+  switch (a.c) {
+#define HSF_LEAF(CBV)                                                                         \
+  case CBV: {                                                                                \
+    auto k = leaf_contract_kernel<R, CBV>;                                                   \
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
+    if (e != cudaSuccess) return e;                                                          \
+    k<<<grid, 128, smem, st>>>(a);                                                           \
+    break;                                                                                   \
+  }
+    HSF_LEAF(1) HSF_LEAF(2) HSF_LEAF(3) HSF_LEAF(4) HSF_LEAF(5)
+#undef HSF_LEAF
+    default:
+      return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_leaf_contract(const LeafArgs &a, int precision, cudaStream_t st) {
+  if (a.S <= 0 || a.num_parents <= 0) return cudaSuccess;
+  return precision == 0 ? leaf_dispatch<float>(a, st) : leaf_dispatch<double>(a, st);
+}
+
+cudaError_t launch_index_prep(const IndexArgs &a, cudaStream_t st) {
+  if (a.S <= 0) return cudaSuccess;
+  index_prep_kernel<<<(unsigned)((a.S + 255) / 256), 256, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_range_index(uint64_t *dst, int64_t count, const PermArgs &perm, cudaStream_t st) {
+  if (count <= 0) return cudaSuccess;
+  range_index_kernel<<<(unsigned)((count + 255) / 256), 256, 0, st>>>(dst, count, perm);
   return cudaGetLastError();
 }
 

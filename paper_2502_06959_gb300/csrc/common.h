@@ -24,6 +24,23 @@ struct DevOp {
   int32_t pos[3];        // tile bit of each operand qubit, pos[0] = matrix MSB
   int32_t mat;           // offset (complex elements) into the program's matrix pool
   int32_t digit_stride;  // > 0: matrix = pool[mat + digit * digit_stride] (Schmidt factor)
+  int32_t slot[3];       // register slot of each operand, -1 if none; dense ops have
+                         // slot[0] > slot[1] > slot[2] (matrix MSB on the highest slot)
+  int32_t kcase;         // dense ops: which unrolled slot pattern applies (see sweep.cu)
+  int32_t pad;
+};
+
+// A register group: consecutive ops whose dense operands lie in `nslots` tile bits;
+// every thread holds the 2^RB amplitudes spanned by slots[0..RB) (filled with other
+// tile bits when fewer are needed) for one assignment of the remaining tile bits.
+constexpr int kMaxSlots = 5;
+// register-resident sweep: amplitudes per thread = 2^kRegBits, CTA tile = 2^kRegTile
+constexpr int kRegBitsC64 = 4, kRegTileC64 = 13;
+constexpr int kRegBitsC128 = 3, kRegTileC128 = 12;
+struct DevGroup {
+  int32_t slots[kMaxSlots];   // tile bits, ascending
+  int32_t first_op;
+  int32_t num_ops;
   int32_t pad;
 };
 
@@ -44,7 +61,36 @@ struct SweepArgs {
   int32_t tiles_per_node;
   int32_t read_parent;   // 1: tile is loaded from node/radix in src
   int32_t init_zero;     // 1: tile starts from |0...0>
-  int32_t pad;
+  const DevGroup *groups;// register groups of the pass (register-resident kernel)
+  int32_t num_groups;
+  int32_t rbits;         // register slots per thread (5 for complex64, 4 for complex128)
+};
+
+// Leaf level contracted at the requested amplitudes: for every parent node (level
+// B-1) and bitstring s, amp(s) += sum_m (L^a_m phi_a)(x_a) * (L^b_m phi_b)(x_b), where
+// L_m is the leaf level's whole program (Schmidt factor m, then gates) acting on the
+// 2^c lowest storage bits.
+struct LeafArgs {
+  const void *Pa, *Pb;   // parent states, node-major
+  int32_t ha, hb;
+  int64_t num_parents;
+  const void *La, *Lb;   // [r][2^c][2^c] row-major, both sides padded to the same c
+  int32_t c, r;
+  int32_t m_first;       // digits [m_first, r) of the first parent are in the path range
+  int32_t m_last;        // digits [0, m_last) of the last parent are in the path range
+  const uint64_t *ia, *ib;   // storage index of every bitstring on each side
+  int64_t S;
+  int32_t parents_per_group, num_groups;
+  double *partial;       // [num_groups][S][2]
+};
+
+// Storage index of every bitstring on both sides (bit permutation of x_a, x_b).
+struct IndexArgs {
+  const uint64_t *bits;
+  int64_t S;
+  int32_t nb, ha, hb;
+  int32_t store_a[64], store_b[64];   // storage bit of each local qubit
+  uint64_t *ia, *ib;
 };
 
 // Path accumulation over leaf half states (bitstring output).
@@ -53,7 +99,7 @@ struct GatherArgs {
   const void *B;         // b-side leaves [paths][2^hb]
   int64_t num_paths;
   int32_t ha, hb;
-  const uint64_t *bits;  // bitstrings (bit q = qubit q)
+  const uint64_t *ia, *ib;   // storage index of every bitstring on each side
   int64_t S;
   int32_t paths_per_group;
   int32_t num_groups;
@@ -70,6 +116,8 @@ struct WindowArgs {
   uint64_t window;       // amplitudes kept: index x_a * 2^hb + x_b < window
   double *out;           // complex128 accumulator (re, im)
   double *comp;          // Neumaier compensation (re, im)
+  const uint64_t *row_index;  // storage index of x_a = 0..M-1 (a side)
+  const uint64_t *col_index;  // storage index of x_b = 0..N-1 (b side)
 };
 
 struct BlockSvdArgs {
@@ -97,5 +145,13 @@ cudaError_t launch_window(const WindowArgs &a, int precision, cudaStream_t st);
 cudaError_t launch_finalize(double *out, const double *comp, int64_t count, cudaStream_t st);
 cudaError_t launch_zero(double *p, int64_t count, cudaStream_t st);
 cudaError_t launch_block_svd(const BlockSvdArgs &a, cudaStream_t st);
+cudaError_t launch_leaf_contract(const LeafArgs &a, int precision, cudaStream_t st);
+cudaError_t launch_index_prep(const IndexArgs &a, cudaStream_t st);
+struct PermArgs {
+  int32_t h;
+  int32_t store[64];     // storage bit of each local qubit
+};
+// dst[i] = storage index of local index i, i < count.
+cudaError_t launch_range_index(uint64_t *dst, int64_t count, const PermArgs &perm, cudaStream_t st);
 
 }  // namespace hsf

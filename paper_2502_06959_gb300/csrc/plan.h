@@ -1,6 +1,7 @@
 // Host-side plan of a joint-cut HSF simulation (internal).
 #pragma once
 
+#include <atomic>
 #include <complex>
 #include <cstdint>
 #include <string>
@@ -43,12 +44,18 @@ struct OpH {
   int block = -1;
 };
 
+struct GroupH {
+  int slots[kMaxSlots] = {-1, -1, -1, -1, -1};   // tile bits held in registers, ascending; -1 unused
+  int first_op = 0, num_ops = 0;
+};
+
 struct PassH {
   uint64_t active = 0;     // storage bits in the tile
   int t = 0;
-  std::vector<OpH> ops;
+  std::vector<OpH> ops;    // storage-bit operands, in application order
+  std::vector<GroupH> groups;   // register groups (register-resident kernel), may be empty
   // device
-  size_t ops_off = 0, mats_off = 0;   // byte offsets in the device table
+  size_t ops_off = 0, mats_off = 0, groups_off = 0;   // byte offsets in the device table
   int num_ops = 0;
 };
 
@@ -60,9 +67,27 @@ struct LevelH {
 struct SideH {
   int h = 0;
   int offset = 0;          // global qubit of local qubit 0
+  std::vector<int> store;  // storage bit of every local qubit
   std::vector<LevelH> levels;   // 0 .. B
+  // leaf contraction: the last level's program as r operators on the 2^leaf_c lowest
+  // storage bits (padded to the plan-wide leaf_c)
+  std::vector<cd> leaf_ops;     // r x 2^c x 2^c
+  size_t leaf_off = 0;
 };
 
+}  // namespace hsf
+
+namespace hsf {
+// planner.cpp
+hsf_status set_error(hsf_status code, const char *fmt, ...);
+const char *last_error();
+hsf_status validate_and_load(hsf_plan &p, const hsf_circuit *c, int cut, const hsf_blocks *bl,
+                             const hsf_plan_opts *o);
+hsf_status check_order(const hsf_plan &p);
+hsf_status decompose_blocks(hsf_plan &p);
+hsf_status build_programs(hsf_plan &p);
+hsf_status upload_programs(hsf_plan &p);
+extern std::atomic<uint64_t> g_launches;
 }  // namespace hsf
 
 struct hsf_plan {
@@ -80,6 +105,8 @@ struct hsf_plan {
   size_t dev_table_bytes = 0;
   int64_t tree_nodes = 0;
   int64_t launches = 0;
+  int leaf_c = 0;                   // > 0: the leaf level can be contracted at bitstrings
+  int rbits = 4;                    // register slots of the register-resident sweep
   struct ProfRec { int kind; cudaEvent_t e0, e1; double bytes, flops; };
   std::vector<ProfRec> prof;
 };

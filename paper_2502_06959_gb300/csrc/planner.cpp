@@ -1,0 +1,812 @@
+// Host planner of the joint-cut HSF library (Sec. II-B, III-A, IV-A, IV-D).
+//
+//   * validate the circuit, the cut and the blocks; classify gates by side
+//     (a: qubits l+1..n-1, b: qubits 0..l);
+//   * check that every crossing gate is in exactly one block, that every block is
+//     convex in the gate DAG and that the listed block order is compatible with it;
+//   * multiply and Schmidt-decompose every block on the GPU (svd.cu), read back ranks,
+//     singular values and factors;
+//   * give every in-half gate a tree level: the number of the last block whose factor
+//     it depends on, so gates that commute with a later Schmidt factor run before the
+//     branching and the children of a path-tree node share that work (prefix reuse);
+//   * per side, store the qubits touched at deeper levels in lower storage bits;
+//   * per level: Schmidt factor first, then gates; merge runs of one-qubit gates;
+//     split into tile passes (a tile holds 2^t amplitudes in shared memory) and
+//     register groups (ops whose dense operands fit the per-thread register block);
+//   * when the leaf level only touches a few low storage bits, precompute its whole
+//     program as one small operator per Schmidt digit, so the leaf level is contracted
+//     directly at the requested bitstrings instead of being simulated.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <functional>
+#include <map>
+#include <memory>
+#include <queue>
+#include <set>
+#include <string>
+#include <vector>
+
+#include "plan.h"
+
+namespace hsf {
+
+thread_local std::string g_err;
+std::atomic<uint64_t> g_launches{0};
+
+hsf_status set_error(hsf_status code, const char *fmt, ...) {
+  char buf[1024];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return code;
+}
+
+const char *last_error() { return g_err.c_str(); }
+
+#define CUDA_TRY(expr)                                                                   \
+  do {                                                                                   \
+    cudaError_t e_ = (expr);                                                             \
+    if (e_ != cudaSuccess)                                                               \
+      return set_error(HSF_ECUDA, "%s failed: %s", #expr, cudaGetErrorString(e_));       \
+  } while (0)
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// Gate matrices (FP64).  R_P(t) = exp(-i t P / 2).
+// ---------------------------------------------------------------------------
+hsf_status named_matrix(int kind, double t, std::vector<cd> &m, int &nq) {
+  const cd I(0.0, 1.0);
+  const double c = std::cos(t / 2), s = std::sin(t / 2);
+  switch (kind) {
+    case HSF_GATE_H: nq = 1; { const double r = 1.0 / std::sqrt(2.0); m = {r, r, r, -r}; } break;
+    case HSF_GATE_X: nq = 1; m = {0.0, 1.0, 1.0, 0.0}; break;
+    case HSF_GATE_Y: nq = 1; m = {0.0, -I, I, 0.0}; break;
+    case HSF_GATE_Z: nq = 1; m = {1.0, 0.0, 0.0, -1.0}; break;
+    case HSF_GATE_S: nq = 1; m = {1.0, 0.0, 0.0, I}; break;
+    case HSF_GATE_T: nq = 1; m = {1.0, 0.0, 0.0, std::exp(I * (M_PI / 4))}; break;
+    case HSF_GATE_RX: nq = 1; m = {c, -I * s, -I * s, c}; break;
+    case HSF_GATE_RY: nq = 1; m = {c, -s, s, c}; break;
+    case HSF_GATE_RZ: nq = 1; m = {std::exp(-I * (t / 2)), 0.0, 0.0, std::exp(I * (t / 2))}; break;
+    case HSF_GATE_CX:
+      nq = 2; m.assign(16, 0.0);
+      m[0 * 4 + 0] = 1; m[1 * 4 + 1] = 1; m[2 * 4 + 3] = 1; m[3 * 4 + 2] = 1;
+      break;
+    case HSF_GATE_CZ:
+      nq = 2; m.assign(16, 0.0);
+      m[0] = 1; m[5] = 1; m[10] = 1; m[15] = -1;
+      break;
+    case HSF_GATE_SWAP:
+      nq = 2; m.assign(16, 0.0);
+      m[0] = 1; m[1 * 4 + 2] = 1; m[2 * 4 + 1] = 1; m[15] = 1;
+      break;
+    case HSF_GATE_ISWAP:
+      nq = 2; m.assign(16, 0.0);
+      m[0] = 1; m[1 * 4 + 2] = I; m[2 * 4 + 1] = I; m[15] = 1;
+      break;
+    case HSF_GATE_RZZ: {
+      nq = 2; m.assign(16, 0.0);
+      const cd em = std::exp(-I * (t / 2)), ep = std::exp(I * (t / 2));
+      m[0] = em; m[5] = ep; m[10] = ep; m[15] = em;
+      break;
+    }
+    default:
+      return set_error(HSF_EINVAL, "unknown gate kind %d", kind);
+  }
+  return HSF_OK;
+}
+
+std::vector<cd> matmul(const std::vector<cd> &a, const std::vector<cd> &b, int d) {
+  std::vector<cd> r((size_t)d * d, 0.0);
+  for (int i = 0; i < d; ++i)
+    for (int k = 0; k < d; ++k) {
+      const cd aik = a[(size_t)i * d + k];
+      if (aik == 0.0) continue;
+      for (int j = 0; j < d; ++j) r[(size_t)i * d + j] += aik * b[(size_t)k * d + j];
+    }
+  return r;
+}
+
+bool is_diagonal(const std::vector<cd> &m, int d) {
+  for (int i = 0; i < d; ++i)
+    for (int j = 0; j < d; ++j)
+      if (i != j && m[(size_t)i * d + j] != 0.0) return false;
+  return true;
+}
+
+int popcount64(uint64_t x) { return __builtin_popcountll(x); }
+
+// ---------------------------------------------------------------------------
+// DAG with blocks contracted to single nodes; Kahn's algorithm with the smallest
+// gate index first.  The listed block order is enforced as extra edges.
+// ---------------------------------------------------------------------------
+struct Node {
+  bool is_block = false;
+  int id = 0;
+  int key = 0;
+  std::vector<int> succ;
+  int indeg = 0;
+};
+
+hsf_status execution_order(const hsf_plan &p, std::vector<std::pair<bool, int>> &order) {
+  const int G = (int)p.gates.size();
+  const int B = (int)p.blocks.size();
+  std::vector<int> owner(G, -1);
+  for (int b = 0; b < B; ++b)
+    for (int gi : p.blocks[b].gates) owner[gi] = b;
+  std::vector<Node> nodes(B + G);
+  std::vector<char> used(B + G, 0);
+  for (int b = 0; b < B; ++b) {
+    nodes[b].is_block = true;
+    nodes[b].id = b;
+    nodes[b].key = *std::min_element(p.blocks[b].gates.begin(), p.blocks[b].gates.end());
+    used[b] = 1;
+  }
+  for (int gi = 0; gi < G; ++gi)
+    if (owner[gi] < 0) {
+      nodes[B + gi].id = gi;
+      nodes[B + gi].key = gi;
+      used[B + gi] = 1;
+    }
+  auto nid = [&](int gi) { return owner[gi] >= 0 ? owner[gi] : B + gi; };
+  std::set<std::pair<int, int>> edges;
+  std::vector<int> last(p.n, -1);
+  for (int gi = 0; gi < G; ++gi) {
+    const int v = nid(gi);
+    for (int j = 0; j < p.gates[gi].nq; ++j) {
+      const int q = p.gates[gi].q[j];
+      if (last[q] >= 0) {
+        const int u = nid(last[q]);
+        if (u != v) edges.insert({u, v});
+      }
+      last[q] = gi;
+    }
+  }
+  for (int b = 0; b + 1 < B; ++b) edges.insert({b, b + 1});
+  for (auto &e : edges) {
+    nodes[e.first].succ.push_back(e.second);
+    nodes[e.second].indeg++;
+  }
+  using QE = std::pair<int, int>;
+  std::priority_queue<QE, std::vector<QE>, std::greater<QE>> pq;
+  int total = 0;
+  for (int v = 0; v < B + G; ++v) {
+    total += used[v];
+    if (used[v] && nodes[v].indeg == 0) pq.push({nodes[v].key, v});
+  }
+  order.clear();
+  while (!pq.empty()) {
+    const int v = pq.top().second;
+    pq.pop();
+    order.push_back({nodes[v].is_block, nodes[v].id});
+    for (int w : nodes[v].succ)
+      if (--nodes[w].indeg == 0) pq.push({nodes[w].key, w});
+  }
+  if ((int)order.size() != total)
+    return set_error(HSF_EBLOCK, "a block is not convex in the circuit DAG, or the blocks are not "
+                                 "listed in an order compatible with the circuit");
+  return HSF_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Ops.
+// ---------------------------------------------------------------------------
+void merge_one_qubit_runs(std::vector<OpH> &ops) {
+  std::vector<OpH> out;
+  std::map<int, int> last;   // qubit -> index in out of the last op touching it
+  for (auto &op : ops) {
+    if (op.nq == 1 && op.digits == 1) {
+      auto it = last.find(op.q[0]);
+      if (it != last.end()) {
+        OpH &prev = out[it->second];
+        if (prev.nq == 1 && prev.digits == 1) {
+          // prev then op (the ops in between do not touch this qubit): op * prev
+          std::vector<cd> a = op.m, b = prev.m;
+          if (op.type == OP_DIAG) a = {op.m[0], 0.0, 0.0, op.m[1]};
+          if (prev.type == OP_DIAG) b = {prev.m[0], 0.0, 0.0, prev.m[1]};
+          std::vector<cd> c = matmul(a, b, 2);
+          if (op.type == OP_DIAG && prev.type == OP_DIAG) {
+            prev.m = {c[0], c[3]};
+          } else {
+            prev.type = OP_DENSE;
+            prev.m = c;
+          }
+          continue;
+        }
+      }
+    }
+    out.push_back(op);
+    for (int j = 0; j < op.nq; ++j) last[op.q[j]] = (int)out.size() - 1;
+  }
+  ops.swap(out);
+}
+
+// Reorder the operands of an op (new operand x = old operand perm[x]) and permute
+// its matrices (every digit) to match: new index bit (nq-1-x) = old bit (nq-1-perm[x]).
+void permute_operands(OpH &op, const int *perm) {
+  const int nq = op.nq;
+  const int d = 1 << nq;
+  auto sigma = [&](int a) {
+    int r = 0;
+    for (int x = 0; x < nq; ++x)
+      if ((a >> (nq - 1 - x)) & 1) r |= 1 << (nq - 1 - perm[x]);
+    return r;
+  };
+  const int per = op.type == OP_DENSE ? d * d : d;
+  std::vector<cd> out(op.m.size());
+  for (int dg = 0; dg < op.digits; ++dg) {
+    const cd *src = op.m.data() + (size_t)dg * per;
+    cd *dst = out.data() + (size_t)dg * per;
+    if (op.type == OP_DENSE) {
+      for (int a = 0; a < d; ++a)
+        for (int b = 0; b < d; ++b) dst[a * d + b] = src[sigma(a) * d + sigma(b)];
+    } else {
+      for (int a = 0; a < d; ++a) dst[a] = src[sigma(a)];
+    }
+  }
+  op.m.swap(out);
+  int q[3] = {op.q[0], op.q[1], op.q[2]};
+  for (int x = 0; x < nq; ++x) op.q[x] = q[perm[x]];
+}
+
+// Split a level program into passes whose dense ops only touch the tile's qubits.
+void split_passes(LevelH &lv, int h, int tmax) {
+  lv.passes.clear();
+  const uint64_t full = (h >= 64) ? ~0ull : ((1ull << h) - 1ull);
+  if (h <= tmax) {
+    PassH ps;
+    ps.active = full;
+    ps.t = h;
+    ps.ops = lv.ops;
+    lv.passes.push_back(ps);
+    return;
+  }
+  std::vector<OpH> rem = lv.ops;
+  while (!rem.empty()) {
+    uint64_t active = 0, blocked = 0;
+    std::vector<OpH> here, later;
+    for (auto &op : rem) {
+      uint64_t qm = 0;
+      for (int j = 0; j < op.nq; ++j) qm |= 1ull << op.q[j];
+      if (qm & blocked) {
+        later.push_back(op);
+        blocked |= qm;
+        continue;
+      }
+      if (op.type == OP_DENSE && (qm & ~active)) {
+        if (popcount64(active | qm) <= tmax) {
+          active |= qm;
+        } else {
+          later.push_back(op);
+          blocked |= qm;
+          continue;
+        }
+      }
+      here.push_back(op);
+    }
+    for (int q = 0; q < h && popcount64(active) < tmax; ++q) active |= 1ull << q;
+    PassH ps;
+    ps.active = active;
+    ps.t = popcount64(active);
+    ps.ops = here;
+    lv.passes.push_back(ps);
+    rem.swap(later);
+  }
+  if (lv.passes.empty()) {
+    PassH ps;
+    for (int q = 0; q < tmax; ++q) ps.active |= 1ull << q;
+    ps.t = tmax;
+    lv.passes.push_back(ps);
+  }
+}
+
+// Register groups: consecutive ops whose dense operands fit `rb` tile bits.
+void build_groups(PassH &ps, int rb) {
+  ps.groups.clear();
+  if (ps.t < rb) return;                     // the plain shared-memory kernel runs it
+  int tile_bit[64];
+  int tb = 0;
+  for (int q = 0; q < 64; ++q) tile_bit[q] = (ps.active >> q) & 1ull ? tb++ : -1;
+  uint32_t cur = 0;
+  int first = 0;
+  auto close = [&](int end) {
+    if (end == first && !ps.groups.empty()) return;
+    GroupH g;
+    g.first_op = first;
+    g.num_ops = end - first;
+    int k = 0;
+    for (int b = 0; b < ps.t && k < rb; ++b)
+      if (cur & (1u << b)) g.slots[k++] = b;
+    for (int b = 0; b < ps.t && k < rb; ++b)     // fill with the lowest free tile bits
+      if (!(cur & (1u << b))) { cur |= 1u << b; g.slots[k++] = b; }
+    std::sort(g.slots, g.slots + k);
+    ps.groups.push_back(g);
+    first = end;
+    cur = 0;
+  };
+  for (int o = 0; o < (int)ps.ops.size(); ++o) {
+    const OpH &op = ps.ops[o];
+    if (op.type == OP_DIAG) continue;
+    uint32_t need = 0;
+    for (int j = 0; j < op.nq; ++j) need |= 1u << tile_bit[op.q[j]];
+    if (__builtin_popcount(cur | need) <= rb) {
+      cur |= need;
+    } else {
+      close(o);
+      cur = need;
+    }
+  }
+  if (first < (int)ps.ops.size() || ps.groups.empty()) close((int)ps.ops.size());
+}
+
+// Apply one op to a vector over the 2^c lowest storage bits (host, FP64).
+void host_apply(std::vector<cd> &v, int c, const OpH &op, int digit) {
+  const int nq = op.nq, d = 1 << nq;
+  const int per = op.type == OP_DENSE ? d * d : d;
+  const cd *m = op.m.data() + (op.digits > 1 ? (size_t)digit * per : 0);
+  const int dim = 1 << c;
+  if (op.type == OP_DIAG) {
+    for (int i = 0; i < dim; ++i) {
+      int idx = 0;
+      for (int x = 0; x < nq; ++x) idx |= ((i >> op.q[x]) & 1) << (nq - 1 - x);
+      v[i] *= m[idx];
+    }
+    return;
+  }
+  int mask = 0;
+  for (int x = 0; x < nq; ++x) mask |= 1 << op.q[x];
+  for (int i = 0; i < dim; ++i) {
+    if (i & mask) continue;
+    cd in[8], out[8];
+    int addr[8];
+    for (int k = 0; k < d; ++k) {
+      int a = i;
+      for (int x = 0; x < nq; ++x)
+        if ((k >> (nq - 1 - x)) & 1) a |= 1 << op.q[x];
+      addr[k] = a;
+      in[k] = v[a];
+    }
+    for (int r = 0; r < d; ++r) {
+      out[r] = 0.0;
+      for (int k = 0; k < d; ++k) out[r] += m[r * d + k] * in[k];
+    }
+    for (int k = 0; k < d; ++k) v[addr[k]] = out[k];
+  }
+}
+
+template <typename C>
+void pack_pass(const PassH &ps, std::vector<DevOp> &dops, std::vector<C> &mats, std::vector<DevGroup> &dgroups) {
+  int tile_bit[64];
+  int tb = 0;
+  for (int q = 0; q < 64; ++q) tile_bit[q] = (ps.active >> q) & 1ull ? tb++ : -1;
+  std::vector<int> group_of(ps.ops.size(), -1);
+  for (int g = 0; g < (int)ps.groups.size(); ++g)
+    for (int o = ps.groups[g].first_op; o < ps.groups[g].first_op + ps.groups[g].num_ops; ++o) group_of[o] = g;
+  for (size_t o = 0; o < ps.ops.size(); ++o) {
+    OpH op = ps.ops[o];
+    int slot[3] = {-1, -1, -1};
+    const GroupH *G = group_of[o] >= 0 ? &ps.groups[group_of[o]] : nullptr;
+    auto slot_of = [&](int storage_bit) {
+      if (!G) return -1;
+      const int tbit = tile_bit[storage_bit];
+      for (int j = 0; j < kMaxSlots && G->slots[j] >= 0; ++j)
+        if (G->slots[j] == tbit && tbit >= 0) return j;
+      return -1;
+    };
+    int kcase = 0;
+    if (G) {
+      int perm[3] = {0, 1, 2};
+      int sl[3];
+      for (int x = 0; x < op.nq; ++x) sl[x] = slot_of(op.q[x]);
+      // dense: slots descending; diag: slot operands first, descending
+      std::sort(perm, perm + op.nq, [&](int a, int b) {
+        const int ka = sl[a], kb = sl[b];
+        if ((ka >= 0) != (kb >= 0)) return ka >= 0;
+        return ka > kb;
+      });
+      permute_operands(op, perm);
+      int ns = 0;
+      for (int x = 0; x < op.nq; ++x) {
+        slot[x] = slot_of(op.q[x]);
+        if (slot[x] >= 0) ++ns;
+      }
+      if (op.type == OP_DENSE) {
+        kcase = op.nq == 1 ? slot[0]
+              : op.nq == 2 ? 16 + (slot[0] << 3) + slot[1]
+                           : 128 + (slot[0] << 6) + (slot[1] << 3) + slot[2];
+      } else {
+        kcase = ns;
+      }
+    }
+    DevOp d{};
+    d.type = op.type;
+    d.nq = op.nq;
+    for (int x = 0; x < 3; ++x) {
+      d.pos[x] = 0;
+      d.slot[x] = slot[x];
+    }
+    for (int x = 0; x < op.nq; ++x) {
+      const int q = op.q[x];
+      d.pos[x] = tile_bit[q] >= 0 ? tile_bit[q] : kFixedBit + q;
+    }
+    d.kcase = kcase;
+    d.mat = (int32_t)mats.size();
+    const int per = op.type == OP_DENSE ? (1 << (2 * op.nq)) : (1 << op.nq);
+    d.digit_stride = op.digits > 1 ? per : 0;
+    for (auto &z : op.m) {
+      C c;
+      c.x = (decltype(c.x))z.real();
+      c.y = (decltype(c.y))z.imag();
+      mats.push_back(c);
+    }
+    dops.push_back(d);
+  }
+  for (auto &g : ps.groups) {
+    DevGroup dg{};
+    for (int j = 0; j < kMaxSlots; ++j) dg.slots[j] = g.slots[j];
+    dg.first_op = g.first_op;
+    dg.num_ops = g.num_ops;
+    dgroups.push_back(dg);
+  }
+}
+
+}  // namespace
+
+hsf_status build_programs(hsf_plan &p) {
+  const int B = (int)p.blocks.size();
+  std::vector<std::pair<bool, int>> order;
+  hsf_status st = execution_order(p, order);
+  if (st != HSF_OK) return st;
+  p.rbits = p.precision == HSF_PREC_C64 ? kRegBitsC64 : kRegBitsC128;
+  int leaf_c = B > 0 && p.radix[B] <= 8 ? 0 : -1;
+  for (int s = 0; s < 2; ++s) {
+    SideH &sd = p.side[s];
+    sd.h = s == 0 ? p.na : p.nb;
+    sd.offset = s == 0 ? p.cut + 1 : 0;
+    sd.levels.assign(B + 1, LevelH{});
+    for (int b = 0; b < B; ++b) {           // Schmidt factors open levels 1..B
+      const BlockH &bk = p.blocks[b];
+      const std::vector<int> &qs = s == 0 ? bk.qa : bk.qb;
+      OpH op;
+      op.type = OP_DENSE;
+      op.nq = (int)qs.size();
+      for (int j = 0; j < op.nq; ++j) op.q[j] = qs[j] - sd.offset;
+      op.digits = bk.rank;
+      op.block = b;
+      op.m = s == 0 ? bk.x : bk.y;
+      sd.levels[b + 1].ops.push_back(op);
+    }
+    std::vector<int> qlevel(sd.h, 0);
+    int blocks_seen = 0;
+    for (auto &item : order) {
+      if (item.first) {
+        const int b = item.second;
+        const std::vector<int> &qs = s == 0 ? p.blocks[b].qa : p.blocks[b].qb;
+        for (int q : qs) qlevel[q - sd.offset] = std::max(qlevel[q - sd.offset], b + 1);
+        blocks_seen = std::max(blocks_seen, b + 1);
+        continue;
+      }
+      const GateH &g = p.gates[item.second];
+      if (g.side != s) continue;
+      int lvl = 0;
+      if (p.flags & HSF_FLAG_NO_LIGHTCONE) {
+        lvl = blocks_seen;
+      } else {
+        for (int j = 0; j < g.nq; ++j) lvl = std::max(lvl, qlevel[g.q[j] - sd.offset]);
+      }
+      for (int j = 0; j < g.nq; ++j) qlevel[g.q[j] - sd.offset] = lvl;
+      OpH op;
+      op.type = g.diag ? OP_DIAG : OP_DENSE;
+      op.nq = g.nq;
+      for (int j = 0; j < g.nq; ++j) op.q[j] = g.q[j] - sd.offset;
+      const int d = 1 << g.nq;
+      if (g.diag) {
+        op.m.resize(d);
+        for (int i = 0; i < d; ++i) op.m[i] = g.m[(size_t)i * d + i];
+      } else {
+        op.m = g.m;
+      }
+      sd.levels[lvl].ops.push_back(op);
+    }
+    // storage order: qubits touched at deeper levels get lower storage bits
+    std::vector<int> deep(sd.h, -1);
+    for (int k = 0; k <= B; ++k)
+      for (auto &op : sd.levels[k].ops)
+        for (int j = 0; j < op.nq; ++j) deep[op.q[j]] = std::max(deep[op.q[j]], k);
+    std::vector<int> qs(sd.h);
+    for (int q = 0; q < sd.h; ++q) qs[q] = q;
+    if (!(p.flags & HSF_FLAG_IDENTITY_STORAGE))
+      std::stable_sort(qs.begin(), qs.end(), [&](int x, int y) {
+        if (deep[x] != deep[y]) return deep[x] > deep[y];
+        return s == 0 ? x < y : x > y;          // nearest to the cut first
+      });
+    sd.store.assign(sd.h, 0);
+    for (int i = 0; i < sd.h; ++i) sd.store[qs[i]] = i;
+    for (auto &lv : sd.levels)
+      for (auto &op : lv.ops)
+        for (int j = 0; j < op.nq; ++j) op.q[j] = sd.store[op.q[j]];
+    for (auto &lv : sd.levels) merge_one_qubit_runs(lv.ops);
+    if (leaf_c >= 0) {
+      int c = 0;
+      for (auto &op : sd.levels[B].ops)
+        for (int j = 0; j < op.nq; ++j) c = std::max(c, op.q[j] + 1);
+      leaf_c = c <= 5 ? std::max(leaf_c, c) : -1;
+    }
+    for (auto &lv : sd.levels) {
+      split_passes(lv, sd.h, p.tile_max);
+      if (!(p.flags & HSF_FLAG_NO_REGISTER_SWEEP))
+        for (auto &ps : lv.passes) build_groups(ps, p.rbits);
+    }
+  }
+  // leaf operators L_m: the leaf program with digit m applied to every basis vector
+  p.leaf_c = 0;
+  const size_t csz = p.precision == HSF_PREC_C64 ? 8 : 16;
+  if (leaf_c > 0 && leaf_c <= std::min(p.side[0].h, p.side[1].h) &&
+      2 * p.radix[B] * (size_t)(1 << leaf_c) * ((1 << leaf_c) + 1) * csz <= 96 * 1024) {
+    p.leaf_c = leaf_c;
+    const int dim = 1 << leaf_c;
+    const int r = (int)p.radix[B];
+    for (int s = 0; s < 2; ++s) {
+      SideH &sd = p.side[s];
+      sd.leaf_ops.assign((size_t)r * dim * dim, 0.0);
+      for (int m = 0; m < r; ++m)
+        for (int col = 0; col < dim; ++col) {
+          std::vector<cd> v(dim, 0.0);
+          v[col] = 1.0;
+          for (auto &op : sd.levels[B].ops) host_apply(v, leaf_c, op, m);
+          for (int row = 0; row < dim; ++row) sd.leaf_ops[((size_t)m * dim + row) * dim + col] = v[row];
+        }
+    }
+  }
+  return HSF_OK;
+}
+
+hsf_status upload_programs(hsf_plan &p) {
+  std::vector<unsigned char> host;
+  auto align = [&](size_t a) { while (host.size() % a) host.push_back(0); };
+  auto append = [&](const void *ptr, size_t bytes) {
+    host.insert(host.end(), (const unsigned char *)ptr, (const unsigned char *)ptr + bytes);
+  };
+  int64_t launches = 0;
+  for (int s = 0; s < 2; ++s) {
+    for (auto &lv : p.side[s].levels)
+      for (auto &ps : lv.passes) {
+        std::vector<DevOp> dops;
+        std::vector<DevGroup> dgroups;
+        ps.num_ops = (int)ps.ops.size();
+        if (p.precision == HSF_PREC_C64) {
+          std::vector<float2> mats;
+          pack_pass(ps, dops, mats, dgroups);
+          align(256); ps.ops_off = host.size(); append(dops.data(), dops.size() * sizeof(DevOp));
+          align(256); ps.mats_off = host.size(); append(mats.data(), mats.size() * sizeof(float2));
+        } else {
+          std::vector<double2> mats;
+          pack_pass(ps, dops, mats, dgroups);
+          align(256); ps.ops_off = host.size(); append(dops.data(), dops.size() * sizeof(DevOp));
+          align(256); ps.mats_off = host.size(); append(mats.data(), mats.size() * sizeof(double2));
+        }
+        align(256); ps.groups_off = host.size(); append(dgroups.data(), dgroups.size() * sizeof(DevGroup));
+        ++launches;
+      }
+    SideH &sd = p.side[s];
+    align(256);
+    sd.leaf_off = host.size();
+    for (auto &z : sd.leaf_ops) {
+      if (p.precision == HSF_PREC_C64) {
+        float2 c = make_float2((float)z.real(), (float)z.imag());
+        append(&c, sizeof c);
+      } else {
+        double2 c = make_double2(z.real(), z.imag());
+        append(&c, sizeof c);
+      }
+    }
+  }
+  align(256);
+  if (host.empty()) host.resize(256);
+  CUDA_TRY(cudaMalloc(&p.dev_table, host.size()));
+  p.dev_table_bytes = host.size();
+  CUDA_TRY(cudaMemcpy(p.dev_table, host.data(), host.size(), cudaMemcpyHostToDevice));
+  p.launches = launches / 2;
+  return HSF_OK;
+}
+
+hsf_status check_order(const hsf_plan &p) {
+  std::vector<std::pair<bool, int>> order;
+  return execution_order(p, order);
+}
+
+// Multiply and decompose every block on the device; read back ranks and factors.
+hsf_status decompose_blocks(hsf_plan &p) {
+  const int B = (int)p.blocks.size();
+  if (B == 0) return HSF_OK;
+  std::vector<int32_t> bk(3 * B), gbeg(B + 1, 0), gdesc;
+  std::vector<double> gm;
+  for (int b = 0; b < B; ++b) {
+    BlockH &blk = p.blocks[b];
+    const int k = (int)blk.qubits.size();
+    bk[3 * b] = k;
+    bk[3 * b + 1] = (int)blk.qa.size();
+    bk[3 * b + 2] = (int)blk.qb.size();
+    for (int gi : blk.gates) {
+      const GateH &g = p.gates[gi];
+      gdesc.push_back(g.nq);
+      for (int j = 0; j < 3; ++j) {
+        int pos = 0;
+        if (j < g.nq) {
+          const int idx = (int)(std::find(blk.qubits.begin(), blk.qubits.end(), g.q[j]) - blk.qubits.begin());
+          pos = k - 1 - idx;      // block qubits are listed most significant first
+        }
+        gdesc.push_back(pos);
+      }
+      gdesc.push_back((int32_t)(gm.size() / 2));
+      for (auto &z : g.m) {
+        gm.push_back(z.real());
+        gm.push_back(z.imag());
+      }
+    }
+    gbeg[b + 1] = (int32_t)(gdesc.size() / 5);
+  }
+  const size_t nf = (size_t)B * 64 * 64 * 2;
+  size_t off = 0;
+  auto take = [&](size_t bytes) { size_t o = off; off += (bytes + 255) / 256 * 256; return o; };
+  const size_t o_bk = take(bk.size() * 4), o_gb = take(gbeg.size() * 4), o_gd = take(gdesc.size() * 4 + 4),
+               o_gm = take(gm.size() * 8 + 8), o_sig = take((size_t)B * 64 * 8), o_rank = take((size_t)B * 4),
+               o_x = take(nf * 8), o_y = take(nf * 8), o_sw = take((size_t)B * 4);
+  unsigned char *d = nullptr;
+  CUDA_TRY(cudaMalloc(&d, off));
+  std::unique_ptr<unsigned char, void (*)(unsigned char *)> guard(d, [](unsigned char *q) { cudaFree(q); });
+  CUDA_TRY(cudaMemcpy(d + o_bk, bk.data(), bk.size() * 4, cudaMemcpyHostToDevice));
+  CUDA_TRY(cudaMemcpy(d + o_gb, gbeg.data(), gbeg.size() * 4, cudaMemcpyHostToDevice));
+  if (!gdesc.empty()) CUDA_TRY(cudaMemcpy(d + o_gd, gdesc.data(), gdesc.size() * 4, cudaMemcpyHostToDevice));
+  if (!gm.empty()) CUDA_TRY(cudaMemcpy(d + o_gm, gm.data(), gm.size() * 8, cudaMemcpyHostToDevice));
+  BlockSvdArgs a{};
+  a.num_blocks = B;
+  a.block_k = (const int32_t *)(d + o_bk);
+  a.gate_begin = (const int32_t *)(d + o_gb);
+  a.gate_desc = (const int32_t *)(d + o_gd);
+  a.gate_mats = (const double *)(d + o_gm);
+  a.rank_tol = p.rank_tol;
+  a.max_sweeps = 60;
+  a.sigma = (double *)(d + o_sig);
+  a.rank = (int32_t *)(d + o_rank);
+  a.xf = (double *)(d + o_x);
+  a.yf = (double *)(d + o_y);
+  a.sweeps_used = (int32_t *)(d + o_sw);
+  CUDA_TRY(launch_block_svd(a, 0));
+  g_launches++;
+  CUDA_TRY(cudaDeviceSynchronize());
+  std::vector<double> sig((size_t)B * 64), xf(nf), yf(nf);
+  std::vector<int32_t> rank(B);
+  CUDA_TRY(cudaMemcpy(sig.data(), d + o_sig, sig.size() * 8, cudaMemcpyDeviceToHost));
+  CUDA_TRY(cudaMemcpy(rank.data(), d + o_rank, rank.size() * 4, cudaMemcpyDeviceToHost));
+  CUDA_TRY(cudaMemcpy(xf.data(), d + o_x, nf * 8, cudaMemcpyDeviceToHost));
+  CUDA_TRY(cudaMemcpy(yf.data(), d + o_y, nf * 8, cudaMemcpyDeviceToHost));
+  for (int b = 0; b < B; ++b) {
+    BlockH &blk = p.blocks[b];
+    blk.rank = rank[b];
+    if (blk.rank <= 0) return set_error(HSF_ENUMERIC, "block %d decomposed to rank 0", b);
+    blk.sigma.assign(sig.begin() + (size_t)b * 64, sig.begin() + (size_t)b * 64 + blk.rank);
+    for (double s : blk.sigma)
+      if (!std::isfinite(s)) return set_error(HSF_ENUMERIC, "block %d: non-finite singular value", b);
+    const int ea = 1 << (2 * (int)blk.qa.size()), eb = 1 << (2 * (int)blk.qb.size());
+    blk.x.clear();
+    blk.y.clear();
+    for (int m = 0; m < blk.rank; ++m) {
+      for (int e = 0; e < ea; ++e) {
+        const size_t i = (((size_t)b * 64 + m) * 64 + e) * 2;
+        blk.x.push_back(cd(xf[i], xf[i + 1]));
+      }
+      for (int e = 0; e < eb; ++e) {
+        const size_t i = (((size_t)b * 64 + m) * 64 + e) * 2;
+        blk.y.push_back(cd(yf[i], yf[i + 1]));
+      }
+    }
+  }
+  return HSF_OK;
+}
+
+hsf_status validate_and_load(hsf_plan &p, const hsf_circuit *c, int cut, const hsf_blocks *bl,
+                             const hsf_plan_opts *o) {
+  if (!c || !bl) return set_error(HSF_EINVAL, "circuit and blocks must not be NULL");
+  if (c->n < 2 || c->n > 62) return set_error(HSF_EINVAL, "n = %d outside 2..62", c->n);
+  if (cut < 0 || cut > c->n - 2) return set_error(HSF_EINVAL, "cut %d outside 0..n-2", cut);
+  if (c->num_gates < 0 || (c->num_gates > 0 && !c->gates)) return set_error(HSF_EINVAL, "bad gate array");
+  p.n = c->n;
+  p.cut = cut;
+  p.nb = cut + 1;
+  p.na = c->n - cut - 1;
+  p.max_paths = 1ull << 40;
+  if (o) {
+    p.precision = o->precision;
+    p.gemm_mode = o->gemm_mode;
+    p.rank_tol = o->rank_tol > 0 ? o->rank_tol : 1e-12;
+    if (o->max_paths) p.max_paths = o->max_paths;
+    p.flags = o->flags;
+  }
+  if (p.precision != HSF_PREC_C64 && p.precision != HSF_PREC_C128)
+    return set_error(HSF_EINVAL, "precision %d", p.precision);
+  if (p.gemm_mode < 0 || p.gemm_mode > 3) return set_error(HSF_EINVAL, "gemm_mode %d", p.gemm_mode);
+  // a shared-memory tile holds at most 2^13 (complex64) or 2^12 (complex128) amplitudes
+  const int tcap = p.precision == HSF_PREC_C64 ? kRegTileC64 : kRegTileC128;
+  p.tile_max = (o && o->tile_bits) ? o->tile_bits : tcap;
+  if (p.tile_max < 3 || p.tile_max > tcap) return set_error(HSF_EINVAL, "tile_bits %d outside 3..%d", p.tile_max, tcap);
+  if (p.na > 40 || p.nb > 40) return set_error(HSF_EINVAL, "half of %d/%d qubits is too large", p.na, p.nb);
+  p.gates.resize(c->num_gates);
+  for (int i = 0; i < c->num_gates; ++i) {
+    const hsf_gate &g = c->gates[i];
+    GateH &h = p.gates[i];
+    h.kind = g.kind;
+    h.param = g.param;
+    h.param_id = g.param_id;
+    if (g.param_id >= 0 && o && o->angles) {
+      if (g.param_id >= o->num_angles) return set_error(HSF_EINVAL, "gate %d: param_id %d >= num_angles", i, g.param_id);
+      h.param = o->angles[g.param_id];
+    }
+    int nq = 0;
+    if (g.kind == HSF_GATE_MATRIX) {
+      nq = g.nq;
+      if (nq < 1 || nq > 3) return set_error(HSF_EINVAL, "gate %d: matrix gates take 1..3 qubits", i);
+      if (!g.mat) return set_error(HSF_EINVAL, "gate %d: matrix pointer is NULL", i);
+      const int d = 1 << nq;
+      h.m.resize((size_t)d * d);
+      for (int e = 0; e < d * d; ++e) h.m[e] = cd(g.mat[2 * e], g.mat[2 * e + 1]);
+      for (auto &z : h.m)
+        if (!std::isfinite(z.real()) || !std::isfinite(z.imag()))
+          return set_error(HSF_EINVAL, "gate %d: non-finite matrix", i);
+    } else {
+      hsf_status st = named_matrix(g.kind, h.param, h.m, nq);
+      if (st != HSF_OK) return st;
+      if (g.nq != nq) return set_error(HSF_EINVAL, "gate %d: kind %d takes %d qubits, got %d", i, g.kind, nq, g.nq);
+    }
+    h.nq = nq;
+    for (int j = 0; j < nq; ++j) {
+      h.q[j] = g.q[j];
+      if (g.q[j] < 0 || g.q[j] >= c->n) return set_error(HSF_EINVAL, "gate %d: qubit %d out of range", i, g.q[j]);
+      for (int k = 0; k < j; ++k)
+        if (g.q[k] == g.q[j]) return set_error(HSF_EINVAL, "gate %d: repeated qubit %d", i, g.q[j]);
+    }
+    h.diag = is_diagonal(h.m, 1 << nq);
+    bool hi = false, lo = false;
+    for (int j = 0; j < nq; ++j) (h.q[j] > cut ? hi : lo) = true;
+    h.side = (hi && lo) ? 2 : (hi ? 0 : 1);
+  }
+  if (bl->num_blocks < 0 || bl->num_blocks > 64)
+    return set_error(HSF_EINVAL, "num_blocks %d outside 0..64", bl->num_blocks);
+  if (bl->num_blocks > 0 && (!bl->offsets || !bl->gate_idx)) return set_error(HSF_EINVAL, "bad block arrays");
+  std::vector<int> owner(c->num_gates, -1);
+  p.blocks.resize(bl->num_blocks);
+  for (int b = 0; b < bl->num_blocks; ++b) {
+    const int lo = bl->offsets[b], hi = bl->offsets[b + 1];
+    if (lo < 0 || hi < lo) return set_error(HSF_EINVAL, "block %d: bad offsets", b);
+    if (hi == lo) return set_error(HSF_EBLOCK, "block %d is empty", b);
+    BlockH &blk = p.blocks[b];
+    std::set<int> qs;
+    bool crossing = false;
+    for (int e = lo; e < hi; ++e) {
+      const int gi = bl->gate_idx[e];
+      if (gi < 0 || gi >= c->num_gates) return set_error(HSF_EINVAL, "block %d: gate index %d out of range", b, gi);
+      if (owner[gi] >= 0) return set_error(HSF_EBLOCK, "gate %d is in blocks %d and %d", gi, owner[gi], b);
+      owner[gi] = b;
+      blk.gates.push_back(gi);
+      for (int j = 0; j < p.gates[gi].nq; ++j) qs.insert(p.gates[gi].q[j]);
+      crossing |= p.gates[gi].side == 2;
+    }
+    if (!crossing) return set_error(HSF_EBLOCK, "block %d holds no gate crossing the cut", b);
+    std::sort(blk.gates.begin(), blk.gates.end());
+    blk.qubits.assign(qs.rbegin(), qs.rend());
+    for (int q : blk.qubits) (q > cut ? blk.qa : blk.qb).push_back(q);
+    if (blk.qa.size() > 3 || blk.qb.size() > 3)
+      return set_error(HSF_ERANK, "block %d spans %zu|%zu qubits; at most 3 per side", b, blk.qa.size(), blk.qb.size());
+  }
+  for (int i = 0; i < c->num_gates; ++i)
+    if (p.gates[i].side == 2 && owner[i] < 0)
+      return set_error(HSF_EBLOCK, "gate %d crosses the cut but is in no block", i);
+  return HSF_OK;
+}
+
+}  // namespace hsf

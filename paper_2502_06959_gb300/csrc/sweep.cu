@@ -156,11 +156,268 @@ __global__ void __launch_bounds__(256) sweep_kernel(SweepArgs a) {
   }
 }
 
+// ---------------------------------------------------------------------------
+// Register-resident variant.  The CTA stages 2^T amplitudes (T = 14 for complex64,
+// 13 for complex128) of one or more tiles in shared memory, padded by one element
+// every 32 (bank-conflict-free strided access).  The pass's ops come in register
+// groups: every thread loads the 2^RB amplitudes spanned by the group's slots for its
+// assignment of the other tile bits, applies all ops of the group in registers, and
+// writes them back; dense ops are fully unrolled per slot pattern (kcase).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t pad32(uint32_t u) { return u + (u >> 5); }
+
+template <int J, int NR, typename C>
+__device__ __forceinline__ void ap1(C (&v)[NR], const C *__restrict__ m) {
+  const C m0 = m[0], m1 = m[1], m2 = m[2], m3 = m[3];
+#pragma unroll
+  for (int i = 0; i < NR; ++i) {
+    if (i & (1 << J)) continue;
+    const int k = i | (1 << J);
+    const C x0 = v[i], x1 = v[k];
+    v[i] = cfma(m1, x1, cmul(m0, x0));
+    v[k] = cfma(m3, x1, cmul(m2, x0));
+  }
+}
+
+template <int J, int K, int NR, typename C>
+__device__ __forceinline__ void ap2(C (&v)[NR], const C *m0) {
+#pragma unroll
+  for (int i = 0; i < NR; ++i) {
+    if (i & ((1 << J) | (1 << K))) continue;
+    // matrix rows are re-read per quad (L1 broadcast) to keep register use low
+    const C *m = m0;
+    asm volatile("" : "+l"(m));
+    const int id[4] = {i, i | (1 << K), i | (1 << J), i | (1 << J) | (1 << K)};
+    C x[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) x[c] = v[id[c]];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      C acc = cmul(m[4 * r], x[0]);
+#pragma unroll
+      for (int c = 1; c < 4; ++c) acc = cfma(m[4 * r + c], x[c], acc);
+      v[id[r]] = acc;
+    }
+  }
+}
+
+template <int J, int K, int L, int NR, typename C>
+__device__ __forceinline__ void ap3(C (&v)[NR], const C *m0) {
+#pragma unroll
+  for (int i = 0; i < NR; ++i) {
+    if (i & ((1 << J) | (1 << K) | (1 << L))) continue;
+    // reload the 8x8 matrix per octet rather than keeping 64 entries live
+    const C *m = m0;
+    asm volatile("" : "+l"(m));
+    int id[8];
+#pragma unroll
+    for (int c = 0; c < 8; ++c)
+      id[c] = i | ((c & 4) ? (1 << J) : 0) | ((c & 2) ? (1 << K) : 0) | ((c & 1) ? (1 << L) : 0);
+    C x[8];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) x[c] = v[id[c]];
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      C acc = cmul(m[8 * r], x[0]);
+#pragma unroll
+      for (int c = 1; c < 8; ++c) acc = cfma(m[8 * r + c], x[c], acc);
+      v[id[r]] = acc;
+    }
+  }
+}
+
+#define KC1(J) (J)
+#define KC2(J, K) (16 + ((J) << 3) + (K))
+#define KC3(J, K, L) (128 + ((J) << 6) + ((K) << 3) + (L))
+
+template <int NR, typename C>
+__device__ __forceinline__ void apply_dense(C (&v)[NR], int kcase, const C *__restrict__ m) {
+  // only slot patterns inside the 2^RB register block are instantiated
+#define HSF_C1(J) case KC1(J): if constexpr ((1 << (J)) < NR) ap1<J>(v, m); break;
+#define HSF_C2(J, K) case KC2(J, K): if constexpr ((1 << (J)) < NR) ap2<J, K>(v, m); break;
+#define HSF_C3(J, K, L) case KC3(J, K, L): if constexpr ((1 << (J)) < NR) ap3<J, K, L>(v, m); break;
+  switch (kcase) {
+    HSF_C1(0) HSF_C1(1) HSF_C1(2) HSF_C1(3) HSF_C1(4)
+    HSF_C2(1, 0) HSF_C2(2, 0) HSF_C2(2, 1) HSF_C2(3, 0) HSF_C2(3, 1) HSF_C2(3, 2)
+    HSF_C2(4, 0) HSF_C2(4, 1) HSF_C2(4, 2) HSF_C2(4, 3)
+    HSF_C3(2, 1, 0) HSF_C3(3, 1, 0) HSF_C3(3, 2, 0) HSF_C3(3, 2, 1)
+    HSF_C3(4, 1, 0) HSF_C3(4, 2, 0) HSF_C3(4, 2, 1) HSF_C3(4, 3, 0) HSF_C3(4, 3, 1) HSF_C3(4, 3, 2)
+    default: break;
+  }
+#undef HSF_C1
+#undef HSF_C2
+#undef HSF_C3
+}
+
+template <typename R, int RB, int T>
+__global__ void __launch_bounds__(512, 1) sweep_reg_kernel(SweepArgs a) {
+  using C = typename CT<R>::T;
+  constexpr int NR = 1 << RB;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C *s = reinterpret_cast<C *>(smem_raw);
+  const int t = a.t;
+  const int tb = t - RB;                     // thread bits per item
+  const int ipc = 1 << (T - t);              // items per CTA
+  const uint32_t tmask = (1u << t) - 1u;
+  const uint64_t full = (1ull << a.h) - 1ull;
+  const uint64_t inactive = full & ~a.active_mask;
+  const bool contiguous = a.active_mask == ((1ull << t) - 1ull);
+  const C *mats = reinterpret_cast<const C *>(a.mats);
+  const int64_t items = a.num_nodes * (int64_t)a.tiles_per_node;
+  const uint64_t state = 1ull << a.h;
+  const int tid = threadIdx.x;
+  const int il = tid >> tb;                  // my item within the CTA
+  const uint32_t inst = (uint32_t)tid & ((1u << tb) - 1u);
+
+  for (int64_t item0 = (int64_t)blockIdx.x * ipc; item0 < items; item0 += (int64_t)gridDim.x * ipc) {
+    // ---- load the CTA's tiles (coalesced) ----
+    for (uint32_t e = tid; e < (1u << T); e += blockDim.x) {
+      const int64_t item = item0 + (e >> t);
+      if (item >= items) break;
+      const uint32_t u = e & tmask;
+      const int64_t nl = item / a.tiles_per_node;
+      const uint64_t tile = (uint64_t)(item % a.tiles_per_node);
+      const uint64_t base = deposit(tile, inactive);
+      const uint64_t off = contiguous ? (base | u) : (base | deposit(u, a.active_mask));
+      C v;
+      if (a.init_zero) {
+        v.x = (off == 0) ? R(1) : R(0);
+        v.y = R(0);
+      } else {
+        const int64_t node = a.node_lo + nl;
+        const C *src = a.read_parent
+                           ? reinterpret_cast<const C *>(a.src) + (uint64_t)(node / a.radix - a.parent_lo) * state
+                           : reinterpret_cast<const C *>(a.dst) + (uint64_t)nl * state;
+        v = src[off];
+      }
+      s[pad32(e)] = v;
+    }
+    __syncthreads();
+
+    const int64_t my_item = item0 + il;
+    const bool valid = my_item < items;
+    const int64_t my_node = a.node_lo + (valid ? my_item / a.tiles_per_node : 0);
+    const int digit = a.radix > 1 ? (int)(my_node % a.radix) : 0;
+    const uint64_t my_base = valid ? deposit((uint64_t)(my_item % a.tiles_per_node), inactive) : 0ull;
+
+    for (int g = 0; g < a.num_groups; ++g) {
+      const DevGroup G = a.groups[g];
+      uint32_t smask = 0;
+      uint32_t w[RB];
+#pragma unroll
+      for (int j = 0; j < RB; ++j) {
+        w[j] = 1u << G.slots[j];
+        smask |= w[j];
+      }
+      const uint32_t ubase = ((uint32_t)il << t) | (uint32_t)deposit(inst, tmask & ~smask);
+      C v[NR];
+#pragma unroll
+      for (int i = 0; i < NR; ++i) {
+        uint32_t u = ubase;
+#pragma unroll
+        for (int j = 0; j < RB; ++j)
+          if (i & (1 << j)) u += w[j];
+        v[i] = s[pad32(u)];
+      }
+      for (int o = G.first_op; o < G.first_op + G.num_ops; ++o) {
+        const DevOp op = a.ops[o];
+        const C *m = mats + op.mat + (op.digit_stride > 0 ? digit * op.digit_stride : 0);
+        if (op.type == OP_DIAG) {
+          // operands are ordered slot operands first (kcase = their count); the
+          // others are bits of this thread's instance or of the tile's fixed bits
+          const int ns = op.kcase;
+          int tpart = 0;
+          for (int x = ns; x < op.nq; ++x) {
+            const int p = op.pos[x];
+            const int bit = p >= kFixedBit ? (int)((my_base >> (p - kFixedBit)) & 1ull) : (int)((ubase >> p) & 1u);
+            tpart |= bit << (op.nq - 1 - x);
+          }
+          const int sh = op.nq - ns;            // slot bits sit above the fixed part
+          if (ns == 0) {
+            const C d = m[tpart];
+#pragma unroll
+            for (int i = 0; i < NR; ++i) v[i] = cmul(d, v[i]);
+          } else if (ns == 1) {
+            const C d0 = m[tpart], d1 = m[tpart | (1 << sh)];
+            const int s0 = op.slot[0];
+#pragma unroll
+            for (int i = 0; i < NR; ++i) v[i] = cmul(((i >> s0) & 1) ? d1 : d0, v[i]);
+          } else if (ns == 2) {
+            const C d0 = m[tpart], d1 = m[tpart | (1 << sh)], d2 = m[tpart | (2 << sh)], d3 = m[tpart | (3 << sh)];
+            const int s0 = op.slot[0], s1 = op.slot[1];
+#pragma unroll
+            for (int i = 0; i < NR; ++i) {
+              const int b0 = (i >> s0) & 1, b1 = (i >> s1) & 1;
+              const C d = b0 ? (b1 ? d3 : d2) : (b1 ? d1 : d0);
+              v[i] = cmul(d, v[i]);
+            }
+          } else {
+            const int s0 = op.slot[0], s1 = op.slot[1], s2 = op.slot[2];
+#pragma unroll
+            for (int i = 0; i < NR; ++i) {
+              const int idx = (((i >> s0) & 1) << 2) | (((i >> s1) & 1) << 1) | ((i >> s2) & 1);
+              v[i] = cmul(m[idx], v[i]);
+            }
+          }
+        } else {
+          apply_dense<NR>(v, op.kcase, m);
+        }
+      }
+      // recompute the addresses instead of keeping 2^RB of them live across the ops
+      uint32_t ub2 = ubase;
+      asm volatile("" : "+r"(ub2));
+#pragma unroll
+      for (int j = 0; j < RB; ++j) asm volatile("" : "+r"(w[j]));
+#pragma unroll
+      for (int i = 0; i < NR; ++i) {
+        uint32_t u = ub2;
+#pragma unroll
+        for (int j = 0; j < RB; ++j)
+          if (i & (1 << j)) u += w[j];
+        s[pad32(u)] = v[i];
+      }
+      __syncthreads();
+    }
+
+    // ---- store ----
+    for (uint32_t e = tid; e < (1u << T); e += blockDim.x) {
+      const int64_t item = item0 + (e >> t);
+      if (item >= items) break;
+      const uint32_t u = e & tmask;
+      const int64_t nl = item / a.tiles_per_node;
+      const uint64_t tile = (uint64_t)(item % a.tiles_per_node);
+      const uint64_t base = deposit(tile, inactive);
+      const uint64_t off = contiguous ? (base | u) : (base | deposit(u, a.active_mask));
+      reinterpret_cast<C *>(a.dst)[(uint64_t)nl * state + off] = s[pad32(e)];
+    }
+    __syncthreads();
+  }
+}
+
 }  // namespace
 
 cudaError_t launch_sweep(const SweepArgs &a, int precision, cudaStream_t st) {
   if (a.num_nodes <= 0) return cudaSuccess;
   const int64_t items = a.num_nodes * (int64_t)a.tiles_per_node;
+  if (a.groups && a.t >= a.rbits) {
+    const int T = precision == 0 ? kRegTileC64 : kRegTileC128;
+    const int64_t ipc = 1ll << (T - a.t);
+    const int64_t ctas = (items + ipc - 1) / ipc;
+    const int grid = (int)(ctas < (1 << 20) ? ctas : (1 << 20));
+    const size_t smem = (size_t)((1u << T) + (1u << (T - 5))) * (precision == 0 ? 8 : 16);
+    if (precision == 0) {
+      auto k = sweep_reg_kernel<float, kRegBitsC64, kRegTileC64>;
+      cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+      k<<<grid, 512, smem, st>>>(a);
+    } else {
+      auto k = sweep_reg_kernel<double, kRegBitsC128, kRegTileC128>;
+      cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+      k<<<grid, 512, smem, st>>>(a);
+    }
+    return cudaGetLastError();
+  }
   const int grid = (int)(items < (1 << 20) ? items : (1 << 20));
   if (precision == 0) {
     const size_t smem = (size_t)8 << a.t;

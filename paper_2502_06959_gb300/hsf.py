@@ -27,6 +27,8 @@ PREC = {"c64": 0, "c128": 1}
 GEMM = {"fp32": 0, "bf16x3": 1, "tf32x3": 2, "tf32": 3}
 FLAG_NO_LIGHTCONE = 1
 FLAG_NO_LEAF_CONTRACT = 2
+FLAG_NO_REGISTER_SWEEP = 4
+FLAG_IDENTITY_STORAGE = 8
 
 
 class HsfError(RuntimeError):
@@ -63,7 +65,8 @@ class hsf_plan_info(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int32), ("n_a", ctypes.c_int32), ("n_b", ctypes.c_int32),
                 ("num_blocks", ctypes.c_int32), ("num_paths", ctypes.c_uint64),
                 ("precision", ctypes.c_int32), ("max_rank", ctypes.c_int32),
-                ("tree_nodes", ctypes.c_int64), ("num_launches", ctypes.c_int64)]
+                ("tree_nodes", ctypes.c_int64), ("num_launches", ctypes.c_int64),
+                ("leaf_bits", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 # symbol -> (restype, argtypes); also the list the load test checks against the header
@@ -88,7 +91,7 @@ SIGNATURES = {
     "hsf_version": (ctypes.c_char_p, []),
 }
 
-KERNEL_KINDS = ("sweep", "gather", "reduce", "window", "other")
+KERNEL_KINDS = ("sweep", "gather", "reduce", "window", "other", "leaf")
 
 
 class hsf_kernel_stat(ctypes.Structure):

@@ -250,3 +250,35 @@ def test_c2_full_size_sampled_paths(path_range):
     got, ginfo = gpu_amps(pr, "c64", bitstrings=pr.bitstrings, path_range=path_range)
     assert ginfo["num_paths"] == 4 ** 8
     check(got, want, "c64")
+
+
+@pytest.mark.parametrize("prec", ["c128", "c64"])
+@pytest.mark.parametrize("seed", range(4))
+def test_leaf_contraction_matches_materialised_leaves(prec, seed):
+    """The leaf level contracted at the bitstrings equals the materialised leaves
+    summed by gather-dot, and both equal the oracle (several digits per block,
+    unaligned path ranges)."""
+    from paper_2502_06959_gb300 import hsf
+    pr = W.random_brickwork(12, 5, 7, block_after=(2, 4, 7), block_kind="mixed", block_len=3,
+                            seed=40 + seed)
+    rng = np.random.default_rng(seed)
+    bs = W.random_bitstrings(rng, pr.n, 257)
+    ref = O.schrodinger(pr.n, pr.gates)[bs.astype(np.int64)]
+    got, info = gpu_amps(pr, prec, bitstrings=bs)
+    assert info["leaf_bits"] > 0
+    check(got, ref, prec)
+    got2, info2 = gpu_amps(pr, prec, bitstrings=bs, flags=hsf.FLAG_NO_LEAF_CONTRACT)
+    check(got2, ref, prec)
+    P = info["num_paths"]
+    for (a, b) in ((1, P - 1), (3, 6), (P // 2 + 1, P // 2 + 2)):
+        want, _ = O.hsf_amplitudes(pr.n, pr.gates, pr.cut, pr.blocks, bitstrings=bs, path_range=(a, b))
+        got, _ = gpu_amps(pr, prec, bitstrings=bs, path_range=(a, b))
+        check(got, want, prec)
+
+
+def test_c2_plan_uses_leaf_contraction_and_register_kernel():
+    pr = W.workload_c2(num_bitstrings=16)
+    plan = H().Plan.from_problem(pr)
+    assert plan.info["leaf_bits"] == 4
+    assert plan.info["tree_nodes"] == sum(4 ** k for k in range(9))
+    plan.close()
