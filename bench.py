@@ -46,6 +46,10 @@ def parse():
     ap.add_argument("--precision", default="c64", choices=["c64", "c128"])
     ap.add_argument("--no-extras", action="store_true", help="skip plain-cut and CPU baseline legs")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU-baseline sample time")
+    ap.add_argument("--paths", type=int, default=0,
+                    help="profiling aid: simulate only the first N paths (0 = all)")
+    ap.add_argument("--budget-gb", type=float, default=0.0,
+                    help="profiling aid: cap the workspace (path chunks shrink to fit)")
     return ap.parse_args()
 
 
@@ -221,7 +225,9 @@ def main():
     plan0 = hsf.Plan.from_problem(pr, precision=args.precision)
     info = dict(plan0.info)
     free, _ = torch.cuda.mem_get_info()
-    ws_bytes = hsf.hsf_workspace_size(plan0.handle, S, 0, int(free * 0.7))
+    budget = int(args.budget_gb * 2 ** 30) if args.budget_gb else int(free * 0.7)
+    ws_bytes = hsf.hsf_workspace_size(plan0.handle, S, 0, budget)
+    p_end = args.paths if args.paths else 0
     ws = torch.empty(ws_bytes, dtype=torch.uint8, device=dev)
 
     def step(plan_each=True):
@@ -229,7 +235,7 @@ def main():
             h = hsf.hsf_plan_create(pr.n, pr.gates, pr.cut, pr.blocks, precision=args.precision)
         else:
             h = plan0.handle
-        hsf.hsf_run(h, bits.data_ptr(), S, 0, 0, 0, out.data_ptr(), ws.data_ptr(), ws_bytes,
+        hsf.hsf_run(h, bits.data_ptr(), S, 0, 0, p_end, out.data_ptr(), ws.data_ptr(), ws_bytes,
                     stream.cuda_stream)
         return h
 
@@ -293,7 +299,7 @@ def main():
     for _ in range(args.steps):
         dbits.copy_(hbits, non_blocking=True)
         h = hsf.hsf_plan_create(pr.n, pr.gates, pr.cut, pr.blocks, precision=args.precision)
-        hsf.hsf_run(h, dbits.data_ptr(), S, 0, 0, 0, out.data_ptr(), ws.data_ptr(), ws_bytes,
+        hsf.hsf_run(h, dbits.data_ptr(), S, 0, 0, p_end, out.data_ptr(), ws.data_ptr(), ws_bytes,
                     stream.cuda_stream)
         hout.copy_(out, non_blocking=True)
         handles.append(h)
@@ -341,6 +347,9 @@ def main():
         "clocks": clk.summary(),
     }
 
+    if args.paths:
+        line["config"]["paths_simulated"] = args.paths
+        line["value"] = None       # a partial path sum is not a circuit
     if rank == 0 and not args.no_extras:
         # joint vs plain cut: the same circuit with one block per crossing gate (2^32
         # paths) timed on a fixed path budget and extrapolated

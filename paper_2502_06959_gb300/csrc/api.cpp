@@ -69,7 +69,7 @@ RunLayout layout_for(const hsf_plan &p, size_t num_bits, uint64_t window, uint64
   }
   if (num_bits > 0) {
     const uint64_t units = L.leaf ? (chunk + p.radix[B] - 1) / p.radix[B] + 1 : chunk;
-    L.ppg = L.leaf ? 16 : 64;
+    L.ppg = 64;
     while ((units + L.ppg - 1) / L.ppg > 65535) L.ppg *= 2;
     L.groups = (int32_t)((units + L.ppg - 1) / L.ppg);
     L.off_partial = off;

@@ -249,12 +249,37 @@ __device__ __forceinline__ void apply_dense(C (&v)[NR], int kcase, const C *__re
 #undef HSF_C3
 }
 
+// Asynchronous global -> shared copy of one amplitude (8 or 16 bytes).
+template <int BYTES>
+__device__ __forceinline__ void cp_async_elem(void *smem, const void *gmem) {
+  const uint32_t sa = (uint32_t)__cvta_generic_to_shared(smem);
+  if constexpr (BYTES == 8)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem) : "memory");
+  else
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+// Per-batch addressing of the items (tiles) a CTA holds.
+template <int MAXI>
+struct ItemInfo {
+  int64_t src[MAXI], dst[MAXI];   // element offsets of each item's tile origin
+  uint64_t base[MAXI];            // fixed storage bits of each item's tile
+  int digit[MAXI];
+  int nvalid;
+};
+
 template <typename R, int RB, int T>
 __global__ void __launch_bounds__(512, 1) sweep_reg_kernel(SweepArgs a) {
   using C = typename CT<R>::T;
   constexpr int NR = 1 << RB;
+  constexpr int MAXI = 1 << (T - RB);        // most items a CTA can hold
+  constexpr uint32_t BUF = (1u << T) + (1u << (T - 5));   // padded tile elements
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  C *s = reinterpret_cast<C *>(smem_raw);
+  C *sbuf = reinterpret_cast<C *>(smem_raw);   // two tile buffers (double buffering)
+  __shared__ ItemInfo<MAXI> info[2];
   const int t = a.t;
   const int tb = t - RB;                     // thread bits per item
   const int ipc = 1 << (T - t);              // items per CTA
@@ -264,41 +289,67 @@ __global__ void __launch_bounds__(512, 1) sweep_reg_kernel(SweepArgs a) {
   const bool contiguous = a.active_mask == ((1ull << t) - 1ull);
   const C *mats = reinterpret_cast<const C *>(a.mats);
   const int64_t items = a.num_nodes * (int64_t)a.tiles_per_node;
-  const uint64_t state = 1ull << a.h;
+  const int tpn_bits = a.h - t;              // tiles per node = 2^(h - t)
   const int tid = threadIdx.x;
   const int il = tid >> tb;                  // my item within the CTA
   const uint32_t inst = (uint32_t)tid & ((1u << tb) - 1u);
+  const C *src = reinterpret_cast<const C *>(a.read_parent ? a.src : a.dst);
+  C *dst = reinterpret_cast<C *>(a.dst);
+  const int64_t stride = (int64_t)gridDim.x * ipc;
 
-  for (int64_t item0 = (int64_t)blockIdx.x * ipc; item0 < items; item0 += (int64_t)gridDim.x * ipc) {
-    // ---- load the CTA's tiles (coalesced) ----
-    for (uint32_t e = tid; e < (1u << T); e += blockDim.x) {
-      const int64_t item = item0 + (e >> t);
-      if (item >= items) break;
+  // Start the copies of the batch beginning at item0 into buffer `slot`.
+  auto prefetch = [&](int64_t item0, int slot) {
+    ItemInfo<MAXI> &in = info[slot];
+    const int nvalid = (int)min((int64_t)ipc, items - item0);
+    for (int j = tid; j < nvalid; j += blockDim.x) {
+      const int64_t item = item0 + j;
+      const int64_t nl = item >> tpn_bits;
+      const uint64_t tile = (uint64_t)item & ((1ull << tpn_bits) - 1ull);
+      const uint64_t base = contiguous ? (tile << t) : deposit(tile, inactive);
+      const int64_t node = a.node_lo + nl;
+      const int64_t srcnode = a.read_parent ? node / a.radix - a.parent_lo : nl;
+      in.src[j] = (srcnode << a.h) + (int64_t)base;
+      in.dst[j] = (nl << a.h) + (int64_t)base;
+      in.base[j] = base;
+      in.digit[j] = a.radix > 1 ? (int)(node % a.radix) : 0;
+    }
+    if (tid == 0) in.nvalid = nvalid;
+    __syncthreads();
+    C *sb = sbuf + slot * BUF;
+    const uint32_t total = (uint32_t)nvalid << t;
+    for (uint32_t e = tid; e < total; e += blockDim.x) {
+      const int j = (int)(e >> t);
       const uint32_t u = e & tmask;
-      const int64_t nl = item / a.tiles_per_node;
-      const uint64_t tile = (uint64_t)(item % a.tiles_per_node);
-      const uint64_t base = deposit(tile, inactive);
-      const uint64_t off = contiguous ? (base | u) : (base | deposit(u, a.active_mask));
-      C v;
       if (a.init_zero) {
-        v.x = (off == 0) ? R(1) : R(0);
+        C v;
+        v.x = (in.base[j] == 0 && u == 0) ? R(1) : R(0);
         v.y = R(0);
+        sb[pad32(e)] = v;
       } else {
-        const int64_t node = a.node_lo + nl;
-        const C *src = a.read_parent
-                           ? reinterpret_cast<const C *>(a.src) + (uint64_t)(node / a.radix - a.parent_lo) * state
-                           : reinterpret_cast<const C *>(a.dst) + (uint64_t)nl * state;
-        v = src[off];
+        cp_async_elem<(int)sizeof(C)>(sb + pad32(e), src + in.src[j] + (int64_t)(contiguous ? u : deposit(u, a.active_mask)));
       }
-      s[pad32(e)] = v;
+    }
+    cp_async_commit();
+  };
+
+  int64_t item0 = (int64_t)blockIdx.x * ipc;
+  if (item0 < items) prefetch(item0, 0);
+  for (int k = 0; item0 < items; item0 += stride, ++k) {
+    const int slot = k & 1;
+    const int64_t next = item0 + stride;
+    if (next < items) {
+      prefetch(next, slot ^ 1);
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
     }
     __syncthreads();
-
-    const int64_t my_item = item0 + il;
-    const bool valid = my_item < items;
-    const int64_t my_node = a.node_lo + (valid ? my_item / a.tiles_per_node : 0);
-    const int digit = a.radix > 1 ? (int)(my_node % a.radix) : 0;
-    const uint64_t my_base = valid ? deposit((uint64_t)(my_item % a.tiles_per_node), inactive) : 0ull;
+    C *s = sbuf + slot * BUF;
+    const ItemInfo<MAXI> &in = info[slot];
+    const int nvalid = in.nvalid;
+    const bool valid = il < nvalid;
+    const int digit = valid ? in.digit[il] : 0;
+    const uint64_t my_base = valid ? in.base[il] : 0ull;
 
     for (int g = 0; g < a.num_groups; ++g) {
       const DevGroup G = a.groups[g];
@@ -379,16 +430,29 @@ __global__ void __launch_bounds__(512, 1) sweep_reg_kernel(SweepArgs a) {
       __syncthreads();
     }
 
-    // ---- store ----
-    for (uint32_t e = tid; e < (1u << T); e += blockDim.x) {
-      const int64_t item = item0 + (e >> t);
-      if (item >= items) break;
-      const uint32_t u = e & tmask;
-      const int64_t nl = item / a.tiles_per_node;
-      const uint64_t tile = (uint64_t)(item % a.tiles_per_node);
-      const uint64_t base = deposit(tile, inactive);
-      const uint64_t off = contiguous ? (base | u) : (base | deposit(u, a.active_mask));
-      reinterpret_cast<C *>(a.dst)[(uint64_t)nl * state + off] = s[pad32(e)];
+    // ---- store (pairs of amplitudes per thread when the tile is contiguous) ----
+    const uint32_t total = (uint32_t)nvalid << t;
+    if (contiguous && t >= 1) {
+      for (uint32_t e = 2 * tid; e < total; e += 2 * blockDim.x) {
+        const int j = (int)(e >> t);
+        const uint32_t u = e & tmask;
+        const C v0 = s[pad32(e)], v1 = s[pad32(e + 1)];
+        C *gp = dst + in.dst[j] + u;
+        if constexpr (sizeof(C) == 8) {
+          float4 q;
+          q.x = v0.x; q.y = v0.y; q.z = v1.x; q.w = v1.y;
+          *reinterpret_cast<float4 *>(gp) = q;
+        } else {
+          gp[0] = v0;
+          gp[1] = v1;
+        }
+      }
+    } else {
+      for (uint32_t e = tid; e < total; e += blockDim.x) {
+        const int j = (int)(e >> t);
+        const uint32_t u = e & tmask;
+        dst[in.dst[j] + (int64_t)(contiguous ? u : deposit(u, a.active_mask))] = s[pad32(e)];
+      }
     }
     __syncthreads();
   }
@@ -404,7 +468,7 @@ cudaError_t launch_sweep(const SweepArgs &a, int precision, cudaStream_t st) {
     const int64_t ipc = 1ll << (T - a.t);
     const int64_t ctas = (items + ipc - 1) / ipc;
     const int grid = (int)(ctas < (1 << 20) ? ctas : (1 << 20));
-    const size_t smem = (size_t)((1u << T) + (1u << (T - 5))) * (precision == 0 ? 8 : 16);
+    const size_t smem = 2 * (size_t)((1u << T) + (1u << (T - 5))) * (precision == 0 ? 8 : 16);
     if (precision == 0) {
       auto k = sweep_reg_kernel<float, kRegBitsC64, kRegTileC64>;
       cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
