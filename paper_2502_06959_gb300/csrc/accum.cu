@@ -196,6 +196,74 @@ __global__ void __launch_bounds__(128) leaf_contract_kernel(LeafArgs a) {
   dst[1] = (double)acci;
 }
 
+// Leaf contraction, register variant (2^C <= 16 and r <= 8).  RM consecutive threads
+// serve one bitstring, one Schmidt digit m each: the thread keeps row x_a(s) of L^a_m and
+// row x_b(s) of L^b_m in registers for all parents of its group, reads the two chunks
+// (shared by the RM threads, so one coalesced request), and the RM per-digit sums are
+// added with shuffles at the end.
+template <typename R, int CB, int RM>
+__global__ void __launch_bounds__(128) leaf_contract_reg_kernel(LeafArgs a) {
+  using C = typename CT<R>::T;
+  constexpr int D = 1 << CB;
+  constexpr int SPB = 128 / RM;                // bitstrings per CTA
+  const int m = threadIdx.x % RM;
+  const int64_t s = (int64_t)blockIdx.x * SPB + threadIdx.x / RM;
+  const int g = blockIdx.y;
+  const bool on = s < a.S && m < a.r;
+  uint64_t ia = 0, ib = 0;
+  if (s < a.S) {
+    ia = a.ia[s];
+    ib = a.ib[s];
+  }
+  const int ra = (int)(ia & (D - 1)), rb = (int)(ib & (D - 1));
+  const uint64_t ba = ia - ra, bb = ib - rb;
+  C la[D], lb[D];
+  {
+    const C *gLa = reinterpret_cast<const C *>(a.La) + ((size_t)(on ? m : 0) * D + ra) * D;
+    const C *gLb = reinterpret_cast<const C *>(a.Lb) + ((size_t)(on ? m : 0) * D + rb) * D;
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      la[k] = gLa[k];
+      lb[k] = gLb[k];
+    }
+  }
+  const int64_t j0 = (int64_t)g * a.parents_per_group;
+  const int64_t j1 = min(a.num_parents, j0 + a.parents_per_group);
+  R accr = R(0), acci = R(0);
+  if (on) {
+    for (int64_t j = j0; j < j1; ++j) {
+      if ((j == 0 && m < a.m_first) || (j == a.num_parents - 1 && m >= a.m_last)) continue;
+      const C *pa = reinterpret_cast<const C *>(a.Pa) + ((uint64_t)j << a.ha) + ba;
+      const C *pb = reinterpret_cast<const C *>(a.Pb) + ((uint64_t)j << a.hb) + bb;
+      R var = R(0), vai = R(0), vbr = R(0), vbi = R(0);
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        const C x = pa[k];
+        var = fma(la[k].x, x.x, fma(-la[k].y, x.y, var));
+        vai = fma(la[k].x, x.y, fma(la[k].y, x.x, vai));
+      }
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        const C x = pb[k];
+        vbr = fma(lb[k].x, x.x, fma(-lb[k].y, x.y, vbr));
+        vbi = fma(lb[k].x, x.y, fma(lb[k].y, x.x, vbi));
+      }
+      accr = fma(var, vbr, fma(-vai, vbi, accr));
+      acci = fma(var, vbi, fma(vai, vbr, acci));
+    }
+  }
+#pragma unroll
+  for (int o = RM / 2; o > 0; o >>= 1) {
+    accr += __shfl_xor_sync(0xffffffffu, accr, o);
+    acci += __shfl_xor_sync(0xffffffffu, acci, o);
+  }
+  if (m == 0 && s < a.S) {
+    double *dst = a.partial + 2 * ((int64_t)g * a.S + s);
+    dst[0] = (double)accr;
+    dst[1] = (double)acci;
+  }
+}
+
 __global__ void index_prep_kernel(IndexArgs a) {
   const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= a.S) return;
@@ -257,9 +325,29 @@ cudaError_t launch_window(const WindowArgs &a, int precision, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+template <typename R, int CB>
+cudaError_t leaf_reg_dispatch(const LeafArgs &a, cudaStream_t st) {
+  const int rm = a.r <= 1 ? 1 : a.r <= 2 ? 2 : a.r <= 4 ? 4 : 8;
+  dim3 grid((unsigned)((a.S * rm + 127) / 128), (unsigned)a.num_groups);
+  switch (rm) {
+    case 1: leaf_contract_reg_kernel<R, CB, 1><<<grid, 128, 0, st>>>(a); break;
+    case 2: leaf_contract_reg_kernel<R, CB, 2><<<grid, 128, 0, st>>>(a); break;
+    case 4: leaf_contract_reg_kernel<R, CB, 4><<<grid, 128, 0, st>>>(a); break;
+    default: leaf_contract_reg_kernel<R, CB, 8><<<grid, 128, 0, st>>>(a); break;
+  }
+  return cudaGetLastError();
+}
+
 template <typename R>
 cudaError_t leaf_dispatch(const LeafArgs &a, cudaStream_t st) {
   using C = typename CT<R>::T;
+  switch (a.c) {
+    case 1: return leaf_reg_dispatch<R, 1>(a, st);
+    case 2: return leaf_reg_dispatch<R, 2>(a, st);
+    case 3: return leaf_reg_dispatch<R, 3>(a, st);
+    case 4: return leaf_reg_dispatch<R, 4>(a, st);
+    default: break;
+  }
   dim3 grid((unsigned)((a.S + 127) / 128), (unsigned)a.num_groups);
   const int D = 1 << a.c;
   const size_t smem = (size_t)2 * a.r * D * (D + 1) * sizeof(C);

@@ -329,6 +329,13 @@ hsf_status hsf_run(hsf_plan *p, const uint64_t *bits, size_t num, uint64_t windo
           a.groups = ps.groups.empty() ? nullptr : (const DevGroup *)((unsigned char *)p->dev_table + ps.groups_off);
           a.num_groups = (int32_t)ps.groups.size();
           a.rbits = p->rbits;
+          const size_t blk = ps.table_end - ps.ops_off;
+          if (!ps.groups.empty() && blk <= (size_t)kMaxStageBytes) {
+            a.stage_src = (unsigned char *)p->dev_table + ps.ops_off;
+            a.stage_bytes = (int32_t)((blk + 15) / 16 * 16);
+            a.stage_mats_off = (int32_t)(ps.mats_off - ps.ops_off);
+            a.stage_groups_off = (int32_t)(ps.groups_off - ps.ops_off);
+          }
           const double amps = (double)a.num_nodes * (double)(1ull << sd.h);
           double fl = 0.0;
           for (const OpH &op : ps.ops) fl += amps * (op.type == OP_DENSE ? 8.0 * (1 << op.nq) : 6.0);

@@ -63,8 +63,15 @@ struct SweepArgs {
   int32_t init_zero;     // 1: tile starts from |0...0>
   const DevGroup *groups;// register groups of the pass (register-resident kernel)
   int32_t num_groups;
-  int32_t rbits;         // register slots per thread (5 for complex64, 4 for complex128)
+  int32_t rbits;         // register slots per thread
+  // The pass's ops, matrices and groups lie in one contiguous table block; when
+  // stage_bytes > 0 the kernel copies it to shared memory first.
+  const void *stage_src;
+  int32_t stage_bytes;
+  int32_t stage_mats_off, stage_groups_off;   // byte offsets within the block
+  int32_t pad2;
 };
+constexpr int kMaxStageBytes = 48 * 1024;
 
 // Leaf level contracted at the requested amplitudes: for every parent node (level
 // B-1) and bitstring s, amp(s) += sum_m (L^a_m phi_a)(x_a) * (L^b_m phi_b)(x_b), where

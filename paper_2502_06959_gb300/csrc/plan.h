@@ -56,6 +56,7 @@ struct PassH {
   std::vector<GroupH> groups;   // register groups (register-resident kernel), may be empty
   // device
   size_t ops_off = 0, mats_off = 0, groups_off = 0;   // byte offsets in the device table
+  size_t table_end = 0;                                // end of this pass's block
   int num_ops = 0;
 };
 

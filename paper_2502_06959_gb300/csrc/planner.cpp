@@ -226,6 +226,59 @@ void merge_one_qubit_runs(std::vector<OpH> &ops) {
   ops.swap(out);
 }
 
+// Absorb every one-qubit op into the next two-qubit op on its qubit (nothing else
+// touches the qubit in between, so applying it right before that op is the same):
+// U followed by a CZ / RZZ / CX on (a, b) becomes one 4x4 op, which costs what the two
+// one-qubit ops cost and makes the diagonal gate free.
+void absorb_into_two_qubit(std::vector<OpH> &ops) {
+  std::vector<char> dead(ops.size(), 0);
+  std::map<int, int> pending;   // qubit -> index of its unabsorbed one-qubit op
+  for (size_t o = 0; o < ops.size(); ++o) {
+    OpH &op = ops[o];
+    if (op.nq == 1 && op.digits == 1) {
+      pending[op.q[0]] = (int)o;
+      continue;
+    }
+    if (op.nq == 2 && op.digits == 1) {
+      for (int x = 0; x < 2; ++x) {
+        auto it = pending.find(op.q[x]);
+        if (it == pending.end()) continue;
+        const OpH &u = ops[it->second];
+        std::vector<cd> um = u.m;
+        if (u.type == OP_DIAG) um = {u.m[0], 0.0, 0.0, u.m[1]};
+        // U on operand x (x = 0 is the matrix MSB) as a 4x4 acting before op
+        std::vector<cd> e(16, 0.0);
+        for (int i = 0; i < 4; ++i)
+          for (int j = 0; j < 4; ++j) {
+            const int ix = x == 0 ? i >> 1 : i & 1, jx = x == 0 ? j >> 1 : j & 1;
+            const int io = x == 0 ? i & 1 : i >> 1, jo = x == 0 ? j & 1 : j >> 1;
+            if (io == jo) e[i * 4 + j] = um[ix * 2 + jx];
+          }
+        std::vector<cd> full = op.m;
+        if (op.type == OP_DIAG) {
+          full.assign(16, 0.0);
+          for (int i = 0; i < 4; ++i) full[i * 5] = op.m[i];
+        }
+        std::vector<cd> prod = matmul(full, e, 4);
+        if (op.type == OP_DIAG && u.type == OP_DIAG) {
+          op.m = {prod[0], prod[5], prod[10], prod[15]};
+        } else {
+          op.type = OP_DENSE;
+          op.m = prod;
+        }
+        dead[it->second] = 1;
+        pending.erase(it);
+      }
+      continue;
+    }
+    for (int x = 0; x < op.nq; ++x) pending.erase(op.q[x]);
+  }
+  std::vector<OpH> out;
+  for (size_t o = 0; o < ops.size(); ++o)
+    if (!dead[o]) out.push_back(ops[o]);
+  ops.swap(out);
+}
+
 // Reorder the operands of an op (new operand x = old operand perm[x]) and permute
 // its matrices (every digit) to match: new index bit (nq-1-x) = old bit (nq-1-perm[x]).
 void permute_operands(OpH &op, const int *perm) {
@@ -435,6 +488,7 @@ void pack_pass(const PassH &ps, std::vector<DevOp> &dops, std::vector<C> &mats, 
       d.pos[x] = tile_bit[q] >= 0 ? tile_bit[q] : kFixedBit + q;
     }
     d.kcase = kcase;
+    if (sizeof(C) == 8 && (mats.size() & 1)) mats.push_back(C{});   // 16-byte aligned rows
     d.mat = (int32_t)mats.size();
     const int per = op.type == OP_DENSE ? (1 << (2 * op.nq)) : (1 << op.nq);
     d.digit_stride = op.digits > 1 ? per : 0;
@@ -530,7 +584,10 @@ hsf_status build_programs(hsf_plan &p) {
     for (auto &lv : sd.levels)
       for (auto &op : lv.ops)
         for (int j = 0; j < op.nq; ++j) op.q[j] = sd.store[op.q[j]];
-    for (auto &lv : sd.levels) merge_one_qubit_runs(lv.ops);
+    for (auto &lv : sd.levels) {
+      merge_one_qubit_runs(lv.ops);
+      if (!(p.flags & HSF_FLAG_NO_REGISTER_SWEEP)) absorb_into_two_qubit(lv.ops);
+    }
     if (leaf_c >= 0) {
       int c = 0;
       for (auto &op : sd.levels[B].ops)
@@ -591,6 +648,7 @@ hsf_status upload_programs(hsf_plan &p) {
           align(256); ps.mats_off = host.size(); append(mats.data(), mats.size() * sizeof(double2));
         }
         align(256); ps.groups_off = host.size(); append(dgroups.data(), dgroups.size() * sizeof(DevGroup));
+        ps.table_end = host.size();
         ++launches;
       }
     SideH &sd = p.side[s];

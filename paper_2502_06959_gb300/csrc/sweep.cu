@@ -166,9 +166,23 @@ __global__ void __launch_bounds__(256) sweep_kernel(SweepArgs a) {
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ uint32_t pad32(uint32_t u) { return u + (u >> 5); }
 
+// Two consecutive complex entries (16-byte aligned for complex64).
+template <typename C>
+__device__ __forceinline__ void ld2(const C *p, C &a, C &b) {
+  if constexpr (sizeof(C) == 8) {
+    const float4 q = *reinterpret_cast<const float4 *>(p);
+    a.x = q.x; a.y = q.y; b.x = q.z; b.y = q.w;
+  } else {
+    a = p[0];
+    b = p[1];
+  }
+}
+
 template <int J, int NR, typename C>
 __device__ __forceinline__ void ap1(C (&v)[NR], const C *__restrict__ m) {
-  const C m0 = m[0], m1 = m[1], m2 = m[2], m3 = m[3];
+  C m0, m1, m2, m3;
+  ld2(m, m0, m1);
+  ld2(m + 2, m2, m3);
 #pragma unroll
   for (int i = 0; i < NR; ++i) {
     if (i & (1 << J)) continue;
@@ -193,9 +207,13 @@ __device__ __forceinline__ void ap2(C (&v)[NR], const C *m0) {
     for (int c = 0; c < 4; ++c) x[c] = v[id[c]];
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
-      C acc = cmul(m[4 * r], x[0]);
-#pragma unroll
-      for (int c = 1; c < 4; ++c) acc = cfma(m[4 * r + c], x[c], acc);
+      C r0, r1, r2, r3;
+      ld2(m + 4 * r, r0, r1);
+      ld2(m + 4 * r + 2, r2, r3);
+      C acc = cmul(r0, x[0]);
+      acc = cfma(r1, x[1], acc);
+      acc = cfma(r2, x[2], acc);
+      acc = cfma(r3, x[3], acc);
       v[id[r]] = acc;
     }
   }
@@ -296,6 +314,18 @@ __global__ void __launch_bounds__(512, 1) sweep_reg_kernel(SweepArgs a) {
   const C *src = reinterpret_cast<const C *>(a.read_parent ? a.src : a.dst);
   C *dst = reinterpret_cast<C *>(a.dst);
   const int64_t stride = (int64_t)gridDim.x * ipc;
+  // op tables: staged in shared memory after the two tile buffers when they fit
+  const DevOp *ops = a.ops;
+  const DevGroup *groups = a.groups;
+  if (a.stage_bytes > 0) {
+    unsigned char *st = reinterpret_cast<unsigned char *>(sbuf + 2 * BUF);
+    const int4 *gs = reinterpret_cast<const int4 *>(a.stage_src);
+    for (int e = tid; e < a.stage_bytes / 16; e += blockDim.x) reinterpret_cast<int4 *>(st)[e] = gs[e];
+    ops = reinterpret_cast<const DevOp *>(st);
+    mats = reinterpret_cast<const C *>(st + a.stage_mats_off);
+    groups = reinterpret_cast<const DevGroup *>(st + a.stage_groups_off);
+    __syncthreads();
+  }
 
   // Start the copies of the batch beginning at item0 into buffer `slot`.
   auto prefetch = [&](int64_t item0, int slot) {
@@ -352,7 +382,7 @@ __global__ void __launch_bounds__(512, 1) sweep_reg_kernel(SweepArgs a) {
     const uint64_t my_base = valid ? in.base[il] : 0ull;
 
     for (int g = 0; g < a.num_groups; ++g) {
-      const DevGroup G = a.groups[g];
+      const DevGroup G = groups[g];
       uint32_t smask = 0;
       uint32_t w[RB];
 #pragma unroll
@@ -371,7 +401,7 @@ __global__ void __launch_bounds__(512, 1) sweep_reg_kernel(SweepArgs a) {
         v[i] = s[pad32(u)];
       }
       for (int o = G.first_op; o < G.first_op + G.num_ops; ++o) {
-        const DevOp op = a.ops[o];
+        const DevOp op = ops[o];
         const C *m = mats + op.mat + (op.digit_stride > 0 ? digit * op.digit_stride : 0);
         if (op.type == OP_DIAG) {
           // operands are ordered slot operands first (kcase = their count); the
@@ -468,7 +498,8 @@ cudaError_t launch_sweep(const SweepArgs &a, int precision, cudaStream_t st) {
     const int64_t ipc = 1ll << (T - a.t);
     const int64_t ctas = (items + ipc - 1) / ipc;
     const int grid = (int)(ctas < (1 << 20) ? ctas : (1 << 20));
-    const size_t smem = 2 * (size_t)((1u << T) + (1u << (T - 5))) * (precision == 0 ? 8 : 16);
+    const size_t smem = 2 * (size_t)((1u << T) + (1u << (T - 5))) * (precision == 0 ? 8 : 16) +
+                        (size_t)a.stage_bytes;
     if (precision == 0) {
       auto k = sweep_reg_kernel<float, kRegBitsC64, kRegTileC64>;
       cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
