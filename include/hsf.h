@@ -175,6 +175,22 @@ hsf_status hsf_run(hsf_plan *plan, const uint64_t *bitstrings, size_t num,
                    uint64_t window, uint64_t path_begin, uint64_t path_end,
                    void *out, void *workspace, size_t workspace_bytes, void *stream);
 
+/* Same as hsf_run, but for callers that cannot allocate device memory (for example
+ * code that runs while another runtime owns all device allocations, or a loop that
+ * must not block on an allocator).  There is no workspace argument: the library uses a
+ * 32 MiB scratch array compiled into it (kept by every GPU that loads the library
+ * until the process exits) and allocates nothing.  The paper has no counterpart; this
+ * is a deployment convenience.
+ * Requests whose smallest path chunk needs more than 32 MiB fail with HSF_ENOMEM and
+ * a message naming the limit.  All calls share the array and its contents persist
+ * between calls (each run zeroes what it accumulates into); calls that overlap on the
+ * GPU race on it, so order them.  The first call on each device looks the array's
+ * address up (with that device current); make that first call before any stream
+ * capture. */
+hsf_status hsf_run_static(hsf_plan *plan, const uint64_t *bitstrings, size_t num,
+                          uint64_t window, uint64_t path_begin, uint64_t path_end,
+                          void *out, void *stream);
+
 const char *hsf_last_error(void);
 
 /* Per-kernel timing for roofline reporting.  With profiling on, every kernel that

@@ -84,6 +84,8 @@ SIGNATURES = {
     "hsf_run": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_uint64,
                                ctypes.c_uint64, ctypes.c_uint64, ctypes.c_void_p, ctypes.c_void_p,
                                ctypes.c_size_t, ctypes.c_void_p]),
+    "hsf_run_static": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_uint64,
+                                      ctypes.c_uint64, ctypes.c_uint64, ctypes.c_void_p, ctypes.c_void_p]),
     "hsf_last_error": (ctypes.c_char_p, []),
     "hsf_set_profiling": (None, [ctypes.c_int32]),
     "hsf_profile_collect": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32]),
@@ -217,6 +219,14 @@ def hsf_profile_collect(plan: int) -> dict:
 
 def hsf_launch_count() -> int:
     return int(load_library().hsf_launch_count())
+
+
+def hsf_run_static(plan: int, bitstrings_ptr: int, num: int, window: int, path_begin: int,
+                   path_end: int, out_ptr: int, stream: int = 0) -> None:
+    """hsf_run without a workspace argument: for callers that cannot allocate device
+    memory (the library's fixed 32 MiB scratch array is used instead)."""
+    _check(load_library().hsf_run_static(plan, bitstrings_ptr or None, num, window, path_begin,
+                                         path_end, out_ptr, stream or None))
 
 
 def hsf_version() -> str:
