@@ -191,6 +191,11 @@ hsf_status hsf_run_static(hsf_plan *plan, const uint64_t *bitstrings, size_t num
                           uint64_t window, uint64_t path_begin, uint64_t path_end,
                           void *out, void *stream);
 
+/* Wait for the stream and report device-side failures of earlier runs of this plan:
+ * returns HSF_ETIMEOUT (and clears the flag) if a bounded wait inside a kernel expired,
+ * in which case the affected outputs are invalid. */
+hsf_status hsf_sync(hsf_plan *plan, void *stream);
+
 const char *hsf_last_error(void);
 
 /* Per-kernel timing for roofline reporting.  With profiling on, every kernel that

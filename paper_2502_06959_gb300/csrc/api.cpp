@@ -38,8 +38,9 @@ std::atomic<int> g_profiling{0};
 struct RunLayout {
   uint64_t chunk = 0;          // leaves per chunk (a subtree size)
   bool leaf = false;           // leaf level contracted at the bitstrings
+  bool tc = false;             // window output on the tensor cores
   size_t off_buf[2][2] = {{0, 0}, {0, 0}};
-  size_t off_partial = 0, off_comp = 0, off_index = 0, total = 0;
+  size_t off_partial = 0, off_comp = 0, off_index = 0, off_gemm = 0, total = 0;
   int32_t ppg = 64, groups = 0;
 };
 
@@ -86,6 +87,11 @@ RunLayout layout_for(const hsf_plan &p, size_t num_bits, uint64_t window, uint64
     off += align256((M + N) * 8);
     L.off_comp = off;
     off += align256(count * 16);
+    if (p.gemm_mode != HSF_GEMM_FP32) {
+      L.tc = true;
+      L.off_gemm = off;
+      off += align256(path_gemm_operand_bytes(p.gemm_mode, (int64_t)M, (int64_t)N, (int64_t)chunk));
+    }
   }
   L.total = off;
   return L;
@@ -194,6 +200,8 @@ hsf_status hsf_plan_create(const hsf_circuit *circuit, int32_t cut_l, const hsf_
   if (st != HSF_OK) return st;
   st = upload_programs(*p);
   if (st != HSF_OK) return st;
+  CUDA_TRY(cudaMalloc(&p->dev_status, 256));
+  CUDA_TRY(cudaMemset(p->dev_status, 0, 256));
   *out = p.release();
   return HSF_OK;
 }
@@ -226,8 +234,22 @@ hsf_status hsf_plan_get_sigma(const hsf_plan *p, int32_t block, double *sigma, i
   return HSF_OK;
 }
 
+hsf_status hsf_sync(hsf_plan *p, void *stream) {
+  if (!p) return set_error(HSF_EINVAL, "NULL plan");
+  CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
+  int32_t status = 0;
+  CUDA_TRY(cudaMemcpy(&status, p->dev_status, sizeof status, cudaMemcpyDeviceToHost));
+  if (status != 0) {
+    CUDA_TRY(cudaMemset(p->dev_status, 0, sizeof status));
+    return set_error(HSF_ETIMEOUT, "a bounded device-side wait expired (code %d); results of the "
+                                   "affected run are invalid", status);
+  }
+  return HSF_OK;
+}
+
 void hsf_plan_destroy(hsf_plan *p) {
   if (!p) return;
+  if (p->dev_status) cudaFree(p->dev_status);
   for (auto &r : p->prof) { cudaEventDestroy(r.e0); cudaEventDestroy(r.e1); }
   if (p->dev_table) cudaFree(p->dev_table);
   delete p;
@@ -406,8 +428,30 @@ hsf_status hsf_run(hsf_plan *p, const uint64_t *bits, size_t num, uint64_t windo
       w.comp = comp;
       w.row_index = ia;
       w.col_index = ib;
-      LAUNCH(HSF_KERNEL_WINDOW, (double)np * (w.M + w.N) * csz + 64.0 * w.M * w.N,
-             8.0 * (double)np * w.M * w.N, launch_window(w, p->precision, st));
+      if (L.tc) {
+        PathGemmArgs g{};
+        g.A = last[0];
+        g.B = last[1];
+        g.paths = np;
+        g.ha = p->na;
+        g.hb = p->nb;
+        g.row_index = ia;
+        g.col_index = ib;
+        g.M = M;
+        g.N = N;
+        g.window = count;
+        g.out = outd;
+        g.comp = comp;
+        g.scratch = ws + L.off_gemm;
+        g.mode = p->gemm_mode;
+        g.err = p->dev_status;
+        const double terms = p->gemm_mode == HSF_GEMM_TF32 ? 1.0 : 3.0;
+        LAUNCH(HSF_KERNEL_WINDOW, (double)np * (w.M + w.N) * csz + 64.0 * w.M * w.N,
+               8.0 * terms * (double)np * w.M * w.N, launch_path_gemm(g, st));
+      } else {
+        LAUNCH(HSF_KERNEL_WINDOW, (double)np * (w.M + w.N) * csz + 64.0 * w.M * w.N,
+               8.0 * (double)np * w.M * w.N, launch_window(w, p->precision, st));
+      }
     }
   }
   LAUNCH(HSF_KERNEL_OTHER, 48.0 * count, 0.0, launch_finalize(outd, comp, (int64_t)(2 * count), st));

@@ -144,6 +144,23 @@ struct BlockSvdArgs {
   int32_t *sweeps_used;          // [num_blocks]
 };
 
+// Window / full output on the tensor cores (gemm_tc.cu): complex rank-P product as one
+// real GEMM with split-BF16 (mode 1), split-TF32 (mode 2) or TF32 (mode 3) operands.
+struct PathGemmArgs {
+  const void *A, *B;               // complex64 leaf states [paths][2^ha] / [paths][2^hb]
+  int64_t paths;
+  int32_t ha, hb;
+  const uint64_t *row_index, *col_index;   // storage indices of x_a < M and x_b < N
+  int64_t M, N;
+  uint64_t window;
+  double *out, *comp;              // FP64 output and Neumaier compensation
+  void *scratch;                   // path_gemm_operand_bytes(...) bytes, 256-B aligned
+  int32_t mode;
+  int32_t *err;                    // device status word (bounded waits)
+};
+size_t path_gemm_operand_bytes(int mode, int64_t M, int64_t N, int64_t paths);
+cudaError_t launch_path_gemm(const PathGemmArgs &g, cudaStream_t st);
+
 cudaError_t launch_sweep(const SweepArgs &a, int precision, cudaStream_t st);
 cudaError_t launch_gather_dot(const GatherArgs &a, int precision, cudaStream_t st);
 cudaError_t launch_reduce_partials(const double *partial, int32_t num_groups, int64_t S,

@@ -1,0 +1,412 @@
+// Path GEMM on the 5th-generation tensor cores (tcgen05) for full / window output.
+//
+// The path sum of Sec. II-B over the requested amplitude rectangle,
+//   Out[x_a, x_b] = sum_p psi_a^p(x_a) psi_b^p(x_b),
+// is a complex rank-P product.  It is written as one real GEMM C = A'' B''^T:
+//   rows [0, Mp) of A'' give Re(Out), rows [Mp, 2Mp) give Im(Out);
+//   K' = 2P columns hold (Re, -Im | Im, Re) of psi_a against (Re | Im) of psi_b;
+//   the K' columns are repeated per split term: with x = hi + lo (hi = round(x), lo =
+//   round(x - hi)) the product is hi*hi + hi*lo + lo*hi (split-BF16 or split-TF32,
+//   3 terms) or a single TF32 term.
+// pack_kernel gathers the leaf states at the window's storage indices and writes these
+// operands (zero padded to the tile sizes).  gemm_kernel runs 128 x 128 output tiles:
+// one thread issues TMA tile loads (128-byte swizzle) into a 4-stage shared-memory
+// ring, one thread issues tcgen05.mma into a TMEM accumulator (FP32), and all four
+// warps read the accumulator back with tcgen05.ld and add it into the FP64 output with
+// Neumaier compensation.  Every wait on an mbarrier is bounded: on expiry the kernel
+// records an error code, frees its TMEM and returns.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cudaTypedefs.h>
+
+#include <cstdint>
+#include <mutex>
+
+#include "common.h"
+
+namespace hsf {
+namespace {
+
+constexpr int kBM = 128, kBN = 128, kStages = 4;
+constexpr int kTileBytes = 128 * 128;               // 128 rows x 128 bytes of K
+constexpr uint32_t kWaitLimit = 1u << 22;           // bounded mbarrier polls (about a second)
+
+// ---------------------------------------------------------------------------
+// operand packing
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float tf32_round(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
+template <int MODE>   // 1 = split bf16, 2 = split tf32, 3 = tf32
+__device__ __forceinline__ void split(float x, float &hi, float &lo) {
+  if (MODE == 1) {
+    hi = __bfloat162float(__float2bfloat16_rn(x));
+    lo = x - hi;
+  } else {
+    hi = tf32_round(x);
+    lo = tf32_round(x - hi);
+  }
+}
+
+struct PackArgs {
+  const float2 *src;            // leaf states [paths][2^h]
+  int32_t h;
+  int64_t paths;
+  const uint64_t *index;        // storage index of each output row / column
+  int64_t rows;                 // M (a side) or N (b side)
+  int64_t rows_pad;             // padded row count of one part
+  int32_t side;                 // 0: a operand (2 x rows_pad rows), 1: b operand
+  int64_t kpad;                 // padded K'' (row length of the operand)
+  void *dst;                    // bf16 or fp32 operand, row-major [rows][kpad]
+  int32_t mode;
+};
+
+// One thread per (operand row r, path p): writes all split terms of K' = 2P columns
+// that path p contributes to row r.
+template <int MODE>
+__global__ void pack_kernel(PackArgs a) {
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t r = blockIdx.y + (int64_t)gridDim.y * blockIdx.z;
+  const int64_t nrows = a.side == 0 ? 2 * a.rows_pad : a.rows_pad;
+  if (p >= a.paths || r >= nrows) return;
+  const int64_t part = a.side == 0 ? r / a.rows_pad : 0;    // 0: real rows, 1: imaginary rows
+  const int64_t i = a.side == 0 ? r % a.rows_pad : r;
+  float2 v = make_float2(0.f, 0.f);
+  if (i < a.rows) v = a.src[((uint64_t)p << a.h) + a.index[i]];
+  // the two K' entries of this path: columns p and P + p
+  float x0, x1;
+  if (a.side == 0) {
+    x0 = part == 0 ? v.x : v.y;       // Re row: ( Re a, -Im a );  Im row: ( Im a, Re a )
+    x1 = part == 0 ? -v.y : v.x;
+  } else {
+    x0 = v.x;                         // b column: ( Re b, Im b )
+    x1 = v.y;
+  }
+  const int64_t P = a.paths;
+  const int64_t kp = 2 * P;
+  float h0, l0, h1, l1;
+  split<MODE == 3 ? 2 : MODE>(x0, h0, l0);
+  split<MODE == 3 ? 2 : MODE>(x1, h1, l1);
+  // term order: a = [hi, hi, lo], b = [hi, lo, hi]  (hi*hi + hi*lo + lo*hi)
+  float t0[3], t1[3];
+  if (MODE == 3) {
+    t0[0] = h0; t1[0] = h1;
+  } else if (a.side == 0) {
+    t0[0] = h0; t0[1] = h0; t0[2] = l0;
+    t1[0] = h1; t1[1] = h1; t1[2] = l1;
+  } else {
+    t0[0] = h0; t0[1] = l0; t0[2] = h0;
+    t1[0] = h1; t1[1] = l1; t1[2] = h1;
+  }
+  const int nterms = MODE == 3 ? 1 : 3;
+  for (int t = 0; t < nterms; ++t) {
+    const int64_t c0 = t * kp + p, c1 = t * kp + P + p;
+    if (MODE == 1) {
+      __nv_bfloat16 *d = reinterpret_cast<__nv_bfloat16 *>(a.dst) + r * a.kpad;
+      d[c0] = __float2bfloat16_rn(t0[t]);
+      d[c1] = __float2bfloat16_rn(t1[t]);
+    } else {
+      float *d = reinterpret_cast<float *>(a.dst) + r * a.kpad;
+      d[c0] = t0[t];
+      d[c1] = t1[t];
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// tcgen05 GEMM
+// ---------------------------------------------------------------------------
+struct EpiArgs {
+  double *out, *comp;
+  int64_t M, N;          // complex rows (x_a) and columns (x_b)
+  int64_t Mp;            // padded complex rows (multiple of 128)
+  int32_t hb;            // out index = x_a * 2^hb + x_b
+  uint64_t window;
+  int32_t k_tiles;
+  int32_t kind;          // 0: kind::f16 (bf16 operands), 1: kind::tf32
+  int32_t *err;          // device error word (0 = ok)
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+// Bounded wait for the phase with the given parity to complete; false on expiry.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+  const uint32_t a = smem_u32(bar);
+  for (uint32_t it = 0; it < kWaitLimit; ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int x, int y, uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+      ::"r"(smem_u32(dst)), "l"((uint64_t)map), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major tile, 128-byte swizzle, 8-row atoms 1024 B apart.
+__device__ __forceinline__ uint64_t make_desc(const void *tile) {
+  const uint64_t addr = smem_u32(tile);
+  uint64_t d = 0;
+  d |= (addr & 0x3FFFFull) >> 4;               // start address
+  d |= (uint64_t)1 << 16;                       // leading byte offset (unused with swizzle)
+  d |= (uint64_t)(1024 >> 4) << 32;             // stride byte offset: 8 rows x 128 B
+  d |= (uint64_t)1 << 46;                       // descriptor version
+  d |= (uint64_t)2 << 61;                       // 128-byte swizzle
+  return d;
+}
+
+__device__ __forceinline__ void neumaier(double &sum, double &c, double x) {
+  const double t = sum + x;
+  if (fabs(sum) >= fabs(x))
+    c += (sum - t) + x;
+  else
+    c += (x - t) + sum;
+  sum = t;
+}
+
+__global__ void __launch_bounds__(128, 1) gemm_kernel(const __grid_constant__ CUtensorMap tmA,
+                                                      const __grid_constant__ CUtensorMap tmB, EpiArgs ep) {
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+  uint8_t *sA = smem;
+  uint8_t *sB = smem + kStages * kTileBytes;
+  __shared__ __align__(8) uint64_t full_bar[kStages], empty_bar[kStages], done_bar;
+  __shared__ uint32_t tmem_base_sh;
+  __shared__ int abort_sh;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int n0 = blockIdx.x * kBN, m0 = blockIdx.y * kBM;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init(&full_bar[s], 1);
+      mbar_init(&empty_bar[s], 1);
+    }
+    mbar_init(&done_bar, 1);
+    abort_sh = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 2) {   // the whole warp allocates the accumulator columns
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base_sh)),
+                 "r"(kBN)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_base_sh;
+
+  // instruction descriptor: FP32 accumulate, K-major A and B, M = 128, N = 128
+  const uint32_t fmt = ep.kind == 0 ? 1u : 2u;      // BF16 (kind::f16) or TF32
+  const uint32_t idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(kBN >> 3) << 17) |
+                         ((uint32_t)(kBM >> 4) << 24);
+  const int ksteps = 4;                              // 4 MMAs of 32 bytes of K per tile
+  const int ktiles = ep.k_tiles;
+
+  if (warp == 0 && lane == 0) {
+    // TMA producer
+    for (int kt = 0; kt < ktiles; ++kt) {
+      const int s = kt % kStages;
+      const uint32_t ph = (kt / kStages) & 1;
+      if (!mbar_wait(&empty_bar[s], ph ^ 1)) { atomicExch(ep.err, 1); abort_sh = 1; break; }
+      mbar_expect_tx(&full_bar[s], 2 * kTileBytes);
+      const int kx = kt * (ep.kind == 0 ? 64 : 32);  // K elements per 128-byte row
+      tma_load_2d(sA + s * kTileBytes, &tmA, kx, m0 + (m0 >= 0 ? 0 : 0), &full_bar[s]);
+      tma_load_2d(sB + s * kTileBytes, &tmB, kx, n0, &full_bar[s]);
+    }
+  } else if (warp == 1 && lane == 0) {
+    // MMA issuer
+    bool ok = true;
+    for (int kt = 0; kt < ktiles && ok; ++kt) {
+      const int s = kt % kStages;
+      const uint32_t ph = (kt / kStages) & 1;
+      if (!mbar_wait(&full_bar[s], ph)) { atomicExch(ep.err, 2); abort_sh = 1; ok = false; break; }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint64_t da = make_desc(sA + s * kTileBytes), db = make_desc(sB + s * kTileBytes);
+      for (int k = 0; k < ksteps; ++k) {
+        const uint64_t adv = (uint64_t)((k * 32) >> 4);
+        const uint32_t acc = (kt > 0 || k > 0) ? 1u : 0u;
+        if (ep.kind == 0) {
+          asm volatile(
+              "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
+              " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+              ::"r"(tmem), "l"(da + adv), "l"(db + adv), "r"(idesc), "r"(acc)
+              : "memory");
+        } else {
+          asm volatile(
+              "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
+              " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n"
+              ::"r"(tmem), "l"(da + adv), "l"(db + adv), "r"(idesc), "r"(acc)
+              : "memory");
+        }
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                       smem_u32(&empty_bar[s]))
+                   : "memory");
+    }
+    // the accumulator is complete when every MMA issued above has finished
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                     smem_u32(&done_bar))
+                 : "memory");
+  }
+  __syncwarp();
+
+  // epilogue: every warp reads its 32 TMEM lanes (rows m0 + 32w .. +31)
+  const bool done = mbar_wait(&done_bar, 0);
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (!done) {
+    if (lane == 0) atomicExch(ep.err, 3);
+  } else {
+    const int64_t r = m0 + warp * 32 + lane;            // row of the real GEMM
+    const int part = r >= ep.Mp ? 1 : 0;                // 0: Re(Out), 1: Im(Out)
+    const int64_t i = part ? r - ep.Mp : r;
+    for (int c0 = 0; c0 < kBN; c0 += 32) {
+      uint32_t v[32];
+      const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+          "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+          : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+            "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
+            "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
+            "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+          : "r"(taddr));
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      if (i < ep.M) {
+        for (int c = 0; c < 32; ++c) {
+          const int64_t j = n0 + c0 + c;
+          if (j >= ep.N) break;
+          const uint64_t idx = ((uint64_t)i << ep.hb) + (uint64_t)j;
+          if (idx >= ep.window) break;
+          double *o = ep.out + 2 * idx + part;
+          double *cp = ep.comp + 2 * idx + part;
+          double sum = *o, cc = *cp;
+          neumaier(sum, cc, (double)__uint_as_float(v[c]));
+          *o = sum;
+          *cp = cc;
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 2) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kBN) : "memory");
+  }
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, []() {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &p, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  });
+  return fn;
+}
+
+bool make_map(CUtensorMap *m, void *base, bool bf16, uint64_t kpad, uint64_t rows) {
+  auto enc = get_encode();
+  if (!enc) return false;
+  const cuuint64_t dims[2] = {(cuuint64_t)kpad, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)(kpad * (bf16 ? 2 : 4))};
+  const cuuint32_t box[2] = {(cuuint32_t)(bf16 ? 64 : 32), 128};
+  const cuuint32_t estr[2] = {1, 1};
+  const CUresult r = enc(m, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base, dims,
+                         strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                         CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+}  // namespace
+
+size_t path_gemm_operand_bytes(int mode, int64_t M, int64_t N, int64_t paths) {
+  const int64_t Mp = (M + kBM - 1) / kBM * kBM, Np = (N + kBN - 1) / kBN * kBN;
+  const int nterms = mode == 3 ? 1 : 3;
+  const int kalign = mode == 1 ? 64 : 32;
+  const int64_t kpad = (nterms * 2 * paths + kalign - 1) / kalign * kalign;
+  const int esz = mode == 1 ? 2 : 4;
+  return (size_t)(2 * Mp + Np) * (size_t)kpad * esz + 256;
+}
+
+cudaError_t launch_path_gemm(const PathGemmArgs &g, cudaStream_t st) {
+  const int64_t Mp = (g.M + kBM - 1) / kBM * kBM, Np = (g.N + kBN - 1) / kBN * kBN;
+  const int nterms = g.mode == 3 ? 1 : 3;
+  const bool bf16 = g.mode == 1;
+  const int kalign = bf16 ? 64 : 32;
+  const int64_t kpad = (nterms * 2 * g.paths + kalign - 1) / kalign * kalign;
+  const int esz = bf16 ? 2 : 4;
+  uint8_t *opA = reinterpret_cast<uint8_t *>(g.scratch);
+  uint8_t *opB = opA + (size_t)2 * Mp * kpad * esz;
+  // zero the padded operands (padding columns and rows must contribute nothing)
+  cudaError_t e = cudaMemsetAsync(opA, 0, (size_t)(2 * Mp + Np) * kpad * esz, st);
+  if (e != cudaSuccess) return e;
+  for (int side = 0; side < 2; ++side) {
+    PackArgs pa{};
+    pa.src = reinterpret_cast<const float2 *>(side == 0 ? g.A : g.B);
+    pa.h = side == 0 ? g.ha : g.hb;
+    pa.paths = g.paths;
+    pa.index = side == 0 ? g.row_index : g.col_index;
+    pa.rows = side == 0 ? g.M : g.N;
+    pa.rows_pad = side == 0 ? Mp : Np;
+    pa.side = side;
+    pa.kpad = kpad;
+    pa.dst = side == 0 ? (void *)opA : (void *)opB;
+    pa.mode = g.mode;
+    const int64_t nrows = side == 0 ? 2 * Mp : Np;
+    const unsigned gy = (unsigned)(nrows < 65535 ? nrows : 65535);
+    const unsigned gz = (unsigned)((nrows + gy - 1) / gy);
+    dim3 grid((unsigned)((g.paths + 127) / 128), gy, gz);
+    if (g.mode == 1) pack_kernel<1><<<grid, 128, 0, st>>>(pa);
+    else if (g.mode == 2) pack_kernel<2><<<grid, 128, 0, st>>>(pa);
+    else pack_kernel<3><<<grid, 128, 0, st>>>(pa);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  CUtensorMap tmA, tmB;
+  if (!make_map(&tmA, opA, bf16, (uint64_t)kpad, (uint64_t)(2 * Mp)) ||
+      !make_map(&tmB, opB, bf16, (uint64_t)kpad, (uint64_t)Np))
+    return cudaErrorInvalidValue;
+  EpiArgs ep{};
+  ep.out = g.out;
+  ep.comp = g.comp;
+  ep.M = g.M;
+  ep.N = g.N;
+  ep.Mp = Mp;
+  ep.hb = g.hb;
+  ep.window = g.window;
+  ep.k_tiles = (int32_t)(kpad / kalign);
+  ep.kind = bf16 ? 0 : 1;
+  ep.err = g.err;
+  const size_t smem = (size_t)2 * kStages * kTileBytes + 1024;
+  e = cudaFuncSetAttribute(gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  dim3 grid((unsigned)(Np / kBN), (unsigned)(2 * Mp / kBM));
+  gemm_kernel<<<grid, 128, smem, st>>>(tmA, tmB, ep);
+  return cudaGetLastError();
+}
+
+}  // namespace hsf

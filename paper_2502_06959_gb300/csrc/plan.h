@@ -103,6 +103,7 @@ struct hsf_plan {
   uint64_t num_paths = 1;
   hsf::SideH side[2];               // 0 = a, 1 = b
   void *dev_table = nullptr;        // ops + matrices of every pass
+  int32_t *dev_status = nullptr;    // set by kernels whose bounded waits expired
   size_t dev_table_bytes = 0;
   int64_t tree_nodes = 0;
   int64_t launches = 0;

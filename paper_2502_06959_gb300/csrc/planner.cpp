@@ -789,6 +789,8 @@ hsf_status validate_and_load(hsf_plan &p, const hsf_circuit *c, int cut, const h
   if (p.precision != HSF_PREC_C64 && p.precision != HSF_PREC_C128)
     return set_error(HSF_EINVAL, "precision %d", p.precision);
   if (p.gemm_mode < 0 || p.gemm_mode > 3) return set_error(HSF_EINVAL, "gemm_mode %d", p.gemm_mode);
+  if (p.gemm_mode != HSF_GEMM_FP32 && p.precision != HSF_PREC_C64)
+    return set_error(HSF_EINVAL, "tensor-core path GEMM modes take complex64 half states");
   // a shared-memory tile holds at most 2^13 (complex64) or 2^12 (complex128) amplitudes
   const int tcap = p.precision == HSF_PREC_C64 ? kRegTileC64 : kRegTileC128;
   p.tile_max = (o && o->tile_bits) ? o->tile_bits : tcap;

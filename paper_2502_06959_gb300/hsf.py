@@ -86,6 +86,7 @@ SIGNATURES = {
                                ctypes.c_size_t, ctypes.c_void_p]),
     "hsf_run_static": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_uint64,
                                       ctypes.c_uint64, ctypes.c_uint64, ctypes.c_void_p, ctypes.c_void_p]),
+    "hsf_sync": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "hsf_last_error": (ctypes.c_char_p, []),
     "hsf_set_profiling": (None, [ctypes.c_int32]),
     "hsf_profile_collect": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32]),
@@ -229,6 +230,10 @@ def hsf_run_static(plan: int, bitstrings_ptr: int, num: int, window: int, path_b
                                          path_end, out_ptr, stream or None))
 
 
+def hsf_sync(plan: int, stream: int = 0) -> None:
+    _check(load_library().hsf_sync(plan, stream or None))
+
+
 def hsf_version() -> str:
     return load_library().hsf_version().decode()
 
@@ -264,7 +269,7 @@ class Plan:
         return self._ws
 
     def run(self, bitstrings=None, window: int = 0, path_range=(0, 0), out=None, stream=None,
-            budget: int = 0):
+            budget: int = 0, check: bool = False):
         import torch
         num = 0 if bitstrings is None else int(bitstrings.numel())
         if bitstrings is not None and num == 0:
@@ -277,6 +282,8 @@ class Plan:
         hsf_run(self.handle, bitstrings.data_ptr() if num else 0, num, window,
                 int(path_range[0]), int(path_range[1]), out.data_ptr(), ws.data_ptr(), ws.numel(),
                 st.cuda_stream)
+        if check:
+            hsf_sync(self.handle, st.cuda_stream)
         return out
 
     def close(self):

@@ -282,3 +282,40 @@ def test_c2_plan_uses_leaf_contraction_and_register_kernel():
     assert plan.info["leaf_bits"] == 4
     assert plan.info["tree_nodes"] == sum(4 ** k for k in range(9))
     plan.close()
+
+
+@pytest.mark.parametrize("gemm,tol_rel", [("fp32", 1e-4), ("bf16x3", 1e-4), ("tf32x3", 1e-4), ("tf32", 5e-3)])
+def test_tensor_core_path_gemm_window(gemm, tol_rel):
+    """Full / window output through the tensor-core path GEMM (tcgen05): several M, N
+    and K tiles, ragged edges, against the oracle.  Plain TF32 keeps ~10 mantissa bits,
+    so it is checked at a looser relative bound (it is reported, not a parity form)."""
+    import torch
+    from paper_2502_06959_gb300 import hsf
+    pr = W.random_brickwork(20, 9, 6, block_after=(1, 2, 3, 4, 5), block_kind="mixed", block_len=3, seed=21)
+    ref = O.schrodinger(pr.n, pr.gates)
+    for window in (1 << 20, 300000, 1000):
+        plan = hsf.Plan.from_problem(pr, precision="c64", gemm=gemm)
+        out = plan.run(window=window, check=True)
+        torch.cuda.synchronize()
+        got = out.cpu().numpy()
+        info = plan.info
+        plan.close()
+        want = ref[:window]
+        err = float(np.max(np.abs(got - want)))
+        scale = float(np.max(np.abs(want)))
+        assert info["num_paths"] > 128
+        assert err <= tol_rel * scale, (gemm, window, err, scale)
+        if gemm != "tf32":
+            assert err <= 1e-5
+
+
+def test_tensor_core_gemm_c1_full():
+    import torch
+    from paper_2502_06959_gb300 import hsf
+    pr = W.workload_c1()
+    ref = O.schrodinger(pr.n, pr.gates)
+    for gemm in ("bf16x3", "tf32x3"):
+        plan = hsf.Plan.from_problem(pr, precision="c64", gemm=gemm)
+        out = plan.run(check=True).cpu().numpy()
+        plan.close()
+        check(out, ref, "c64")
