@@ -134,7 +134,7 @@ typedef struct hsf_plan_info {
   int64_t num_launches;     /* sweep launches per side for one full run             */
   int32_t leaf_bits;        /* > 0: bitstring runs contract the leaf level directly,
                                its program spans this many low storage bits          */
-  int32_t reserved;
+  int32_t num_params;       /* 1 + the largest param_id of a rotation gate          */
 } hsf_plan_info;
 
 /* Plan a circuit: validates the circuit, cut and blocks, multiplies every block and
@@ -190,6 +190,25 @@ hsf_status hsf_run(hsf_plan *plan, const uint64_t *bitstrings, size_t num,
 hsf_status hsf_run_static(hsf_plan *plan, const uint64_t *bitstrings, size_t num,
                           uint64_t window, uint64_t path_begin, uint64_t path_end,
                           void *out, void *stream);
+
+/* Adjoint gradient of a real loss L of the amplitudes at `bitstrings` with respect
+ * to the shared angles (gate param_id): grad[j] = dL/dtheta_j, j < num_params.
+ *   gout: device complex128 per bitstring, the upstream gradient
+ *         g_s = dL/dRe(amp_s) + i dL/dIm(amp_s) (PyTorch's convention; for
+ *         L = sum_s |amp_s|^2 it is 2 amp_s).
+ *   grad: device double[num_params]; num_params must cover every param_id.
+ * Rotations inside one half are differentiated by walking the path tree backwards
+ * (uncomputing unitary gates, never the Schmidt factors, which are taken from the
+ * forward's stored node states); rotations inside a cut block by the HSF sum with
+ * the block replaced by its derivative, Schmidt-decomposed on the device (the
+ * amplitude is linear in the block matrix, Sec. IV-A).  Supported rotation kinds:
+ * RX, RY, RZ, RZZ.  The whole path tree is kept: the workspace must hold every
+ * node state twice (hsf_grad_workspace_size).  The first call builds the gradient
+ * programs and derivative plans (synchronous). */
+hsf_status hsf_grad_workspace_size(hsf_plan *plan, size_t num_bitstrings, size_t *bytes);
+hsf_status hsf_grad(hsf_plan *plan, const uint64_t *bitstrings, size_t num, const void *gout,
+                    double *grad, int32_t num_params, void *workspace, size_t workspace_bytes,
+                    void *stream);
 
 /* Wait for the stream and report device-side failures of earlier runs of this plan:
  * returns HSF_ETIMEOUT (and clears the flag) if a bounded wait inside a kernel expired,

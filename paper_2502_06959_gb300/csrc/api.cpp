@@ -181,27 +181,8 @@ hsf_status hsf_plan_create(const hsf_circuit *circuit, int32_t cut_l, const hsf_
   if (st != HSF_OK) return st;
   st = decompose_blocks(*p);
   if (st != HSF_OK) return st;
-  const int B = (int)p->blocks.size();
-  p->radix.assign(B + 1, 1);
-  p->below.assign(B + 1, 1);
-  long double paths = 1;
-  for (int b = 0; b < B; ++b) {
-    p->radix[b + 1] = (uint64_t)p->blocks[b].rank;
-    paths *= p->blocks[b].rank;
-  }
-  if (paths > (long double)p->max_paths || paths > (long double)(1ull << 62))
-    return set_error(HSF_ERANK, "%.0Lf paths exceed max_paths %llu", paths, (unsigned long long)p->max_paths);
-  p->num_paths = (uint64_t)paths;
-  for (int k = B - 1; k >= 0; --k) p->below[k] = p->below[k + 1] * p->radix[k + 1];
-  int64_t nodes = 0;
-  for (int k = 0; k <= B; ++k) nodes += (int64_t)(p->num_paths / p->below[k]);
-  p->tree_nodes = nodes;
-  st = build_programs(*p);
+  st = finish_plan(*p);
   if (st != HSF_OK) return st;
-  st = upload_programs(*p);
-  if (st != HSF_OK) return st;
-  CUDA_TRY(cudaMalloc(&p->dev_status, 256));
-  CUDA_TRY(cudaMemset(p->dev_status, 0, 256));
   *out = p.release();
   return HSF_OK;
 }
@@ -221,6 +202,7 @@ hsf_status hsf_plan_get_info(const hsf_plan *p, hsf_plan_info *info) {
   info->tree_nodes = p->tree_nodes;
   info->num_launches = p->launches;
   info->leaf_bits = p->leaf_c;
+  info->num_params = p->num_params;
   return HSF_OK;
 }
 
@@ -247,13 +229,7 @@ hsf_status hsf_sync(hsf_plan *p, void *stream) {
   return HSF_OK;
 }
 
-void hsf_plan_destroy(hsf_plan *p) {
-  if (!p) return;
-  if (p->dev_status) cudaFree(p->dev_status);
-  for (auto &r : p->prof) { cudaEventDestroy(r.e0); cudaEventDestroy(r.e1); }
-  if (p->dev_table) cudaFree(p->dev_table);
-  delete p;
-}
+void hsf_plan_destroy(hsf_plan *p) { delete p; }
 
 hsf_status hsf_workspace_size(const hsf_plan *p, size_t num_bits, uint64_t window, size_t budget, size_t *bytes) {
   if (!p || !bytes) return set_error(HSF_EINVAL, "NULL argument");

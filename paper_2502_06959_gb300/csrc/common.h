@@ -27,6 +27,8 @@ struct DevOp {
   int32_t slot[3];       // register slot of each operand, -1 if none; dense ops have
                          // slot[0] > slot[1] > slot[2] (matrix MSB on the highest slot)
   int32_t kcase;         // dense ops: which unrolled slot pattern applies (see sweep.cu)
+  int32_t param;         // gradient programs: angle index of this rotation, else -1
+  int32_t kmat;          // gradient programs: offset of K = (dG/dtheta) G^-1 in the pool
   int32_t pad;
 };
 
@@ -131,7 +133,9 @@ struct BlockSvdArgs {
   // inputs
   int32_t num_blocks;
   const int32_t *block_k;        // [num_blocks] total qubits k, k_a, k_b packed as 3 ints
-  const int32_t *gate_begin;     // [num_blocks + 1] into gate descriptors
+  const int32_t *term_begin;     // [num_blocks + 1] into terms: the block matrix is the
+                                 // sum over its terms of the product of the term's gates
+  const int32_t *gate_begin;     // [num_terms + 1] into gate descriptors
   const int32_t *gate_desc;      // per gate: nq, pos0, pos1, pos2, mat offset (5 ints)
   const double *gate_mats;       // complex128 pool (re, im)
   double rank_tol;
@@ -159,6 +163,44 @@ struct PathGemmArgs {
   int32_t *err;                    // device status word (bounded waits)
 };
 size_t path_gemm_operand_bytes(int mode, int64_t M, int64_t N, int64_t paths);
+
+// Adjoint sweep over one pass of one tree level, in reverse op order (adjoint.cu).
+struct AdjointArgs {
+  const DevOp *ops;
+  int32_t num_ops;
+  int32_t first_op;        // ops [first_op, num_ops) are undone; 1 skips the Schmidt factor
+  const void *mats;
+  void *psi, *mu;          // this level's states and cotangents, node-major
+  int32_t h, t;
+  uint64_t active_mask;
+  int64_t num_nodes;
+  int32_t tiles_per_node;
+  int32_t pad;
+  double *grad;            // per-angle accumulators
+};
+struct LeafCotArgs {
+  const void *psi_a, *psi_b;
+  void *mu_a, *mu_b;
+  int32_t ha, hb;
+  int64_t paths;
+  const uint64_t *ia, *ib;
+  const double *gout;      // upstream gradient g_s (complex128)
+  int64_t S;
+};
+struct PullbackArgs {
+  const void *mu_child;    // children cotangents (level k), node-major
+  void *mu_parent;         // parent cotangents (level k-1), overwritten
+  const void *factor;      // [radix][2^nf][2^nf] factor matrices of this side
+  int32_t h, nf;
+  int32_t fq[3];           // storage bits of the factor's operands (fq[0] = matrix MSB)
+  int32_t radix;
+  int64_t parent_lo, child_lo, num_parents, num_children;
+};
+cudaError_t launch_adjoint(const AdjointArgs &a, int precision, cudaStream_t st);
+cudaError_t launch_leaf_cot(const LeafCotArgs &a, int precision, cudaStream_t st);
+cudaError_t launch_factor_pullback(const PullbackArgs &a, int precision, cudaStream_t st);
+cudaError_t launch_grad_dot(const double *gout, const double *ampd, int64_t S, double *grad, cudaStream_t st);
+cudaError_t launch_zero_bytes(void *p, size_t bytes, cudaStream_t st);
 cudaError_t launch_path_gemm(const PathGemmArgs &g, cudaStream_t st);
 
 cudaError_t launch_sweep(const SweepArgs &a, int precision, cudaStream_t st);

@@ -21,6 +21,8 @@ struct GateH {
   double param = 0.0;
   int param_id = -1;
   std::vector<cd> m;       // 2^nq x 2^nq, row-major
+  std::vector<cd> dm;      // rotations: dG/dtheta, 2^nq x 2^nq
+  std::vector<cd> k;       // rotations: K = (dG/dtheta) G^-1 = -i/2 P, 2^nq x 2^nq
   bool diag = false;
   int side = 0;            // 0 = a (all qubits > l), 1 = b (all <= l), 2 = crossing
 };
@@ -42,6 +44,8 @@ struct OpH {
   std::vector<cd> m;       // dense: 4^nq per digit; diag: 2^nq per digit
   int digits = 1;          // > 1: Schmidt factor, matrices for every digit
   int block = -1;
+  int param = -1;          // gradient programs: angle index of an unfused rotation
+  std::vector<cd> k;       // its K = (dG/dtheta) G^-1 (same form as m: dense or diagonal)
 };
 
 struct GroupH {
@@ -86,8 +90,18 @@ hsf_status validate_and_load(hsf_plan &p, const hsf_circuit *c, int cut, const h
                              const hsf_plan_opts *o);
 hsf_status check_order(const hsf_plan &p);
 hsf_status decompose_blocks(hsf_plan &p);
-hsf_status build_programs(hsf_plan &p);
-hsf_status upload_programs(hsf_plan &p);
+hsf_status build_programs(hsf_plan &p, bool grad = false);
+hsf_status upload_programs(hsf_plan &p, bool grad = false);
+// One Schmidt decomposition job: the matrix is the sum over `terms` of the product of
+// each term's gates (gate indices of the plan; a negative index -1-g uses gate g's
+// derivative dG/dtheta instead of G).  Results go to `out` (rank, sigma, x, y).
+struct SvdJob {
+  int block;
+  std::vector<std::vector<int>> terms;
+};
+hsf_status run_svd_jobs(const hsf_plan &p, const std::vector<SvdJob> &jobs, std::vector<BlockH> &out);
+// Path counts, gate programs, device tables and the status word of a decomposed plan.
+hsf_status finish_plan(hsf_plan &p);
 extern std::atomic<uint64_t> g_launches;
 }  // namespace hsf
 
@@ -102,8 +116,12 @@ struct hsf_plan {
   std::vector<uint64_t> below;      // below[k] = product of radix[k+1..B] (subtree leaves)
   uint64_t num_paths = 1;
   hsf::SideH side[2];               // 0 = a, 1 = b
+  hsf::SideH gside[2];              // gradient programs (rotations kept unfused)
+  bool grad_ready = false;
+  int num_params = 0;               // 1 + largest param_id of the circuit
   void *dev_table = nullptr;        // ops + matrices of every pass
   int32_t *dev_status = nullptr;    // set by kernels whose bounded waits expired
+  void *dev_gtable = nullptr;       // gradient programs (built on first hsf_grad)
   size_t dev_table_bytes = 0;
   int64_t tree_nodes = 0;
   int64_t launches = 0;
@@ -111,4 +129,21 @@ struct hsf_plan {
   int rbits = 4;                    // register slots of the register-resident sweep
   struct ProfRec { int kind; cudaEvent_t e0, e1; double bytes, flops; };
   std::vector<ProfRec> prof;
+  // gradients: derivative plans of blocks whose gates carry angles
+  struct DerivPlan { int block, param; hsf_plan *plan; };
+  std::vector<DerivPlan> dplans;
+  void *dev_factors = nullptr;      // Schmidt factors of every level (gradient pullback)
+  std::vector<size_t> factor_off[2];// byte offset of level k's factors (k >= 1)
+
+  hsf_plan() = default;
+  hsf_plan(const hsf_plan &) = delete;
+  hsf_plan &operator=(const hsf_plan &) = delete;
+  ~hsf_plan() {
+    for (auto &r : prof) { cudaEventDestroy(r.e0); cudaEventDestroy(r.e1); }
+    for (auto &d : dplans) delete d.plan;
+    if (dev_table) cudaFree(dev_table);
+    if (dev_gtable) cudaFree(dev_gtable);
+    if (dev_status) cudaFree(dev_status);
+    if (dev_factors) cudaFree(dev_factors);
+  }
 };

@@ -200,11 +200,11 @@ void merge_one_qubit_runs(std::vector<OpH> &ops) {
   std::vector<OpH> out;
   std::map<int, int> last;   // qubit -> index in out of the last op touching it
   for (auto &op : ops) {
-    if (op.nq == 1 && op.digits == 1) {
+    if (op.nq == 1 && op.digits == 1 && op.param < 0 && op.block < 0) {
       auto it = last.find(op.q[0]);
       if (it != last.end()) {
         OpH &prev = out[it->second];
-        if (prev.nq == 1 && prev.digits == 1) {
+        if (prev.nq == 1 && prev.digits == 1 && prev.param < 0 && prev.block < 0) {
           // prev then op (the ops in between do not touch this qubit): op * prev
           std::vector<cd> a = op.m, b = prev.m;
           if (op.type == OP_DIAG) a = {op.m[0], 0.0, 0.0, op.m[1]};
@@ -235,11 +235,11 @@ void absorb_into_two_qubit(std::vector<OpH> &ops) {
   std::map<int, int> pending;   // qubit -> index of its unabsorbed one-qubit op
   for (size_t o = 0; o < ops.size(); ++o) {
     OpH &op = ops[o];
-    if (op.nq == 1 && op.digits == 1) {
+    if (op.nq == 1 && op.digits == 1 && op.block < 0) {
       pending[op.q[0]] = (int)o;
       continue;
     }
-    if (op.nq == 2 && op.digits == 1) {
+    if (op.nq == 2 && op.digits == 1 && op.block < 0) {
       for (int x = 0; x < 2; ++x) {
         auto it = pending.find(op.q[x]);
         if (it == pending.end()) continue;
@@ -498,6 +498,18 @@ void pack_pass(const PassH &ps, std::vector<DevOp> &dops, std::vector<C> &mats, 
       c.y = (decltype(c.y))z.imag();
       mats.push_back(c);
     }
+    d.param = op.param;
+    d.kmat = -1;
+    if (op.param >= 0) {
+      if (sizeof(C) == 8 && (mats.size() & 1)) mats.push_back(C{});
+      d.kmat = (int32_t)mats.size();
+      for (auto &z : op.k) {
+        C c;
+        c.x = (decltype(c.x))z.real();
+        c.y = (decltype(c.y))z.imag();
+        mats.push_back(c);
+      }
+    }
     dops.push_back(d);
   }
   for (auto &g : ps.groups) {
@@ -511,15 +523,15 @@ void pack_pass(const PassH &ps, std::vector<DevOp> &dops, std::vector<C> &mats, 
 
 }  // namespace
 
-hsf_status build_programs(hsf_plan &p) {
+hsf_status build_programs(hsf_plan &p, bool grad) {
   const int B = (int)p.blocks.size();
   std::vector<std::pair<bool, int>> order;
   hsf_status st = execution_order(p, order);
   if (st != HSF_OK) return st;
   p.rbits = p.precision == HSF_PREC_C64 ? kRegBitsC64 : kRegBitsC128;
-  int leaf_c = B > 0 && p.radix[B] <= 8 ? 0 : -1;
+  int leaf_c = !grad && B > 0 && p.radix[B] <= 8 ? 0 : -1;
   for (int s = 0; s < 2; ++s) {
-    SideH &sd = p.side[s];
+    SideH &sd = grad ? p.gside[s] : p.side[s];
     sd.h = s == 0 ? p.na : p.nb;
     sd.offset = s == 0 ? p.cut + 1 : 0;
     sd.levels.assign(B + 1, LevelH{});
@@ -565,6 +577,15 @@ hsf_status build_programs(hsf_plan &p) {
       } else {
         op.m = g.m;
       }
+      if (grad && g.param_id >= 0 && !g.k.empty()) {
+        op.param = g.param_id;
+        if (g.diag) {
+          op.k.resize(d);
+          for (int i = 0; i < d; ++i) op.k[i] = g.k[(size_t)i * d + i];
+        } else {
+          op.k = g.k;
+        }
+      }
       sd.levels[lvl].ops.push_back(op);
     }
     // storage order: qubits touched at deeper levels get lower storage bits
@@ -586,7 +607,7 @@ hsf_status build_programs(hsf_plan &p) {
         for (int j = 0; j < op.nq; ++j) op.q[j] = sd.store[op.q[j]];
     for (auto &lv : sd.levels) {
       merge_one_qubit_runs(lv.ops);
-      if (!(p.flags & HSF_FLAG_NO_REGISTER_SWEEP)) absorb_into_two_qubit(lv.ops);
+      if (!grad && !(p.flags & HSF_FLAG_NO_REGISTER_SWEEP)) absorb_into_two_qubit(lv.ops);
     }
     if (leaf_c >= 0) {
       int c = 0;
@@ -596,10 +617,11 @@ hsf_status build_programs(hsf_plan &p) {
     }
     for (auto &lv : sd.levels) {
       split_passes(lv, sd.h, p.tile_max);
-      if (!(p.flags & HSF_FLAG_NO_REGISTER_SWEEP))
+      if (!grad && !(p.flags & HSF_FLAG_NO_REGISTER_SWEEP))
         for (auto &ps : lv.passes) build_groups(ps, p.rbits);
     }
   }
+  if (grad) return HSF_OK;
   // leaf operators L_m: the leaf program with digit m applied to every basis vector
   p.leaf_c = 0;
   const size_t csz = p.precision == HSF_PREC_C64 ? 8 : 16;
@@ -623,7 +645,7 @@ hsf_status build_programs(hsf_plan &p) {
   return HSF_OK;
 }
 
-hsf_status upload_programs(hsf_plan &p) {
+hsf_status upload_programs(hsf_plan &p, bool grad) {
   std::vector<unsigned char> host;
   auto align = [&](size_t a) { while (host.size() % a) host.push_back(0); };
   auto append = [&](const void *ptr, size_t bytes) {
@@ -631,7 +653,7 @@ hsf_status upload_programs(hsf_plan &p) {
   };
   int64_t launches = 0;
   for (int s = 0; s < 2; ++s) {
-    for (auto &lv : p.side[s].levels)
+    for (auto &lv : (grad ? p.gside[s] : p.side[s]).levels)
       for (auto &ps : lv.passes) {
         std::vector<DevOp> dops;
         std::vector<DevGroup> dgroups;
@@ -651,7 +673,7 @@ hsf_status upload_programs(hsf_plan &p) {
         ps.table_end = host.size();
         ++launches;
       }
-    SideH &sd = p.side[s];
+    SideH &sd = grad ? p.gside[s] : p.side[s];
     align(256);
     sd.leaf_off = host.size();
     for (auto &z : sd.leaf_ops) {
@@ -666,10 +688,36 @@ hsf_status upload_programs(hsf_plan &p) {
   }
   align(256);
   if (host.empty()) host.resize(256);
-  CUDA_TRY(cudaMalloc(&p.dev_table, host.size()));
-  p.dev_table_bytes = host.size();
-  CUDA_TRY(cudaMemcpy(p.dev_table, host.data(), host.size(), cudaMemcpyHostToDevice));
-  p.launches = launches / 2;
+  void *&table = grad ? p.dev_gtable : p.dev_table;
+  CUDA_TRY(cudaMalloc(&table, host.size()));
+  if (!grad) p.dev_table_bytes = host.size();
+  CUDA_TRY(cudaMemcpy(table, host.data(), host.size(), cudaMemcpyHostToDevice));
+  if (!grad) p.launches = launches / 2;
+  return HSF_OK;
+}
+
+hsf_status finish_plan(hsf_plan &p) {
+  const int B = (int)p.blocks.size();
+  p.radix.assign(B + 1, 1);
+  p.below.assign(B + 1, 1);
+  long double paths = 1;
+  for (int b = 0; b < B; ++b) {
+    p.radix[b + 1] = (uint64_t)p.blocks[b].rank;
+    paths *= p.blocks[b].rank;
+  }
+  if (paths > (long double)p.max_paths || paths > (long double)(1ull << 62))
+    return set_error(HSF_ERANK, "%.0Lf paths exceed max_paths %llu", paths, (unsigned long long)p.max_paths);
+  p.num_paths = (uint64_t)paths;
+  for (int k = B - 1; k >= 0; --k) p.below[k] = p.below[k + 1] * p.radix[k + 1];
+  int64_t nodes = 0;
+  for (int k = 0; k <= B; ++k) nodes += (int64_t)(p.num_paths / p.below[k]);
+  p.tree_nodes = nodes;
+  hsf_status st = build_programs(p);
+  if (st != HSF_OK) return st;
+  st = upload_programs(p);
+  if (st != HSF_OK) return st;
+  CUDA_TRY(cudaMalloc(&p.dev_status, 256));
+  CUDA_TRY(cudaMemset(p.dev_status, 0, 256));
   return HSF_OK;
 }
 
@@ -678,53 +726,60 @@ hsf_status check_order(const hsf_plan &p) {
   return execution_order(p, order);
 }
 
-// Multiply and decompose every block on the device; read back ranks and factors.
-hsf_status decompose_blocks(hsf_plan &p) {
-  const int B = (int)p.blocks.size();
-  if (B == 0) return HSF_OK;
-  std::vector<int32_t> bk(3 * B), gbeg(B + 1, 0), gdesc;
+// Multiply and decompose blocks on the device (svd.cu); read back ranks and factors.
+hsf_status run_svd_jobs(const hsf_plan &p, const std::vector<SvdJob> &jobs, std::vector<BlockH> &out) {
+  const int J = (int)jobs.size();
+  out.assign(J, BlockH{});
+  if (J == 0) return HSF_OK;
+  std::vector<int32_t> bk(3 * J), tbeg(J + 1, 0), gbeg(1, 0), gdesc;
   std::vector<double> gm;
-  for (int b = 0; b < B; ++b) {
-    BlockH &blk = p.blocks[b];
+  for (int j = 0; j < J; ++j) {
+    const BlockH &blk = p.blocks[jobs[j].block];
     const int k = (int)blk.qubits.size();
-    bk[3 * b] = k;
-    bk[3 * b + 1] = (int)blk.qa.size();
-    bk[3 * b + 2] = (int)blk.qb.size();
-    for (int gi : blk.gates) {
-      const GateH &g = p.gates[gi];
-      gdesc.push_back(g.nq);
-      for (int j = 0; j < 3; ++j) {
-        int pos = 0;
-        if (j < g.nq) {
-          const int idx = (int)(std::find(blk.qubits.begin(), blk.qubits.end(), g.q[j]) - blk.qubits.begin());
-          pos = k - 1 - idx;      // block qubits are listed most significant first
+    bk[3 * j] = k;
+    bk[3 * j + 1] = (int)blk.qa.size();
+    bk[3 * j + 2] = (int)blk.qb.size();
+    for (const auto &term : jobs[j].terms) {
+      for (int code : term) {
+        const bool deriv = code < 0;
+        const GateH &g = p.gates[deriv ? -1 - code : code];
+        gdesc.push_back(g.nq);
+        for (int x = 0; x < 3; ++x) {
+          int pos = 0;
+          if (x < g.nq) {
+            const int idx = (int)(std::find(blk.qubits.begin(), blk.qubits.end(), g.q[x]) - blk.qubits.begin());
+            pos = k - 1 - idx;      // block qubits are listed most significant first
+          }
+          gdesc.push_back(pos);
         }
-        gdesc.push_back(pos);
+        gdesc.push_back((int32_t)(gm.size() / 2));
+        for (auto &z : (deriv ? g.dm : g.m)) {
+          gm.push_back(z.real());
+          gm.push_back(z.imag());
+        }
       }
-      gdesc.push_back((int32_t)(gm.size() / 2));
-      for (auto &z : g.m) {
-        gm.push_back(z.real());
-        gm.push_back(z.imag());
-      }
+      gbeg.push_back((int32_t)(gdesc.size() / 5));
     }
-    gbeg[b + 1] = (int32_t)(gdesc.size() / 5);
+    tbeg[j + 1] = (int32_t)(gbeg.size() - 1);
   }
-  const size_t nf = (size_t)B * 64 * 64 * 2;
+  const size_t nf = (size_t)J * 64 * 64 * 2;
   size_t off = 0;
   auto take = [&](size_t bytes) { size_t o = off; off += (bytes + 255) / 256 * 256; return o; };
-  const size_t o_bk = take(bk.size() * 4), o_gb = take(gbeg.size() * 4), o_gd = take(gdesc.size() * 4 + 4),
-               o_gm = take(gm.size() * 8 + 8), o_sig = take((size_t)B * 64 * 8), o_rank = take((size_t)B * 4),
-               o_x = take(nf * 8), o_y = take(nf * 8), o_sw = take((size_t)B * 4);
+  const size_t o_bk = take(bk.size() * 4), o_tb = take(tbeg.size() * 4), o_gb = take(gbeg.size() * 4),
+               o_gd = take(gdesc.size() * 4 + 4), o_gm = take(gm.size() * 8 + 8), o_sig = take((size_t)J * 64 * 8),
+               o_rank = take((size_t)J * 4), o_x = take(nf * 8), o_y = take(nf * 8), o_sw = take((size_t)J * 4);
   unsigned char *d = nullptr;
   CUDA_TRY(cudaMalloc(&d, off));
   std::unique_ptr<unsigned char, void (*)(unsigned char *)> guard(d, [](unsigned char *q) { cudaFree(q); });
   CUDA_TRY(cudaMemcpy(d + o_bk, bk.data(), bk.size() * 4, cudaMemcpyHostToDevice));
+  CUDA_TRY(cudaMemcpy(d + o_tb, tbeg.data(), tbeg.size() * 4, cudaMemcpyHostToDevice));
   CUDA_TRY(cudaMemcpy(d + o_gb, gbeg.data(), gbeg.size() * 4, cudaMemcpyHostToDevice));
   if (!gdesc.empty()) CUDA_TRY(cudaMemcpy(d + o_gd, gdesc.data(), gdesc.size() * 4, cudaMemcpyHostToDevice));
   if (!gm.empty()) CUDA_TRY(cudaMemcpy(d + o_gm, gm.data(), gm.size() * 8, cudaMemcpyHostToDevice));
   BlockSvdArgs a{};
-  a.num_blocks = B;
+  a.num_blocks = J;
   a.block_k = (const int32_t *)(d + o_bk);
+  a.term_begin = (const int32_t *)(d + o_tb);
   a.gate_begin = (const int32_t *)(d + o_gb);
   a.gate_desc = (const int32_t *)(d + o_gd);
   a.gate_mats = (const double *)(d + o_gm);
@@ -738,32 +793,51 @@ hsf_status decompose_blocks(hsf_plan &p) {
   CUDA_TRY(launch_block_svd(a, 0));
   g_launches++;
   CUDA_TRY(cudaDeviceSynchronize());
-  std::vector<double> sig((size_t)B * 64), xf(nf), yf(nf);
-  std::vector<int32_t> rank(B);
+  std::vector<double> sig((size_t)J * 64), xf(nf), yf(nf);
+  std::vector<int32_t> rank(J);
   CUDA_TRY(cudaMemcpy(sig.data(), d + o_sig, sig.size() * 8, cudaMemcpyDeviceToHost));
   CUDA_TRY(cudaMemcpy(rank.data(), d + o_rank, rank.size() * 4, cudaMemcpyDeviceToHost));
   CUDA_TRY(cudaMemcpy(xf.data(), d + o_x, nf * 8, cudaMemcpyDeviceToHost));
   CUDA_TRY(cudaMemcpy(yf.data(), d + o_y, nf * 8, cudaMemcpyDeviceToHost));
-  for (int b = 0; b < B; ++b) {
-    BlockH &blk = p.blocks[b];
-    blk.rank = rank[b];
-    if (blk.rank <= 0) return set_error(HSF_ENUMERIC, "block %d decomposed to rank 0", b);
-    blk.sigma.assign(sig.begin() + (size_t)b * 64, sig.begin() + (size_t)b * 64 + blk.rank);
-    for (double s : blk.sigma)
-      if (!std::isfinite(s)) return set_error(HSF_ENUMERIC, "block %d: non-finite singular value", b);
-    const int ea = 1 << (2 * (int)blk.qa.size()), eb = 1 << (2 * (int)blk.qb.size());
-    blk.x.clear();
-    blk.y.clear();
-    for (int m = 0; m < blk.rank; ++m) {
+  for (int j = 0; j < J; ++j) {
+    BlockH &r = out[j];
+    const BlockH &src = p.blocks[jobs[j].block];
+    r.gates = src.gates;
+    r.qubits = src.qubits;
+    r.qa = src.qa;
+    r.qb = src.qb;
+    r.rank = rank[j];
+    r.sigma.assign(sig.begin() + (size_t)j * 64, sig.begin() + (size_t)j * 64 + std::max(0, r.rank));
+    for (double sv : r.sigma)
+      if (!std::isfinite(sv)) return set_error(HSF_ENUMERIC, "block %d: non-finite singular value", jobs[j].block);
+    const int ea = 1 << (2 * (int)r.qa.size()), eb = 1 << (2 * (int)r.qb.size());
+    for (int m = 0; m < r.rank; ++m) {
       for (int e = 0; e < ea; ++e) {
-        const size_t i = (((size_t)b * 64 + m) * 64 + e) * 2;
-        blk.x.push_back(cd(xf[i], xf[i + 1]));
+        const size_t i = (((size_t)j * 64 + m) * 64 + e) * 2;
+        r.x.push_back(cd(xf[i], xf[i + 1]));
       }
       for (int e = 0; e < eb; ++e) {
-        const size_t i = (((size_t)b * 64 + m) * 64 + e) * 2;
-        blk.y.push_back(cd(yf[i], yf[i + 1]));
+        const size_t i = (((size_t)j * 64 + m) * 64 + e) * 2;
+        r.y.push_back(cd(yf[i], yf[i + 1]));
       }
     }
+  }
+  return HSF_OK;
+}
+
+hsf_status decompose_blocks(hsf_plan &p) {
+  const int B = (int)p.blocks.size();
+  std::vector<SvdJob> jobs(B);
+  for (int b = 0; b < B; ++b) {
+    jobs[b].block = b;
+    jobs[b].terms = {p.blocks[b].gates};
+  }
+  std::vector<BlockH> res;
+  hsf_status st = run_svd_jobs(p, jobs, res);
+  if (st != HSF_OK) return st;
+  for (int b = 0; b < B; ++b) {
+    if (res[b].rank <= 0) return set_error(HSF_ENUMERIC, "block %d decomposed to rank 0", b);
+    p.blocks[b] = res[b];
   }
   return HSF_OK;
 }
@@ -824,6 +898,20 @@ hsf_status validate_and_load(hsf_plan &p, const hsf_circuit *c, int cut, const h
       if (g.nq != nq) return set_error(HSF_EINVAL, "gate %d: kind %d takes %d qubits, got %d", i, g.kind, nq, g.nq);
     }
     h.nq = nq;
+    if (g.kind == HSF_GATE_RX || g.kind == HSF_GATE_RY || g.kind == HSF_GATE_RZ || g.kind == HSF_GATE_RZZ) {
+      // G = exp(-i t P / 2): K = dG/dt G^-1 = -i/2 P and dG/dt = K G
+      const int d = 1 << nq;
+      std::vector<cd> P((size_t)d * d, 0.0);
+      const cd I(0.0, 1.0);
+      if (g.kind == HSF_GATE_RX) P = {0.0, 1.0, 1.0, 0.0};
+      if (g.kind == HSF_GATE_RY) P = {0.0, -I, I, 0.0};
+      if (g.kind == HSF_GATE_RZ) P = {1.0, 0.0, 0.0, -1.0};
+      if (g.kind == HSF_GATE_RZZ) { P[0] = 1.0; P[5] = -1.0; P[10] = -1.0; P[15] = 1.0; }
+      h.k.resize(P.size());
+      for (size_t e = 0; e < P.size(); ++e) h.k[e] = cd(0.0, -0.5) * P[e];
+      h.dm = matmul(h.k, h.m, d);
+      if (g.param_id >= 0) p.num_params = std::max(p.num_params, g.param_id + 1);
+    }
     for (int j = 0; j < nq; ++j) {
       h.q[j] = g.q[j];
       if (g.q[j] < 0 || g.q[j] >= c->n) return set_error(HSF_EINVAL, "gate %d: qubit %d out of range", i, g.q[j]);

@@ -50,11 +50,14 @@ __global__ void __launch_bounds__(kThreads) block_svd_kernel(BlockSvdArgs a) {
   const int D = 1 << k;
   const int tid = threadIdx.x;
 
-  // 1. block product
+  // 1. block product (a sum of products when the block has several terms, e.g. the
+  //    product rule of a derivative); the running sum is kept in W
+  const int t0 = a.term_begin[b], t1 = a.term_begin[b + 1];
+  for (int term = t0; term < t1; ++term) {
   for (int e = tid; e < D * D; e += blockDim.x)
     U[e] = make_double2((e / D) == (e % D) ? 1.0 : 0.0, 0.0);
   __syncthreads();
-  for (int gi = a.gate_begin[b]; gi < a.gate_begin[b + 1]; ++gi) {
+  for (int gi = a.gate_begin[term]; gi < a.gate_begin[term + 1]; ++gi) {
     const int *gd = a.gate_desc + 5 * gi;
     const int nq = gd[0];
     const int pos[3] = {gd[1], gd[2], gd[3]};
@@ -92,6 +95,18 @@ __global__ void __launch_bounds__(kThreads) block_svd_kernel(BlockSvdArgs a) {
         U[rows[s] * D + col] = acc;
       }
     }
+    __syncthreads();
+  }
+  if (t1 - t0 > 1) {
+    for (int e = tid; e < D * D; e += blockDim.x) {
+      const double2 prev = term == t0 ? make_double2(0.0, 0.0) : W[e];
+      W[e] = make_double2(prev.x + U[e].x, prev.y + U[e].y);
+    }
+    __syncthreads();
+  }
+  }
+  if (t1 - t0 > 1) {
+    for (int e = tid; e < D * D; e += blockDim.x) U[e] = W[e];
     __syncthreads();
   }
 

@@ -66,7 +66,7 @@ class hsf_plan_info(ctypes.Structure):
                 ("num_blocks", ctypes.c_int32), ("num_paths", ctypes.c_uint64),
                 ("precision", ctypes.c_int32), ("max_rank", ctypes.c_int32),
                 ("tree_nodes", ctypes.c_int64), ("num_launches", ctypes.c_int64),
-                ("leaf_bits", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("leaf_bits", ctypes.c_int32), ("num_params", ctypes.c_int32)]
 
 
 # symbol -> (restype, argtypes); also the list the load test checks against the header
@@ -87,6 +87,9 @@ SIGNATURES = {
     "hsf_run_static": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_uint64,
                                       ctypes.c_uint64, ctypes.c_uint64, ctypes.c_void_p, ctypes.c_void_p]),
     "hsf_sync": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "hsf_grad_workspace_size": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]),
+    "hsf_grad": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p,
+                                ctypes.c_int32, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
     "hsf_last_error": (ctypes.c_char_p, []),
     "hsf_set_profiling": (None, [ctypes.c_int32]),
     "hsf_profile_collect": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32]),
@@ -230,6 +233,18 @@ def hsf_run_static(plan: int, bitstrings_ptr: int, num: int, window: int, path_b
                                          path_end, out_ptr, stream or None))
 
 
+def hsf_grad_workspace_size(plan: int, num_bitstrings: int) -> int:
+    out = ctypes.c_size_t()
+    _check(load_library().hsf_grad_workspace_size(plan, num_bitstrings, ctypes.byref(out)))
+    return out.value
+
+
+def hsf_grad(plan: int, bitstrings_ptr: int, num: int, gout_ptr: int, grad_ptr: int, num_params: int,
+             workspace_ptr: int, workspace_bytes: int, stream: int = 0) -> None:
+    _check(load_library().hsf_grad(plan, bitstrings_ptr, num, gout_ptr, grad_ptr, num_params,
+                                   workspace_ptr, workspace_bytes, stream or None))
+
+
 def hsf_sync(plan: int, stream: int = 0) -> None:
     _check(load_library().hsf_sync(plan, stream or None))
 
@@ -286,6 +301,21 @@ class Plan:
             hsf_sync(self.handle, st.cuda_stream)
         return out
 
+    def grad(self, bitstrings, gout, num_params: int = 0, stream=None):
+        """dL/dtheta (float64 CUDA tensor) for the upstream gradient gout (complex128,
+        one per bitstring)."""
+        import torch
+        num = int(bitstrings.numel())
+        num_params = max(num_params, int(self.info["num_params"]))
+        need = hsf_grad_workspace_size(self.handle, num)
+        ws = torch.empty(max(need, 256), dtype=torch.uint8, device="cuda")
+        g = torch.empty(max(num_params, 1), dtype=torch.float64, device="cuda")
+        st = stream if stream is not None else torch.cuda.current_stream()
+        gout = gout.to(torch.complex128).contiguous()
+        hsf_grad(self.handle, bitstrings.data_ptr(), num, gout.data_ptr(), g.data_ptr(), num_params,
+                 ws.data_ptr(), ws.numel(), st.cuda_stream)
+        return g[:num_params]
+
     def close(self):
         if self.handle:
             hsf_plan_destroy(self.handle)
@@ -296,3 +326,48 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+
+def _autograd_function():
+    import torch
+
+    class HSFAmplitudes(torch.autograd.Function):
+        """amps = HSFAmplitudes.apply(angles, problem, bitstrings, precision)
+
+        Forward: plan the circuit with the given shared angles (param_id j takes
+        angles[j]) and return the complex128 amplitudes at the bitstrings.  Backward:
+        the library's adjoint pass (hsf_grad) maps the upstream gradient of the
+        amplitudes to dL/dangles."""
+
+        @staticmethod
+        def forward(ctx, angles, problem, bitstrings, precision="c64"):
+            ang = angles.detach().to("cpu", torch.float64).numpy()
+            plan = Plan(problem.n, problem.gates, problem.cut, problem.blocks, precision=precision,
+                        angles=ang)
+            amps = plan.run(bitstrings)
+            ctx.plan = plan
+            ctx.bits = bitstrings
+            ctx.nparams = angles.numel()
+            ctx.dtype = angles.dtype
+            ctx.device = angles.device
+            return amps
+
+        @staticmethod
+        def backward(ctx, gout):
+            g = ctx.plan.grad(ctx.bits, gout, ctx.nparams)
+            ctx.plan.close()
+            return g.to(device=ctx.device, dtype=ctx.dtype), None, None, None
+
+    return HSFAmplitudes
+
+
+_FUNCTION = None
+
+
+def __getattr__(name):
+    global _FUNCTION
+    if name == "HSFAmplitudes":
+        if _FUNCTION is None:
+            _FUNCTION = _autograd_function()
+        return _FUNCTION
+    raise AttributeError(name)
