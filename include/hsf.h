@@ -210,6 +210,39 @@ hsf_status hsf_grad(hsf_plan *plan, const uint64_t *bitstrings, size_t num, cons
                     double *grad, int32_t num_params, void *workspace, size_t workspace_bytes,
                     void *stream);
 
+/* Batches: many circuits (uneven n, path counts, outputs) recorded once into a CUDA
+ * graph and replayed with one launch.  Items run one after another inside the graph
+ * and share `workspace` (hsf_batch_workspace_size: the largest item's need); every
+ * plan, bitstring array and output must stay alive and at the same address while
+ * the batch exists.  Recording happens on `stream` (stream capture); profiling must be
+ * off while recording. */
+typedef struct hsf_batch hsf_batch;
+typedef struct hsf_batch_item {
+  hsf_plan *plan;
+  const uint64_t *bitstrings;   /* device, or NULL                          */
+  size_t num;
+  uint64_t window;              /* with bitstrings == NULL: leading amplitudes */
+  void *out;                    /* device complex128                        */
+} hsf_batch_item;
+hsf_status hsf_batch_workspace_size(const hsf_batch_item *items, int32_t count, size_t *bytes);
+hsf_status hsf_batch_create(const hsf_batch_item *items, int32_t count, void *workspace,
+                            size_t workspace_bytes, void *stream, hsf_batch **out);
+hsf_status hsf_batch_launch(hsf_batch *batch, void *stream);
+/* Kernel launches in one replay of the batch graph. */
+int64_t hsf_batch_nodes(const hsf_batch *batch);
+void hsf_batch_destroy(hsf_batch *batch);
+
+/* Autotuner: for this circuit shape and request, plan and time each candidate
+ * sweep configuration (shared-memory tile width 2^tile_bits, register-group fusion on
+ * or off) on the current device and write the fastest into opts->tile_bits and
+ * opts->flags.  Results are appended to the text file cache_path (may be NULL) keyed by
+ * a hash of the circuit structure and request, and reused on later calls.  Timing
+ * runs use `workspace` (hsf_workspace_size bytes for the request) and synchronise. */
+hsf_status hsf_tune(const hsf_circuit *circuit, int32_t cut_l, const hsf_blocks *blocks,
+                    hsf_plan_opts *opts, size_t num_bitstrings, const uint64_t *bitstrings,
+                    uint64_t window, const char *cache_path, void *workspace,
+                    size_t workspace_bytes);
+
 /* Wait for the stream and report device-side failures of earlier runs of this plan:
  * returns HSF_ETIMEOUT (and clears the flag) if a bounded wait inside a kernel expired,
  * in which case the affected outputs are invalid. */

@@ -61,6 +61,11 @@ class hsf_plan_opts(ctypes.Structure):
                 ("reserved", ctypes.c_int32)]
 
 
+class hsf_batch_item(ctypes.Structure):
+    _fields_ = [("plan", ctypes.c_void_p), ("bitstrings", ctypes.c_void_p), ("num", ctypes.c_size_t),
+                ("window", ctypes.c_uint64), ("out", ctypes.c_void_p)]
+
+
 class hsf_plan_info(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int32), ("n_a", ctypes.c_int32), ("n_b", ctypes.c_int32),
                 ("num_blocks", ctypes.c_int32), ("num_paths", ctypes.c_uint64),
@@ -87,6 +92,15 @@ SIGNATURES = {
     "hsf_run_static": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_uint64,
                                       ctypes.c_uint64, ctypes.c_uint64, ctypes.c_void_p, ctypes.c_void_p]),
     "hsf_sync": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "hsf_batch_workspace_size": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(ctypes.c_size_t)]),
+    "hsf_batch_create": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_size_t,
+                                        ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]),
+    "hsf_batch_launch": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "hsf_batch_nodes": (ctypes.c_int64, [ctypes.c_void_p]),
+    "hsf_batch_destroy": (None, [ctypes.c_void_p]),
+    "hsf_tune": (ctypes.c_int, [ctypes.POINTER(hsf_circuit), ctypes.c_int32, ctypes.POINTER(hsf_blocks),
+                                ctypes.POINTER(hsf_plan_opts), ctypes.c_size_t, ctypes.c_void_p, ctypes.c_uint64,
+                                ctypes.c_char_p, ctypes.c_void_p, ctypes.c_size_t]),
     "hsf_grad_workspace_size": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]),
     "hsf_grad": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p,
                                 ctypes.c_int32, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
@@ -243,6 +257,70 @@ def hsf_grad(plan: int, bitstrings_ptr: int, num: int, gout_ptr: int, grad_ptr: 
              workspace_ptr: int, workspace_bytes: int, stream: int = 0) -> None:
     _check(load_library().hsf_grad(plan, bitstrings_ptr, num, gout_ptr, grad_ptr, num_params,
                                    workspace_ptr, workspace_bytes, stream or None))
+
+
+def hsf_tune(n: int, gates, cut: int, blocks, num: int = 0, bitstrings_ptr: int = 0, window: int = 0,
+             cache_path: Optional[str] = None, precision: str = "c64", gemm: str = "fp32",
+             budget: int = 0) -> dict:
+    """Autotune the sweep configuration for this circuit shape; returns the plan options
+    (tile_bits, flags) to pass to hsf_plan_create."""
+    import torch
+    lib = load_library()
+    circ, bl, keep = _marshal(n, gates, blocks)
+    opts = hsf_plan_opts()
+    opts.precision = PREC[precision]
+    opts.gemm_mode = GEMM[gemm]
+    probe = hsf_plan_create(n, gates, cut, blocks, precision=precision, gemm=gemm)
+    if budget == 0:
+        budget = int(torch.cuda.mem_get_info()[0] * 0.5)
+    need = hsf_workspace_size(probe, num, window, budget)
+    hsf_plan_destroy(probe)
+    ws = torch.empty(need, dtype=torch.uint8, device="cuda")
+    _check(lib.hsf_tune(ctypes.byref(circ), cut, ctypes.byref(bl), ctypes.byref(opts), num,
+                        bitstrings_ptr or None, window, cache_path.encode() if cache_path else None,
+                        ws.data_ptr(), need))
+    return {"tile_bits": opts.tile_bits, "flags": opts.flags}
+
+
+class Batch:
+    """A CUDA graph holding hsf_run of every (plan, request) item; launch() replays it."""
+
+    def __init__(self, items, stream=None):
+        import torch
+        lib = load_library()
+        self.items = items          # keep plans, inputs and outputs alive
+        arr = (hsf_batch_item * len(items))()
+        for i, it in enumerate(items):
+            bits = it.get("bitstrings")
+            arr[i].plan = it["plan"].handle
+            arr[i].bitstrings = bits.data_ptr() if bits is not None else None
+            arr[i].num = bits.numel() if bits is not None else 0
+            arr[i].window = it.get("window", 0)
+            arr[i].out = it["out"].data_ptr()
+        need = ctypes.c_size_t()
+        _check(lib.hsf_batch_workspace_size(arr, len(items), ctypes.byref(need)))
+        self.ws = torch.empty(need.value, dtype=torch.uint8, device="cuda")
+        self.stream = stream or torch.cuda.Stream()
+        h = ctypes.c_void_p()
+        _check(lib.hsf_batch_create(arr, len(items), self.ws.data_ptr(), self.ws.numel(),
+                                    self.stream.cuda_stream, ctypes.byref(h)))
+        self.handle = h.value
+        self.nodes = int(lib.hsf_batch_nodes(self.handle))
+
+    def launch(self, stream=None):
+        st = stream or self.stream
+        _check(load_library().hsf_batch_launch(self.handle, st.cuda_stream))
+
+    def close(self):
+        if self.handle:
+            load_library().hsf_batch_destroy(self.handle)
+            self.handle = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def hsf_sync(plan: int, stream: int = 0) -> None:
