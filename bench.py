@@ -50,6 +50,12 @@ def parse():
                     help="profiling aid: simulate only the first N paths (0 = all)")
     ap.add_argument("--budget-gb", type=float, default=0.0,
                     help="profiling aid: cap the workspace (path chunks shrink to fit)")
+    ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c4", "c5", "c1"],
+                    help="c2 (default, n=30 bitstrings); c3: 64 uneven circuits in one CUDA graph "
+                         "(window output, tensor-core path GEMM); c4: QAOA n=28 adjoint gradients; "
+                         "c5: n=36, 2^20 bitstrings; c1: n=12 all amplitudes")
+    ap.add_argument("--gemm", default="bf16x3", choices=["fp32", "bf16x3", "tf32x3", "tf32"])
+    ap.add_argument("--tune", action="store_true", help="c3: autotune one circuit per qubit count")
     return ap.parse_args()
 
 
@@ -195,10 +201,141 @@ def run_reference(args):
 # ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
+def _timed(torch, stream, fn, steps):
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(steps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1)
+
+
+def bench_other(args):
+    """Secondary workloads (one GPU): c3 batched graph, c4 gradients, c5 n=36, c1 parity."""
+    import torch
+    from paper_2502_06959_gb300 import hsf
+    from paper_2502_06959_gb300 import workloads as W
+    torch.cuda.set_device(0)
+    hsf.load_library()
+    stream = torch.cuda.current_stream()
+    hbm_peak, bf16_peak, sm_max, peak_src = peaks()
+    line = {"n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "data": "synthetic"}
+    if args.workload == "c3":
+        probs = W.workload_c3()
+        tuned = {}
+        if args.tune:
+            import tempfile
+            cache = os.path.join(tempfile.gettempdir(), "hsf_tune_cache.txt")
+            for pr in probs:
+                if pr.n in tuned:
+                    continue
+                window = min(1 << pr.n, 1 << 24)
+                tuned[pr.n] = hsf.hsf_tune(pr.n, pr.gates, pr.cut, pr.blocks, window=window, cache_path=cache,
+                                           gemm=args.gemm)
+        items = []
+        for pr in probs:
+            window = min(1 << pr.n, 1 << 24)
+            opts = tuned.get(pr.n, {})
+            plan = hsf.Plan.from_problem(pr, precision="c64", gemm=args.gemm, **opts)
+            items.append(dict(plan=plan, window=window,
+                              out=torch.empty(window, dtype=torch.complex128, device="cuda")))
+        gstream = torch.cuda.Stream()          # graphs are recorded on a non-default stream
+        batch = hsf.Batch(items, stream=gstream)
+        for _ in range(args.warmup):
+            batch.launch(gstream)
+        l0 = hsf.hsf_launch_count()
+        with ClockSampler(0) as clk:
+            ms = _timed(torch, gstream, lambda: batch.launch(gstream), args.steps)
+        launches = hsf.hsf_launch_count() - l0
+        # the path GEMM of the largest circuit, timed alone with per-kernel events
+        big = max(items, key=lambda it: it["plan"].n * 10 ** 6 + it["plan"].info["num_paths"])
+        hsf.hsf_set_profiling(True)
+        big["plan"].run(window=big["window"], out=big["out"])
+        torch.cuda.synchronize()
+        st = hsf.hsf_profile_collect(big["plan"].handle)
+        hsf.hsf_set_profiling(False)
+        w = st["window"]
+        tf = w["flops"] / (w["ms"] / 1e3) / 1e12 if w["ms"] else 0.0
+        paths = [it["plan"].info["num_paths"] for it in items]
+        ns = [it["plan"].n for it in items]
+        line.update({
+            "metric": "HSF circuits/s (64 uneven circuits, one CUDA graph, window output)",
+            "value": len(items) * args.steps / (ms / 1e3), "unit": "circuits/s",
+            "ms_per_step": ms / args.steps, "dtype": "c64+" + args.gemm,
+            "config": {"workload": "c3_64_uneven_n20to32_window2^24", "circuits": len(items),
+                       "n_range": [min(ns), max(ns)], "paths_range": [min(paths), max(paths)],
+                       "graph_kernel_nodes": batch.nodes, "tuned": bool(args.tune),
+                       "step": "one graph replay of hsf_run for all 64 plans"},
+            "gpu_launches": int(launches),
+            "roofline": {"bound": "tensor", "kernel": "path_gemm (largest circuit)", "achieved": tf,
+                         "peak": bf16_peak, "unit": "TFLOP/s", "frac": tf / bf16_peak, "traffic": None,
+                         "peak_source": peak_src + " (bf16 dense; counted flops = 3 bf16 products)",
+                         "gemm_ms": w["ms"], "circuit_n": big["plan"].n,
+                         "circuit_paths": big["plan"].info["num_paths"]},
+            "clocks": clk.summary(),
+        })
+        batch.close()
+        for it in items:
+            it["plan"].close()
+    elif args.workload == "c4":
+        pr = W.workload_c4()
+        bits = torch.from_numpy(pr.bitstrings.view(np.int64)).cuda()
+        theta = torch.tensor(pr.params, dtype=torch.float64, requires_grad=True)
+
+        def step():
+            amps = hsf.HSFAmplitudes.apply(theta, pr, bits, "c64")
+            loss = (amps.abs() ** 2).sum()
+            theta.grad = None
+            loss.backward()
+        for _ in range(args.warmup):
+            step()
+        l0 = hsf.hsf_launch_count()
+        with ClockSampler(0) as clk:
+            ms = _timed(torch, stream, step, args.steps)
+        launches = hsf.hsf_launch_count() - l0
+        line.update({
+            "metric": "QAOA gradients/s (n=28, p=4, 1024 bitstrings, adjoint through every path)",
+            "value": args.steps / (ms / 1e3), "unit": "gradients/s", "ms_per_step": ms / args.steps,
+            "dtype": "c64", "config": {"workload": "c4_qaoa_n28_p4_1024bitstrings", "params": int(pr.num_params),
+                                       "step": "plan + forward + hsf_grad (autograd Function)"},
+            "gpu_launches": int(launches), "clocks": clk.summary()})
+    else:
+        pr = W.workload_c5() if args.workload == "c5" else W.workload_c1()
+        plan = hsf.Plan.from_problem(pr, precision="c64" if args.workload == "c5" else "c128")
+        bits = None
+        if pr.bitstrings is not None:
+            bits = torch.from_numpy(pr.bitstrings.view(np.int64)).cuda()
+        for _ in range(args.warmup):
+            plan.run(bits)
+        hsf.hsf_set_profiling(True)
+        l0 = hsf.hsf_launch_count()
+        with ClockSampler(0) as clk:
+            ms = _timed(torch, stream, lambda: plan.run(bits), args.steps)
+        launches = hsf.hsf_launch_count() - l0
+        st = hsf.hsf_profile_collect(plan.handle)
+        hsf.hsf_set_profiling(False)
+        line.update({
+            "metric": f"HSF circuits/s ({pr.name})", "value": args.steps / (ms / 1e3), "unit": "circuits/s",
+            "ms_per_step": ms / args.steps, "dtype": "c64" if args.workload == "c5" else "c128",
+            "config": {"workload": pr.name, "n": pr.n, "paths": int(plan.info["num_paths"]),
+                       "step": "run only (plan reused)"},
+            "gpu_launches": int(launches),
+            "kernels": {k: {"launches": int(v["launches"]), "ms": v["ms"]} for k, v in st.items() if v["launches"]},
+            "clocks": clk.summary()})
+        plan.close()
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.workload != "c2":
+        bench_other(args)
         return
     import torch
     world = int(os.environ.get("WORLD_SIZE", "1"))

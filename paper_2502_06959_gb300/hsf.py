@@ -300,7 +300,10 @@ class Batch:
         need = ctypes.c_size_t()
         _check(lib.hsf_batch_workspace_size(arr, len(items), ctypes.byref(need)))
         self.ws = torch.empty(need.value, dtype=torch.uint8, device="cuda")
-        self.stream = stream or torch.cuda.Stream()
+        # stream capture needs a non-default stream
+        if stream is None or stream.cuda_stream == 0:
+            stream = torch.cuda.Stream()
+        self.stream = stream
         h = ctypes.c_void_p()
         _check(lib.hsf_batch_create(arr, len(items), self.ws.data_ptr(), self.ws.numel(),
                                     self.stream.cuda_stream, ctypes.byref(h)))

@@ -319,3 +319,17 @@ def test_tensor_core_gemm_c1_full():
         out = plan.run(check=True).cpu().numpy()
         plan.close()
         check(out, ref, "c64")
+
+
+@pytest.mark.parametrize("path_range", [(0, 4), (1 << 23, (1 << 23) + 2)])
+def test_c5_n36_sampled_paths(path_range):
+    """n = 36 (18|18, the full state would be 512 GB), 12 blocks (4^12 paths), 2^20
+    bitstrings, in the benchmark's launch configuration, on path ranges the oracle sums
+    path by path."""
+    pr = W.workload_c5()
+    want, info = O.hsf_amplitudes(pr.n, pr.gates, pr.cut, pr.blocks, bitstrings=pr.bitstrings,
+                                  path_range=path_range)
+    assert info["num_paths"] == 4 ** 12
+    got, ginfo = gpu_amps(pr, "c64", bitstrings=pr.bitstrings, path_range=path_range)
+    assert ginfo["num_paths"] == 4 ** 12
+    check(got, want, "c64")
