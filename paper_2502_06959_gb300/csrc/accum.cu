@@ -235,18 +235,31 @@ __global__ void __launch_bounds__(128) leaf_contract_reg_kernel(LeafArgs a) {
       if ((j == 0 && m < a.m_first) || (j == a.num_parents - 1 && m >= a.m_last)) continue;
       const C *pa = reinterpret_cast<const C *>(a.Pa) + ((uint64_t)j << a.ha) + ba;
       const C *pb = reinterpret_cast<const C *>(a.Pb) + ((uint64_t)j << a.hb) + bb;
+      // both chunks are requested before any arithmetic (16-byte loads: the chunks
+      // start at multiples of 2^C amplitudes)
+      C xa[D], xb[D];
+      if constexpr (sizeof(C) == 8 && D >= 2) {
+#pragma unroll
+        for (int k = 0; k < D; k += 2) {
+          const float4 qa = *reinterpret_cast<const float4 *>(pa + k);
+          const float4 qb = *reinterpret_cast<const float4 *>(pb + k);
+          xa[k].x = qa.x; xa[k].y = qa.y; xa[k + 1].x = qa.z; xa[k + 1].y = qa.w;
+          xb[k].x = qb.x; xb[k].y = qb.y; xb[k + 1].x = qb.z; xb[k + 1].y = qb.w;
+        }
+      } else {
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+          xa[k] = pa[k];
+          xb[k] = pb[k];
+        }
+      }
       R var = R(0), vai = R(0), vbr = R(0), vbi = R(0);
 #pragma unroll
       for (int k = 0; k < D; ++k) {
-        const C x = pa[k];
-        var = fma(la[k].x, x.x, fma(-la[k].y, x.y, var));
-        vai = fma(la[k].x, x.y, fma(la[k].y, x.x, vai));
-      }
-#pragma unroll
-      for (int k = 0; k < D; ++k) {
-        const C x = pb[k];
-        vbr = fma(lb[k].x, x.x, fma(-lb[k].y, x.y, vbr));
-        vbi = fma(lb[k].x, x.y, fma(lb[k].y, x.x, vbi));
+        var = fma(la[k].x, xa[k].x, fma(-la[k].y, xa[k].y, var));
+        vai = fma(la[k].x, xa[k].y, fma(la[k].y, xa[k].x, vai));
+        vbr = fma(lb[k].x, xb[k].x, fma(-lb[k].y, xb[k].y, vbr));
+        vbi = fma(lb[k].x, xb[k].y, fma(lb[k].y, xb[k].x, vbi));
       }
       accr = fma(var, vbr, fma(-vai, vbi, accr));
       acci = fma(var, vbi, fma(vai, vbr, acci));

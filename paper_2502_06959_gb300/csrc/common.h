@@ -37,8 +37,9 @@ struct DevOp {
 // tile bits when fewer are needed) for one assignment of the remaining tile bits.
 constexpr int kMaxSlots = 5;
 // register-resident sweep: amplitudes per thread = 2^kRegBits, CTA tile = 2^kRegTile
-constexpr int kRegBitsC64 = 4, kRegTileC64 = 13;
-constexpr int kRegBitsC128 = 3, kRegTileC128 = 12;
+constexpr int kRegBitsC64 = 4, kRegTileC64 = 12;
+constexpr int kRegBitsC128 = 3, kRegTileC128 = 11;
+constexpr int kSweepThreads = 256;       // 2^(tile - reg bits); two CTAs per SM
 struct DevGroup {
   int32_t slots[kMaxSlots];   // tile bits, ascending
   int32_t first_op;
@@ -73,7 +74,7 @@ struct SweepArgs {
   int32_t stage_mats_off, stage_groups_off;   // byte offsets within the block
   int32_t pad2;
 };
-constexpr int kMaxStageBytes = 48 * 1024;
+constexpr int kMaxStageBytes = 24 * 1024;   // keeps two sweep CTAs resident per SM
 
 // Leaf level contracted at the requested amplitudes: for every parent node (level
 // B-1) and bitstring s, amp(s) += sum_m (L^a_m phi_a)(x_a) * (L^b_m phi_b)(x_b), where

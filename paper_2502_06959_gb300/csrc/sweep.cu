@@ -290,7 +290,7 @@ struct ItemInfo {
 };
 
 template <typename R, int RB, int T>
-__global__ void __launch_bounds__(512, 1) sweep_reg_kernel(SweepArgs a) {
+__global__ void __launch_bounds__(kSweepThreads, 2) sweep_reg_kernel(SweepArgs a) {
   using C = typename CT<R>::T;
   constexpr int NR = 1 << RB;
   constexpr int MAXI = 1 << (T - RB);        // most items a CTA can hold
@@ -504,12 +504,12 @@ cudaError_t launch_sweep(const SweepArgs &a, int precision, cudaStream_t st) {
       auto k = sweep_reg_kernel<float, kRegBitsC64, kRegTileC64>;
       cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       if (e != cudaSuccess) return e;
-      k<<<grid, 512, smem, st>>>(a);
+      k<<<grid, kSweepThreads, smem, st>>>(a);
     } else {
       auto k = sweep_reg_kernel<double, kRegBitsC128, kRegTileC128>;
       cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       if (e != cudaSuccess) return e;
-      k<<<grid, 512, smem, st>>>(a);
+      k<<<grid, kSweepThreads, smem, st>>>(a);
     }
     return cudaGetLastError();
   }
