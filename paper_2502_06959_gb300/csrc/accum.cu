@@ -277,6 +277,105 @@ __global__ void __launch_bounds__(128) leaf_contract_reg_kernel(LeafArgs a) {
   }
 }
 
+// Leaf contraction with the parents' chunks streamed through shared memory: the CTA's
+// bitstrings need 2 x 2^C amplitudes of every parent; they are copied with cp.async a
+// few parents ahead (kDepth stages), so the DRAM / L2 latency of the next parents hides
+// behind the arithmetic on the current one.  Thread roles as in the register variant.
+constexpr int kDepth = 4;
+
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+  const uint32_t sa = (uint32_t)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+template <int CB, int RM>
+__global__ void __launch_bounds__(128) leaf_contract_async_kernel(LeafArgs a) {
+  using C = float2;
+  constexpr int D = 1 << CB;
+  constexpr int SPB = 128 / RM;                // bitstrings per CTA
+  constexpr int STAGE = SPB * 2 * D;           // complex elements per parent
+  __shared__ __align__(16) C buf[kDepth][STAGE];
+  const int m = threadIdx.x % RM;
+  const int sl = threadIdx.x / RM;
+  const int64_t s = (int64_t)blockIdx.x * SPB + sl;
+  const int g = blockIdx.y;
+  const bool on = s < a.S && m < a.r;
+  uint64_t ia = 0, ib = 0;
+  if (s < a.S) {
+    ia = a.ia[s];
+    ib = a.ib[s];
+  }
+  const int ra = (int)(ia & (D - 1)), rb = (int)(ib & (D - 1));
+  const uint64_t ba = ia - ra, bb = ib - rb;
+  C la[D], lb[D];
+  {
+    const C *gLa = reinterpret_cast<const C *>(a.La) + ((size_t)(on ? m : 0) * D + ra) * D;
+    const C *gLb = reinterpret_cast<const C *>(a.Lb) + ((size_t)(on ? m : 0) * D + rb) * D;
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      la[k] = gLa[k];
+      lb[k] = gLb[k];
+    }
+  }
+  const int64_t j0 = (int64_t)g * a.parents_per_group;
+  const int64_t j1 = min(a.num_parents, j0 + a.parents_per_group);
+  const int64_t np = j1 - j0;
+  // copy plan: the RM threads of a bitstring share its 2 chunks of D amplitudes
+  // (D / 2 16-byte pieces each); piece q of the bitstring goes to thread q % RM
+  constexpr int PIECES = 2 * D / 2;            // 16-byte pieces per bitstring and parent
+  auto issue = [&](int64_t jj, int stage) {
+    if (jj < j1 && s < a.S) {
+      const C *pa = reinterpret_cast<const C *>(a.Pa) + ((uint64_t)jj << a.ha) + ba;
+      const C *pb = reinterpret_cast<const C *>(a.Pb) + ((uint64_t)jj << a.hb) + bb;
+      C *dst = buf[stage] + sl * 2 * D;
+      for (int q = m; q < PIECES; q += RM) {
+        const int side = q / (D / 2), off = 2 * (q % (D / 2));
+        cp_async16(dst + side * D + off, (side == 0 ? pa : pb) + off);
+      }
+    }
+    cp_commit();
+  };
+#pragma unroll
+  for (int d = 0; d < kDepth - 1; ++d) issue(j0 + d, d);
+  float accr = 0.f, acci = 0.f;
+  for (int64_t t = 0; t < np; ++t) {
+    issue(j0 + t + kDepth - 1, (int)((t + kDepth - 1) % kDepth));
+    cp_wait<kDepth - 1>();
+    __syncthreads();
+    const int64_t j = j0 + t;
+    const bool use = on && !((j == 0 && m < a.m_first) || (j == a.num_parents - 1 && m >= a.m_last));
+    if (use) {
+      const C *x = buf[t % kDepth] + sl * 2 * D;
+      float var = 0.f, vai = 0.f, vbr = 0.f, vbi = 0.f;
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        const C xa = x[k], xb = x[D + k];
+        var = fmaf(la[k].x, xa.x, fmaf(-la[k].y, xa.y, var));
+        vai = fmaf(la[k].x, xa.y, fmaf(la[k].y, xa.x, vai));
+        vbr = fmaf(lb[k].x, xb.x, fmaf(-lb[k].y, xb.y, vbr));
+        vbi = fmaf(lb[k].x, xb.y, fmaf(lb[k].y, xb.x, vbi));
+      }
+      accr = fmaf(var, vbr, fmaf(-vai, vbi, accr));
+      acci = fmaf(var, vbi, fmaf(vai, vbr, acci));
+    }
+    __syncthreads();                           // the stage is refilled next iteration
+  }
+  cp_wait<0>();
+#pragma unroll
+  for (int o = RM / 2; o > 0; o >>= 1) {
+    accr += __shfl_xor_sync(0xffffffffu, accr, o);
+    acci += __shfl_xor_sync(0xffffffffu, acci, o);
+  }
+  if (m == 0 && s < a.S) {
+    double *dst = a.partial + 2 * ((int64_t)g * a.S + s);
+    dst[0] = (double)accr;
+    dst[1] = (double)acci;
+  }
+}
+
 __global__ void index_prep_kernel(IndexArgs a) {
   const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= a.S) return;
@@ -342,6 +441,15 @@ template <typename R, int CB>
 cudaError_t leaf_reg_dispatch(const LeafArgs &a, cudaStream_t st) {
   const int rm = a.r <= 1 ? 1 : a.r <= 2 ? 2 : a.r <= 4 ? 4 : 8;
   dim3 grid((unsigned)((a.S * rm + 127) / 128), (unsigned)a.num_groups);
+  if constexpr (sizeof(R) == 4 && CB >= 1) {
+    switch (rm) {
+      case 1: leaf_contract_async_kernel<CB, 1><<<grid, 128, 0, st>>>(a); break;
+      case 2: leaf_contract_async_kernel<CB, 2><<<grid, 128, 0, st>>>(a); break;
+      case 4: leaf_contract_async_kernel<CB, 4><<<grid, 128, 0, st>>>(a); break;
+      default: leaf_contract_async_kernel<CB, 8><<<grid, 128, 0, st>>>(a); break;
+    }
+    return cudaGetLastError();
+  }
   switch (rm) {
     case 1: leaf_contract_reg_kernel<R, CB, 1><<<grid, 128, 0, st>>>(a); break;
     case 2: leaf_contract_reg_kernel<R, CB, 2><<<grid, 128, 0, st>>>(a); break;

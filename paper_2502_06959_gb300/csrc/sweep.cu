@@ -164,7 +164,10 @@ __global__ void __launch_bounds__(256) sweep_kernel(SweepArgs a) {
 // assignment of the other tile bits, applies all ops of the group in registers, and
 // writes them back; dense ops are fully unrolled per slot pattern (kcase).
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ uint32_t pad32(uint32_t u) { return u + (u >> 5); }
+// Shared-memory position of tile element u: bits 4..7 and 8..11 are folded into bits
+// 0..3 (XOR), so the 16 lanes of a half-warp land in 16 different 8-byte bank pairs
+// whenever their four lowest varying tile bits have distinct residues mod 4.
+__device__ __forceinline__ uint32_t pad32(uint32_t u) { return u ^ (((u >> 4) ^ (u >> 8)) & 15u); }
 
 // Two consecutive complex entries (16-byte aligned for complex64).
 template <typename C>
@@ -294,7 +297,7 @@ __global__ void __launch_bounds__(kSweepThreads, 2) sweep_reg_kernel(SweepArgs a
   using C = typename CT<R>::T;
   constexpr int NR = 1 << RB;
   constexpr int MAXI = 1 << (T - RB);        // most items a CTA can hold
-  constexpr uint32_t BUF = (1u << T) + (1u << (T - 5));   // padded tile elements
+  constexpr uint32_t BUF = 1u << T;                       // tile elements (swizzled)
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C *sbuf = reinterpret_cast<C *>(smem_raw);   // two tile buffers (double buffering)
   __shared__ ItemInfo<MAXI> info[2];
@@ -498,8 +501,7 @@ cudaError_t launch_sweep(const SweepArgs &a, int precision, cudaStream_t st) {
     const int64_t ipc = 1ll << (T - a.t);
     const int64_t ctas = (items + ipc - 1) / ipc;
     const int grid = (int)(ctas < (1 << 20) ? ctas : (1 << 20));
-    const size_t smem = 2 * (size_t)((1u << T) + (1u << (T - 5))) * (precision == 0 ? 8 : 16) +
-                        (size_t)a.stage_bytes;
+    const size_t smem = 2 * (size_t)(1u << T) * (precision == 0 ? 8 : 16) + (size_t)a.stage_bytes;
     if (precision == 0) {
       auto k = sweep_reg_kernel<float, kRegBitsC64, kRegTileC64>;
       cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
