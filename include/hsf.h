@@ -121,6 +121,8 @@ typedef struct hsf_plan_opts {
 #define HSF_FLAG_NO_LEAF_CONTRACT 2 /* always materialise leaf half states         */
 #define HSF_FLAG_NO_REGISTER_SWEEP 4 /* sweep with one shared-memory pass per op     */
 #define HSF_FLAG_IDENTITY_STORAGE 8  /* store local qubit q at storage bit q          */
+#define HSF_FLAG_REG5 16             /* complex64: 32 amplitudes per thread in the
+                                        register-resident sweep (default 16)          */
 
 typedef struct hsf_plan hsf_plan;
 
@@ -148,6 +150,11 @@ hsf_status hsf_plan_create(const hsf_circuit *circuit, int32_t cut_l,
                            hsf_plan **out);
 
 hsf_status hsf_plan_get_info(const hsf_plan *plan, hsf_plan_info *info);
+
+/* Human-readable description of the plan's programs (storage order, tree levels,
+ * tile passes, register groups, ops) written to buf (NUL-terminated, at most cap bytes).
+ * Returns the size needed including the NUL, or -1 for a NULL plan. */
+int64_t hsf_plan_describe(const hsf_plan *plan, char *buf, int64_t cap);
 
 /* Singular values (descending, only the kept ones) and rank of block k; copies at
  * most cap values into sigma (host). */

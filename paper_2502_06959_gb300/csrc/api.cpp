@@ -216,6 +216,56 @@ hsf_status hsf_plan_get_sigma(const hsf_plan *p, int32_t block, double *sigma, i
   return HSF_OK;
 }
 
+int64_t hsf_plan_describe(const hsf_plan *p, char *buf, int64_t cap) {
+  if (!p) return -1;
+  std::string out;
+  char line[512];
+  for (int s = 0; s < 2; ++s) {
+    const SideH &sd = p->side[s];
+    std::snprintf(line, sizeof line, "side %c: h=%d store=[", s == 0 ? 'a' : 'b', sd.h);
+    out += line;
+    for (int q = 0; q < sd.h; ++q) {
+      std::snprintf(line, sizeof line, "%s%d", q ? "," : "", sd.store[q]);
+      out += line;
+    }
+    out += "]\n";
+    for (size_t k = 0; k < sd.levels.size(); ++k) {
+      const LevelH &lv = sd.levels[k];
+      std::snprintf(line, sizeof line, " level %zu: radix %llu, %zu ops, %zu passes\n", k,
+                    (unsigned long long)p->radix[k], lv.ops.size(), lv.passes.size());
+      out += line;
+      for (size_t pi = 0; pi < lv.passes.size(); ++pi) {
+        const PassH &ps = lv.passes[pi];
+        std::snprintf(line, sizeof line, "  pass %zu: active=0x%llx t=%d ops=%zu groups=%zu\n", pi,
+                      (unsigned long long)ps.active, ps.t, ps.ops.size(), ps.groups.size());
+        out += line;
+        for (size_t g = 0; g < ps.groups.size(); ++g) {
+          const GroupH &G = ps.groups[g];
+          std::snprintf(line, sizeof line, "   group %zu: slots=%d,%d,%d,%d,%d ops[%d..%d):", g, G.slots[0], G.slots[1],
+                        G.slots[2], G.slots[3], G.slots[4], G.first_op, G.first_op + G.num_ops);
+          out += line;
+          for (int o = G.first_op; o < G.first_op + G.num_ops; ++o) {
+            const OpH &op = ps.ops[o];
+            std::snprintf(line, sizeof line, " %s%d(%d%s%s%s%s)", op.type == OP_DENSE ? "D" : "d", op.nq, op.q[0],
+                          op.nq > 1 ? "," : "", op.nq > 1 ? std::to_string(op.q[1]).c_str() : "",
+                          op.nq > 2 ? "," : "", op.nq > 2 ? std::to_string(op.q[2]).c_str() : "");
+            out += line;
+          }
+          out += "\n";
+        }
+      }
+    }
+  }
+  std::snprintf(line, sizeof line, "leaf_bits=%d paths=%llu\n", p->leaf_c, (unsigned long long)p->num_paths);
+  out += line;
+  if (buf && cap > 0) {
+    const int64_t n = std::min<int64_t>(cap - 1, (int64_t)out.size());
+    std::memcpy(buf, out.data(), (size_t)n);
+    buf[n] = 0;
+  }
+  return (int64_t)out.size() + 1;
+}
+
 hsf_status hsf_sync(hsf_plan *p, void *stream) {
   if (!p) return set_error(HSF_EINVAL, "NULL plan");
   CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));

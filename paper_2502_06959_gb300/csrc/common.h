@@ -29,8 +29,10 @@ struct DevOp {
   int32_t kcase;         // dense ops: which unrolled slot pattern applies (see sweep.cu)
   int32_t param;         // gradient programs: angle index of this rotation, else -1
   int32_t kmat;          // gradient programs: offset of K = (dG/dtheta) G^-1 in the pool
-  int32_t pad;
+  int32_t kidx;          // dense ops: index 0..24 of the slot pattern (jump-table dispatch)
+  int32_t pad[2];        // 64 bytes: read as four int4
 };
+static_assert(sizeof(DevOp) == 64, "DevOp is read as four int4");
 
 // A register group: consecutive ops whose dense operands lie in `nslots` tile bits;
 // every thread holds the 2^RB amplitudes spanned by slots[0..RB) (filled with other

@@ -488,6 +488,22 @@ void pack_pass(const PassH &ps, std::vector<DevOp> &dops, std::vector<C> &mats, 
       d.pos[x] = tile_bit[q] >= 0 ? tile_bit[q] : kFixedBit + q;
     }
     d.kcase = kcase;
+    d.kidx = -1;
+    if (G && op.type == OP_DENSE) {
+      // dense index of the slot pattern: 1q J -> J; 2q (J>K) -> 5 + pair; 3q -> 15 + triple
+      static const int pair_idx[5][5] = {{-1, -1, -1, -1, -1}, {0, -1, -1, -1, -1}, {1, 2, -1, -1, -1},
+                                         {3, 4, 5, -1, -1}, {6, 7, 8, 9, -1}};
+      if (op.nq == 1) d.kidx = slot[0];
+      else if (op.nq == 2) d.kidx = 5 + pair_idx[slot[0]][slot[1]];
+      else {
+        int t = 0, found = -1;
+        for (int J = 2; J < 5 && found < 0; ++J)
+          for (int K = 1; K < J && found < 0; ++K)
+            for (int L = 0; L < K && found < 0; ++L, ++t)
+              if (J == slot[0] && K == slot[1] && L == slot[2]) found = t;
+        d.kidx = 15 + found;
+      }
+    }
     if (sizeof(C) == 8 && (mats.size() & 1)) mats.push_back(C{});   // 16-byte aligned rows
     d.mat = (int32_t)mats.size();
     const int per = op.type == OP_DENSE ? (1 << (2 * op.nq)) : (1 << op.nq);
@@ -528,7 +544,7 @@ hsf_status build_programs(hsf_plan &p, bool grad) {
   std::vector<std::pair<bool, int>> order;
   hsf_status st = execution_order(p, order);
   if (st != HSF_OK) return st;
-  p.rbits = p.precision == HSF_PREC_C64 ? kRegBitsC64 : kRegBitsC128;
+  p.rbits = p.precision == HSF_PREC_C64 ? ((p.flags & HSF_FLAG_REG5) ? 5 : kRegBitsC64) : kRegBitsC128;
   int leaf_c = !grad && B > 0 && p.radix[B] <= 8 ? 0 : -1;
   for (int s = 0; s < 2; ++s) {
     SideH &sd = grad ? p.gside[s] : p.side[s];

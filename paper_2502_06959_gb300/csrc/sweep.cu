@@ -252,17 +252,19 @@ __device__ __forceinline__ void ap3(C (&v)[NR], const C *m0) {
 #define KC3(J, K, L) (128 + ((J) << 6) + ((K) << 3) + (L))
 
 template <int NR, typename C>
-__device__ __forceinline__ void apply_dense(C (&v)[NR], int kcase, const C *__restrict__ m) {
-  // only slot patterns inside the 2^RB register block are instantiated
-#define HSF_C1(J) case KC1(J): if constexpr ((1 << (J)) < NR) ap1<J>(v, m); break;
-#define HSF_C2(J, K) case KC2(J, K): if constexpr ((1 << (J)) < NR) ap2<J, K>(v, m); break;
-#define HSF_C3(J, K, L) case KC3(J, K, L): if constexpr ((1 << (J)) < NR) ap3<J, K, L>(v, m); break;
-  switch (kcase) {
-    HSF_C1(0) HSF_C1(1) HSF_C1(2) HSF_C1(3) HSF_C1(4)
-    HSF_C2(1, 0) HSF_C2(2, 0) HSF_C2(2, 1) HSF_C2(3, 0) HSF_C2(3, 1) HSF_C2(3, 2)
-    HSF_C2(4, 0) HSF_C2(4, 1) HSF_C2(4, 2) HSF_C2(4, 3)
-    HSF_C3(2, 1, 0) HSF_C3(3, 1, 0) HSF_C3(3, 2, 0) HSF_C3(3, 2, 1)
-    HSF_C3(4, 1, 0) HSF_C3(4, 2, 0) HSF_C3(4, 2, 1) HSF_C3(4, 3, 0) HSF_C3(4, 3, 1) HSF_C3(4, 3, 2)
+__device__ __forceinline__ void apply_dense(C (&v)[NR], int kidx, const C *__restrict__ m) {
+  // kidx enumerates the slot patterns densely (1q: J; 2q: 5 + pair; 3q: 15 + triple), so the
+  // switch compiles to a jump table; patterns outside the 2^RB register block are empty
+#define HSF_C1(I, J) case I: if constexpr ((1 << (J)) < NR) ap1<J>(v, m); break;
+#define HSF_C2(I, J, K) case I: if constexpr ((1 << (J)) < NR) ap2<J, K>(v, m); break;
+#define HSF_C3(I, J, K, L) case I: if constexpr ((1 << (J)) < NR) ap3<J, K, L>(v, m); break;
+  switch (kidx) {
+    HSF_C1(0, 0) HSF_C1(1, 1) HSF_C1(2, 2) HSF_C1(3, 3) HSF_C1(4, 4)
+    HSF_C2(5, 1, 0) HSF_C2(6, 2, 0) HSF_C2(7, 2, 1) HSF_C2(8, 3, 0) HSF_C2(9, 3, 1) HSF_C2(10, 3, 2)
+    HSF_C2(11, 4, 0) HSF_C2(12, 4, 1) HSF_C2(13, 4, 2) HSF_C2(14, 4, 3)
+    HSF_C3(15, 2, 1, 0) HSF_C3(16, 3, 1, 0) HSF_C3(17, 3, 2, 0) HSF_C3(18, 3, 2, 1)
+    HSF_C3(19, 4, 1, 0) HSF_C3(20, 4, 2, 0) HSF_C3(21, 4, 2, 1) HSF_C3(22, 4, 3, 0) HSF_C3(23, 4, 3, 1)
+    HSF_C3(24, 4, 3, 2)
     default: break;
   }
 #undef HSF_C1
@@ -293,7 +295,7 @@ struct ItemInfo {
 };
 
 template <typename R, int RB, int T>
-__global__ void __launch_bounds__(kSweepThreads, 2) sweep_reg_kernel(SweepArgs a) {
+__global__ void __launch_bounds__(1 << (T - RB), 2) sweep_reg_kernel(SweepArgs a) {
   using C = typename CT<R>::T;
   constexpr int NR = 1 << RB;
   constexpr int MAXI = 1 << (T - RB);        // most items a CTA can hold
@@ -394,41 +396,57 @@ __global__ void __launch_bounds__(kSweepThreads, 2) sweep_reg_kernel(SweepArgs a
         smask |= w[j];
       }
       const uint32_t ubase = ((uint32_t)il << t) | (uint32_t)deposit(inst, tmask & ~smask);
+      // the swizzle is linear over the tile bits and ubase has no slot bits, so the
+      // position of element i is swz(ubase) ^ (XOR of swz(w_j) over the bits j of i)
+      const uint32_t sbase = pad32(ubase);
+      uint32_t sw[RB];
+#pragma unroll
+      for (int j = 0; j < RB; ++j) sw[j] = pad32(w[j]);
       C v[NR];
 #pragma unroll
       for (int i = 0; i < NR; ++i) {
-        uint32_t u = ubase;
+        uint32_t u = sbase;
 #pragma unroll
         for (int j = 0; j < RB; ++j)
-          if (i & (1 << j)) u += w[j];
-        v[i] = s[pad32(u)];
+          if (i & (1 << j)) u ^= sw[j];
+        v[i] = s[u];
       }
       for (int o = G.first_op; o < G.first_op + G.num_ops; ++o) {
-        const DevOp op = ops[o];
-        const C *m = mats + op.mat + (op.digit_stride > 0 ? digit * op.digit_stride : 0);
-        if (op.type == OP_DIAG) {
+        // the op record is read as four int4 into scalars (no local-memory copy)
+        const int4 *o4 = reinterpret_cast<const int4 *>(ops + o);
+        const int4 w0 = o4[0], w1 = o4[1], w2 = o4[2], w3 = o4[3];
+        const int op_type = w0.x, op_nq = w0.y;
+        const int pos_[3] = {w0.z, w0.w, w1.x};
+        const int op_mat = w1.y, op_dstride = w1.z;
+        const int slot_[3] = {w1.w, w2.x, w2.y};
+        const int op_kcase = w2.z, op_kidx = w3.y;
+        (void)w3;
+        const C *m = mats + op_mat + (op_dstride > 0 ? digit * op_dstride : 0);
+        if (op_type == OP_DIAG) {
           // operands are ordered slot operands first (kcase = their count); the
           // others are bits of this thread's instance or of the tile's fixed bits
-          const int ns = op.kcase;
+          const int ns = op_kcase;
           int tpart = 0;
-          for (int x = ns; x < op.nq; ++x) {
-            const int p = op.pos[x];
+#pragma unroll
+          for (int x = 0; x < 3; ++x) {
+            if (x < ns || x >= op_nq) continue;
+            const int p = pos_[x];
             const int bit = p >= kFixedBit ? (int)((my_base >> (p - kFixedBit)) & 1ull) : (int)((ubase >> p) & 1u);
-            tpart |= bit << (op.nq - 1 - x);
+            tpart |= bit << (op_nq - 1 - x);
           }
-          const int sh = op.nq - ns;            // slot bits sit above the fixed part
+          const int sh = op_nq - ns;            // slot bits sit above the fixed part
           if (ns == 0) {
             const C d = m[tpart];
 #pragma unroll
             for (int i = 0; i < NR; ++i) v[i] = cmul(d, v[i]);
           } else if (ns == 1) {
             const C d0 = m[tpart], d1 = m[tpart | (1 << sh)];
-            const int s0 = op.slot[0];
+            const int s0 = slot_[0];
 #pragma unroll
             for (int i = 0; i < NR; ++i) v[i] = cmul(((i >> s0) & 1) ? d1 : d0, v[i]);
           } else if (ns == 2) {
             const C d0 = m[tpart], d1 = m[tpart | (1 << sh)], d2 = m[tpart | (2 << sh)], d3 = m[tpart | (3 << sh)];
-            const int s0 = op.slot[0], s1 = op.slot[1];
+            const int s0 = slot_[0], s1 = slot_[1];
 #pragma unroll
             for (int i = 0; i < NR; ++i) {
               const int b0 = (i >> s0) & 1, b1 = (i >> s1) & 1;
@@ -436,7 +454,7 @@ __global__ void __launch_bounds__(kSweepThreads, 2) sweep_reg_kernel(SweepArgs a
               v[i] = cmul(d, v[i]);
             }
           } else {
-            const int s0 = op.slot[0], s1 = op.slot[1], s2 = op.slot[2];
+            const int s0 = slot_[0], s1 = slot_[1], s2 = slot_[2];
 #pragma unroll
             for (int i = 0; i < NR; ++i) {
               const int idx = (((i >> s0) & 1) << 2) | (((i >> s1) & 1) << 1) | ((i >> s2) & 1);
@@ -444,21 +462,21 @@ __global__ void __launch_bounds__(kSweepThreads, 2) sweep_reg_kernel(SweepArgs a
             }
           }
         } else {
-          apply_dense<NR>(v, op.kcase, m);
+          apply_dense<NR>(v, op_kidx, m);
         }
       }
       // recompute the addresses instead of keeping 2^RB of them live across the ops
-      uint32_t ub2 = ubase;
-      asm volatile("" : "+r"(ub2));
+      uint32_t sb2 = sbase;
+      asm volatile("" : "+r"(sb2));
 #pragma unroll
-      for (int j = 0; j < RB; ++j) asm volatile("" : "+r"(w[j]));
+      for (int j = 0; j < RB; ++j) asm volatile("" : "+r"(sw[j]));
 #pragma unroll
       for (int i = 0; i < NR; ++i) {
-        uint32_t u = ub2;
+        uint32_t u = sb2;
 #pragma unroll
         for (int j = 0; j < RB; ++j)
-          if (i & (1 << j)) u += w[j];
-        s[pad32(u)] = v[i];
+          if (i & (1 << j)) u ^= sw[j];
+        s[u] = v[i];
       }
       __syncthreads();
     }
@@ -503,10 +521,11 @@ cudaError_t launch_sweep(const SweepArgs &a, int precision, cudaStream_t st) {
     const int grid = (int)(ctas < (1 << 20) ? ctas : (1 << 20));
     const size_t smem = 2 * (size_t)(1u << T) * (precision == 0 ? 8 : 16) + (size_t)a.stage_bytes;
     if (precision == 0) {
-      auto k = sweep_reg_kernel<float, kRegBitsC64, kRegTileC64>;
+      auto k = a.rbits == 5 ? sweep_reg_kernel<float, 5, kRegTileC64> : sweep_reg_kernel<float, kRegBitsC64, kRegTileC64>;
+      const int threads = 1 << (kRegTileC64 - (a.rbits == 5 ? 5 : kRegBitsC64));
       cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       if (e != cudaSuccess) return e;
-      k<<<grid, kSweepThreads, smem, st>>>(a);
+      k<<<grid, threads, smem, st>>>(a);
     } else {
       auto k = sweep_reg_kernel<double, kRegBitsC128, kRegTileC128>;
       cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -29,6 +29,7 @@ FLAG_NO_LIGHTCONE = 1
 FLAG_NO_LEAF_CONTRACT = 2
 FLAG_NO_REGISTER_SWEEP = 4
 FLAG_IDENTITY_STORAGE = 8
+FLAG_REG5 = 16
 
 
 class HsfError(RuntimeError):
@@ -92,6 +93,7 @@ SIGNATURES = {
     "hsf_run_static": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_uint64,
                                       ctypes.c_uint64, ctypes.c_uint64, ctypes.c_void_p, ctypes.c_void_p]),
     "hsf_sync": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "hsf_plan_describe": (ctypes.c_int64, [ctypes.c_void_p, ctypes.c_char_p, ctypes.c_int64]),
     "hsf_batch_workspace_size": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(ctypes.c_size_t)]),
     "hsf_batch_create": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_size_t,
                                         ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]),
@@ -324,6 +326,14 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+def hsf_plan_describe(plan: int) -> str:
+    lib = load_library()
+    n = lib.hsf_plan_describe(plan, None, 0)
+    buf = ctypes.create_string_buffer(int(n))
+    lib.hsf_plan_describe(plan, buf, n)
+    return buf.value.decode()
 
 
 def hsf_sync(plan: int, stream: int = 0) -> None:
