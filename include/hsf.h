@@ -123,6 +123,7 @@ typedef struct hsf_plan_opts {
 #define HSF_FLAG_IDENTITY_STORAGE 8  /* store local qubit q at storage bit q          */
 #define HSF_FLAG_REG5 16             /* complex64: 32 amplitudes per thread in the
                                         register-resident sweep (default 16)          */
+#define HSF_FLAG_REG3 32             /* complex64: 8 amplitudes per thread             */
 
 typedef struct hsf_plan hsf_plan;
 

@@ -48,6 +48,21 @@ hsf_status set_error(hsf_status code, const char *fmt, ...) {
 
 const char *last_error() { return g_err.c_str(); }
 
+// Plan-time device work (block SVDs, table uploads) runs on a private non-blocking stream
+// of the calling thread, so planning the next circuit on the host overlaps with work the
+// caller has queued on its own streams.
+cudaStream_t plan_stream() {
+  thread_local cudaStream_t st = nullptr;
+  thread_local int dev = -1;
+  int cur = 0;
+  cudaGetDevice(&cur);
+  if (!st || dev != cur) {
+    cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    dev = cur;
+  }
+  return st;
+}
+
 #define CUDA_TRY(expr)                                                                   \
   do {                                                                                   \
     cudaError_t e_ = (expr);                                                             \
@@ -544,7 +559,9 @@ hsf_status build_programs(hsf_plan &p, bool grad) {
   std::vector<std::pair<bool, int>> order;
   hsf_status st = execution_order(p, order);
   if (st != HSF_OK) return st;
-  p.rbits = p.precision == HSF_PREC_C64 ? ((p.flags & HSF_FLAG_REG5) ? 5 : kRegBitsC64) : kRegBitsC128;
+  p.rbits = p.precision == HSF_PREC_C64
+                ? ((p.flags & HSF_FLAG_REG5) ? 5 : (p.flags & HSF_FLAG_REG3) ? 3 : kRegBitsC64)
+                : kRegBitsC128;
   int leaf_c = !grad && B > 0 && p.radix[B] <= 8 ? 0 : -1;
   for (int s = 0; s < 2; ++s) {
     SideH &sd = grad ? p.gside[s] : p.side[s];
@@ -707,7 +724,8 @@ hsf_status upload_programs(hsf_plan &p, bool grad) {
   void *&table = grad ? p.dev_gtable : p.dev_table;
   CUDA_TRY(cudaMalloc(&table, host.size()));
   if (!grad) p.dev_table_bytes = host.size();
-  CUDA_TRY(cudaMemcpy(table, host.data(), host.size(), cudaMemcpyHostToDevice));
+  CUDA_TRY(cudaMemcpyAsync(table, host.data(), host.size(), cudaMemcpyHostToDevice, plan_stream()));
+  CUDA_TRY(cudaStreamSynchronize(plan_stream()));
   if (!grad) p.launches = launches / 2;
   return HSF_OK;
 }
@@ -733,7 +751,8 @@ hsf_status finish_plan(hsf_plan &p) {
   st = upload_programs(p);
   if (st != HSF_OK) return st;
   CUDA_TRY(cudaMalloc(&p.dev_status, 256));
-  CUDA_TRY(cudaMemset(p.dev_status, 0, 256));
+  CUDA_TRY(cudaMemsetAsync(p.dev_status, 0, 256, plan_stream()));
+  CUDA_TRY(cudaStreamSynchronize(plan_stream()));
   return HSF_OK;
 }
 
@@ -784,14 +803,16 @@ hsf_status run_svd_jobs(const hsf_plan &p, const std::vector<SvdJob> &jobs, std:
   const size_t o_bk = take(bk.size() * 4), o_tb = take(tbeg.size() * 4), o_gb = take(gbeg.size() * 4),
                o_gd = take(gdesc.size() * 4 + 4), o_gm = take(gm.size() * 8 + 8), o_sig = take((size_t)J * 64 * 8),
                o_rank = take((size_t)J * 4), o_x = take(nf * 8), o_y = take(nf * 8), o_sw = take((size_t)J * 4);
+  cudaStream_t pst = plan_stream();
   unsigned char *d = nullptr;
-  CUDA_TRY(cudaMalloc(&d, off));
-  std::unique_ptr<unsigned char, void (*)(unsigned char *)> guard(d, [](unsigned char *q) { cudaFree(q); });
-  CUDA_TRY(cudaMemcpy(d + o_bk, bk.data(), bk.size() * 4, cudaMemcpyHostToDevice));
-  CUDA_TRY(cudaMemcpy(d + o_tb, tbeg.data(), tbeg.size() * 4, cudaMemcpyHostToDevice));
-  CUDA_TRY(cudaMemcpy(d + o_gb, gbeg.data(), gbeg.size() * 4, cudaMemcpyHostToDevice));
-  if (!gdesc.empty()) CUDA_TRY(cudaMemcpy(d + o_gd, gdesc.data(), gdesc.size() * 4, cudaMemcpyHostToDevice));
-  if (!gm.empty()) CUDA_TRY(cudaMemcpy(d + o_gm, gm.data(), gm.size() * 8, cudaMemcpyHostToDevice));
+  CUDA_TRY(cudaMallocAsync((void **)&d, off, pst));
+  std::unique_ptr<unsigned char, void (*)(unsigned char *)> guard(
+      d, [](unsigned char *q) { cudaFreeAsync(q, plan_stream()); });
+  CUDA_TRY(cudaMemcpyAsync(d + o_bk, bk.data(), bk.size() * 4, cudaMemcpyHostToDevice, pst));
+  CUDA_TRY(cudaMemcpyAsync(d + o_tb, tbeg.data(), tbeg.size() * 4, cudaMemcpyHostToDevice, pst));
+  CUDA_TRY(cudaMemcpyAsync(d + o_gb, gbeg.data(), gbeg.size() * 4, cudaMemcpyHostToDevice, pst));
+  if (!gdesc.empty()) CUDA_TRY(cudaMemcpyAsync(d + o_gd, gdesc.data(), gdesc.size() * 4, cudaMemcpyHostToDevice, pst));
+  if (!gm.empty()) CUDA_TRY(cudaMemcpyAsync(d + o_gm, gm.data(), gm.size() * 8, cudaMemcpyHostToDevice, pst));
   BlockSvdArgs a{};
   a.num_blocks = J;
   a.block_k = (const int32_t *)(d + o_bk);
@@ -806,15 +827,15 @@ hsf_status run_svd_jobs(const hsf_plan &p, const std::vector<SvdJob> &jobs, std:
   a.xf = (double *)(d + o_x);
   a.yf = (double *)(d + o_y);
   a.sweeps_used = (int32_t *)(d + o_sw);
-  CUDA_TRY(launch_block_svd(a, 0));
+  CUDA_TRY(launch_block_svd(a, pst));
   g_launches++;
-  CUDA_TRY(cudaDeviceSynchronize());
   std::vector<double> sig((size_t)J * 64), xf(nf), yf(nf);
   std::vector<int32_t> rank(J);
-  CUDA_TRY(cudaMemcpy(sig.data(), d + o_sig, sig.size() * 8, cudaMemcpyDeviceToHost));
-  CUDA_TRY(cudaMemcpy(rank.data(), d + o_rank, rank.size() * 4, cudaMemcpyDeviceToHost));
-  CUDA_TRY(cudaMemcpy(xf.data(), d + o_x, nf * 8, cudaMemcpyDeviceToHost));
-  CUDA_TRY(cudaMemcpy(yf.data(), d + o_y, nf * 8, cudaMemcpyDeviceToHost));
+  CUDA_TRY(cudaMemcpyAsync(sig.data(), d + o_sig, sig.size() * 8, cudaMemcpyDeviceToHost, pst));
+  CUDA_TRY(cudaMemcpyAsync(rank.data(), d + o_rank, rank.size() * 4, cudaMemcpyDeviceToHost, pst));
+  CUDA_TRY(cudaMemcpyAsync(xf.data(), d + o_x, nf * 8, cudaMemcpyDeviceToHost, pst));
+  CUDA_TRY(cudaMemcpyAsync(yf.data(), d + o_y, nf * 8, cudaMemcpyDeviceToHost, pst));
+  CUDA_TRY(cudaStreamSynchronize(pst));
   for (int j = 0; j < J; ++j) {
     BlockH &r = out[j];
     const BlockH &src = p.blocks[jobs[j].block];

@@ -298,7 +298,7 @@ template <typename R, int RB, int T>
 __global__ void __launch_bounds__(1 << (T - RB), 2) sweep_reg_kernel(SweepArgs a) {
   using C = typename CT<R>::T;
   constexpr int NR = 1 << RB;
-  constexpr int MAXI = 1 << (T - RB);        // most items a CTA can hold
+  constexpr int MAXI = 64;                   // most items a CTA holds (t >= T - 6)
   constexpr uint32_t BUF = 1u << T;                       // tile elements (swizzled)
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C *sbuf = reinterpret_cast<C *>(smem_raw);   // two tile buffers (double buffering)
@@ -514,15 +514,17 @@ __global__ void __launch_bounds__(1 << (T - RB), 2) sweep_reg_kernel(SweepArgs a
 cudaError_t launch_sweep(const SweepArgs &a, int precision, cudaStream_t st) {
   if (a.num_nodes <= 0) return cudaSuccess;
   const int64_t items = a.num_nodes * (int64_t)a.tiles_per_node;
-  if (a.groups && a.t >= a.rbits) {
-    const int T = precision == 0 ? kRegTileC64 : kRegTileC128;
+  const int T = precision == 0 ? kRegTileC64 : kRegTileC128;
+  if (a.groups && a.t >= a.rbits && a.t >= T - 6) {
     const int64_t ipc = 1ll << (T - a.t);
     const int64_t ctas = (items + ipc - 1) / ipc;
     const int grid = (int)(ctas < (1 << 20) ? ctas : (1 << 20));
     const size_t smem = 2 * (size_t)(1u << T) * (precision == 0 ? 8 : 16) + (size_t)a.stage_bytes;
     if (precision == 0) {
-      auto k = a.rbits == 5 ? sweep_reg_kernel<float, 5, kRegTileC64> : sweep_reg_kernel<float, kRegBitsC64, kRegTileC64>;
-      const int threads = 1 << (kRegTileC64 - (a.rbits == 5 ? 5 : kRegBitsC64));
+      auto k = a.rbits == 5   ? sweep_reg_kernel<float, 5, kRegTileC64>
+               : a.rbits == 3 ? sweep_reg_kernel<float, 3, kRegTileC64>
+                              : sweep_reg_kernel<float, kRegBitsC64, kRegTileC64>;
+      const int threads = 1 << (kRegTileC64 - a.rbits);
       cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       if (e != cudaSuccess) return e;
       k<<<grid, threads, smem, st>>>(a);

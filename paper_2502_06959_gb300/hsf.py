@@ -30,6 +30,7 @@ FLAG_NO_LEAF_CONTRACT = 2
 FLAG_NO_REGISTER_SWEEP = 4
 FLAG_IDENTITY_STORAGE = 8
 FLAG_REG5 = 16
+FLAG_REG3 = 32
 
 
 class HsfError(RuntimeError):
