@@ -56,6 +56,9 @@ def parse():
                          "c5: n=36, 2^20 bitstrings; c1: n=12 all amplitudes")
     ap.add_argument("--gemm", default="bf16x3", choices=["fp32", "bf16x3", "tf32x3", "tf32"])
     ap.add_argument("--tune", action="store_true", help="c3: autotune one circuit per qubit count")
+    ap.add_argument("--max-n", type=int, default=0, help="c3 profiling aid: drop circuits above this n")
+    ap.add_argument("--largest-only", action="store_true",
+                    help="c3 profiling aid: run only the largest circuit once (no graph)")
     return ap.parse_args()
 
 
@@ -225,6 +228,17 @@ def bench_other(args):
             "scaling": "weak", "vs_baseline": None, "data": "synthetic"}
     if args.workload == "c3":
         probs = W.workload_c3()
+        if args.max_n:
+            probs = [pr for pr in probs if pr.n <= args.max_n]
+        if args.largest_only:
+            pr = max(probs, key=lambda q: (q.n, len(q.blocks)))
+            plan = hsf.Plan.from_problem(pr, precision="c64", gemm=args.gemm)
+            window = min(1 << pr.n, 1 << 24)
+            out = plan.run(window=window, check=True)
+            torch.cuda.synchronize()
+            print(json.dumps({"largest": pr.name, "paths": int(plan.info["num_paths"]), "window": window}))
+            plan.close()
+            return
         tuned = {}
         if args.tune:
             import tempfile
