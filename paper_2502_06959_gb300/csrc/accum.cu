@@ -291,12 +291,21 @@ __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_grou
 template <int N>
 __device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
+// bytes of the cp.async stage ring of leaf_contract_async_kernel<CB, RM>
+constexpr size_t leaf_ring_bytes(int cb, int rm) { return (size_t)kDepth * (128 / rm) * ((2u << cb) + 2) * 8; }
+
 template <int CB, int RM>
 __global__ void __launch_bounds__(128) leaf_contract_async_kernel(LeafArgs a) {
   using C = float2;
   constexpr int D = 1 << CB;
   constexpr int SPB = 128 / RM;                // bitstrings per CTA
-  constexpr int STAGE = SPB * 2 * D;           // complex elements per parent
+  // Stage row of one bitstring: its a chunk then its b chunk, padded by one 16-byte
+  // piece so that consecutive bitstrings start 4 banks apart and the 16-byte reads of
+  // the (up to 8) bitstrings of a warp fall in distinct banks.
+  constexpr int SB = 2 * D + 2;
+  constexpr int STAGE = SPB * SB;
+  constexpr int PIECES = D;                    // 16-byte pieces per bitstring and parent
+  constexpr int HALF = D / 2;                  // pieces per side
   __shared__ __align__(16) C buf[kDepth][STAGE];
   const int m = threadIdx.x % RM;
   const int sl = threadIdx.x / RM;
@@ -309,7 +318,6 @@ __global__ void __launch_bounds__(128) leaf_contract_async_kernel(LeafArgs a) {
     ib = a.ib[s];
   }
   const int ra = (int)(ia & (D - 1)), rb = (int)(ib & (D - 1));
-  const uint64_t ba = ia - ra, bb = ib - rb;
   C la[D], lb[D];
   {
     const C *gLa = reinterpret_cast<const C *>(a.La) + ((size_t)(on ? m : 0) * D + ra) * D;
@@ -323,17 +331,24 @@ __global__ void __launch_bounds__(128) leaf_contract_async_kernel(LeafArgs a) {
   const int64_t j0 = (int64_t)g * a.parents_per_group;
   const int64_t j1 = min(a.num_parents, j0 + a.parents_per_group);
   const int64_t np = j1 - j0;
-  // copy plan: the RM threads of a bitstring share its 2 chunks of D amplitudes
-  // (D / 2 16-byte pieces each); piece q of the bitstring goes to thread q % RM
-  constexpr int PIECES = 2 * D / 2;            // 16-byte pieces per bitstring and parent
+  // the RM threads of a bitstring (adjacent lanes of one warp) copy its pieces:
+  // piece q = m + i*RM; pieces [0, HALF) are the a chunk, [HALF, D) the b chunk
+  const C *pa = reinterpret_cast<const C *>(a.Pa) + (ia - ra);
+  const C *pb = reinterpret_cast<const C *>(a.Pb) + (ib - rb);
   auto issue = [&](int64_t jj, int stage) {
     if (jj < j1 && s < a.S) {
-      const C *pa = reinterpret_cast<const C *>(a.Pa) + ((uint64_t)jj << a.ha) + ba;
-      const C *pb = reinterpret_cast<const C *>(a.Pb) + ((uint64_t)jj << a.hb) + bb;
-      C *dst = buf[stage] + sl * 2 * D;
-      for (int q = m; q < PIECES; q += RM) {
-        const int side = q / (D / 2), off = 2 * (q % (D / 2));
-        cp_async16(dst + side * D + off, (side == 0 ? pa : pb) + off);
+      C *row = buf[stage] + sl * SB;
+      const C *sa = pa + ((uint64_t)jj << a.ha);
+      const C *sb = pb + ((uint64_t)jj << a.hb);
+#pragma unroll
+      for (int i = 0; i < (PIECES + RM - 1) / RM; ++i) {
+        const int q = m + i * RM;
+        if (q < PIECES) {
+          if (q < HALF)
+            cp_async16(row + 2 * q, sa + 2 * q);
+          else
+            cp_async16(row + 2 * q, sb + 2 * (q - HALF));
+        }
       }
     }
     cp_commit();
@@ -342,26 +357,32 @@ __global__ void __launch_bounds__(128) leaf_contract_async_kernel(LeafArgs a) {
   for (int d = 0; d < kDepth - 1; ++d) issue(j0 + d, d);
   float accr = 0.f, acci = 0.f;
   for (int64_t t = 0; t < np; ++t) {
+    // parent t has landed for this thread; the warp barrier publishes the other lanes'
+    // pieces and orders every lane's reads of parent t-1 before its stage is refilled
+    cp_wait<kDepth - 2>();
+    __syncwarp();
     issue(j0 + t + kDepth - 1, (int)((t + kDepth - 1) % kDepth));
-    cp_wait<kDepth - 1>();
-    __syncthreads();
     const int64_t j = j0 + t;
     const bool use = on && !((j == 0 && m < a.m_first) || (j == a.num_parents - 1 && m >= a.m_last));
     if (use) {
-      const C *x = buf[t % kDepth] + sl * 2 * D;
+      const float4 *x = reinterpret_cast<const float4 *>(buf[t % kDepth] + sl * SB);
       float var = 0.f, vai = 0.f, vbr = 0.f, vbi = 0.f;
 #pragma unroll
-      for (int k = 0; k < D; ++k) {
-        const C xa = x[k], xb = x[D + k];
-        var = fmaf(la[k].x, xa.x, fmaf(-la[k].y, xa.y, var));
-        vai = fmaf(la[k].x, xa.y, fmaf(la[k].y, xa.x, vai));
-        vbr = fmaf(lb[k].x, xb.x, fmaf(-lb[k].y, xb.y, vbr));
-        vbi = fmaf(lb[k].x, xb.y, fmaf(lb[k].y, xb.x, vbi));
+      for (int k2 = 0; k2 < HALF; ++k2) {
+        const float4 xa = x[k2], xb = x[HALF + k2];
+        const C a0 = la[2 * k2], a1 = la[2 * k2 + 1], b0 = lb[2 * k2], b1 = lb[2 * k2 + 1];
+        var = fmaf(a0.x, xa.x, fmaf(-a0.y, xa.y, var));
+        vai = fmaf(a0.x, xa.y, fmaf(a0.y, xa.x, vai));
+        var = fmaf(a1.x, xa.z, fmaf(-a1.y, xa.w, var));
+        vai = fmaf(a1.x, xa.w, fmaf(a1.y, xa.z, vai));
+        vbr = fmaf(b0.x, xb.x, fmaf(-b0.y, xb.y, vbr));
+        vbi = fmaf(b0.x, xb.y, fmaf(b0.y, xb.x, vbi));
+        vbr = fmaf(b1.x, xb.z, fmaf(-b1.y, xb.w, vbr));
+        vbi = fmaf(b1.x, xb.w, fmaf(b1.y, xb.z, vbi));
       }
       accr = fmaf(var, vbr, fmaf(-vai, vbi, accr));
       acci = fmaf(var, vbi, fmaf(vai, vbr, acci));
     }
-    __syncthreads();                           // the stage is refilled next iteration
   }
   cp_wait<0>();
 #pragma unroll
@@ -439,17 +460,25 @@ cudaError_t launch_window(const WindowArgs &a, int precision, cudaStream_t st) {
 
 template <typename R, int CB>
 cudaError_t leaf_reg_dispatch(const LeafArgs &a, cudaStream_t st) {
-  const int rm = a.r <= 1 ? 1 : a.r <= 2 ? 2 : a.r <= 4 ? 4 : 8;
-  dim3 grid((unsigned)((a.S * rm + 127) / 128), (unsigned)a.num_groups);
+  int rm = a.r <= 1 ? 1 : a.r <= 2 ? 2 : a.r <= 4 ? 4 : 8;
   if constexpr (sizeof(R) == 4 && CB >= 1) {
+    // keep the stage ring (kDepth x 128/rm bitstrings x (2^(CB+1)+2) complex) within the
+    // 48 KB of static shared memory: threads with m >= r idle
+    while (rm < 8 && leaf_ring_bytes(CB, rm) > 48 * 1024) rm *= 2;
+    dim3 grid((unsigned)((a.S * rm + 127) / 128), (unsigned)a.num_groups);
     switch (rm) {
-      case 1: leaf_contract_async_kernel<CB, 1><<<grid, 128, 0, st>>>(a); break;
-      case 2: leaf_contract_async_kernel<CB, 2><<<grid, 128, 0, st>>>(a); break;
+      case 1:
+        if constexpr (leaf_ring_bytes(CB, 1) <= 48 * 1024) leaf_contract_async_kernel<CB, 1><<<grid, 128, 0, st>>>(a);
+        break;
+      case 2:
+        if constexpr (leaf_ring_bytes(CB, 2) <= 48 * 1024) leaf_contract_async_kernel<CB, 2><<<grid, 128, 0, st>>>(a);
+        break;
       case 4: leaf_contract_async_kernel<CB, 4><<<grid, 128, 0, st>>>(a); break;
       default: leaf_contract_async_kernel<CB, 8><<<grid, 128, 0, st>>>(a); break;
     }
     return cudaGetLastError();
   }
+  dim3 grid((unsigned)((a.S * rm + 127) / 128), (unsigned)a.num_groups);
   switch (rm) {
     case 1: leaf_contract_reg_kernel<R, CB, 1><<<grid, 128, 0, st>>>(a); break;
     case 2: leaf_contract_reg_kernel<R, CB, 2><<<grid, 128, 0, st>>>(a); break;

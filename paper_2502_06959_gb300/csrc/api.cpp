@@ -461,8 +461,8 @@ hsf_status hsf_run(hsf_plan *p, const uint64_t *bits, size_t num, uint64_t windo
         g.paths = np;
         g.ha = p->na;
         g.hb = p->nb;
-        g.row_index = ia;
-        g.col_index = ib;
+        g.perm_a = perm_of(p->side[0]);
+        g.perm_b = perm_of(p->side[1]);
         g.M = M;
         g.N = N;
         g.window = count;

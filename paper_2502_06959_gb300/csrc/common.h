@@ -153,11 +153,15 @@ struct BlockSvdArgs {
 
 // Window / full output on the tensor cores (gemm_tc.cu): complex rank-P product as one
 // real GEMM with split-BF16 (mode 1), split-TF32 (mode 2) or TF32 (mode 3) operands.
+struct PermArgs {
+  int32_t h;
+  int32_t store[64];     // storage bit of each local qubit
+};
 struct PathGemmArgs {
   const void *A, *B;               // complex64 leaf states [paths][2^ha] / [paths][2^hb]
   int64_t paths;
   int32_t ha, hb;
-  const uint64_t *row_index, *col_index;   // storage indices of x_a < M and x_b < N
+  PermArgs perm_a, perm_b;         // storage bit of each local qubit of x_a / x_b
   int64_t M, N;
   uint64_t window;
   double *out, *comp;              // FP64 output and Neumaier compensation
@@ -216,10 +220,6 @@ cudaError_t launch_zero(double *p, int64_t count, cudaStream_t st);
 cudaError_t launch_block_svd(const BlockSvdArgs &a, cudaStream_t st);
 cudaError_t launch_leaf_contract(const LeafArgs &a, int precision, cudaStream_t st);
 cudaError_t launch_index_prep(const IndexArgs &a, cudaStream_t st);
-struct PermArgs {
-  int32_t h;
-  int32_t store[64];     // storage bit of each local qubit
-};
 // dst[i] = storage index of local index i, i < count.
 cudaError_t launch_range_index(uint64_t *dst, int64_t count, const PermArgs &perm, cudaStream_t st);
 

@@ -19,6 +19,7 @@
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
 
+#include <algorithm>
 #include <cstdint>
 #include <mutex>
 
@@ -55,63 +56,102 @@ struct PackArgs {
   const float2 *src;            // leaf states [paths][2^h]
   int32_t h;
   int64_t paths;
-  const uint64_t *index;        // storage index of each output row / column
   int64_t rows;                 // M (a side) or N (b side)
   int64_t rows_pad;             // padded row count of one part
   int32_t side;                 // 0: a operand (2 x rows_pad rows), 1: b operand
   int64_t kpad;                 // padded K'' (row length of the operand)
   void *dst;                    // bf16 or fp32 operand, row-major [rows][kpad]
-  int32_t mode;
+  // Rows are enumerated in storage order: enumeration index j has storage index
+  // sum_k bit_k(j) << upos[k] and row (local index) sum_k bit_k(j) << ibit[k], with
+  // upos ascending, so consecutive j read consecutive amplitudes.
+  int32_t w;                    // enumerated bits: rows <= 2^w
+  int8_t upos[64], ibit[64];
 };
 
-// One thread per (operand row r, path p): writes all split terms of K' = 2P columns
-// that path p contributes to row r.
+constexpr int kPackRows = 32, kPackPaths = 64;
+
+// One CTA moves a tile of 32 rows x 64 paths: the reads run along the storage index of
+// each path's leaf state, the tile is transposed in shared memory, and the writes run
+// along K (paths) of each operand row.  Each path contributes K' = 2P columns per row;
+// each split term is a further block of 2P columns.
 template <int MODE>
-__global__ void pack_kernel(PackArgs a) {
-  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t r = blockIdx.y + (int64_t)gridDim.y * blockIdx.z;
-  const int64_t nrows = a.side == 0 ? 2 * a.rows_pad : a.rows_pad;
-  if (p >= a.paths || r >= nrows) return;
-  const int64_t part = a.side == 0 ? r / a.rows_pad : 0;    // 0: real rows, 1: imaginary rows
-  const int64_t i = a.side == 0 ? r % a.rows_pad : r;
-  float2 v = make_float2(0.f, 0.f);
-  if (i < a.rows) v = a.src[((uint64_t)p << a.h) + a.index[i]];
-  // the two K' entries of this path: columns p and P + p
-  float x0, x1;
-  if (a.side == 0) {
-    x0 = part == 0 ? v.x : v.y;       // Re row: ( Re a, -Im a );  Im row: ( Im a, Re a )
-    x1 = part == 0 ? -v.y : v.x;
-  } else {
-    x0 = v.x;                         // b column: ( Re b, Im b )
-    x1 = v.y;
+__global__ void __launch_bounds__(256) pack_kernel(PackArgs a) {
+  __shared__ float2 tile[kPackRows][kPackPaths + 1];
+  const int lane = threadIdx.x & 31, wy = threadIdx.x >> 5;
+  const int64_t j = (int64_t)blockIdx.x * kPackRows + lane;
+  const int64_t p0 = ((int64_t)blockIdx.z * gridDim.y + blockIdx.y) * kPackPaths;
+  uint64_t u = 0;
+  int64_t i = 0;
+  for (int k = 0; k < a.w; ++k)
+    if ((j >> k) & 1) {
+      u |= 1ull << a.upos[k];
+      i |= 1ll << a.ibit[k];
+    }
+  const int rv = (j >> a.w) == 0 && i < a.rows;
+#pragma unroll
+  for (int t = 0; t < kPackPaths / 8; ++t) {
+    const int pl = wy + 8 * t;
+    const int64_t p = p0 + pl;
+    float2 v = make_float2(0.f, 0.f);
+    if (rv && p < a.paths) v = a.src[((uint64_t)p << a.h) + u];
+    tile[lane][pl] = v;
   }
-  const int64_t P = a.paths;
-  const int64_t kp = 2 * P;
-  float h0, l0, h1, l1;
-  split<MODE == 3 ? 2 : MODE>(x0, h0, l0);
-  split<MODE == 3 ? 2 : MODE>(x1, h1, l1);
-  // term order: a = [hi, hi, lo], b = [hi, lo, hi]  (hi*hi + hi*lo + lo*hi)
-  float t0[3], t1[3];
-  if (MODE == 3) {
-    t0[0] = h0; t1[0] = h1;
-  } else if (a.side == 0) {
-    t0[0] = h0; t0[1] = h0; t0[2] = l0;
-    t1[0] = h1; t1[1] = h1; t1[2] = l1;
-  } else {
-    t0[0] = h0; t0[1] = l0; t0[2] = h0;
-    t1[0] = h1; t1[1] = l1; t1[2] = h1;
-  }
-  const int nterms = MODE == 3 ? 1 : 3;
-  for (int t = 0; t < nterms; ++t) {
-    const int64_t c0 = t * kp + p, c1 = t * kp + P + p;
-    if (MODE == 1) {
-      __nv_bfloat16 *d = reinterpret_cast<__nv_bfloat16 *>(a.dst) + r * a.kpad;
-      d[c0] = __float2bfloat16_rn(t0[t]);
-      d[c1] = __float2bfloat16_rn(t1[t]);
-    } else {
-      float *d = reinterpret_cast<float *>(a.dst) + r * a.kpad;
-      d[c0] = t0[t];
-      d[c1] = t1[t];
+  __syncthreads();
+  const int64_t P = a.paths, kp = 2 * P;
+  constexpr int nterms = MODE == 3 ? 1 : 3;
+#pragma unroll 1
+  for (int t = 0; t < kPackRows / 8; ++t) {
+    const int rl = wy + 8 * t;
+    const int64_t ir = __shfl_sync(0xffffffffu, i, rl);
+    if (!__shfl_sync(0xffffffffu, rv, rl)) continue;        // padding rows stay zero
+#pragma unroll
+    for (int hp = 0; hp < 2; ++hp) {
+      const int pl = lane + 32 * hp;
+      const int64_t p = p0 + pl;
+      if (p >= P) continue;
+      const float2 v = tile[rl][pl];
+#pragma unroll
+      for (int part = 0; part < 2; ++part) {
+        if (a.side == 1 && part == 1) break;
+        // the two K' entries of this path: columns p and P + p
+        //   a Re row: ( Re a, -Im a );  a Im row: ( Im a, Re a );  b column: ( Re b, Im b )
+        float x0, x1;
+        if (a.side == 0) {
+          x0 = part == 0 ? v.x : v.y;
+          x1 = part == 0 ? -v.y : v.x;
+        } else {
+          x0 = v.x;
+          x1 = v.y;
+        }
+        float h0, l0, h1, l1;
+        split<MODE == 3 ? 2 : MODE>(x0, h0, l0);
+        split<MODE == 3 ? 2 : MODE>(x1, h1, l1);
+        // term order: a = [hi, hi, lo], b = [hi, lo, hi]  (hi*hi + hi*lo + lo*hi)
+        float t0[3], t1[3];
+        if (MODE == 3) {
+          t0[0] = h0; t1[0] = h1;
+        } else if (a.side == 0) {
+          t0[0] = h0; t0[1] = h0; t0[2] = l0;
+          t1[0] = h1; t1[1] = h1; t1[2] = l1;
+        } else {
+          t0[0] = h0; t0[1] = l0; t0[2] = h0;
+          t1[0] = h1; t1[1] = l1; t1[2] = h1;
+        }
+        const int64_t r = part * a.rows_pad + ir;
+#pragma unroll
+        for (int tt = 0; tt < nterms; ++tt) {
+          const int64_t c0 = tt * kp + p, c1 = tt * kp + P + p;
+          if (MODE == 1) {
+            __nv_bfloat16 *d = reinterpret_cast<__nv_bfloat16 *>(a.dst) + r * a.kpad;
+            d[c0] = __float2bfloat16_rn(t0[tt]);
+            d[c1] = __float2bfloat16_rn(t1[tt]);
+          } else {
+            float *d = reinterpret_cast<float *>(a.dst) + r * a.kpad;
+            d[c0] = t0[tt];
+            d[c1] = t1[tt];
+          }
+        }
+      }
     }
   }
 }
@@ -128,6 +168,8 @@ struct EpiArgs {
   int32_t k_tiles;
   int32_t kind;          // 0: kind::f16 (bf16 operands), 1: kind::tf32
   int32_t *err;          // device error word (0 = ok)
+  int32_t num_m, num_n;  // output tiles along the real rows and along x_b
+  int32_t group_m;       // tile order: groups of group_m row tiles, rows fastest
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -191,7 +233,13 @@ __global__ void __launch_bounds__(128, 1) gemm_kernel(const __grid_constant__ CU
   __shared__ uint32_t tmem_base_sh;
   __shared__ int abort_sh;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int n0 = blockIdx.x * kBN, m0 = blockIdx.y * kBM;
+  // grouped tile order: the CTAs in flight cover group_m row tiles x a few column tiles,
+  // so the column operand tiles are read from DRAM once and the row operand stays in L2
+  const int per_group = ep.group_m * ep.num_n;
+  const int first_m = (int)(blockIdx.x / per_group) * ep.group_m;
+  const int gm = min(ep.group_m, ep.num_m - first_m);
+  const int local = (int)(blockIdx.x % per_group);
+  const int m0 = (first_m + local % gm) * kBM, n0 = (local / gm) * kBN;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStages; ++s) {
@@ -228,7 +276,7 @@ __global__ void __launch_bounds__(128, 1) gemm_kernel(const __grid_constant__ CU
       if (!mbar_wait(&empty_bar[s], ph ^ 1)) { atomicExch(ep.err, 1); abort_sh = 1; break; }
       mbar_expect_tx(&full_bar[s], 2 * kTileBytes);
       const int kx = kt * (ep.kind == 0 ? 64 : 32);  // K elements per 128-byte row
-      tma_load_2d(sA + s * kTileBytes, &tmA, kx, m0 + (m0 >= 0 ? 0 : 0), &full_bar[s]);
+      tma_load_2d(sA + s * kTileBytes, &tmA, kx, m0, &full_bar[s]);
       tma_load_2d(sB + s * kTileBytes, &tmB, kx, n0, &full_bar[s]);
     }
   } else if (warp == 1 && lane == 0) {
@@ -369,20 +417,30 @@ cudaError_t launch_path_gemm(const PathGemmArgs &g, cudaStream_t st) {
     pa.src = reinterpret_cast<const float2 *>(side == 0 ? g.A : g.B);
     pa.h = side == 0 ? g.ha : g.hb;
     pa.paths = g.paths;
-    pa.index = side == 0 ? g.row_index : g.col_index;
     pa.rows = side == 0 ? g.M : g.N;
     pa.rows_pad = side == 0 ? Mp : Np;
     pa.side = side;
     pa.kpad = kpad;
     pa.dst = side == 0 ? (void *)opA : (void *)opB;
-    pa.mode = g.mode;
-    const int64_t nrows = side == 0 ? 2 * Mp : Np;
-    const unsigned gy = (unsigned)(nrows < 65535 ? nrows : 65535);
-    const unsigned gz = (unsigned)((nrows + gy - 1) / gy);
-    dim3 grid((unsigned)((g.paths + 127) / 128), gy, gz);
-    if (g.mode == 1) pack_kernel<1><<<grid, 128, 0, st>>>(pa);
-    else if (g.mode == 2) pack_kernel<2><<<grid, 128, 0, st>>>(pa);
-    else pack_kernel<3><<<grid, 128, 0, st>>>(pa);
+    // enumerate the rows' local bits in ascending storage-bit order
+    const PermArgs &pm = side == 0 ? g.perm_a : g.perm_b;
+    int w = 0;
+    while (w < pa.h && (1ll << w) < pa.rows) ++w;
+    pa.w = w;
+    int order[64];
+    for (int q = 0; q < w; ++q) order[q] = q;
+    std::sort(order, order + w, [&](int x, int y) { return pm.store[x] < pm.store[y]; });
+    for (int k = 0; k < w; ++k) {
+      pa.upos[k] = (int8_t)pm.store[order[k]];
+      pa.ibit[k] = (int8_t)order[k];
+    }
+    const int64_t ptiles = (g.paths + kPackPaths - 1) / kPackPaths;
+    const unsigned gy = (unsigned)(ptiles < 65535 ? ptiles : 65535);
+    const unsigned gz = (unsigned)((ptiles + gy - 1) / gy);
+    dim3 grid((unsigned)(((1ll << w) + kPackRows - 1) / kPackRows), gy, gz);
+    if (g.mode == 1) pack_kernel<1><<<grid, 256, 0, st>>>(pa);
+    else if (g.mode == 2) pack_kernel<2><<<grid, 256, 0, st>>>(pa);
+    else pack_kernel<3><<<grid, 256, 0, st>>>(pa);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
@@ -404,8 +462,12 @@ cudaError_t launch_path_gemm(const PathGemmArgs &g, cudaStream_t st) {
   const size_t smem = (size_t)2 * kStages * kTileBytes + 1024;
   e = cudaFuncSetAttribute(gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  dim3 grid((unsigned)(Np / kBN), (unsigned)(2 * Mp / kBM));
-  gemm_kernel<<<grid, 128, smem, st>>>(tmA, tmB, ep);
+  ep.num_m = (int32_t)(2 * Mp / kBM);
+  ep.num_n = (int32_t)(Np / kBN);
+  // as many row tiles per group as keep about 48 MB of the row operand in L2
+  const int64_t row_tile_bytes = (int64_t)kBM * kpad * esz;
+  ep.group_m = (int32_t)std::max<int64_t>(1, std::min<int64_t>(ep.num_m, (48ll << 20) / row_tile_bytes));
+  gemm_kernel<<<(unsigned)((int64_t)ep.num_m * ep.num_n), 128, smem, st>>>(tmA, tmB, ep);
   return cudaGetLastError();
 }
 

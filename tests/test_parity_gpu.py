@@ -276,6 +276,58 @@ def test_leaf_contraction_matches_materialised_leaves(prec, seed):
         check(got, want, prec)
 
 
+def _leaf_rank_problem(rank, tail, seed):
+    """A 12-qubit brickwork whose last block has Schmidt rank 1, 2, 4 or 8, followed by
+    `tail` further layers (which widen the leaf program's light cone)."""
+    pr = W.random_brickwork(12, 5, 3, block_after=(2,), block_kind="rzz", block_len=2, seed=seed)
+    rng = np.random.default_rng(seed + 1000)
+    g = list(pr.gates)
+    blk = []
+
+    def add(gate):
+        blk.append(len(g))
+        g.append(gate)
+
+    if rank == 1:                       # CZ CZ = identity: one product term
+        add(W.Gate("cz", (6, 5)))
+        add(W.Gate("cz", (6, 5)))
+    elif rank == 2:
+        add(W.Gate("rzz", (6, 5), param=float(rng.uniform(0, 2 * np.pi))))
+    elif rank == 4:
+        add(W.Gate("cx", (5, 6)))
+        add(W.Gate("matrix", (6,), matrix=W.haar_u2(rng)))
+        add(W.Gate("matrix", (5,), matrix=W.haar_u2(rng)))
+        add(W.Gate("rzz", (6, 5), param=float(rng.uniform(0, 2 * np.pi))))
+    else:                               # three crossing pairs: rank 2^3
+        add(W.Gate("cz", (6, 5)))
+        add(W.Gate("cz", (7, 4)))
+        add(W.Gate("cz", (8, 3)))
+    for t in range(tail):
+        W._u2_layer(rng, g, range(12))
+        W._cz_brickwork(g, 12, 5, t % 2)
+    return W.Problem(n=12, gates=g, cut=5, blocks=list(pr.blocks) + [blk])
+
+
+@pytest.mark.parametrize("prec", ["c128", "c64"])
+@pytest.mark.parametrize("rank", [1, 2, 4, 8])
+@pytest.mark.parametrize("tail", [0, 1, 2])
+def test_leaf_contraction_every_rank_and_width(prec, rank, tail):
+    """Leaf contraction for every operator count the kernels specialise on (1, 2, 4, 8
+    threads per bitstring) and leaf programs of several widths, against the state
+    vector and against materialised leaves."""
+    from paper_2502_06959_gb300 import hsf
+    pr = _leaf_rank_problem(rank, tail, seed=70 + rank + 10 * tail)
+    rng = np.random.default_rng(rank + 10 * tail)
+    bs = W.random_bitstrings(rng, pr.n, 300)
+    ref = O.schrodinger(pr.n, pr.gates)[bs.astype(np.int64)]
+    got, info = gpu_amps(pr, prec, bitstrings=bs)
+    if tail == 0:
+        assert info["leaf_bits"] > 0
+    check(got, ref, prec)
+    got2, _ = gpu_amps(pr, prec, bitstrings=bs, flags=hsf.FLAG_NO_LEAF_CONTRACT)
+    check(got2, ref, prec)
+
+
 def test_c2_plan_uses_leaf_contraction_and_register_kernel():
     pr = W.workload_c2(num_bitstrings=16)
     plan = H().Plan.from_problem(pr)
