@@ -75,6 +75,11 @@ struct SweepArgs {
   int32_t stage_bytes;
   int32_t stage_mats_off, stage_groups_off;   // byte offsets within the block
   int32_t pad2;
+  // Register kernel with a tile of 2^T elements and 2^L threads (t >= L): element
+  // tid + k * 2^L of a CTA's tile buffer belongs to item item_of[k] and sits at storage
+  // offset deposit(tid, active_mask) | elem_off[k] from that item's tile origin.
+  uint64_t elem_off[32];
+  uint8_t item_of[32];
 };
 constexpr int kMaxStageBytes = 24 * 1024;   // keeps two sweep CTAs resident per SM
 

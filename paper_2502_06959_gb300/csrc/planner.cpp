@@ -241,52 +241,114 @@ void merge_one_qubit_runs(std::vector<OpH> &ops) {
   ops.swap(out);
 }
 
-// Absorb every one-qubit op into the next two-qubit op on its qubit (nothing else
-// touches the qubit in between, so applying it right before that op is the same):
-// U followed by a CZ / RZZ / CX on (a, b) becomes one 4x4 op, which costs what the two
-// one-qubit ops cost and makes the diagonal gate free.
+// Matrix of op for Schmidt digit d (ops without digits have one matrix), as a dense
+// 2^nq x 2^nq matrix.
+std::vector<cd> dense_of(const OpH &op, int d) {
+  const int dim = 1 << op.nq;
+  const size_t per = op.type == OP_DENSE ? (size_t)dim * dim : (size_t)dim;
+  const cd *m = op.m.data() + (op.digits > 1 ? (size_t)d * per : 0);
+  if (op.type == OP_DENSE) return std::vector<cd>(m, m + per);
+  std::vector<cd> full((size_t)dim * dim, 0.0);
+  for (int i = 0; i < dim; ++i) full[(size_t)i * (dim + 1)] = m[i];
+  return full;
+}
+
+// A one-qubit matrix u on operand x (x = 0 is the matrix MSB) of a two-qubit op, as 4x4.
+std::vector<cd> embed_operand(const std::vector<cd> &u, int x) {
+  std::vector<cd> e(16, 0.0);
+  for (int i = 0; i < 4; ++i)
+    for (int j = 0; j < 4; ++j) {
+      const int ix = x == 0 ? i >> 1 : i & 1, jx = x == 0 ? j >> 1 : j & 1;
+      const int io = x == 0 ? i & 1 : i >> 1, jo = x == 0 ? j & 1 : j >> 1;
+      if (io == jo) e[i * 4 + j] = u[ix * 2 + jx];
+    }
+  return e;
+}
+
+// op <- (u on operand x) applied before (after = false) or after (after = true) op, for
+// every digit of either; both stay diagonal when both are.
+void fold_one_qubit(OpH &op, const OpH &u, int x, bool after) {
+  const int D = std::max(op.digits, u.digits);
+  const bool diag = op.type == OP_DIAG && u.type == OP_DIAG;
+  std::vector<cd> out;
+  for (int d = 0; d < D; ++d) {
+    const std::vector<cd> e = op.nq == 2 ? embed_operand(dense_of(u, d), x) : dense_of(u, d);
+    const std::vector<cd> prod =
+        after ? matmul(e, dense_of(op, d), 1 << op.nq) : matmul(dense_of(op, d), e, 1 << op.nq);
+    if (diag) {
+      for (int i = 0; i < (1 << op.nq); ++i) out.push_back(prod[(size_t)i * ((1 << op.nq) + 1)]);
+    } else {
+      out.insert(out.end(), prod.begin(), prod.end());
+    }
+  }
+  op.type = diag ? OP_DIAG : OP_DENSE;
+  op.m.swap(out);
+  op.digits = D;
+  if (u.block >= 0) op.block = u.block;
+}
+
+// Fold one-qubit ops into two-qubit ops (forward-only programs):
+//  * into the next two-qubit op on the qubit (nothing touches the qubit in between, so
+//    applying the one-qubit op right before it is the same): U then CZ / RZZ / CX on
+//    (a, b) becomes one 4x4 op, which costs what the one-qubit op costs and makes the
+//    diagonal gate free.  A Schmidt factor on one qubit folds the same way; the 4x4 op
+//    then carries one matrix per digit.
+//  * a one-qubit op with no later two-qubit op on its qubit folds into the previous op
+//    on the qubit (applied after it), when that op is a two-qubit op or a factor.
 void absorb_into_two_qubit(std::vector<OpH> &ops) {
   std::vector<char> dead(ops.size(), 0);
   std::map<int, int> pending;   // qubit -> index of its unabsorbed one-qubit op
   for (size_t o = 0; o < ops.size(); ++o) {
     OpH &op = ops[o];
-    if (op.nq == 1 && op.digits == 1 && op.block < 0) {
+    if (op.nq == 1 && op.param < 0) {
+      auto it = pending.find(op.q[0]);
+      if (it != pending.end() && op.digits == 1 && op.block < 0) {
+        // a one-qubit op right after another one (e.g. after a Schmidt factor): one op
+        fold_one_qubit(ops[it->second], op, 0, true);
+        dead[o] = 1;
+        continue;
+      }
       pending[op.q[0]] = (int)o;
       continue;
     }
-    if (op.nq == 2 && op.digits == 1 && op.block < 0) {
+    if (op.nq == 2 && op.digits == 1 && op.block < 0 && op.param < 0) {
       for (int x = 0; x < 2; ++x) {
         auto it = pending.find(op.q[x]);
         if (it == pending.end()) continue;
         const OpH &u = ops[it->second];
-        std::vector<cd> um = u.m;
-        if (u.type == OP_DIAG) um = {u.m[0], 0.0, 0.0, u.m[1]};
-        // U on operand x (x = 0 is the matrix MSB) as a 4x4 acting before op
-        std::vector<cd> e(16, 0.0);
-        for (int i = 0; i < 4; ++i)
-          for (int j = 0; j < 4; ++j) {
-            const int ix = x == 0 ? i >> 1 : i & 1, jx = x == 0 ? j >> 1 : j & 1;
-            const int io = x == 0 ? i & 1 : i >> 1, jo = x == 0 ? j & 1 : j >> 1;
-            if (io == jo) e[i * 4 + j] = um[ix * 2 + jx];
-          }
-        std::vector<cd> full = op.m;
-        if (op.type == OP_DIAG) {
-          full.assign(16, 0.0);
-          for (int i = 0; i < 4; ++i) full[i * 5] = op.m[i];
+        if (u.digits > 1 && op.digits > 1) {            // two factors: keep apart
+          pending.erase(it);
+          continue;
         }
-        std::vector<cd> prod = matmul(full, e, 4);
-        if (op.type == OP_DIAG && u.type == OP_DIAG) {
-          op.m = {prod[0], prod[5], prod[10], prod[15]};
-        } else {
-          op.type = OP_DENSE;
-          op.m = prod;
-        }
+        fold_one_qubit(op, u, x, false);
         dead[it->second] = 1;
         pending.erase(it);
       }
       continue;
     }
     for (int x = 0; x < op.nq; ++x) pending.erase(op.q[x]);
+  }
+  // what is left pending has no later op on its qubit: fold it into the previous one
+  for (auto &kv : pending) {
+    const int o = kv.second;
+    const OpH &u = ops[o];
+    if (u.digits > 1 || u.block >= 0) continue;
+    int prev = -1;
+    for (int j = o - 1; j >= 0 && prev < 0; --j) {
+      if (dead[j]) continue;
+      for (int x = 0; x < ops[j].nq; ++x)
+        if (ops[j].q[x] == u.q[0]) prev = j;
+    }
+    if (prev < 0 || ops[prev].param >= 0) continue;
+    OpH &tgt = ops[prev];
+    if (tgt.nq == 2) {
+      fold_one_qubit(tgt, u, tgt.q[0] == u.q[0] ? 0 : 1, true);
+    } else if (tgt.nq == 1 && tgt.digits > 1) {
+      fold_one_qubit(tgt, u, 0, true);
+    } else {
+      continue;
+    }
+    dead[o] = 1;
   }
   std::vector<OpH> out;
   for (size_t o = 0; o < ops.size(); ++o)

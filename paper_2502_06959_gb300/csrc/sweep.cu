@@ -332,6 +332,21 @@ __global__ void __launch_bounds__(1 << (T - RB), 2) sweep_reg_kernel(SweepArgs a
     __syncthreads();
   }
 
+  // Fast copy path (t >= LNT, no |0> start): thread tid moves elements tid + k * NT,
+  // k < NR, whose swizzled position is closed-form (the swizzle folds tile bits 4..11
+  // into bits 0..3: bits 4..7 come from tid, bits 8..11 from tid and k).
+  constexpr int LNT = T - RB;
+  constexpr int NT = 1 << LNT;
+  const bool fast = t >= LNT && !a.init_zero;
+  const uint64_t dep_tid = contiguous ? (uint64_t)tid : deposit((uint64_t)tid, a.active_mask);
+  const uint32_t tsw = (uint32_t)tid ^ ((((uint32_t)tid >> 4) ^ ((uint32_t)tid >> 8)) & 15u);
+  auto fast_pos = [&](int k) -> uint32_t {
+    if constexpr (LNT >= 8)
+      return (tsw ^ (((uint32_t)k << (LNT - 8)) & 15u)) + ((uint32_t)k << LNT);
+    else
+      return pad32((uint32_t)tid + ((uint32_t)k << LNT));
+  };
+
   // Start the copies of the batch beginning at item0 into buffer `slot`.
   auto prefetch = [&](int64_t item0, int slot) {
     ItemInfo<MAXI> &in = info[slot];
@@ -351,6 +366,16 @@ __global__ void __launch_bounds__(1 << (T - RB), 2) sweep_reg_kernel(SweepArgs a
     if (tid == 0) in.nvalid = nvalid;
     __syncthreads();
     C *sb = sbuf + slot * BUF;
+    if (fast) {
+#pragma unroll
+      for (int k = 0; k < NR; ++k) {
+        const int j = a.item_of[k];
+        if (j < nvalid)
+          cp_async_elem<(int)sizeof(C)>(sb + fast_pos(k), src + in.src[j] + (int64_t)(dep_tid | a.elem_off[k]));
+      }
+      cp_async_commit();
+      return;
+    }
     const uint32_t total = (uint32_t)nvalid << t;
     for (uint32_t e = tid; e < total; e += blockDim.x) {
       const int j = (int)(e >> t);
@@ -395,7 +420,11 @@ __global__ void __launch_bounds__(1 << (T - RB), 2) sweep_reg_kernel(SweepArgs a
         w[j] = 1u << G.slots[j];
         smask |= w[j];
       }
-      const uint32_t ubase = ((uint32_t)il << t) | (uint32_t)deposit(inst, tmask & ~smask);
+      // this thread's instance bits fill the tile bits that are not slots (ascending)
+      uint32_t dep = inst;
+#pragma unroll
+      for (int j = 0; j < RB; ++j) dep = insert_zero(dep, G.slots[j]);
+      const uint32_t ubase = ((uint32_t)il << t) | dep;
       // the swizzle is linear over the tile bits and ubase has no slot bits, so the
       // position of element i is swz(ubase) ^ (XOR of swz(w_j) over the bits j of i)
       const uint32_t sbase = pad32(ubase);
@@ -481,9 +510,15 @@ __global__ void __launch_bounds__(1 << (T - RB), 2) sweep_reg_kernel(SweepArgs a
       __syncthreads();
     }
 
-    // ---- store (pairs of amplitudes per thread when the tile is contiguous) ----
+    // ---- store ----
     const uint32_t total = (uint32_t)nvalid << t;
-    if (contiguous && t >= 1) {
+    if (fast) {
+#pragma unroll
+      for (int k = 0; k < NR; ++k) {
+        const int j = a.item_of[k];
+        if (j < nvalid) dst[in.dst[j] + (int64_t)(dep_tid | a.elem_off[k])] = s[fast_pos(k)];
+      }
+    } else if (contiguous && t >= 1) {
       for (uint32_t e = 2 * tid; e < total; e += 2 * blockDim.x) {
         const int j = (int)(e >> t);
         const uint32_t u = e & tmask;
@@ -511,11 +546,27 @@ __global__ void __launch_bounds__(1 << (T - RB), 2) sweep_reg_kernel(SweepArgs a
 
 }  // namespace
 
-cudaError_t launch_sweep(const SweepArgs &a, int precision, cudaStream_t st) {
-  if (a.num_nodes <= 0) return cudaSuccess;
-  const int64_t items = a.num_nodes * (int64_t)a.tiles_per_node;
+cudaError_t launch_sweep(const SweepArgs &args, int precision, cudaStream_t st) {
+  if (args.num_nodes <= 0) return cudaSuccess;
+  const int64_t items = args.num_nodes * (int64_t)args.tiles_per_node;
   const int T = precision == 0 ? kRegTileC64 : kRegTileC128;
-  if (a.groups && a.t >= a.rbits && a.t >= T - 6) {
+  if (args.groups && args.t >= args.rbits && args.t >= T - 6) {
+    // element k of a thread (element tid + k * 2^L of the tile buffer, L = T - rbits)
+    SweepArgs a = args;
+    const int L = T - a.rbits, nk = 1 << a.rbits;
+    for (int k = 0; k < 32; ++k) {
+      a.elem_off[k] = 0;
+      a.item_of[k] = 255;
+    }
+    if (a.t >= L)
+      for (int k = 0; k < nk && k < 32; ++k) {
+        const uint64_t within = (uint64_t)(k & ((1 << (a.t - L)) - 1)) << L;   // tile-local bits >= L
+        uint64_t dep = 0, m = a.active_mask;
+        for (int b = 0; m; ++b, m &= m - 1)
+          if ((within >> b) & 1ull) dep |= m & (~m + 1);
+        a.elem_off[k] = dep;
+        a.item_of[k] = (uint8_t)(k >> (a.t - L));
+      }
     const int64_t ipc = 1ll << (T - a.t);
     const int64_t ctas = (items + ipc - 1) / ipc;
     const int grid = (int)(ctas < (1 << 20) ? ctas : (1 << 20));
@@ -536,6 +587,7 @@ cudaError_t launch_sweep(const SweepArgs &a, int precision, cudaStream_t st) {
     }
     return cudaGetLastError();
   }
+  const SweepArgs &a = args;
   const int grid = (int)(items < (1 << 20) ? items : (1 << 20));
   if (precision == 0) {
     const size_t smem = (size_t)8 << a.t;
