@@ -124,6 +124,10 @@ typedef struct hsf_plan_opts {
 #define HSF_FLAG_REG5 16             /* complex64: 32 amplitudes per thread in the
                                         register-resident sweep (default 16)          */
 #define HSF_FLAG_REG3 32             /* complex64: 8 amplitudes per thread             */
+#define HSF_FLAG_NO_TC_LEVEL 64      /* complex64: sweep every tree level on the CUDA
+                                        cores; by default a level whose program acts
+                                        only on the 6 lowest storage bits runs as a
+                                        TF32x3 tensor-core product per Schmidt digit */
 
 typedef struct hsf_plan hsf_plan;
 
@@ -270,6 +274,7 @@ typedef enum hsf_kernel_kind {
   HSF_KERNEL_WINDOW = 3,     /* window / full path GEMM                      */
   HSF_KERNEL_OTHER = 4,      /* zero-fill, index maps, finalize              */
   HSF_KERNEL_LEAF = 5,       /* leaf level contracted at the bitstrings      */
+  HSF_KERNEL_LEVEL_MMA = 6,  /* tree level as a tensor-core product per digit */
   HSF_NUM_KERNEL_KINDS = 8
 } hsf_kernel_kind;
 

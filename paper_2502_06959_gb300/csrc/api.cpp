@@ -231,10 +231,12 @@ int64_t hsf_plan_describe(const hsf_plan *p, char *buf, int64_t cap) {
     out += "]\n";
     for (size_t k = 0; k < sd.levels.size(); ++k) {
       const LevelH &lv = sd.levels[k];
-      std::snprintf(line, sizeof line, " level %zu: radix %llu, %zu ops, %zu passes\n", k,
-                    (unsigned long long)p->radix[k], lv.ops.size(), lv.passes.size());
+      std::snprintf(line, sizeof line, " level %zu: radix %llu, %zu ops, %s\n", k,
+                    (unsigned long long)p->radix[k], lv.ops.size(),
+                    lv.mma ? "tensor-core product (TF32x3) on the 6 lowest storage bits"
+                           : (std::to_string(lv.passes.size()) + " passes").c_str());
       out += line;
-      for (size_t pi = 0; pi < lv.passes.size(); ++pi) {
+      for (size_t pi = 0; pi < lv.passes.size() && !lv.mma; ++pi) {
         const PassH &ps = lv.passes[pi];
         std::snprintf(line, sizeof line, "  pass %zu: active=0x%llx t=%d ops=%zu groups=%zu\n", pi,
                       (unsigned long long)ps.active, ps.t, ps.ops.size(), ps.groups.size());
@@ -356,7 +358,24 @@ hsf_status hsf_run(hsf_plan *p, const uint64_t *bits, size_t num, uint64_t windo
         void *dst = ws + L.off_buf[s][k & 1];
         const void *par = ws + L.off_buf[s][(k + 1) & 1];
         const LevelH &lv = sd.levels[k];
-        for (size_t pi = 0; pi < lv.passes.size(); ++pi) {
+        if (lv.mma) {
+          LevelMmaArgs g{};
+          g.parent = (const float *)par;
+          g.child = (float *)dst;
+          g.w = (unsigned char *)p->dev_table + lv.w_off;
+          g.h = sd.h;
+          g.radix = (int32_t)p->radix[k];
+          g.node_lo = lo;
+          g.num_nodes = hi - lo;
+          g.parent_lo = prev_lo;
+          g.err = p->dev_status;
+          const double amps = (double)(hi - lo) * (double)(1ull << sd.h);
+          const double parents = (double)((hi - 1) / g.radix - lo / g.radix + 1) * (double)(1ull << sd.h);
+          // TF32x3: three 128 x 128 x 128 real products per 64-amplitude row
+          LAUNCH(HSF_KERNEL_LEVEL_MMA, (amps + parents) * csz, 3.0 * 2.0 * 128.0 * 128.0 * (amps / 64.0),
+                 launch_level_mma(g, st));
+        }
+        for (size_t pi = 0; pi < lv.passes.size() && !lv.mma; ++pi) {
           const PassH &ps = lv.passes[pi];
           SweepArgs a{};
           a.ops = (const DevOp *)((unsigned char *)p->dev_table + ps.ops_off);

@@ -19,18 +19,19 @@ enum : int32_t { OP_DENSE = 0, OP_DIAG = 1 };
 constexpr int32_t kFixedBit = 64;   // pos >= kFixedBit: storage bit (pos - 64) outside the tile
 
 struct DevOp {
+  // the first 16 bytes are all a dense op needs in the register kernel
   int32_t type;          // OP_DENSE: 2^nq x 2^nq matrix; OP_DIAG: 2^nq phases
-  int32_t nq;            // 1..3
-  int32_t pos[3];        // tile bit of each operand qubit, pos[0] = matrix MSB
+  int32_t kidx;          // dense ops: index 0..24 of the slot pattern (jump-table dispatch)
   int32_t mat;           // offset (complex elements) into the program's matrix pool
   int32_t digit_stride;  // > 0: matrix = pool[mat + digit * digit_stride] (Schmidt factor)
-  int32_t slot[3];       // register slot of each operand, -1 if none; dense ops have
-                         // slot[0] > slot[1] > slot[2] (matrix MSB on the highest slot)
+  int32_t nq;            // 1..3
   int32_t kcase;         // dense ops: which unrolled slot pattern applies (see sweep.cu)
   int32_t param;         // gradient programs: angle index of this rotation, else -1
   int32_t kmat;          // gradient programs: offset of K = (dG/dtheta) G^-1 in the pool
-  int32_t kidx;          // dense ops: index 0..24 of the slot pattern (jump-table dispatch)
-  int32_t pad[2];        // 64 bytes: read as four int4
+  int32_t pos[3];        // tile bit of each operand qubit, pos[0] = matrix MSB
+  int32_t slot[3];       // register slot of each operand, -1 if none; dense ops have
+                         // slot[0] > slot[1] > slot[2] (matrix MSB on the highest slot)
+  int32_t pad[2];        // 64 bytes: read as int4 words
 };
 static_assert(sizeof(DevOp) == 64, "DevOp is read as four int4");
 
@@ -175,6 +176,28 @@ struct PathGemmArgs {
   int32_t *err;                    // device status word (bounded waits)
 };
 size_t path_gemm_operand_bytes(int mode, int64_t M, int64_t N, int64_t paths);
+
+// Tensor-core tree level (gemm_tc.cu): child node g (digit m = g % radix) =
+// U_m (x) I applied to its parent, where U_m acts on the kMmaBits lowest storage bits.
+// Each parent is a row-major [2^(h - kMmaBits)][2^kMmaBits] complex matrix whose rows
+// ("columns" of U_m) are contiguous, so the level is a real GEMM with K = 2^(kMmaBits+1).
+constexpr int kMmaBits = 6;
+constexpr int kMmaMinH = kMmaBits + 7;           // at least one 128-row tile per node
+constexpr size_t kMmaWPartBytes = 128 * 128 * 4;  // one TF32 part of W (64 KB)
+struct LevelMmaArgs {
+  const float *parent;     // previous level buffer, complex64 as float pairs
+  float *child;            // this level's buffer
+  const void *w;           // per digit: W hi image then W lo image (kMmaWPartBytes each)
+  int32_t h;
+  int32_t radix;
+  int64_t node_lo;         // level-global index of the first node held in child
+  int64_t num_nodes;
+  int64_t parent_lo;       // level-global index of the first node held in parent
+  int32_t *err;            // device status word (bounded waits)
+};
+cudaError_t launch_level_mma(const LevelMmaArgs &a, cudaStream_t st);
+// host: the kernel's shared-memory image of W (128 x 128 real, K-major, 128-byte swizzle)
+void level_mma_image(const double *w, float *hi, float *lo);
 
 // Adjoint sweep over one pass of one tree level, in reverse op order (adjoint.cu).
 struct AdjointArgs {

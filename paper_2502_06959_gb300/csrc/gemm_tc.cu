@@ -21,6 +21,7 @@
 
 #include <algorithm>
 #include <cstdint>
+#include <cstring>
 #include <mutex>
 
 #include "common.h"
@@ -361,6 +362,240 @@ __global__ void __launch_bounds__(128, 1) gemm_kernel(const __grid_constant__ CU
 }
 
 // ---------------------------------------------------------------------------
+// Tensor-core tree level
+// ---------------------------------------------------------------------------
+// Child g of a level whose program sits on the 6 lowest storage bits is U_m applied to
+// every 64-amplitude row of its parent (m = g % radix).  Real form, k = 2 r + (re, im):
+// child[row][n] = sum_k parent[row][k] W_m[n][k], W_m 128 x 128.  A CTA serves one digit:
+// it keeps W_m (TF32 hi and lo parts, 128 KB) in shared memory and walks 128-row tiles
+// of the parents (MMA M = 128 rows, N = 128, K = 128 in four 32-float chunks).  Four
+// producer warps split each chunk into TF32 hi and lo parts in the MMA's 128-byte
+// swizzled layout; one thread issues hi*hi + lo*hi + hi*lo (tcgen05.mma kind::tf32)
+// into one of two TMEM accumulators; four epilogue warps read the other back and
+// write the child rows.  Every wait is bounded; on expiry the CTA records an error,
+// drains its MMAs, frees TMEM and returns.
+constexpr int kLvlStages = 3;
+constexpr int kLvlChunk = 128 * 128;            // bytes: 128 rows x 32 floats
+constexpr int kLvlThreads = 320;                // 4 low-part, 4 epilogue, 1 MMA, 1 TMA warp
+constexpr size_t kLvlSmem = 2 * kMmaWPartBytes + (size_t)kLvlStages * 2 * kLvlChunk + 1024;
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint64_t *bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ void mma_tf32(uint32_t d, uint64_t da, uint64_t db, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n"
+      ::"r"(d), "l"(da), "l"(db), "r"(idesc), "r"(acc)
+      : "memory");
+}
+// byte offset of (row, 16-byte piece q) in a 128-row K-major tile with 128-byte swizzle
+__device__ __forceinline__ uint32_t swz_off(int row, int q) {
+  return (uint32_t)((row >> 3) * 1024 + (row & 7) * 128 + ((q ^ (row & 7)) << 4));
+}
+
+__global__ void __launch_bounds__(kLvlThreads, 1) level_mma_kernel(const __grid_constant__ CUtensorMap tmP,
+                                                                  LevelMmaArgs a) {
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+  uint8_t *sW = smem;                                   // W hi: 4 chunks, then W lo: 4 chunks
+  uint8_t *sA = smem + 2 * kMmaWPartBytes;              // stage s: hi chunk (raw FP32), lo chunk
+  __shared__ __align__(8) uint64_t loaded[kLvlStages], full_bar[kLvlStages], empty_bar[kLvlStages], tfull[2],
+      tempty[2], drain;
+  __shared__ uint32_t tmem_sh;
+  __shared__ volatile int abort_sh;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t radix = a.radix;
+  const int m = blockIdx.y;
+  const int64_t g_first = a.node_lo + ((m - a.node_lo % radix) % radix + radix) % radix;
+  const int64_t g_end = a.node_lo + a.num_nodes;
+  const int64_t nchild = g_first < g_end ? (g_end - g_first + radix - 1) / radix : 0;
+  const int tb = a.h - kMmaMinH;                        // 2^tb row tiles per node
+  const int64_t units = nchild << tb;
+  const int64_t nchunks = units > blockIdx.x ? ((units - 1 - blockIdx.x) / gridDim.x + 1) * 4 : 0;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kLvlStages; ++s) {
+      mbar_init(&loaded[s], 1);
+      mbar_init(&full_bar[s], 128);
+      mbar_init(&empty_bar[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&tfull[b], 1);
+      mbar_init(&tempty[b], 128);
+    }
+    mbar_init(&drain, 1);
+    abort_sh = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  {
+    const int4 *gw = reinterpret_cast<const int4 *>(reinterpret_cast<const uint8_t *>(a.w) +
+                                                    (size_t)m * 2 * kMmaWPartBytes);
+    int4 *sw4 = reinterpret_cast<int4 *>(sW);
+    for (int i = threadIdx.x; i < (int)(2 * kMmaWPartBytes / 16); i += blockDim.x) sw4[i] = gw[i];
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // visible to the tensor core
+  }
+  if (warp == 8) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_sh)),
+                 "r"(256)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_sh;
+
+  if (warp < 4) {
+    // ---- low parts: lo = x - (x with its 13 low mantissa bits cleared) ----
+    // The TMA lands the raw FP32 chunk in the stage's hi slot; kind::tf32 reads only the
+    // top 19 bits of each operand, so the hi part is that truncation and lo is exact.
+    const int t = threadIdx.x;
+    for (int64_t it = 0; it < nchunks && !abort_sh; ++it) {
+      const int s = (int)(it % kLvlStages);
+      const uint32_t ph = (uint32_t)(it / kLvlStages) & 1u;
+      if (!mbar_wait(&loaded[s], ph)) {
+        atomicExch(a.err, 4);
+        abort_sh = 1;
+        break;
+      }
+      const uint8_t *hi = sA + s * 2 * kLvlChunk;
+      uint8_t *lo = sA + s * 2 * kLvlChunk + kLvlChunk;
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const uint32_t off = (uint32_t)(t + 128 * i) * 16;    // same swizzled place in both
+        const float4 x = *reinterpret_cast<const float4 *>(hi + off);
+        float4 l;
+        l.x = x.x - __uint_as_float(__float_as_uint(x.x) & 0xffffe000u);
+        l.y = x.y - __uint_as_float(__float_as_uint(x.y) & 0xffffe000u);
+        l.z = x.z - __uint_as_float(__float_as_uint(x.z) & 0xffffe000u);
+        l.w = x.w - __uint_as_float(__float_as_uint(x.w) & 0xffffe000u);
+        *reinterpret_cast<float4 *>(lo + off) = l;
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      mbar_arrive(&full_bar[s]);
+    }
+  } else if (warp == 9) {
+    // ---- TMA: chunk c = chunk c % 4 of unit blockIdx.x + (c / 4) * gridDim.x ----
+    if (lane == 0) {
+      int64_t issued = 0;
+      for (int64_t it = 0; it < nchunks && !abort_sh; ++it) {
+        const int s = (int)(it % kLvlStages);
+        const uint32_t ph = (uint32_t)(it / kLvlStages) & 1u;
+        if (!mbar_wait(&empty_bar[s], ph ^ 1)) {
+          atomicExch(a.err, 9);
+          abort_sh = 1;
+          break;
+        }
+        const int64_t u = blockIdx.x + (it >> 2) * gridDim.x;
+        const int64_t g = g_first + (u >> tb) * radix;
+        const int64_t row0 = ((g / radix - a.parent_lo) << (a.h - kMmaBits)) + ((u & ((1 << tb) - 1)) << 7);
+        mbar_expect_tx(&loaded[s], kLvlChunk);
+        tma_load_2d(sA + s * 2 * kLvlChunk, &tmP, (int)(it & 3) * 32, (int)row0, &loaded[s]);
+        issued = it + 1;
+      }
+      // every load issued has landed before the CTA can exit (matters only on abort)
+      for (int64_t it = issued > kLvlStages ? issued - kLvlStages : 0; it < issued; ++it)
+        if (!mbar_wait(&loaded[it % kLvlStages], (uint32_t)(it / kLvlStages) & 1u)) atomicExch(a.err, 10);
+    }
+    __syncwarp();
+  } else if (warp == 8) {
+    // ---- MMA issuer ----
+    if (lane == 0) {
+      const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(128 >> 3) << 17) |
+                             ((uint32_t)(128 >> 4) << 24);
+      int64_t it = 0, tu = 0;
+      for (int64_t u = blockIdx.x; u < units && !abort_sh; u += gridDim.x, ++tu) {
+        const int b = (int)(tu & 1);
+        if (!mbar_wait(&tempty[b], ((uint32_t)(tu >> 1) & 1u) ^ 1u)) {
+          atomicExch(a.err, 5);
+          abort_sh = 1;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t d = tmem + (uint32_t)(b * 128);
+        bool ok = true;
+        for (int kc = 0; kc < 4; ++kc, ++it) {
+          const int s = (int)(it % kLvlStages);
+          const uint32_t ph = (uint32_t)(it / kLvlStages) & 1u;
+          if (!mbar_wait(&full_bar[s], ph)) {
+            atomicExch(a.err, 6);
+            abort_sh = 1;
+            ok = false;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint64_t ahi = make_desc(sA + s * 2 * kLvlChunk), alo = make_desc(sA + s * 2 * kLvlChunk + kLvlChunk);
+          const uint64_t whi = make_desc(sW + kc * kLvlChunk), wlo = make_desc(sW + kMmaWPartBytes + kc * kLvlChunk);
+          // D[n][row] = sum_k W[n][k] parent[row][k]: W is the MMA's A operand (M = 128
+          // output components), the parent rows its B operand (N = 128 rows), so TMEM
+          // lane n holds output component n of every row and the stores coalesce
+#pragma unroll
+          for (int term = 0; term < 3; ++term) {
+            const uint64_t dp = term == 1 ? alo : ahi, dw = term == 2 ? wlo : whi;
+#pragma unroll
+            for (int k = 0; k < 4; ++k)      // 8 TF32 of K (32 bytes) per MMA
+              mma_tf32(d, dw + 2 * k, dp + 2 * k, idesc, (kc | term | k) ? 1u : 0u);
+          }
+          mma_commit(&empty_bar[s]);          // the stage is free once these MMAs finish
+        }
+        if (!ok) break;
+        mma_commit(&tfull[b]);                // the accumulator is complete
+      }
+      // every MMA issued above has finished before TMEM is released
+      mma_commit(&drain);
+      if (!mbar_wait(&drain, 0)) atomicExch(a.err, 7);
+    }
+    __syncwarp();
+  } else {
+    // ---- epilogue: TMEM lane quarter (warp & 3) holds output components 32 (warp & 3)
+    // .. + 31; TMEM column j of the accumulator is row j of the tile ----
+    const int q4 = warp & 3;
+    const int comp = q4 * 32 + lane;
+    int64_t tu = 0;
+    for (int64_t u = blockIdx.x; u < units && !abort_sh; u += gridDim.x, ++tu) {
+      const int b = (int)(tu & 1);
+      if (!mbar_wait(&tfull[b], (uint32_t)(tu >> 1) & 1u)) {
+        atomicExch(a.err, 8);
+        abort_sh = 1;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const int64_t g = g_first + (u >> tb) * radix;
+      float *dst = a.child + (((uint64_t)(g - a.node_lo) << a.h) + ((uint64_t)(u & ((1 << tb) - 1)) << 13)) * 2 + comp;
+#pragma unroll
+      for (int c0 = 0; c0 < 128; c0 += 32) {
+        uint32_t v[32];
+        const uint32_t taddr = tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(b * 128 + c0);
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+            "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+              "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
+              "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
+              "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+            : "r"(taddr));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+        for (int j = 0; j < 32; ++j) dst[(size_t)(c0 + j) * 128] = __uint_as_float(v[j]);
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      mbar_arrive(&tempty[b]);
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 8) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(256) : "memory");
+  }
+}
+
+// ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
 PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
@@ -468,6 +703,59 @@ cudaError_t launch_path_gemm(const PathGemmArgs &g, cudaStream_t st) {
   const int64_t row_tile_bytes = (int64_t)kBM * kpad * esz;
   ep.group_m = (int32_t)std::max<int64_t>(1, std::min<int64_t>(ep.num_m, (48ll << 20) / row_tile_bytes));
   gemm_kernel<<<(unsigned)((int64_t)ep.num_m * ep.num_n), 128, smem, st>>>(tmA, tmB, ep);
+  return cudaGetLastError();
+}
+
+void level_mma_image(const double *w, float *hi, float *lo) {
+  auto rna = [](float x) {               // round to TF32 (nearest, ties away), as cvt.rna.tf32
+    uint32_t u;
+    std::memcpy(&u, &x, 4);
+    if ((u & 0x7f800000u) != 0x7f800000u) u = (u + 0x1000u) & 0xffffe000u;
+    float r;
+    std::memcpy(&r, &u, 4);
+    return r;
+  };
+  for (int n = 0; n < 128; ++n)
+    for (int k = 0; k < 128; ++k) {
+      const float x = (float)w[(size_t)n * 128 + k];
+      const float h = rna(x), l = rna(x - h);
+      const int kc = k >> 5, kk = k & 31;
+      const size_t off = (size_t)kc * kLvlChunk + (size_t)(n >> 3) * 1024 + (size_t)(n & 7) * 128 +
+                         (size_t)((((kk >> 2) ^ (n & 7)) << 4) + (kk & 3) * 4);
+      hi[off / 4] = h;
+      lo[off / 4] = l;
+    }
+}
+
+cudaError_t launch_level_mma(const LevelMmaArgs &a, cudaStream_t st) {
+  if (a.num_nodes <= 0) return cudaSuccess;
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) sms = 148;
+  }
+  const size_t smem = kLvlSmem;
+  cudaError_t e = cudaFuncSetAttribute(level_mma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const int r = a.radix > 0 ? a.radix : 1;
+  const int64_t per_digit_units = ((a.num_nodes + r - 1) / r) << (a.h - kMmaMinH);
+  const int64_t gx = std::min<int64_t>(std::max(1, (sms + r - 1) / r), std::max<int64_t>(1, per_digit_units));
+  // the parents as a [rows][128] FP32 matrix (one row = 64 amplitudes); 32 x 128 boxes
+  const int64_t parents = (a.node_lo + a.num_nodes - 1) / r - a.parent_lo + 1;
+  const int64_t rows = parents << (a.h - kMmaBits);
+  auto enc = get_encode();
+  if (!enc || rows <= 0 || rows > INT32_MAX) return cudaErrorInvalidValue;
+  CUtensorMap tmP;
+  const cuuint64_t dims[2] = {128, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {512};
+  const cuuint32_t box[2] = {32, 128};
+  const cuuint32_t estr[2] = {1, 1};
+  if (enc(&tmP, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float *>(a.parent), dims, strides, box, estr,
+          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    return cudaErrorInvalidValue;
+  level_mma_kernel<<<dim3((unsigned)gx, (unsigned)r), kLvlThreads, smem, st>>>(tmP, a);
   return cudaGetLastError();
 }
 

@@ -67,6 +67,12 @@ struct PassH {
 struct LevelH {
   std::vector<OpH> ops;
   std::vector<PassH> passes;
+  // Tensor-core level (complex64, whole program on the kMmaBits lowest storage bits):
+  // per digit, the program as a real 2^(kMmaBits+1)-square matrix W, stored as the
+  // shared-memory image the kernel loads (TF32 hi part, then lo part).
+  bool mma = false;
+  std::vector<float> wimg;
+  size_t w_off = 0;
 };
 
 struct SideH {

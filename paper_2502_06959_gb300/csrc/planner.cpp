@@ -710,6 +710,38 @@ hsf_status build_programs(hsf_plan &p, bool grad) {
         for (int j = 0; j < op.nq; ++j) c = std::max(c, op.q[j] + 1);
       leaf_c = c <= 5 ? std::max(leaf_c, c) : -1;
     }
+    // levels whose whole program sits on the kMmaBits lowest storage bits run as one
+    // tensor-core product per digit (complex64 forward programs)
+    for (int k = 1; k <= B && !grad; ++k) {
+      LevelH &lv = sd.levels[k];
+      bool ok = p.precision == HSF_PREC_C64 && sd.h >= kMmaMinH && !(p.flags & HSF_FLAG_NO_TC_LEVEL) &&
+                !lv.ops.empty();
+      for (auto &op : lv.ops)
+        for (int j = 0; j < op.nq && ok; ++j) ok = op.q[j] < kMmaBits;
+      if (!ok) continue;
+      const int dim = 1 << kMmaBits, K = 2 * dim;
+      const int r = (int)p.radix[k];
+      lv.mma = true;
+      lv.wimg.assign((size_t)r * 2 * (kMmaWPartBytes / 4), 0.f);
+      std::vector<double> w((size_t)K * K);
+      for (int m = 0; m < r; ++m) {
+        // U_m column by column, then its real form W[2i + a][2j + b] (a, b: re / im)
+        std::fill(w.begin(), w.end(), 0.0);
+        for (int col = 0; col < dim; ++col) {
+          std::vector<cd> v(dim, 0.0);
+          v[col] = 1.0;
+          for (auto &op : lv.ops) host_apply(v, kMmaBits, op, m);
+          for (int row = 0; row < dim; ++row) {
+            w[(size_t)(2 * row) * K + 2 * col] = v[row].real();
+            w[(size_t)(2 * row) * K + 2 * col + 1] = -v[row].imag();
+            w[(size_t)(2 * row + 1) * K + 2 * col] = v[row].imag();
+            w[(size_t)(2 * row + 1) * K + 2 * col + 1] = v[row].real();
+          }
+        }
+        float *hi = lv.wimg.data() + (size_t)m * 2 * (kMmaWPartBytes / 4);
+        level_mma_image(w.data(), hi, hi + kMmaWPartBytes / 4);
+      }
+    }
     for (auto &lv : sd.levels) {
       split_passes(lv, sd.h, p.tile_max);
       if (!grad && !(p.flags & HSF_FLAG_NO_REGISTER_SWEEP))
@@ -769,6 +801,12 @@ hsf_status upload_programs(hsf_plan &p, bool grad) {
         ++launches;
       }
     SideH &sd = grad ? p.gside[s] : p.side[s];
+    for (auto &lv : sd.levels)
+      if (lv.mma) {
+        align(1024);
+        lv.w_off = host.size();
+        append(lv.wimg.data(), lv.wimg.size() * sizeof(float));
+      }
     align(256);
     sd.leaf_off = host.size();
     for (auto &z : sd.leaf_ops) {

@@ -198,10 +198,33 @@ __device__ __forceinline__ void ap1(C (&v)[NR], const C *__restrict__ m) {
 
 template <int J, int K, int NR, typename C>
 __device__ __forceinline__ void ap2(C (&v)[NR], const C *m0) {
+  if constexpr (sizeof(C) == 8) {
+    // complex64: the 4x4 matrix is loaded once and stays in registers for every quad
+    C mm[16];
+#pragma unroll
+    for (int e = 0; e < 16; e += 2) ld2(m0 + e, mm[e], mm[e + 1]);
+#pragma unroll
+    for (int i = 0; i < NR; ++i) {
+      if (i & ((1 << J) | (1 << K))) continue;
+      const int id[4] = {i, i | (1 << K), i | (1 << J), i | (1 << J) | (1 << K)};
+      C x[4];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) x[c] = v[id[c]];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        C acc = cmul(mm[4 * r], x[0]);
+        acc = cfma(mm[4 * r + 1], x[1], acc);
+        acc = cfma(mm[4 * r + 2], x[2], acc);
+        acc = cfma(mm[4 * r + 3], x[3], acc);
+        v[id[r]] = acc;
+      }
+    }
+    return;
+  }
 #pragma unroll
   for (int i = 0; i < NR; ++i) {
     if (i & ((1 << J) | (1 << K))) continue;
-    // matrix rows are re-read per quad (L1 broadcast) to keep register use low
+    // complex128: matrix rows are re-read per quad (L1 broadcast) to keep register use low
     const C *m = m0;
     asm volatile("" : "+l"(m));
     const int id[4] = {i, i | (1 << K), i | (1 << J), i | (1 << J) | (1 << K)};
@@ -441,17 +464,17 @@ __global__ void __launch_bounds__(1 << (T - RB), 2) sweep_reg_kernel(SweepArgs a
         v[i] = s[u];
       }
       for (int o = G.first_op; o < G.first_op + G.num_ops; ++o) {
-        // the op record is read as four int4 into scalars (no local-memory copy)
+        // the op record is read as int4 words into scalars (no local-memory copy); a
+        // dense op needs only the first
         const int4 *o4 = reinterpret_cast<const int4 *>(ops + o);
-        const int4 w0 = o4[0], w1 = o4[1], w2 = o4[2], w3 = o4[3];
-        const int op_type = w0.x, op_nq = w0.y;
-        const int pos_[3] = {w0.z, w0.w, w1.x};
-        const int op_mat = w1.y, op_dstride = w1.z;
-        const int slot_[3] = {w1.w, w2.x, w2.y};
-        const int op_kcase = w2.z, op_kidx = w3.y;
-        (void)w3;
+        const int4 w0 = o4[0];
+        const int op_type = w0.x, op_kidx = w0.y, op_mat = w0.z, op_dstride = w0.w;
         const C *m = mats + op_mat + (op_dstride > 0 ? digit * op_dstride : 0);
         if (op_type == OP_DIAG) {
+          const int4 w1 = o4[1], w2 = o4[2], w3 = o4[3];
+          const int op_nq = w1.x, op_kcase = w1.y;
+          const int pos_[3] = {w2.x, w2.y, w2.z};
+          const int slot_[3] = {w2.w, w3.x, w3.y};
           // operands are ordered slot operands first (kcase = their count); the
           // others are bits of this thread's instance or of the tile's fixed bits
           const int ns = op_kcase;

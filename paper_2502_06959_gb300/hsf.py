@@ -31,6 +31,7 @@ FLAG_NO_REGISTER_SWEEP = 4
 FLAG_IDENTITY_STORAGE = 8
 FLAG_REG5 = 16
 FLAG_REG3 = 32
+FLAG_NO_TC_LEVEL = 64
 
 
 class HsfError(RuntimeError):
@@ -114,7 +115,7 @@ SIGNATURES = {
     "hsf_version": (ctypes.c_char_p, []),
 }
 
-KERNEL_KINDS = ("sweep", "gather", "reduce", "window", "other", "leaf")
+KERNEL_KINDS = ("sweep", "gather", "reduce", "window", "other", "leaf", "level_mma")
 
 
 class hsf_kernel_stat(ctypes.Structure):

@@ -1,0 +1,108 @@
+"""GPU parity of the tensor-core tree level.
+
+A tree level whose program (Schmidt factor, then the gates it hoists) acts only on the
+6 lowest storage bits of a half state with h >= 13 qubits runs as one TF32x3 tensor-core
+product per Schmidt digit.  These cases check it against the FP64 oracle (complex64
+bound: 1e-5 max abs and 1e-4 of the largest reference amplitude) and against the same
+plan swept on the CUDA cores, for bitstring and window outputs, over path ranges that
+start and end inside a parent's group of digits.
+"""
+import numpy as np
+import pytest
+
+import oracle.hsf_oracle as O
+from paper_2502_06959_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    from paper_2502_06959_gb300 import build
+    build.build()
+    from paper_2502_06959_gb300 import hsf
+    hsf.load_library()
+
+
+def check(got, ref):
+    err = float(np.max(np.abs(got - ref))) if ref.size else 0.0
+    scale = float(np.max(np.abs(ref))) if ref.size else 1.0
+    assert err <= 1e-5, err
+    assert err <= 1e-4 * scale, (err, scale)
+    return err
+
+
+def run(pr, bits=None, window=0, path_range=(0, 0), **opts):
+    import torch
+    from paper_2502_06959_gb300 import hsf
+    plan = hsf.Plan(pr.n, pr.gates, pr.cut, pr.blocks, precision="c64", **opts)
+    bs = None
+    if bits is not None:
+        bs = torch.from_numpy(np.asarray(bits, dtype=np.uint64).view(np.int64)).cuda()
+    out = plan.run(bs, window=window, path_range=path_range)
+    torch.cuda.synchronize()
+    desc = hsf.hsf_plan_describe(plan.handle)
+    res = out.cpu().numpy()
+    plan.close()
+    return res, desc
+
+
+def problem(n, kind, seed, blocks_after=(2, 4, 6, 7), layers=8):
+    return W.random_brickwork(n, n // 2 - 1, layers, block_after=blocks_after, block_kind=kind,
+                              block_len=2, seed=seed)
+
+
+@pytest.mark.parametrize("n,kind,seed", [(26, "rzz", 1), (26, "mixed", 2), (28, "cx_rzz_cz", 3)])
+def test_tc_level_bitstrings_against_oracle(n, kind, seed):
+    from paper_2502_06959_gb300 import hsf
+    pr = problem(n, kind, seed)
+    rng = np.random.default_rng(seed)
+    bits = W.random_bitstrings(rng, n, 200)
+    got, desc = run(pr, bits)
+    assert "tensor-core product" in desc, desc
+    ref_cc, desc_cc = run(pr, bits, flags=hsf.FLAG_NO_TC_LEVEL)
+    assert "tensor-core product" not in desc_cc
+    check(got, ref_cc)
+    # TF32x3 keeps FP32-level accuracy: a hi part one TF32 ulp off (rounded where the
+    # tensor core truncates) would show up as ~5e-4 relative error
+    assert np.max(np.abs(got - ref_cc)) <= 2e-5 * np.max(np.abs(ref_cc))
+    plan = hsf.Plan(pr.n, pr.gates, pr.cut, pr.blocks, precision="c64")
+    P = int(plan.info["num_paths"])
+    # single paths are unique only when no block has a repeated singular value (within a
+    # degenerate subspace any orthonormal Schmidt basis is correct); otherwise compare
+    # the full path sum, which is unique
+    sig = [plan.sigma(k) for k in range(len(pr.blocks))]
+    plan.close()
+    distinct = all(np.all(np.abs(np.diff(s)) > 1e-6 * s[0]) for s in sig)
+    ranges = ((0, 3), (1, 6), (P // 2 - 1, P // 2 + 5), (P - 5, P)) if distinct else ((0, P),)
+    for (a, b) in ranges:
+        want, _ = O.hsf_amplitudes(pr.n, pr.gates, pr.cut, pr.blocks, bitstrings=bits, path_range=(a, b))
+        got_r, _ = run(pr, bits, path_range=(a, b))
+        check(got_r, want)
+
+
+def test_tc_level_window_against_cuda_cores_and_oracle():
+    from paper_2502_06959_gb300 import hsf
+    pr = problem(26, "mixed", 5)
+    win = 1 << 18
+    got, desc = run(pr, window=win, path_range=(3, 11))
+    assert "tensor-core product" in desc
+    ref_cc, _ = run(pr, window=win, path_range=(3, 11), flags=hsf.FLAG_NO_TC_LEVEL)
+    check(got, ref_cc)
+    rng = np.random.default_rng(9)
+    idx = rng.choice(win, size=64, replace=False).astype(np.uint64)
+    want, _ = O.hsf_amplitudes(pr.n, pr.gates, pr.cut, pr.blocks, bitstrings=idx, path_range=(3, 11))
+    check(got[idx.astype(np.int64)], want)
+
+
+def test_tc_level_in_n30_plan():
+    """The deepest materialised level of the n = 30 workload runs on the tensor cores."""
+    from paper_2502_06959_gb300 import hsf
+    pr = W.workload_c2(num_bitstrings=16)
+    plan = hsf.Plan.from_problem(pr)
+    desc = hsf.hsf_plan_describe(plan.handle)
+    plan.close()
+    lines = [l for l in desc.splitlines() if l.startswith(" level 7:")]
+    assert len(lines) == 2 and all("tensor-core product" in l for l in lines), desc
