@@ -272,9 +272,11 @@ hsf_status hsf_sync(hsf_plan *p, void *stream) {
   if (!p) return set_error(HSF_EINVAL, "NULL plan");
   CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
   int32_t status = 0;
-  CUDA_TRY(cudaMemcpy(&status, p->dev_status, sizeof status, cudaMemcpyDeviceToHost));
+  CUDA_TRY(cudaMemcpyAsync(&status, p->dev_status, sizeof status, cudaMemcpyDeviceToHost, plan_stream()));
+  CUDA_TRY(cudaStreamSynchronize(plan_stream()));
   if (status != 0) {
-    CUDA_TRY(cudaMemset(p->dev_status, 0, sizeof status));
+    CUDA_TRY(cudaMemsetAsync(p->dev_status, 0, sizeof status, plan_stream()));
+    CUDA_TRY(cudaStreamSynchronize(plan_stream()));
     return set_error(HSF_ETIMEOUT, "a bounded device-side wait expired (code %d); results of the "
                                    "affected run are invalid", status);
   }

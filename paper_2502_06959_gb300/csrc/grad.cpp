@@ -93,7 +93,8 @@ hsf_status ensure_grad(hsf_plan &p) {
   }
   if (host.empty()) host.resize(256);
   CUDA_TRY(cudaMalloc(&p.dev_factors, host.size()));
-  CUDA_TRY(cudaMemcpy(p.dev_factors, host.data(), host.size(), cudaMemcpyHostToDevice));
+  CUDA_TRY(cudaMemcpyAsync(p.dev_factors, host.data(), host.size(), cudaMemcpyHostToDevice, plan_stream()));
+  CUDA_TRY(cudaStreamSynchronize(plan_stream()));
   // derivative blocks: one SVD job per (block, angle) pair
   std::vector<SvdJob> jobs;
   std::vector<std::pair<int, int>> keys;

@@ -822,6 +822,8 @@ hsf_status upload_programs(hsf_plan &p, bool grad) {
   align(256);
   if (host.empty()) host.resize(256);
   void *&table = grad ? p.dev_gtable : p.dev_table;
+  // plain cudaMalloc: hsf_plan_destroy's cudaFree then waits for every kernel that may
+  // still read the table (a stream-ordered pool allocation could be unmapped under them)
   CUDA_TRY(cudaMalloc(&table, host.size()));
   if (!grad) p.dev_table_bytes = host.size();
   CUDA_TRY(cudaMemcpyAsync(table, host.data(), host.size(), cudaMemcpyHostToDevice, plan_stream()));
