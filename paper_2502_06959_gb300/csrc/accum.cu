@@ -306,7 +306,8 @@ __global__ void __launch_bounds__(128) leaf_contract_async_kernel(LeafArgs a) {
   constexpr int STAGE = SPB * SB;
   constexpr int PIECES = D;                    // 16-byte pieces per bitstring and parent
   constexpr int HALF = D / 2;                  // pieces per side
-  __shared__ __align__(16) C buf[kDepth][STAGE];
+  extern __shared__ __align__(16) unsigned char leaf_smem[];   // kDepth stages of STAGE
+  C(*buf)[STAGE] = reinterpret_cast<C(*)[STAGE]>(leaf_smem);
   const int m = threadIdx.x % RM;
   const int sl = threadIdx.x / RM;
   const int64_t s = (int64_t)blockIdx.x * SPB + sl;
@@ -397,6 +398,171 @@ __global__ void __launch_bounds__(128) leaf_contract_async_kernel(LeafArgs a) {
   }
 }
 
+// Leaf contraction for large bitstring counts.  One co-resident wave of CTAs; CTA b
+// owns bitstrings [b * per_cta, (b + 1) * per_cta), and every CTA walks all parents in
+// the same order, so the parents being read at any time are few and stay in L2 however
+// many bitstrings gather from them.  A bitstring's chunk origins, leaf rows and FP32
+// running sum live in shared memory; every kStreamBatch parents the FP32 sums are added
+// into the FP64 partial (one per bitstring: num_groups = 1).
+constexpr int kStreamThreads = 256;
+constexpr int kStreamBatch = 64;
+constexpr int kStreamPerSm = 8;                // CTAs per SM the wave aims for
+constexpr int kStreamSync = 8;                 // parents between grid barriers
+constexpr uint32_t kStreamSpin = 1u << 20;     // bounded barrier wait (polls of ~100 ns)
+
+// Grid barrier for a cooperative launch (all CTAs resident).  It only keeps the CTAs
+// within kStreamSync parents of one another, for L2 locality; results do not depend on
+// it, so on expiry it records an error code and lets the CTA go on.
+__device__ __forceinline__ void stream_barrier(uint32_t *count, volatile uint32_t *gen, uint32_t nblocks,
+                                               int32_t *err) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const uint32_t g = *gen;
+    __threadfence();
+    if (atomicAdd(count, 1u) == nblocks - 1) {
+      *count = 0;
+      __threadfence();
+      atomicAdd((uint32_t *)gen, 1u);
+    } else {
+      uint32_t it = 0;
+      while (*gen == g && ++it < kStreamSpin) __nanosleep(100);
+      if (it >= kStreamSpin) atomicExch(err, 11);
+    }
+  }
+  __syncthreads();
+}
+struct StreamBits {
+  uint32_t oa, ob;                             // chunk origin (storage index) on each side
+  uint32_t rr;                                 // ra | rb << 8
+  uint32_t pad;
+  float2 acc;
+};
+
+template <int CB>
+__global__ void __launch_bounds__(kStreamThreads) leaf_stream_kernel(LeafArgs a, int64_t per_cta) {
+  using C = float2;
+  constexpr int D = 1 << CB;
+  constexpr int LD = D + 2;                    // row stride (complex): 16-byte aligned rows
+  extern __shared__ __align__(16) unsigned char leaf_smem[];
+  C *sLa = reinterpret_cast<C *>(leaf_smem);
+  C *sLb = sLa + a.r * D * LD;
+  StreamBits *bs = reinterpret_cast<StreamBits *>(sLb + a.r * D * LD);
+  const int64_t s0 = (int64_t)blockIdx.x * per_cta;
+  const int ns = (int)(min(a.S, s0 + per_cta) - s0);
+  for (int e = threadIdx.x; e < a.r * D * D; e += blockDim.x) {
+    const int row = e / D, k = e % D;          // row = m * D + output index
+    sLa[row * LD + k] = reinterpret_cast<const C *>(a.La)[e];
+    sLb[row * LD + k] = reinterpret_cast<const C *>(a.Lb)[e];
+  }
+  for (int i = threadIdx.x; i < ns; i += blockDim.x) {
+    const uint64_t ia = a.ia[s0 + i], ib = a.ib[s0 + i];
+    const uint32_t ra = (uint32_t)(ia & (D - 1)), rb = (uint32_t)(ib & (D - 1));
+    bs[i].oa = (uint32_t)(ia - ra);
+    bs[i].ob = (uint32_t)(ib - rb);
+    bs[i].rr = ra | (rb << 8);
+    bs[i].acc = make_float2(0.f, 0.f);
+    a.partial[2 * (s0 + i)] = 0.0;
+    a.partial[2 * (s0 + i) + 1] = 0.0;
+  }
+  __syncthreads();
+  for (int64_t j0 = 0; j0 < a.num_parents; j0 += kStreamBatch) {
+    const int64_t j1 = min(a.num_parents, j0 + kStreamBatch);
+    for (int64_t j = j0; j < j1; ++j) {
+      if (j % kStreamSync == 0 && j > 0) stream_barrier(a.sync, a.sync + 1, gridDim.x, a.err);
+      const int mlo = j == 0 ? a.m_first : 0;
+      const int mhi = j == a.num_parents - 1 ? a.m_last : a.r;
+      const C *Pa = reinterpret_cast<const C *>(a.Pa) + ((uint64_t)j << a.ha);
+      const C *Pb = reinterpret_cast<const C *>(a.Pb) + ((uint64_t)j << a.hb);
+      for (int i = threadIdx.x; i < ns; i += blockDim.x) {
+        const StreamBits st = bs[i];
+        float4 xa[D / 2], xb[D / 2];
+#pragma unroll
+        for (int k2 = 0; k2 < D / 2; ++k2) {
+          xa[k2] = __ldg(reinterpret_cast<const float4 *>(Pa + st.oa) + k2);
+          xb[k2] = __ldg(reinterpret_cast<const float4 *>(Pb + st.ob) + k2);
+        }
+        const int ra = (int)(st.rr & 255u), rb = (int)(st.rr >> 8);
+        float sr = 0.f, si = 0.f;
+        for (int m = mlo; m < mhi; ++m) {
+          const float4 *la = reinterpret_cast<const float4 *>(sLa + (m * D + ra) * LD);
+          const float4 *lb = reinterpret_cast<const float4 *>(sLb + (m * D + rb) * LD);
+          float var = 0.f, vai = 0.f, vbr = 0.f, vbi = 0.f;
+#pragma unroll
+          for (int k2 = 0; k2 < D / 2; ++k2) {
+            const float4 p = la[k2], x = xa[k2], u = lb[k2], y = xb[k2];
+            var = fmaf(p.x, x.x, fmaf(-p.y, x.y, var));
+            vai = fmaf(p.x, x.y, fmaf(p.y, x.x, vai));
+            var = fmaf(p.z, x.z, fmaf(-p.w, x.w, var));
+            vai = fmaf(p.z, x.w, fmaf(p.w, x.z, vai));
+            vbr = fmaf(u.x, y.x, fmaf(-u.y, y.y, vbr));
+            vbi = fmaf(u.x, y.y, fmaf(u.y, y.x, vbi));
+            vbr = fmaf(u.z, y.z, fmaf(-u.w, y.w, vbr));
+            vbi = fmaf(u.z, y.w, fmaf(u.w, y.z, vbi));
+          }
+          sr = fmaf(var, vbr, fmaf(-vai, vbi, sr));
+          si = fmaf(var, vbi, fmaf(vai, vbr, si));
+        }
+        bs[i].acc = make_float2(st.acc.x + sr, st.acc.y + si);
+      }
+    }
+    // every thread only ever touches its own bitstrings i = tid + k * blockDim.x
+    for (int i = threadIdx.x; i < ns; i += blockDim.x) {
+      const float2 c = bs[i].acc;
+      a.partial[2 * (s0 + i)] += (double)c.x;
+      a.partial[2 * (s0 + i) + 1] += (double)c.y;
+      bs[i].acc = make_float2(0.f, 0.f);
+    }
+  }
+}
+
+template <int CB>
+size_t leaf_stream_smem(int r, int64_t per_cta) {
+  return (size_t)2 * r * (1 << CB) * ((1 << CB) + 2) * sizeof(float2) + (size_t)per_cta * sizeof(StreamBits);
+}
+
+// Launch shape of the one-wave kernel for S bitstrings: CTAs (all co-resident) and
+// bitstrings per CTA; false if S does not fit one wave.
+template <int CB>
+bool leaf_stream_shape(int r, int64_t S, int *grid, int64_t *per_cta) {
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) return false;
+  }
+  for (int per_sm = kStreamPerSm; per_sm >= 1; --per_sm) {
+    const int64_t pc = (S + (int64_t)sms * per_sm - 1) / ((int64_t)sms * per_sm);
+    const size_t smem = leaf_stream_smem<CB>(r, pc);
+    if (smem > 200 * 1024) continue;
+    int occ = 0;
+    if (cudaFuncSetAttribute(leaf_stream_kernel<CB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+            cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, leaf_stream_kernel<CB>, kStreamThreads, smem) !=
+            cudaSuccess)
+      return false;
+    if (occ >= per_sm) {
+      *per_cta = pc;
+      *grid = (int)((S + pc - 1) / pc);
+      return true;
+    }
+  }
+  return false;
+}
+
+template <int CB>
+cudaError_t leaf_stream_launch(const LeafArgs &a, cudaStream_t st) {
+  int grid = 0;
+  int64_t per_cta = 0;
+  if (!leaf_stream_shape<CB>(a.r, a.S, &grid, &per_cta)) return cudaErrorInvalidConfiguration;
+  // the barrier words start at zero (and return there after every barrier)
+  cudaError_t e = cudaMemsetAsync(a.sync, 0, 2 * sizeof(uint32_t), st);
+  if (e != cudaSuccess) return e;
+  LeafArgs args = a;
+  void *params[] = {&args, &per_cta};
+  return cudaLaunchCooperativeKernel((const void *)leaf_stream_kernel<CB>, dim3(grid), dim3(kStreamThreads), params,
+                                     leaf_stream_smem<CB>(a.r, per_cta), st);
+}
+
 __global__ void index_prep_kernel(IndexArgs a) {
   const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= a.S) return;
@@ -460,23 +626,24 @@ cudaError_t launch_window(const WindowArgs &a, int precision, cudaStream_t st) {
 
 template <typename R, int CB>
 cudaError_t leaf_reg_dispatch(const LeafArgs &a, cudaStream_t st) {
-  int rm = a.r <= 1 ? 1 : a.r <= 2 ? 2 : a.r <= 4 ? 4 : 8;
+  const int rm = a.r <= 1 ? 1 : a.r <= 2 ? 2 : a.r <= 4 ? 4 : 8;
   if constexpr (sizeof(R) == 4 && CB >= 1) {
-    // keep the stage ring (kDepth x 128/rm bitstrings x (2^(CB+1)+2) complex) within the
-    // 48 KB of static shared memory: threads with m >= r idle
-    while (rm < 8 && leaf_ring_bytes(CB, rm) > 48 * 1024) rm *= 2;
+    // the stage ring (kDepth x 128/rm bitstrings x (2^(CB+1)+2) complex) is dynamic
+    // shared memory: up to 139 KB for one operator per thread at CB = 4
     dim3 grid((unsigned)((a.S * rm + 127) / 128), (unsigned)a.num_groups);
+    auto go = [&](auto kernel, int rmv) -> cudaError_t {
+      const size_t smem = leaf_ring_bytes(CB, rmv);
+      cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+      kernel<<<grid, 128, smem, st>>>(a);
+      return cudaGetLastError();
+    };
     switch (rm) {
-      case 1:
-        if constexpr (leaf_ring_bytes(CB, 1) <= 48 * 1024) leaf_contract_async_kernel<CB, 1><<<grid, 128, 0, st>>>(a);
-        break;
-      case 2:
-        if constexpr (leaf_ring_bytes(CB, 2) <= 48 * 1024) leaf_contract_async_kernel<CB, 2><<<grid, 128, 0, st>>>(a);
-        break;
-      case 4: leaf_contract_async_kernel<CB, 4><<<grid, 128, 0, st>>>(a); break;
-      default: leaf_contract_async_kernel<CB, 8><<<grid, 128, 0, st>>>(a); break;
+      case 1: return go(leaf_contract_async_kernel<CB, 1>, 1);
+      case 2: return go(leaf_contract_async_kernel<CB, 2>, 2);
+      case 4: return go(leaf_contract_async_kernel<CB, 4>, 4);
+      default: return go(leaf_contract_async_kernel<CB, 8>, 8);
     }
-    return cudaGetLastError();
   }
   dim3 grid((unsigned)((a.S * rm + 127) / 128), (unsigned)a.num_groups);
   switch (rm) {
@@ -518,8 +685,28 @@ cudaError_t leaf_dispatch(const LeafArgs &a, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+bool leaf_streams(const LeafArgs &a, int precision) {
+  // worth it once the bitstrings far outnumber the threads of one wave; the chunk
+  // origins must fit 32 bits
+  if (precision != 0 || a.c < 1 || a.c > 3 || a.S < 65536 || a.r > 8 || a.ha > 32 || a.hb > 32) return false;
+  int grid = 0;
+  int64_t pc = 0;
+  switch (a.c) {
+    case 1: return leaf_stream_shape<1>(a.r, a.S, &grid, &pc);
+    case 2: return leaf_stream_shape<2>(a.r, a.S, &grid, &pc);
+    default: return leaf_stream_shape<3>(a.r, a.S, &grid, &pc);
+  }
+}
+
 cudaError_t launch_leaf_contract(const LeafArgs &a, int precision, cudaStream_t st) {
   if (a.S <= 0 || a.num_parents <= 0) return cudaSuccess;
+  if (leaf_streams(a, precision)) {
+    switch (a.c) {
+      case 1: return leaf_stream_launch<1>(a, st);
+      case 2: return leaf_stream_launch<2>(a, st);
+      default: return leaf_stream_launch<3>(a, st);
+    }
+  }
   return precision == 0 ? leaf_dispatch<float>(a, st) : leaf_dispatch<double>(a, st);
 }
 

@@ -40,7 +40,7 @@ struct RunLayout {
   bool leaf = false;           // leaf level contracted at the bitstrings
   bool tc = false;             // window output on the tensor cores
   size_t off_buf[2][2] = {{0, 0}, {0, 0}};
-  size_t off_partial = 0, off_comp = 0, off_index = 0, off_gemm = 0, total = 0;
+  size_t off_partial = 0, off_sync = 0, off_comp = 0, off_index = 0, off_gemm = 0, total = 0;
   int32_t ppg = 64, groups = 0;
 };
 
@@ -75,6 +75,8 @@ RunLayout layout_for(const hsf_plan &p, size_t num_bits, uint64_t window, uint64
     L.groups = (int32_t)((units + L.ppg - 1) / L.ppg);
     L.off_partial = off;
     off += align256((size_t)L.groups * num_bits * 16);
+    L.off_sync = off;
+    off += 256;
     L.off_index = off;
     off += align256(num_bits * 16);
     L.off_comp = off;
@@ -437,6 +439,12 @@ hsf_status hsf_run(hsf_plan *p, const uint64_t *bits, size_t num, uint64_t windo
       la.parents_per_group = L.ppg;
       la.num_groups = (int32_t)((la.num_parents + L.ppg - 1) / L.ppg);
       la.partial = (double *)(ws + L.off_partial);
+      la.sync = (uint32_t *)(ws + L.off_sync);
+      la.err = p->dev_status;
+      if (leaf_streams(la, p->precision)) {
+        la.parents_per_group = (int32_t)la.num_parents;
+        la.num_groups = 1;
+      }
       const double units = (double)la.num_parents * (double)num;
       LAUNCH(HSF_KERNEL_LEAF, units * 2.0 * (1 << la.c) * csz + 16.0 * la.num_groups * num,
              units * la.r * (8.0 * 2.0 * (1 << la.c) + 8.0), launch_leaf_contract(la, p->precision, st));

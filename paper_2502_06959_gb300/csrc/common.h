@@ -100,6 +100,8 @@ struct LeafArgs {
   int64_t S;
   int32_t parents_per_group, num_groups;
   double *partial;       // [num_groups][S][2]
+  uint32_t *sync;        // 2 words of device scratch (grid barrier of the streaming kernel)
+  int32_t *err;          // device status word
 };
 
 // Storage index of every bitstring on both sides (bit permutation of x_a, x_b).
@@ -247,6 +249,9 @@ cudaError_t launch_finalize(double *out, const double *comp, int64_t count, cuda
 cudaError_t launch_zero(double *p, int64_t count, cudaStream_t st);
 cudaError_t launch_block_svd(const BlockSvdArgs &a, cudaStream_t st);
 cudaError_t launch_leaf_contract(const LeafArgs &a, int precision, cudaStream_t st);
+// true when launch_leaf_contract uses the one-wave streaming kernel (large bitstring
+// counts); it then writes a single partial per bitstring (num_groups = 1)
+bool leaf_streams(const LeafArgs &a, int precision);
 cudaError_t launch_index_prep(const IndexArgs &a, cudaStream_t st);
 // dst[i] = storage index of local index i, i < count.
 cudaError_t launch_range_index(uint64_t *dst, int64_t count, const PermArgs &perm, cudaStream_t st);

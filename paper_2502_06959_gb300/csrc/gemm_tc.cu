@@ -375,10 +375,15 @@ __global__ void __launch_bounds__(128, 1) gemm_kernel(const __grid_constant__ CU
 // write the child rows.  Every wait is bounded; on expiry the CTA records an error,
 // drains its MMAs, frees TMEM and returns.
 constexpr int kLvlStages = 3;
+constexpr int kLvlAhead = 8;                    // chunks prefetched into L2 ahead of the loads
 constexpr int kLvlChunk = 128 * 128;            // bytes: 128 rows x 32 floats
 constexpr int kLvlThreads = 320;                // 4 low-part, 4 epilogue, 1 MMA, 1 TMA warp
 constexpr size_t kLvlSmem = 2 * kMmaWPartBytes + (size_t)kLvlStages * 2 * kLvlChunk + 1024;
 
+__device__ __forceinline__ void tma_prefetch_2d(const CUtensorMap *map, int x, int y) {
+  asm volatile("cp.async.bulk.prefetch.tensor.2d.L2.global.tile [%0, {%1, %2}];" ::"l"((uint64_t)map), "r"(x), "r"(y)
+               : "memory");
+}
 __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
@@ -481,19 +486,27 @@ __global__ void __launch_bounds__(kLvlThreads, 1) level_mma_kernel(const __grid_
     }
   } else if (warp == 9) {
     // ---- TMA: chunk c = chunk c % 4 of unit blockIdx.x + (c / 4) * gridDim.x ----
+    // Chunks kLvlAhead ahead are prefetched into L2 (no shared memory), so the stage
+    // loads, which can only start once a stage frees, see L2 rather than DRAM latency.
     if (lane == 0) {
+      auto row_of = [&](int64_t c) {
+        const int64_t u = blockIdx.x + (c >> 2) * gridDim.x;
+        const int64_t g = g_first + (u >> tb) * radix;
+        return ((g / radix - a.parent_lo) << (a.h - kMmaBits)) + ((u & ((1 << tb) - 1)) << 7);
+      };
+      for (int64_t c = 0; c < kLvlAhead && c < nchunks; ++c) tma_prefetch_2d(&tmP, (int)(c & 3) * 32, (int)row_of(c));
       int64_t issued = 0;
       for (int64_t it = 0; it < nchunks && !abort_sh; ++it) {
         const int s = (int)(it % kLvlStages);
         const uint32_t ph = (uint32_t)(it / kLvlStages) & 1u;
+        if (it + kLvlAhead < nchunks)
+          tma_prefetch_2d(&tmP, (int)((it + kLvlAhead) & 3) * 32, (int)row_of(it + kLvlAhead));
         if (!mbar_wait(&empty_bar[s], ph ^ 1)) {
           atomicExch(a.err, 9);
           abort_sh = 1;
           break;
         }
-        const int64_t u = blockIdx.x + (it >> 2) * gridDim.x;
-        const int64_t g = g_first + (u >> tb) * radix;
-        const int64_t row0 = ((g / radix - a.parent_lo) << (a.h - kMmaBits)) + ((u & ((1 << tb) - 1)) << 7);
+        const int64_t row0 = row_of(it);
         mbar_expect_tx(&loaded[s], kLvlChunk);
         tma_load_2d(sA + s * 2 * kLvlChunk, &tmP, (int)(it & 3) * 32, (int)row0, &loaded[s]);
         issued = it + 1;

@@ -42,6 +42,16 @@ def check(got, ref, prec):
     return err
 
 
+def distinct_sigma(pr):
+    """True when no block has a repeated singular value, i.e. every single path (and
+    so every partial path sum) is unique; within a degenerate subspace any orthonormal
+    Schmidt basis is correct and only the full path sum is fixed."""
+    plan = H().Plan(pr.n, pr.gates, pr.cut, pr.blocks, precision="c128")
+    sig = [plan.sigma(k) for k in range(len(pr.blocks))]
+    plan.close()
+    return all(np.all(np.abs(np.diff(v)) > 1e-6 * v[0]) for v in sig)
+
+
 def gpu_amps(pr, prec="c64", bitstrings=None, window=0, path_range=(0, 0), blocks=None, **opts):
     import torch
     plan = H().Plan(pr.n, pr.gates, pr.cut, pr.blocks if blocks is None else blocks,
@@ -326,6 +336,26 @@ def test_leaf_contraction_every_rank_and_width(prec, rank, tail):
     check(got, ref, prec)
     got2, _ = gpu_amps(pr, prec, bitstrings=bs, flags=hsf.FLAG_NO_LEAF_CONTRACT)
     check(got2, ref, prec)
+
+
+@pytest.mark.parametrize("rank,tail", [(1, 0), (2, 1), (4, 0), (4, 1), (8, 0)])
+def test_leaf_contraction_many_bitstrings(rank, tail):
+    """Above 65536 bitstrings the complex64 leaf contraction runs as one wave of CTAs
+    that walk the parents together; every rank and leaf width it takes, against the
+    state vector, plus a path range that starts and ends inside a parent's digits."""
+    pr = _leaf_rank_problem(rank, tail, seed=90 + rank + 10 * tail)
+    rng = np.random.default_rng(7 + rank)
+    bs = W.random_bitstrings(rng, pr.n, 70000)
+    ref = O.schrodinger(pr.n, pr.gates)[bs.astype(np.int64)]
+    got, info = gpu_amps(pr, "c64", bitstrings=bs)
+    check(got, ref, "c64")
+    if not distinct_sigma(pr):
+        return    # single paths are not unique when a block has repeated singular values
+    P = info["num_paths"]
+    sub = bs[:512]
+    want, _ = O.hsf_amplitudes(pr.n, pr.gates, pr.cut, pr.blocks, bitstrings=sub, path_range=(1, P - 1))
+    got_r, _ = gpu_amps(pr, "c64", bitstrings=bs, path_range=(1, P - 1))
+    check(got_r[:512], want, "c64")
 
 
 def test_c2_plan_uses_leaf_contraction_and_register_kernel():
