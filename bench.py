@@ -122,6 +122,30 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+# DRAM traffic per launch relative to the algorithmic bytes, from one ncu capture of the
+# kernel (dram__bytes_read.sum + dram__bytes_write.sum over the launch's algorithmic
+# bytes); valid only for the kernel source it was taken on, identified by the first 16
+# hex digits of its SHA-256.  The summaries named here hold the numbers and commands.
+PROFILED_TRAFFIC = {
+    "sweep": {"ratio": 275.1 / 335.5, "source": "paper_2502_06959_gb300/csrc/sweep.cu",
+              "sha256": "a5699515952870e8", "profile": "profiles/sweep_reg_level6_n30.md"},
+}
+
+
+def _source_hash(rel):
+    import hashlib
+    with open(os.path.join(ROOT, rel), "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def traffic_per_launch(kind, algorithmic_bytes_per_launch):
+    """ncu-derived DRAM bytes per launch, or None when no capture matches the source."""
+    e = PROFILED_TRAFFIC.get(kind)
+    if not e or _source_hash(e["source"]) != e["sha256"]:
+        return None
+    return e["ratio"] * algorithmic_bytes_per_launch
+
+
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -471,13 +495,31 @@ def main():
     e2e_value = args.steps * world / (float(e2e_t.item()) / 1e3)
 
     hbm_peak, bf16_peak, sm_max, peak_src = peaks()
-    sw = kstats.get("sweep", {})
-    sweep_ms = sw.get("ms", 0.0)
-    nl = max(1, sw.get("launches", 1))
-    sweep_gbs = sw.get("bytes", 0.0) / (sweep_ms / 1e3) / 1e9 if sweep_ms else 0.0
-    sweep_tflops = sw.get("flops", 0.0) / (sweep_ms / 1e3) / 1e12 if sweep_ms else 0.0
     fp32_peak_tflops = 152 * 128 * 2 * sm_max * 1e6 / 1e12
+    tf32_peak_tflops = bf16_peak * 1.1 / 2.25          # nominal dense TF32 / BF16 ratio
     total_kernel_ms = sum(v["ms"] for v in kstats.values())
+
+    def roofline_of(kind):
+        st = kstats.get(kind, {})
+        k_ms, nlk = st.get("ms", 0.0), max(1, st.get("launches", 1))
+        gbs = st.get("bytes", 0.0) / (k_ms / 1e3) / 1e9 if k_ms else 0.0
+        tfl = st.get("flops", 0.0) / (k_ms / 1e3) / 1e12 if k_ms else 0.0
+        tr = traffic_per_launch(kind, st.get("bytes", 0.0) / nlk)
+        r = {"kernel": kind, "launches": int(st.get("launches", 0)), "avg_launch_ms": k_ms / nlk,
+             "share": k_ms / total_kernel_ms if total_kernel_ms else 0.0}
+        if kind == "level_mma":
+            # TF32x3 product: counted flops are the three TF32 products actually issued
+            r.update({"bound": "tensor", "achieved": tfl, "peak": tf32_peak_tflops, "unit": "TFLOP/s",
+                      "frac": tfl / tf32_peak_tflops if tf32_peak_tflops else None,
+                      "peak_source": peak_src + " (bf16 x 1.1/2.25 nominal TF32 ratio)",
+                      "hbm_gbs": gbs, "hbm_frac": gbs / hbm_peak if hbm_peak else None, "traffic": tr})
+        else:
+            r.update({"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s",
+                      "frac": gbs / hbm_peak if hbm_peak else None, "traffic": tr, "peak_source": peak_src,
+                      "alu_tflops": tfl, "alu_peak_tflops": fp32_peak_tflops, "alu_frac": tfl / fp32_peak_tflops})
+        return r
+
+    dominant = max(kstats, key=lambda k: kstats[k]["ms"]) if kstats else "sweep"
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -492,12 +534,8 @@ def main():
         "run_only": {"value": args.steps / (ms_run / 1e3), "unit": UNIT, "ms_per_step": ms_run / args.steps},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(S * 8),
                 "d2h_bytes_per_step": int(S * 16)},
-        "roofline": {"bound": "hbm", "kernel": "sweep", "achieved": sweep_gbs, "peak": hbm_peak,
-                     "unit": "GB/s", "frac": sweep_gbs / hbm_peak if hbm_peak else None,
-                     "traffic": None, "peak_source": peak_src,
-                     "avg_launch_ms": sweep_ms / nl, "launches": int(sw.get("launches", 0)),
-                     "alu_tflops": sweep_tflops, "alu_peak_tflops": fp32_peak_tflops,
-                     "alu_frac": sweep_tflops / fp32_peak_tflops},
+        "roofline": roofline_of(dominant),
+        "rooflines": {k: roofline_of(k) for k in ("sweep", "level_mma", "leaf") if k in kstats},
         "kernels": {k: {"launches": int(v["launches"]), "ms": v["ms"],
                         "share": v["ms"] / total_kernel_ms if total_kernel_ms else 0.0}
                     for k, v in kstats.items() if v["launches"]},

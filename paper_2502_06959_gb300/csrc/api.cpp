@@ -446,7 +446,11 @@ hsf_status hsf_run(hsf_plan *p, const uint64_t *bits, size_t num, uint64_t windo
         la.num_groups = 1;
       }
       const double units = (double)la.num_parents * (double)num;
-      LAUNCH(HSF_KERNEL_LEAF, units * 2.0 * (1 << la.c) * csz + 16.0 * la.num_groups * num,
+      // algorithmic DRAM bytes: every parent state read once (at most: the gathered
+      // chunks, when the bitstrings touch few of them) plus the FP64 partials
+      const double gathered = units * 2.0 * (1 << la.c) * csz;
+      const double states = (double)la.num_parents * (double)((1ull << la.ha) + (1ull << la.hb)) * csz;
+      LAUNCH(HSF_KERNEL_LEAF, std::min(gathered, states) + 16.0 * la.num_groups * num,
              units * la.r * (8.0 * 2.0 * (1 << la.c) + 8.0), launch_leaf_contract(la, p->precision, st));
       LAUNCH(HSF_KERNEL_REDUCE, 16.0 * la.num_groups * num + 64.0 * num, 0.0,
              launch_reduce_partials(la.partial, la.num_groups, la.S, outd, comp, st));
