@@ -116,13 +116,20 @@ hsf_status named_matrix(int kind, double t, std::vector<cd> &m, int &nq) {
   return HSF_OK;
 }
 
+// acc += a * b, written out (std::complex's operator* takes a slow path that handles
+// infinities; the planner's matrices are finite)
+inline void cmac(cd &acc, const cd &a, const cd &b) {
+  acc = cd(acc.real() + a.real() * b.real() - a.imag() * b.imag(),
+           acc.imag() + a.real() * b.imag() + a.imag() * b.real());
+}
+
 std::vector<cd> matmul(const std::vector<cd> &a, const std::vector<cd> &b, int d) {
   std::vector<cd> r((size_t)d * d, 0.0);
   for (int i = 0; i < d; ++i)
     for (int k = 0; k < d; ++k) {
       const cd aik = a[(size_t)i * d + k];
       if (aik == 0.0) continue;
-      for (int j = 0; j < d; ++j) r[(size_t)i * d + j] += aik * b[(size_t)k * d + j];
+      for (int j = 0; j < d; ++j) cmac(r[(size_t)i * d + j], aik, b[(size_t)k * d + j]);
     }
   return r;
 }
@@ -484,7 +491,9 @@ void host_apply(std::vector<cd> &v, int c, const OpH &op, int digit) {
     for (int i = 0; i < dim; ++i) {
       int idx = 0;
       for (int x = 0; x < nq; ++x) idx |= ((i >> op.q[x]) & 1) << (nq - 1 - x);
-      v[i] *= m[idx];
+      cd z = 0.0;
+      cmac(z, v[i], m[idx]);
+      v[i] = z;
     }
     return;
   }
@@ -503,7 +512,7 @@ void host_apply(std::vector<cd> &v, int c, const OpH &op, int digit) {
     }
     for (int r = 0; r < d; ++r) {
       out[r] = 0.0;
-      for (int k = 0; k < d; ++k) out[r] += m[r * d + k] * in[k];
+      for (int k = 0; k < d; ++k) cmac(out[r], m[r * d + k], in[k]);
     }
     for (int k = 0; k < d; ++k) v[addr[k]] = out[k];
   }
@@ -616,6 +625,63 @@ void pack_pass(const PassH &ps, std::vector<DevOp> &dops, std::vector<C> &mats, 
 
 }  // namespace
 
+// W images of the tensor-core levels: per digit m, the level's program U_m (64 x 64,
+// column by column) in real form W[2i + a][2j + b] (a, b: re / im), split into TF32 hi
+// and lo parts.  The leaf level is left out when it will be contracted at the bitstrings
+// (leaf_c > 0): it is never swept then.
+void compose_mma_levels(hsf_plan &p, int leaf_c) {
+  const int B = (int)p.blocks.size();
+  const int dim = 1 << kMmaBits, K = 2 * dim;
+  std::vector<double> w((size_t)K * K);
+  std::vector<cd> v(dim);
+  for (int s = 0; s < 2; ++s)
+    for (int k = 1; k <= B; ++k) {
+      LevelH &lv = p.side[s].levels[k];
+      if (!lv.mma) continue;
+      if (k == B && leaf_c > 0) {
+        lv.mma = false;
+        continue;
+      }
+      const int r = (int)p.radix[k];
+      lv.wimg.assign((size_t)r * 2 * (kMmaWPartBytes / 4), 0.f);
+      // the ops after the last digit-dependent one are shared by every digit: compose
+      // them once (S, column-major), then U_m e_col = S (prefix_m e_col), where the
+      // prefix image of a basis vector has few nonzeros
+      size_t split = 0;
+      for (size_t o = 0; o < lv.ops.size(); ++o)
+        if (lv.ops[o].digits > 1) split = o + 1;
+      std::vector<cd> S((size_t)dim * dim);
+      for (int col = 0; col < dim; ++col) {
+        std::fill(v.begin(), v.end(), cd(0.0));
+        v[col] = 1.0;
+        for (size_t o = split; o < lv.ops.size(); ++o) host_apply(v, kMmaBits, lv.ops[o], 0);
+        std::copy(v.begin(), v.end(), S.begin() + (size_t)col * dim);
+      }
+      std::vector<cd> u(dim);
+      for (int m = 0; m < r; ++m) {
+        for (int col = 0; col < dim; ++col) {
+          std::fill(u.begin(), u.end(), cd(0.0));
+          u[col] = 1.0;
+          for (size_t o = 0; o < split; ++o) host_apply(u, kMmaBits, lv.ops[o], m);
+          std::fill(v.begin(), v.end(), cd(0.0));
+          for (int j = 0; j < dim; ++j) {
+            if (u[j] == cd(0.0)) continue;
+            const cd *sj = S.data() + (size_t)j * dim;
+            for (int row = 0; row < dim; ++row) cmac(v[row], sj[row], u[j]);
+          }
+          for (int row = 0; row < dim; ++row) {
+            w[(size_t)(2 * row) * K + 2 * col] = v[row].real();
+            w[(size_t)(2 * row) * K + 2 * col + 1] = -v[row].imag();
+            w[(size_t)(2 * row + 1) * K + 2 * col] = v[row].imag();
+            w[(size_t)(2 * row + 1) * K + 2 * col + 1] = v[row].real();
+          }
+        }
+        float *hi = lv.wimg.data() + (size_t)m * 2 * (kMmaWPartBytes / 4);
+        level_mma_image(w.data(), hi, hi + kMmaWPartBytes / 4);
+      }
+    }
+}
+
 hsf_status build_programs(hsf_plan &p, bool grad) {
   const int B = (int)p.blocks.size();
   std::vector<std::pair<bool, int>> order;
@@ -718,29 +784,7 @@ hsf_status build_programs(hsf_plan &p, bool grad) {
                 !lv.ops.empty();
       for (auto &op : lv.ops)
         for (int j = 0; j < op.nq && ok; ++j) ok = op.q[j] < kMmaBits;
-      if (!ok) continue;
-      const int dim = 1 << kMmaBits, K = 2 * dim;
-      const int r = (int)p.radix[k];
-      lv.mma = true;
-      lv.wimg.assign((size_t)r * 2 * (kMmaWPartBytes / 4), 0.f);
-      std::vector<double> w((size_t)K * K);
-      for (int m = 0; m < r; ++m) {
-        // U_m column by column, then its real form W[2i + a][2j + b] (a, b: re / im)
-        std::fill(w.begin(), w.end(), 0.0);
-        for (int col = 0; col < dim; ++col) {
-          std::vector<cd> v(dim, 0.0);
-          v[col] = 1.0;
-          for (auto &op : lv.ops) host_apply(v, kMmaBits, op, m);
-          for (int row = 0; row < dim; ++row) {
-            w[(size_t)(2 * row) * K + 2 * col] = v[row].real();
-            w[(size_t)(2 * row) * K + 2 * col + 1] = -v[row].imag();
-            w[(size_t)(2 * row + 1) * K + 2 * col] = v[row].imag();
-            w[(size_t)(2 * row + 1) * K + 2 * col + 1] = v[row].real();
-          }
-        }
-        float *hi = lv.wimg.data() + (size_t)m * 2 * (kMmaWPartBytes / 4);
-        level_mma_image(w.data(), hi, hi + kMmaWPartBytes / 4);
-      }
+      if (ok) lv.mma = true;                 // W is composed below, once the leaf is known
     }
     for (auto &lv : sd.levels) {
       split_passes(lv, sd.h, p.tile_max);
@@ -769,6 +813,7 @@ hsf_status build_programs(hsf_plan &p, bool grad) {
         }
     }
   }
+  compose_mma_levels(p, p.leaf_c);
   return HSF_OK;
 }
 

@@ -147,29 +147,44 @@ def _check(code: int):
         raise HsfError(code, load_library().hsf_last_error().decode())
 
 
+# numpy twin of hsf_gate (same field offsets), so a gate list marshals in a few array
+# operations instead of one ctypes attribute write per field
+_GATE_DTYPE = np.dtype({"names": ["kind", "nq", "q", "param", "param_id", "reserved", "mat"],
+                        "formats": [np.int32, np.int32, (np.int32, 4), np.float64, np.int32, np.int32,
+                                    np.uint64],
+                        "offsets": [hsf_gate.kind.offset, hsf_gate.nq.offset, hsf_gate.q.offset,
+                                    hsf_gate.param.offset, hsf_gate.param_id.offset,
+                                    hsf_gate.reserved.offset, hsf_gate.mat.offset],
+                        "itemsize": ctypes.sizeof(hsf_gate)})
+
+
 def _marshal(n: int, gates, blocks: Sequence[Sequence[int]]):
-    arr = (hsf_gate * max(1, len(gates)))()
-    keep = []
-    for i, g in enumerate(gates):
-        e = arr[i]
-        e.kind = KIND[g.kind]
-        e.nq = len(g.qubits)
-        for j, q in enumerate(g.qubits):
-            e.q[j] = int(q)
-        e.param = float(g.param)
-        e.param_id = int(g.param_id)
-        if g.kind == "matrix":
-            m = np.ascontiguousarray(np.asarray(g.matrix, dtype=np.complex128)).view(np.float64)
-            keep.append(m)
-            e.mat = m.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
-    circ = hsf_circuit(n, len(gates), arr)
+    ng = len(gates)
+    arr = np.zeros(max(1, ng), dtype=_GATE_DTYPE)
+    keep = [arr]
+    if ng:
+        arr["kind"][:ng] = [KIND[g.kind] for g in gates]
+        arr["nq"][:ng] = [len(g.qubits) for g in gates]
+        arr["q"][:ng] = [tuple(g.qubits) + (0,) * (4 - len(g.qubits)) for g in gates]
+        arr["param"][:ng] = [g.param for g in gates]
+        arr["param_id"][:ng] = [g.param_id for g in gates]
+        mi = [i for i, g in enumerate(gates) if g.kind == "matrix"]
+        if mi:
+            # all explicit 2x2 / 4x4 matrices in one buffer; each gate points at its slice
+            mats = [np.asarray(gates[i].matrix, dtype=np.complex128).ravel() for i in mi]
+            sizes = np.array([m.size for m in mats])
+            buf = np.ascontiguousarray(np.concatenate(mats)).view(np.float64)
+            keep.append(buf)
+            starts = np.concatenate(([0], np.cumsum(sizes)[:-1])) * 16
+            arr["mat"][mi] = buf.ctypes.data + starts
+    circ = hsf_circuit(n, ng, ctypes.cast(arr.ctypes.data, ctypes.POINTER(hsf_gate)))
     offs = np.zeros(len(blocks) + 1, dtype=np.int32)
     idx = []
     for b, blk in enumerate(blocks):
         idx.extend(int(x) for x in blk)
         offs[b + 1] = len(idx)
     idx = np.asarray(idx if idx else [0], dtype=np.int32)
-    keep += [offs, idx, arr]
+    keep += [offs, idx]
     bl = hsf_blocks(len(blocks), offs.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
                     idx.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)))
     return circ, bl, keep
