@@ -348,12 +348,25 @@ hsf_status hsf_run(hsf_plan *p, const uint64_t *bits, size_t num, uint64_t windo
   const int B = (int)p->blocks.size();
   const int top = L.leaf ? B - 1 : B;
   const uint64_t C = L.chunk;
+  // The two halves are independent until they are combined: side b runs on a second
+  // stream forked from and joined back into the caller's (events; also under capture).
+  // With profiling on, side b stays on the caller's stream, so that every launch's event
+  // pair times that launch alone.
+  const cudaStream_t st_main = st, st_b = g_profiling.load() ? st : side_stream();
+  cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
+  CUDA_TRY(cudaEventCreateWithFlags(&fork_ev, cudaEventDisableTiming));
+  CUDA_TRY(cudaEventCreateWithFlags(&join_ev, cudaEventDisableTiming));
+  std::unique_ptr<CUevent_st, void (*)(cudaEvent_t)> fork_guard(fork_ev, [](cudaEvent_t e) { cudaEventDestroy(e); });
+  std::unique_ptr<CUevent_st, void (*)(cudaEvent_t)> join_guard(join_ev, [](cudaEvent_t e) { cudaEventDestroy(e); });
   for (uint64_t a0 = (path_begin / C) * C; a0 < path_end; a0 += C) {
     const uint64_t c0 = std::max(a0, path_begin), c1 = std::min(a0 + C, path_end);
     if (c0 >= c1) continue;
     const void *last[2] = {nullptr, nullptr};
     int64_t last_lo = 0, last_hi = 0;
+    CUDA_TRY(cudaEventRecord(fork_ev, st_main));
+    CUDA_TRY(cudaStreamWaitEvent(st_b, fork_ev, 0));
     for (int s = 0; s < 2; ++s) {
+      const cudaStream_t st = s == 0 ? st_main : st_b;   // the launches below use `st`
       const SideH &sd = p->side[s];
       int64_t prev_lo = 0;
       for (int k = 0; k <= top; ++k) {
@@ -420,6 +433,8 @@ hsf_status hsf_run(hsf_plan *p, const uint64_t *bits, size_t num, uint64_t windo
         }
       }
     }
+    CUDA_TRY(cudaEventRecord(join_ev, st_b));
+    CUDA_TRY(cudaStreamWaitEvent(st_main, join_ev, 0));
     if (L.leaf) {
       LeafArgs la{};
       la.Pa = last[0];

@@ -91,6 +91,7 @@ struct SideH {
 namespace hsf {
 // planner.cpp
 cudaStream_t plan_stream();   // the calling thread's private non-blocking stream for plan work
+cudaStream_t side_stream();   // the calling thread's second stream for side b of hsf_run
 hsf_status set_error(hsf_status code, const char *fmt, ...);
 const char *last_error();
 hsf_status validate_and_load(hsf_plan &p, const hsf_circuit *c, int cut, const hsf_blocks *bl,

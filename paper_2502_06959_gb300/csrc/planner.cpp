@@ -63,6 +63,19 @@ cudaStream_t plan_stream() {
   return st;
 }
 
+// Second stream of the calling thread on which hsf_run sweeps side b (non-blocking).
+cudaStream_t side_stream() {
+  thread_local cudaStream_t st = nullptr;
+  thread_local int dev = -1;
+  int cur = 0;
+  cudaGetDevice(&cur);
+  if (!st || dev != cur) {
+    cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    dev = cur;
+  }
+  return st;
+}
+
 #define CUDA_TRY(expr)                                                                   \
   do {                                                                                   \
     cudaError_t e_ = (expr);                                                             \
