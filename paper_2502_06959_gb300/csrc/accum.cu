@@ -53,20 +53,40 @@ __global__ void gather_dot_kernel(GatherArgs a) {
   dst[1] = (double)im;
 }
 
-__global__ void reduce_partials_kernel(const double *partial, int32_t num_groups, int64_t S,
-                                       double *out, double *comp) {
-  const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= S) return;
-  double sr = out[2 * s], si = out[2 * s + 1];
-  double cr = comp[2 * s], ci = comp[2 * s + 1];
-  for (int g = 0; g < num_groups; ++g) {
-    neumaier_add(sr, cr, partial[2 * ((int64_t)g * S + s)]);
-    neumaier_add(si, ci, partial[2 * ((int64_t)g * S + s) + 1]);
+// out[s] += sum_g partial[g][s] (compensated).  A CTA takes 32 bitstrings; its 8 rows of
+// threads sum every 8th group each (Neumaier), and row 0 folds the 8 compensated pairs
+// into the running output.
+constexpr int kReduceRows = 8;
+__global__ void __launch_bounds__(32 * kReduceRows) reduce_partials_kernel(const double *partial, int32_t num_groups,
+                                                                           int64_t S, double *out, double *comp) {
+  __shared__ double sh[kReduceRows][32][4];
+  const int64_t s = (int64_t)blockIdx.x * 32 + threadIdx.x;
+  const int y = threadIdx.y;
+  double sr = 0.0, si = 0.0, cr = 0.0, ci = 0.0;
+  if (s < S)
+    for (int g = y; g < num_groups; g += kReduceRows) {
+      const double2 v = reinterpret_cast<const double2 *>(partial)[(int64_t)g * S + s];
+      neumaier_add(sr, cr, v.x);
+      neumaier_add(si, ci, v.y);
+    }
+  sh[y][threadIdx.x][0] = sr;
+  sh[y][threadIdx.x][1] = si;
+  sh[y][threadIdx.x][2] = cr;
+  sh[y][threadIdx.x][3] = ci;
+  __syncthreads();
+  if (y != 0 || s >= S) return;
+  double tr = out[2 * s], ti = out[2 * s + 1];
+  double kr = comp[2 * s], ki = comp[2 * s + 1];
+  for (int r = 0; r < kReduceRows; ++r) {
+    neumaier_add(tr, kr, sh[r][threadIdx.x][0]);
+    neumaier_add(ti, ki, sh[r][threadIdx.x][1]);
+    kr += sh[r][threadIdx.x][2];
+    ki += sh[r][threadIdx.x][3];
   }
-  out[2 * s] = sr;
-  out[2 * s + 1] = si;
-  comp[2 * s] = cr;
-  comp[2 * s + 1] = ci;
+  out[2 * s] = tr;
+  out[2 * s + 1] = ti;
+  comp[2 * s] = kr;
+  comp[2 * s + 1] = ki;
 }
 
 // 32x32 output tile per CTA, 256 threads, 4 outputs per thread, K staged by 16.
@@ -295,7 +315,7 @@ __device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0
 constexpr size_t leaf_ring_bytes(int cb, int rm) { return (size_t)kDepth * (128 / rm) * ((2u << cb) + 2) * 8; }
 
 template <int CB, int RM>
-__global__ void __launch_bounds__(128) leaf_contract_async_kernel(LeafArgs a) {
+__global__ void __launch_bounds__(128, 6) leaf_contract_async_kernel(LeafArgs a) {
   using C = float2;
   constexpr int D = 1 << CB;
   constexpr int SPB = 128 / RM;                // bitstrings per CTA
@@ -610,7 +630,8 @@ cudaError_t launch_gather_dot(const GatherArgs &a, int precision, cudaStream_t s
 cudaError_t launch_reduce_partials(const double *partial, int32_t num_groups, int64_t S,
                                    double *out, double *comp, cudaStream_t st) {
   if (S <= 0) return cudaSuccess;
-  reduce_partials_kernel<<<(unsigned)((S + 255) / 256), 256, 0, st>>>(partial, num_groups, S, out, comp);
+  reduce_partials_kernel<<<(unsigned)((S + 31) / 32), dim3(32, kReduceRows), 0, st>>>(partial, num_groups, S, out,
+                                                                                      comp);
   return cudaGetLastError();
 }
 
