@@ -235,10 +235,12 @@ int64_t hsf_plan_describe(const hsf_plan *p, char *buf, int64_t cap) {
       const LevelH &lv = sd.levels[k];
       std::snprintf(line, sizeof line, " level %zu: radix %llu, %zu ops, %s\n", k,
                     (unsigned long long)p->radix[k], lv.ops.size(),
-                    lv.mma ? "tensor-core product (TF32x3) on the 6 lowest storage bits"
-                           : (std::to_string(lv.passes.size()) + " passes").c_str());
+                    ((lv.mma ? std::string("tensor-core product (TF32x3) on the 6 lowest storage bits, then ")
+                             : std::string()) +
+                     std::to_string(lv.passes.size()) + " passes")
+                        .c_str());
       out += line;
-      for (size_t pi = 0; pi < lv.passes.size() && !lv.mma; ++pi) {
+      for (size_t pi = 0; pi < lv.passes.size(); ++pi) {
         const PassH &ps = lv.passes[pi];
         std::snprintf(line, sizeof line, "  pass %zu: active=0x%llx t=%d ops=%zu groups=%zu\n", pi,
                       (unsigned long long)ps.active, ps.t, ps.ops.size(), ps.groups.size());
@@ -392,14 +394,14 @@ hsf_status hsf_run(hsf_plan *p, const uint64_t *bits, size_t num, uint64_t windo
           LAUNCH(HSF_KERNEL_LEVEL_MMA, (amps + parents) * csz, 3.0 * 2.0 * 128.0 * 128.0 * (amps / 64.0),
                  launch_level_mma(g, st));
         }
-        for (size_t pi = 0; pi < lv.passes.size() && !lv.mma; ++pi) {
+        for (size_t pi = 0; pi < lv.passes.size(); ++pi) {
           const PassH &ps = lv.passes[pi];
           SweepArgs a{};
           a.ops = (const DevOp *)((unsigned char *)p->dev_table + ps.ops_off);
           a.num_ops = ps.num_ops;
           a.h = sd.h;
           a.mats = (unsigned char *)p->dev_table + ps.mats_off;
-          a.read_parent = (pi == 0 && k > 0) ? 1 : 0;
+          a.read_parent = (pi == 0 && k > 0 && !lv.mma) ? 1 : 0;   // after a product: in place
           a.init_zero = (pi == 0 && k == 0) ? 1 : 0;
           a.src = a.read_parent ? par : dst;
           a.dst = dst;

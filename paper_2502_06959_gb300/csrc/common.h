@@ -185,6 +185,7 @@ size_t path_gemm_operand_bytes(int mode, int64_t M, int64_t N, int64_t paths);
 // ("columns" of U_m) are contiguous, so the level is a real GEMM with K = 2^(kMmaBits+1).
 constexpr int kMmaBits = 6;
 constexpr int kMmaMinH = kMmaBits + 7;           // at least one 128-row tile per node
+constexpr int kMmaMinPrefix = 4;                  // ops a partial product must replace
 constexpr size_t kMmaWPartBytes = 128 * 128 * 4;  // one TF32 part of W (64 KB)
 struct LevelMmaArgs {
   const float *parent;     // previous level buffer, complex64 as float pairs

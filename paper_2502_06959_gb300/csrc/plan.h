@@ -73,6 +73,10 @@ struct LevelH {
   bool mma = false;
   std::vector<float> wimg;
   size_t w_off = 0;
+  // candidate: the first mma_prefix ops act on the kMmaBits lowest storage bits (the
+  // whole program when mma_prefix == ops.size()); once chosen, those ops are composed
+  // into W and removed from ops, and the rest run as in-place passes after the product
+  size_t mma_prefix = 0;
 };
 
 struct SideH {

@@ -650,24 +650,31 @@ void compose_mma_levels(hsf_plan &p, int leaf_c) {
   for (int s = 0; s < 2; ++s)
     for (int k = 1; k <= B; ++k) {
       LevelH &lv = p.side[s].levels[k];
-      if (!lv.mma) continue;
-      if (k == B && leaf_c > 0) {
-        lv.mma = false;
-        continue;
+      if (lv.mma_prefix == 0 || (k == B && leaf_c > 0)) continue;
+      // the prefix becomes the product; the rest stays as in-place passes
+      std::vector<OpH> prefix(lv.ops.begin(), lv.ops.begin() + lv.mma_prefix);
+      lv.ops.erase(lv.ops.begin(), lv.ops.begin() + lv.mma_prefix);
+      lv.passes.clear();
+      if (!lv.ops.empty()) {
+        split_passes(lv, p.side[s].h, p.tile_max);
+        if (!(p.flags & HSF_FLAG_NO_REGISTER_SWEEP))
+          for (auto &ps : lv.passes) build_groups(ps, p.rbits);
       }
+      lv.mma = true;
+      const std::vector<OpH> &mops = prefix;
       const int r = (int)p.radix[k];
       lv.wimg.assign((size_t)r * 2 * (kMmaWPartBytes / 4), 0.f);
       // the ops after the last digit-dependent one are shared by every digit: compose
       // them once (S, column-major), then U_m e_col = S (prefix_m e_col), where the
       // prefix image of a basis vector has few nonzeros
       size_t split = 0;
-      for (size_t o = 0; o < lv.ops.size(); ++o)
-        if (lv.ops[o].digits > 1) split = o + 1;
+      for (size_t o = 0; o < mops.size(); ++o)
+        if (mops[o].digits > 1) split = o + 1;
       std::vector<cd> S((size_t)dim * dim);
       for (int col = 0; col < dim; ++col) {
         std::fill(v.begin(), v.end(), cd(0.0));
         v[col] = 1.0;
-        for (size_t o = split; o < lv.ops.size(); ++o) host_apply(v, kMmaBits, lv.ops[o], 0);
+        for (size_t o = split; o < mops.size(); ++o) host_apply(v, kMmaBits, mops[o], 0);
         std::copy(v.begin(), v.end(), S.begin() + (size_t)col * dim);
       }
       std::vector<cd> u(dim);
@@ -675,7 +682,7 @@ void compose_mma_levels(hsf_plan &p, int leaf_c) {
         for (int col = 0; col < dim; ++col) {
           std::fill(u.begin(), u.end(), cd(0.0));
           u[col] = 1.0;
-          for (size_t o = 0; o < split; ++o) host_apply(u, kMmaBits, lv.ops[o], m);
+          for (size_t o = 0; o < split; ++o) host_apply(u, kMmaBits, mops[o], m);
           std::fill(v.begin(), v.end(), cd(0.0));
           for (int j = 0; j < dim; ++j) {
             if (u[j] == cd(0.0)) continue;
@@ -789,15 +796,26 @@ hsf_status build_programs(hsf_plan &p, bool grad) {
         for (int j = 0; j < op.nq; ++j) c = std::max(c, op.q[j] + 1);
       leaf_c = c <= 5 ? std::max(leaf_c, c) : -1;
     }
-    // levels whose whole program sits on the kMmaBits lowest storage bits run as one
-    // tensor-core product per digit (complex64 forward programs)
+    // levels whose program, or a leading run of at least kMmaMinPrefix of its ops holding
+    // every digit-dependent op, sits on the kMmaBits lowest storage bits run that part as
+    // one tensor-core product per digit (complex64 forward programs); W is composed below,
+    // once the leaf is known
     for (int k = 1; k <= B && !grad; ++k) {
       LevelH &lv = sd.levels[k];
-      bool ok = p.precision == HSF_PREC_C64 && sd.h >= kMmaMinH && !(p.flags & HSF_FLAG_NO_TC_LEVEL) &&
-                !lv.ops.empty();
-      for (auto &op : lv.ops)
-        for (int j = 0; j < op.nq && ok; ++j) ok = op.q[j] < kMmaBits;
-      if (ok) lv.mma = true;                 // W is composed below, once the leaf is known
+      if (p.precision != HSF_PREC_C64 || sd.h < kMmaMinH || (p.flags & HSF_FLAG_NO_TC_LEVEL)) break;
+      // a partial product adds a pass: only worth it on large levels
+      const bool large =
+          (long double)(p.num_paths / p.below[k]) * (long double)(1ull << sd.h) >= (long double)(1ull << 26);
+      size_t q = 0;
+      for (; q < lv.ops.size(); ++q) {
+        bool low = true;
+        for (int j = 0; j < lv.ops[q].nq; ++j) low = low && lv.ops[q].q[j] < kMmaBits;
+        if (!low) break;
+      }
+      bool digits_in_prefix = true;
+      for (size_t o = q; o < lv.ops.size(); ++o) digits_in_prefix = digits_in_prefix && lv.ops[o].digits == 1;
+      if (q > 0 && digits_in_prefix && (q == lv.ops.size() || (large && q >= (size_t)kMmaMinPrefix)))
+        lv.mma_prefix = q;
     }
     for (auto &lv : sd.levels) {
       split_passes(lv, sd.h, p.tile_max);
