@@ -364,21 +364,25 @@ __global__ void __launch_bounds__(128, 1) gemm_kernel(const __grid_constant__ CU
 // ---------------------------------------------------------------------------
 // Tensor-core tree level
 // ---------------------------------------------------------------------------
-// Child g of a level whose program sits on the 6 lowest storage bits is U_m applied to
-// every 64-amplitude row of its parent (m = g % radix).  Real form, k = 2 r + (re, im):
-// child[row][n] = sum_k parent[row][k] W_m[n][k], W_m 128 x 128.  A CTA serves one digit:
-// it keeps W_m (TF32 hi and lo parts, 128 KB) in shared memory and walks 128-row tiles
-// of the parents (MMA M = 128 rows, N = 128, K = 128 in four 32-float chunks).  Four
-// producer warps split each chunk into TF32 hi and lo parts in the MMA's 128-byte
-// swizzled layout; one thread issues hi*hi + lo*hi + hi*lo (tcgen05.mma kind::tf32)
-// into one of two TMEM accumulators; four epilogue warps read the other back and
-// write the child rows.  Every wait is bounded; on expiry the CTA records an error,
-// drains its MMAs, frees TMEM and returns.
-constexpr int kLvlStages = 3;
-constexpr int kLvlAhead = 8;                    // chunks prefetched into L2 ahead of the loads
+// Child g of a level whose program (or its leading ops) sits on the 6 lowest storage bits
+// is U_m applied to every 64-amplitude row of its parent (m = g % radix).  Real form,
+// k = 2 r + (re, im): child[row][n] = sum_k W_m[n][k] parent[row][k], W_m 128 x 128.
+// A CTA serves one digit.  W_m's TF32 hi and lo parts sit in tensor memory as the MMA's
+// A operand (lanes = output component n, columns = k), so shared memory holds only the
+// streamed parent rows: 128-row tiles (MMA N = 128) in 32-float K-chunks.  One thread
+// issues TMA loads (128-byte swizzle) into an 8-stage ring and prefetches chunks into L2;
+// four warps compute each chunk's TF32 low part; one thread issues W_hi P_hi + W_hi P_lo +
+// W_lo P_hi (tcgen05.mma kind::tf32, A from TMEM) into one of two TMEM accumulators; four
+// warps read the other back and write the child rows.  Every wait is bounded; on expiry
+// the CTA records an error, drains its MMAs and loads, frees TMEM and returns.
+constexpr int kLvlRaw = 4;                      // TMA stages (raw FP32 chunks = the hi parts)
+constexpr int kLvlLo = 4;                       // low-part buffers
+constexpr int kLvlOut = 4;                      // 32-row output staging buffers (16 KB each)
+constexpr int kLvlAhead = 12;                   // chunks prefetched into L2 ahead of the loads
 constexpr int kLvlChunk = 128 * 128;            // bytes: 128 rows x 32 floats
 constexpr int kLvlThreads = 320;                // 4 low-part, 4 epilogue, 1 MMA, 1 TMA warp
-constexpr size_t kLvlSmem = 2 * kMmaWPartBytes + (size_t)kLvlStages * 2 * kLvlChunk + 1024;
+constexpr uint32_t kLvlTmemCols = 512;          // W hi [0,128), W lo [128,256), D 2 x 128
+constexpr size_t kLvlSmem = (size_t)(kLvlRaw + kLvlLo + kLvlOut) * kLvlChunk + 1024;
 
 __device__ __forceinline__ void tma_prefetch_2d(const CUtensorMap *map, int x, int y) {
   asm volatile("cp.async.bulk.prefetch.tensor.2d.L2.global.tile [%0, {%1, %2}];" ::"l"((uint64_t)map), "r"(x), "r"(y)
@@ -391,28 +395,26 @@ __device__ __forceinline__ void mma_commit(uint64_t *bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
                : "memory");
 }
-__device__ __forceinline__ void mma_tf32(uint32_t d, uint64_t da, uint64_t db, uint32_t idesc, uint32_t acc) {
+// D (TMEM) += A (TMEM) x B (shared-memory descriptor)
+__device__ __forceinline__ void mma_tf32_ts(uint32_t d, uint32_t a, uint64_t db, uint32_t idesc, uint32_t acc) {
   asm volatile(
       "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
-      " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n"
-      ::"r"(d), "l"(da), "l"(db), "r"(idesc), "r"(acc)
+      " tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n}\n"
+      ::"r"(d), "r"(a), "l"(db), "r"(idesc), "r"(acc)
       : "memory");
-}
-// byte offset of (row, 16-byte piece q) in a 128-row K-major tile with 128-byte swizzle
-__device__ __forceinline__ uint32_t swz_off(int row, int q) {
-  return (uint32_t)((row >> 3) * 1024 + (row & 7) * 128 + ((q ^ (row & 7)) << 4));
 }
 
 __global__ void __launch_bounds__(kLvlThreads, 1) level_mma_kernel(const __grid_constant__ CUtensorMap tmP,
                                                                   LevelMmaArgs a) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
-  uint8_t *sW = smem;                                   // W hi: 4 chunks, then W lo: 4 chunks
-  uint8_t *sA = smem + 2 * kMmaWPartBytes;              // stage s: hi chunk (raw FP32), lo chunk
-  __shared__ __align__(8) uint64_t loaded[kLvlStages], full_bar[kLvlStages], empty_bar[kLvlStages], tfull[2],
+  uint8_t *sR = smem;                                   // raw stage r (hi part): sR + r * kLvlChunk
+  uint8_t *sL = sR + kLvlRaw * kLvlChunk;               // low-part buffer l: sL + l * kLvlChunk
+  float *sO = reinterpret_cast<float *>(sL + kLvlLo * kLvlChunk);   // output staging: [2][32 rows][128]
+  __shared__ __align__(8) uint64_t loaded[kLvlRaw], raw_empty[kLvlRaw], full_bar[kLvlLo], lo_empty[kLvlLo], tfull[2],
       tempty[2], drain;
   __shared__ uint32_t tmem_sh;
-  __shared__ volatile int abort_sh;
+  __shared__ volatile int abort_sh, epi_abort;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t radix = a.radix;
   const int m = blockIdx.y;
@@ -424,10 +426,14 @@ __global__ void __launch_bounds__(kLvlThreads, 1) level_mma_kernel(const __grid_
   const int64_t nchunks = units > blockIdx.x ? ((units - 1 - blockIdx.x) / gridDim.x + 1) * 4 : 0;
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < kLvlStages; ++s) {
+    epi_abort = 0;
+    for (int s = 0; s < kLvlRaw; ++s) {
       mbar_init(&loaded[s], 1);
+      mbar_init(&raw_empty[s], 1);
+    }
+    for (int s = 0; s < kLvlLo; ++s) {
       mbar_init(&full_bar[s], 128);
-      mbar_init(&empty_bar[s], 1);
+      mbar_init(&lo_empty[s], 1);
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&tfull[b], 1);
@@ -437,16 +443,9 @@ __global__ void __launch_bounds__(kLvlThreads, 1) level_mma_kernel(const __grid_
     abort_sh = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  {
-    const int4 *gw = reinterpret_cast<const int4 *>(reinterpret_cast<const uint8_t *>(a.w) +
-                                                    (size_t)m * 2 * kMmaWPartBytes);
-    int4 *sw4 = reinterpret_cast<int4 *>(sW);
-    for (int i = threadIdx.x; i < (int)(2 * kMmaWPartBytes / 16); i += blockDim.x) sw4[i] = gw[i];
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // visible to the tensor core
-  }
   if (warp == 8) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_sh)),
-                 "r"(256)
+                 "r"(kLvlTmemCols)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -454,35 +453,66 @@ __global__ void __launch_bounds__(kLvlThreads, 1) level_mma_kernel(const __grid_
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = tmem_sh;
+  if (warp >= 4 && warp < 8) {
+    // W_m into TMEM: lane n holds row n; columns [0,128) the hi part, [128,256) the lo part
+    const int q4 = warp & 3;
+    const float *wrow = reinterpret_cast<const float *>(a.w) + (size_t)m * 2 * 128 * 128 + (size_t)(q4 * 32 + lane) * 128;
+#pragma unroll 1
+    for (int c = 0; c < 8; ++c) {
+      const float *src = wrow + (size_t)(c >> 2) * 128 * 128 + (c & 3) * 32;
+      uint32_t v[32];
+#pragma unroll
+      for (int j = 0; j < 32; j += 4) {
+        const float4 x = *reinterpret_cast<const float4 *>(src + j);
+        v[j] = __float_as_uint(x.x);
+        v[j + 1] = __float_as_uint(x.y);
+        v[j + 2] = __float_as_uint(x.z);
+        v[j + 3] = __float_as_uint(x.w);
+      }
+      const uint32_t taddr = tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(c * 32);
+      asm volatile(
+          "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,"
+          "%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};" ::"r"(taddr),
+          "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]), "r"(v[8]),
+          "r"(v[9]), "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15]), "r"(v[16]),
+          "r"(v[17]), "r"(v[18]), "r"(v[19]), "r"(v[20]), "r"(v[21]), "r"(v[22]), "r"(v[23]), "r"(v[24]),
+          "r"(v[25]), "r"(v[26]), "r"(v[27]), "r"(v[28]), "r"(v[29]), "r"(v[30]), "r"(v[31])
+          : "memory");
+    }
+    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 
   if (warp < 4) {
     // ---- low parts: lo = x - (x with its 13 low mantissa bits cleared) ----
-    // The TMA lands the raw FP32 chunk in the stage's hi slot; kind::tf32 reads only the
-    // top 19 bits of each operand, so the hi part is that truncation and lo is exact.
+    // The TMA lands the raw FP32 chunk in a raw stage; kind::tf32 reads only the top 19
+    // bits of each operand, so the hi part is that truncation and lo is exact.
     const int t = threadIdx.x;
     for (int64_t it = 0; it < nchunks && !abort_sh; ++it) {
-      const int s = (int)(it % kLvlStages);
-      const uint32_t ph = (uint32_t)(it / kLvlStages) & 1u;
-      if (!mbar_wait(&loaded[s], ph)) {
+      const int r = (int)(it % kLvlRaw), l = (int)(it % kLvlLo);
+      if (!mbar_wait(&loaded[r], (uint32_t)(it / kLvlRaw) & 1u) ||
+          !mbar_wait(&lo_empty[l], ((uint32_t)(it / kLvlLo) & 1u) ^ 1u)) {
         atomicExch(a.err, 4);
         abort_sh = 1;
         break;
       }
-      const uint8_t *hi = sA + s * 2 * kLvlChunk;
-      uint8_t *lo = sA + s * 2 * kLvlChunk + kLvlChunk;
+      const uint8_t *hi = sR + r * kLvlChunk;
+      uint8_t *lo = sL + l * kLvlChunk;
 #pragma unroll
       for (int i = 0; i < 8; ++i) {
         const uint32_t off = (uint32_t)(t + 128 * i) * 16;    // same swizzled place in both
         const float4 x = *reinterpret_cast<const float4 *>(hi + off);
-        float4 l;
-        l.x = x.x - __uint_as_float(__float_as_uint(x.x) & 0xffffe000u);
-        l.y = x.y - __uint_as_float(__float_as_uint(x.y) & 0xffffe000u);
-        l.z = x.z - __uint_as_float(__float_as_uint(x.z) & 0xffffe000u);
-        l.w = x.w - __uint_as_float(__float_as_uint(x.w) & 0xffffe000u);
-        *reinterpret_cast<float4 *>(lo + off) = l;
+        float4 v;
+        v.x = x.x - __uint_as_float(__float_as_uint(x.x) & 0xffffe000u);
+        v.y = x.y - __uint_as_float(__float_as_uint(x.y) & 0xffffe000u);
+        v.z = x.z - __uint_as_float(__float_as_uint(x.z) & 0xffffe000u);
+        v.w = x.w - __uint_as_float(__float_as_uint(x.w) & 0xffffe000u);
+        *reinterpret_cast<float4 *>(lo + off) = v;
       }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      mbar_arrive(&full_bar[s]);
+      mbar_arrive(&full_bar[l]);
     }
   } else if (warp == 9) {
     // ---- TMA: chunk c = chunk c % 4 of unit blockIdx.x + (c / 4) * gridDim.x ----
@@ -497,23 +527,22 @@ __global__ void __launch_bounds__(kLvlThreads, 1) level_mma_kernel(const __grid_
       for (int64_t c = 0; c < kLvlAhead && c < nchunks; ++c) tma_prefetch_2d(&tmP, (int)(c & 3) * 32, (int)row_of(c));
       int64_t issued = 0;
       for (int64_t it = 0; it < nchunks && !abort_sh; ++it) {
-        const int s = (int)(it % kLvlStages);
-        const uint32_t ph = (uint32_t)(it / kLvlStages) & 1u;
+        const int s = (int)(it % kLvlRaw);
+        const uint32_t ph = (uint32_t)(it / kLvlRaw) & 1u;
         if (it + kLvlAhead < nchunks)
           tma_prefetch_2d(&tmP, (int)((it + kLvlAhead) & 3) * 32, (int)row_of(it + kLvlAhead));
-        if (!mbar_wait(&empty_bar[s], ph ^ 1)) {
+        if (!mbar_wait(&raw_empty[s], ph ^ 1)) {
           atomicExch(a.err, 9);
           abort_sh = 1;
           break;
         }
-        const int64_t row0 = row_of(it);
         mbar_expect_tx(&loaded[s], kLvlChunk);
-        tma_load_2d(sA + s * 2 * kLvlChunk, &tmP, (int)(it & 3) * 32, (int)row0, &loaded[s]);
+        tma_load_2d(sR + s * kLvlChunk, &tmP, (int)(it & 3) * 32, (int)row_of(it), &loaded[s]);
         issued = it + 1;
       }
       // every load issued has landed before the CTA can exit (matters only on abort)
-      for (int64_t it = issued > kLvlStages ? issued - kLvlStages : 0; it < issued; ++it)
-        if (!mbar_wait(&loaded[it % kLvlStages], (uint32_t)(it / kLvlStages) & 1u)) atomicExch(a.err, 10);
+      for (int64_t it = issued > kLvlRaw ? issued - kLvlRaw : 0; it < issued; ++it)
+        if (!mbar_wait(&loaded[it % kLvlRaw], (uint32_t)(it / kLvlRaw) & 1u)) atomicExch(a.err, 10);
     }
     __syncwarp();
   } else if (warp == 8) {
@@ -530,31 +559,30 @@ __global__ void __launch_bounds__(kLvlThreads, 1) level_mma_kernel(const __grid_
           break;
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const uint32_t d = tmem + (uint32_t)(b * 128);
+        const uint32_t d = tmem + 256u + (uint32_t)(b * 128);
         bool ok = true;
         for (int kc = 0; kc < 4; ++kc, ++it) {
-          const int s = (int)(it % kLvlStages);
-          const uint32_t ph = (uint32_t)(it / kLvlStages) & 1u;
-          if (!mbar_wait(&full_bar[s], ph)) {
+          const int r = (int)(it % kLvlRaw), l = (int)(it % kLvlLo);
+          if (!mbar_wait(&full_bar[l], (uint32_t)(it / kLvlLo) & 1u)) {
             atomicExch(a.err, 6);
             abort_sh = 1;
             ok = false;
             break;
           }
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-          const uint64_t ahi = make_desc(sA + s * 2 * kLvlChunk), alo = make_desc(sA + s * 2 * kLvlChunk + kLvlChunk);
-          const uint64_t whi = make_desc(sW + kc * kLvlChunk), wlo = make_desc(sW + kMmaWPartBytes + kc * kLvlChunk);
-          // D[n][row] = sum_k W[n][k] parent[row][k]: W is the MMA's A operand (M = 128
-          // output components), the parent rows its B operand (N = 128 rows), so TMEM
-          // lane n holds output component n of every row and the stores coalesce
+          const uint64_t phi = make_desc(sR + r * kLvlChunk), plo = make_desc(sL + l * kLvlChunk);
+          // D[n][row] = sum_k W[n][k] parent[row][k]: W (TMEM) is the MMA's A operand
+          // (M = 128 output components), the parent rows its B operand (N = 128 rows)
 #pragma unroll
           for (int term = 0; term < 3; ++term) {
-            const uint64_t dp = term == 1 ? alo : ahi, dw = term == 2 ? wlo : whi;
+            const uint64_t dp = term == 1 ? plo : phi;
+            const uint32_t wcol = (term == 2 ? 128u : 0u) + (uint32_t)(kc * 32);
 #pragma unroll
-            for (int k = 0; k < 4; ++k)      // 8 TF32 of K (32 bytes) per MMA
-              mma_tf32(d, dw + 2 * k, dp + 2 * k, idesc, (kc | term | k) ? 1u : 0u);
+            for (int k = 0; k < 4; ++k)      // 8 TF32 of K per MMA (32 bytes, 8 columns)
+              mma_tf32_ts(d, tmem + wcol + 8u * k, dp + 2 * k, idesc, (kc | term | k) ? 1u : 0u);
           }
-          mma_commit(&empty_bar[s]);          // the stage is free once these MMAs finish
+          mma_commit(&raw_empty[r]);          // both buffers are free once these MMAs finish
+          mma_commit(&lo_empty[l]);
         }
         if (!ok) break;
         mma_commit(&tfull[b]);                // the accumulator is complete
@@ -566,24 +594,32 @@ __global__ void __launch_bounds__(kLvlThreads, 1) level_mma_kernel(const __grid_
     __syncwarp();
   } else {
     // ---- epilogue: TMEM lane quarter (warp & 3) holds output components 32 (warp & 3)
-    // .. + 31; TMEM column j of the accumulator is row j of the tile ----
+    // .. + 31; TMEM column j of the accumulator is row j of the tile.  Each 32-row quarter
+    // is staged in shared memory row-major (the global layout) and written by one bulk
+    // copy: those 32 rows are 16 KB contiguous in the child state. ----
     const int q4 = warp & 3;
     const int comp = q4 * 32 + lane;
-    int64_t tu = 0;
-    for (int64_t u = blockIdx.x; u < units && !abort_sh; u += gridDim.x, ++tu) {
+    const bool leader = warp == 4 && lane == 0;
+    int64_t tu = 0, nq = 0;                              // units done, quarters stored
+    // The four warps meet at named barriers, so they decide to stop together: only they
+    // write epi_abort, before a barrier, and all read it after.
+    for (int64_t u = blockIdx.x; u < units; u += gridDim.x, ++tu) {
       const int b = (int)(tu & 1);
-      if (!mbar_wait(&tfull[b], (uint32_t)(tu >> 1) & 1u)) {
-        atomicExch(a.err, 8);
+      const bool ok = mbar_wait(&tfull[b], (uint32_t)(tu >> 1) & 1u);
+      if (!ok) epi_abort = 1;
+      asm volatile("bar.sync 1, 128;" ::: "memory");
+      if (epi_abort) {
+        if (!ok) atomicExch(a.err, 8);
         abort_sh = 1;
         break;
       }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const int64_t g = g_first + (u >> tb) * radix;
-      float *dst = a.child + (((uint64_t)(g - a.node_lo) << a.h) + ((uint64_t)(u & ((1 << tb) - 1)) << 13)) * 2 + comp;
-#pragma unroll
-      for (int c0 = 0; c0 < 128; c0 += 32) {
+      float *dst = a.child + (((uint64_t)(g - a.node_lo) << a.h) + ((uint64_t)(u & ((1 << tb) - 1)) << 13)) * 2;
+#pragma unroll 1
+      for (int qr = 0; qr < 4; ++qr, ++nq) {
         uint32_t v[32];
-        const uint32_t taddr = tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(b * 128 + c0);
+        const uint32_t taddr = tmem + ((uint32_t)(q4 * 32) << 16) + 256u + (uint32_t)(b * 128 + qr * 32);
         asm volatile(
             "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
             "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
@@ -593,18 +629,32 @@ __global__ void __launch_bounds__(kLvlThreads, 1) level_mma_kernel(const __grid_
               "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
             : "r"(taddr));
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        // the staging buffer of this quarter was last read by the bulk copy two quarters ago
+        if (leader && nq >= kLvlOut) asm volatile("cp.async.bulk.wait_group.read %0;" ::"n"(kLvlOut - 1) : "memory");
+        asm volatile("bar.sync 1, 128;" ::: "memory");
+        float *stage = sO + (size_t)(nq % kLvlOut) * 32 * 128;
 #pragma unroll
-        for (int j = 0; j < 32; ++j) dst[(size_t)(c0 + j) * 128] = __uint_as_float(v[j]);
+        for (int j = 0; j < 32; ++j) stage[j * 128 + comp] = __uint_as_float(v[j]);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("bar.sync 1, 128;" ::: "memory");
+        if (leader) {
+          asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst + (size_t)qr * 32 * 128),
+                       "r"(smem_u32(stage)), "r"(32 * 128 * 4)
+                       : "memory");
+          asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+        }
       }
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       mbar_arrive(&tempty[b]);
     }
+    // the CTA exits only once its output copies are complete
+    if (leader) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (warp == 8) {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(256) : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kLvlTmemCols) : "memory");
   }
 }
 
@@ -728,16 +778,12 @@ void level_mma_image(const double *w, float *hi, float *lo) {
     std::memcpy(&r, &u, 4);
     return r;
   };
-  for (int n = 0; n < 128; ++n)
-    for (int k = 0; k < 128; ++k) {
-      const float x = (float)w[(size_t)n * 128 + k];
-      const float h = rna(x), l = rna(x - h);
-      const int kc = k >> 5, kk = k & 31;
-      const size_t off = (size_t)kc * kLvlChunk + (size_t)(n >> 3) * 1024 + (size_t)(n & 7) * 128 +
-                         (size_t)((((kk >> 2) ^ (n & 7)) << 4) + (kk & 3) * 4);
-      hi[off / 4] = h;
-      lo[off / 4] = l;
-    }
+  // row-major [n][k]: the kernel loads row n into TMEM lane n
+  for (int i = 0; i < 128 * 128; ++i) {
+    const float x = (float)w[i];
+    hi[i] = rna(x);
+    lo[i] = rna(x - hi[i]);
+  }
 }
 
 cudaError_t launch_level_mma(const LevelMmaArgs &a, cudaStream_t st) {
