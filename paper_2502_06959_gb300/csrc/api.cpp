@@ -235,7 +235,10 @@ int64_t hsf_plan_describe(const hsf_plan *p, char *buf, int64_t cap) {
       const LevelH &lv = sd.levels[k];
       std::snprintf(line, sizeof line, " level %zu: radix %llu, %zu ops, %s\n", k,
                     (unsigned long long)p->radix[k], lv.ops.size(),
-                    ((lv.mma ? std::string("tensor-core product (TF32x3) on the 6 lowest storage bits, then ")
+                    ((lv.mma ? std::string("tensor-core product (TF32x3) on the 6 lowest storage bits") +
+                                   (lv.post.empty() ? std::string()
+                                                    : " + " + std::to_string(lv.post.size()) + " ops in its epilogue") +
+                                   ", then "
                              : std::string()) +
                      std::to_string(lv.passes.size()) + " passes")
                         .c_str());
@@ -388,6 +391,8 @@ hsf_status hsf_run(hsf_plan *p, const uint64_t *bits, size_t num, uint64_t windo
           g.num_nodes = hi - lo;
           g.parent_lo = prev_lo;
           g.err = p->dev_status;
+          g.post = (unsigned char *)p->dev_table + lv.post_off;
+          g.num_post = (int32_t)lv.post.size();
           const double amps = (double)(hi - lo) * (double)(1ull << sd.h);
           const double parents = (double)((hi - 1) / g.radix - lo / g.radix + 1) * (double)(1ull << sd.h);
           // TF32x3: three 128 x 128 x 128 real products per 64-amplitude row

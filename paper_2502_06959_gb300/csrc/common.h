@@ -197,7 +197,21 @@ struct LevelMmaArgs {
   int64_t num_nodes;
   int64_t parent_lo;       // level-global index of the first node held in parent
   int32_t *err;            // device status word (bounded waits)
+  const void *post;        // ops applied in the epilogue after the product (MmaPostOp[])
+  int32_t num_post;
+  int32_t pad;
 };
+// A one- or two-qubit op on storage bits < kMmaPostBits, applied by the tensor-core
+// level's epilogue to each staged 32-row quarter (amplitude bits 0..5, row bits 0..4).
+constexpr int kMmaPostBits = kMmaBits + 5;
+constexpr int kMmaMaxPost = 8;
+struct MmaPostOp {
+  int32_t nq;              // 1 or 2
+  int32_t q0, q1;          // storage bits; q0 is the matrix MSB
+  int32_t diag;            // 1: m holds the 2^nq diagonal phases
+  float2 m[16];            // dense 2^nq x 2^nq, row-major (or the diagonal)
+};
+static_assert(sizeof(MmaPostOp) == 144, "MmaPostOp layout");
 cudaError_t launch_level_mma(const LevelMmaArgs &a, cudaStream_t st);
 // host: the kernel's shared-memory image of W (128 x 128 real, K-major, 128-byte swizzle)
 void level_mma_image(const double *w, float *hi, float *lo);

@@ -404,6 +404,64 @@ __device__ __forceinline__ void mma_tf32_ts(uint32_t d, uint32_t a, uint64_t db,
       : "memory");
 }
 
+// One post-product op on a staged quarter: element i (i < 2^11) of the quarter is
+// amplitude i & 63 of row i >> 6, at stage[(i >> 6) * 128 + 2 * (i & 63)] (re, im); its
+// index bits are the storage bits 0..10.  The 128 epilogue threads (t) split the work.
+__device__ __forceinline__ uint32_t ins0(uint32_t v, int b) { return ((v >> b) << (b + 1)) | (v & ((1u << b) - 1u)); }
+__device__ __forceinline__ float2 *post_elem(float *stage, uint32_t i) {
+  return reinterpret_cast<float2 *>(stage + (i >> 6) * 128 + 2 * (i & 63));
+}
+__device__ __forceinline__ float2 cmulf(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+__device__ __forceinline__ void apply_post_op(float *stage, const MmaPostOp *op, int t) {
+  const int nq = __ldg(&op->nq), q0 = __ldg(&op->q0), q1 = __ldg(&op->q1), diag = __ldg(&op->diag);
+  if (diag) {
+    for (uint32_t i = t; i < 2048; i += 128) {
+      int k = (int)((i >> q0) & 1u);
+      if (nq == 2) k = (k << 1) | (int)((i >> q1) & 1u);
+      float2 *e = post_elem(stage, i);
+      *e = cmulf(__ldg(&op->m[k]), *e);
+    }
+  } else if (nq == 1) {
+    const float2 m0 = __ldg(&op->m[0]), m1 = __ldg(&op->m[1]), m2 = __ldg(&op->m[2]), m3 = __ldg(&op->m[3]);
+    for (uint32_t j = t; j < 1024; j += 128) {
+      const uint32_t i0 = ins0(j, q0), i1 = i0 | (1u << q0);
+      float2 *e0 = post_elem(stage, i0), *e1 = post_elem(stage, i1);
+      const float2 x0 = *e0, x1 = *e1;
+      const float2 a = cmulf(m0, x0), b = cmulf(m1, x1), c = cmulf(m2, x0), d = cmulf(m3, x1);
+      *e0 = make_float2(a.x + b.x, a.y + b.y);
+      *e1 = make_float2(c.x + d.x, c.y + d.y);
+    }
+  } else {
+    const int lo = min(q0, q1), hi = max(q0, q1);
+    for (uint32_t j = t; j < 512; j += 128) {
+      const uint32_t base = ins0(ins0(j, lo), hi);
+      float2 *e[4];
+      float2 x[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        e[k] = post_elem(stage, base | ((uint32_t)(k >> 1) << q0) | ((uint32_t)(k & 1) << q1));
+        x[k] = *e[k];
+      }
+      float2 y[4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        float re = 0.f, im = 0.f;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const float2 mm = __ldg(&op->m[r * 4 + k]);
+          re = fmaf(mm.x, x[k].x, fmaf(-mm.y, x[k].y, re));
+          im = fmaf(mm.x, x[k].y, fmaf(mm.y, x[k].x, im));
+        }
+        y[r] = make_float2(re, im);
+      }
+#pragma unroll
+      for (int k = 0; k < 4; ++k) *e[k] = y[k];
+    }
+  }
+}
+
 __global__ void __launch_bounds__(kLvlThreads, 1) level_mma_kernel(const __grid_constant__ CUtensorMap tmP,
                                                                   LevelMmaArgs a) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
@@ -635,6 +693,11 @@ __global__ void __launch_bounds__(kLvlThreads, 1) level_mma_kernel(const __grid_
         float *stage = sO + (size_t)(nq % kLvlOut) * 32 * 128;
 #pragma unroll
         for (int j = 0; j < 32; ++j) stage[j * 128 + comp] = __uint_as_float(v[j]);
+        // the rest of the level's program, on storage bits 0..10 of this quarter
+        for (int o = 0; o < a.num_post; ++o) {
+          asm volatile("bar.sync 1, 128;" ::: "memory");
+          apply_post_op(stage, reinterpret_cast<const MmaPostOp *>(a.post) + o, comp);
+        }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         asm volatile("bar.sync 1, 128;" ::: "memory");
         if (leader) {

@@ -77,6 +77,10 @@ struct LevelH {
   // whole program when mma_prefix == ops.size()); once chosen, those ops are composed
   // into W and removed from ops, and the rest run as in-place passes after the product
   size_t mma_prefix = 0;
+  // ops after the product that stay on storage bits < kMmaPostBits: applied by the
+  // product's epilogue instead of as a pass
+  std::vector<OpH> post;
+  size_t post_off = 0;
 };
 
 struct SideH {

@@ -655,6 +655,17 @@ void compose_mma_levels(hsf_plan &p, int leaf_c) {
       std::vector<OpH> prefix(lv.ops.begin(), lv.ops.begin() + lv.mma_prefix);
       lv.ops.erase(lv.ops.begin(), lv.ops.begin() + lv.mma_prefix);
       lv.passes.clear();
+      // the rest goes into the epilogue when every op is a 1- or 2-qubit op on storage
+      // bits < kMmaPostBits (and the tiles have at least 32 rows of 64 amplitudes)
+      bool post_ok = !lv.ops.empty() && lv.ops.size() <= (size_t)kMmaMaxPost && p.side[s].h >= kMmaPostBits;
+      for (auto &op : lv.ops) {
+        post_ok = post_ok && op.nq <= 2 && op.digits == 1;
+        for (int j = 0; j < op.nq; ++j) post_ok = post_ok && op.q[j] < kMmaPostBits;
+      }
+      if (post_ok) {
+        lv.post.swap(lv.ops);
+        lv.ops.clear();
+      }
       if (!lv.ops.empty()) {
         split_passes(lv, p.side[s].h, p.tile_max);
         if (!(p.flags & HSF_FLAG_NO_REGISTER_SWEEP))
@@ -882,6 +893,18 @@ hsf_status upload_programs(hsf_plan &p, bool grad) {
         align(1024);
         lv.w_off = host.size();
         append(lv.wimg.data(), lv.wimg.size() * sizeof(float));
+        align(256);
+        lv.post_off = host.size();
+        for (const OpH &op : lv.post) {
+          MmaPostOp d{};
+          d.nq = op.nq;
+          d.q0 = op.q[0];
+          d.q1 = op.nq > 1 ? op.q[1] : 0;
+          d.diag = op.type == OP_DIAG ? 1 : 0;
+          const size_t cnt = op.type == OP_DIAG ? (size_t)(1 << op.nq) : (size_t)(1 << (2 * op.nq));
+          for (size_t i = 0; i < cnt && i < 16; ++i) d.m[i] = make_float2((float)op.m[i].real(), (float)op.m[i].imag());
+          append(&d, sizeof d);
+        }
       }
     align(256);
     sd.leaf_off = host.size();
