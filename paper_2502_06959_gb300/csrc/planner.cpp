@@ -814,18 +814,24 @@ hsf_status build_programs(hsf_plan &p, bool grad) {
     for (int k = 1; k <= B && !grad; ++k) {
       LevelH &lv = sd.levels[k];
       if (p.precision != HSF_PREC_C64 || sd.h < kMmaMinH || (p.flags & HSF_FLAG_NO_TC_LEVEL)) break;
-      // a partial product adds a pass: only worth it on large levels
-      const bool large =
-          (long double)(p.num_paths / p.below[k]) * (long double)(1ull << sd.h) >= (long double)(1ull << 26);
+      // a partial product whose rest needs a pass is only worth it on large levels; one
+      // whose rest fits the product's epilogue already on medium ones
+      const long double amps = (long double)(p.num_paths / p.below[k]) * (long double)(1ull << sd.h);
+      const bool large = amps >= (long double)(1ull << 26), medium = amps >= (long double)(1ull << 24);
       size_t q = 0;
       for (; q < lv.ops.size(); ++q) {
         bool low = true;
         for (int j = 0; j < lv.ops[q].nq; ++j) low = low && lv.ops[q].q[j] < kMmaBits;
         if (!low) break;
       }
-      bool digits_in_prefix = true;
-      for (size_t o = q; o < lv.ops.size(); ++o) digits_in_prefix = digits_in_prefix && lv.ops[o].digits == 1;
-      if (q > 0 && digits_in_prefix && (q == lv.ops.size() || (large && q >= (size_t)kMmaMinPrefix)))
+      bool digits_in_prefix = true, post_fit = lv.ops.size() - q <= (size_t)kMmaMaxPost && sd.h >= kMmaPostBits;
+      for (size_t o = q; o < lv.ops.size(); ++o) {
+        digits_in_prefix = digits_in_prefix && lv.ops[o].digits == 1;
+        post_fit = post_fit && lv.ops[o].nq <= 2;
+        for (int j = 0; j < lv.ops[o].nq; ++j) post_fit = post_fit && lv.ops[o].q[j] < kMmaPostBits;
+      }
+      if (q > 0 && digits_in_prefix &&
+          (q == lv.ops.size() || (q >= (size_t)kMmaMinPrefix && (large || (medium && post_fit)))))
         lv.mma_prefix = q;
     }
     for (auto &lv : sd.levels) {
