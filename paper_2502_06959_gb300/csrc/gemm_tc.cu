@@ -380,7 +380,7 @@ constexpr int kLvlLo = 4;                       // low-part buffers
 constexpr int kLvlOut = 4;                      // 32-row output staging buffers (16 KB each)
 constexpr int kLvlAhead = 12;                   // chunks prefetched into L2 ahead of the loads
 constexpr int kLvlChunk = 128 * 128;            // bytes: 128 rows x 32 floats
-constexpr int kLvlThreads = 320;                // 4 low-part, 4 epilogue, 1 MMA, 1 TMA warp
+constexpr int kLvlThreads = 448;                // 4 low-part, 2 x 4 epilogue, 1 MMA, 1 TMA warp
 constexpr uint32_t kLvlTmemCols = 512;          // W hi [0,128), W lo [128,256), D 2 x 128
 constexpr size_t kLvlSmem = (size_t)(kLvlRaw + kLvlLo + kLvlOut) * kLvlChunk + 1024;
 
@@ -472,7 +472,7 @@ __global__ void __launch_bounds__(kLvlThreads, 1) level_mma_kernel(const __grid_
   __shared__ __align__(8) uint64_t loaded[kLvlRaw], raw_empty[kLvlRaw], full_bar[kLvlLo], lo_empty[kLvlLo], tfull[2],
       tempty[2], drain;
   __shared__ uint32_t tmem_sh;
-  __shared__ volatile int abort_sh, epi_abort;
+  __shared__ volatile int abort_sh, epi_abort[2];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t radix = a.radix;
   const int m = blockIdx.y;
@@ -484,7 +484,7 @@ __global__ void __launch_bounds__(kLvlThreads, 1) level_mma_kernel(const __grid_
   const int64_t nchunks = units > blockIdx.x ? ((units - 1 - blockIdx.x) / gridDim.x + 1) * 4 : 0;
 
   if (threadIdx.x == 0) {
-    epi_abort = 0;
+    epi_abort[0] = epi_abort[1] = 0;
     for (int s = 0; s < kLvlRaw; ++s) {
       mbar_init(&loaded[s], 1);
       mbar_init(&raw_empty[s], 1);
@@ -495,7 +495,7 @@ __global__ void __launch_bounds__(kLvlThreads, 1) level_mma_kernel(const __grid_
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&tfull[b], 1);
-      mbar_init(&tempty[b], 128);
+      mbar_init(&tempty[b], 256);
     }
     mbar_init(&drain, 1);
     abort_sh = 0;
@@ -651,22 +651,27 @@ __global__ void __launch_bounds__(kLvlThreads, 1) level_mma_kernel(const __grid_
     }
     __syncwarp();
   } else {
-    // ---- epilogue: TMEM lane quarter (warp & 3) holds output components 32 (warp & 3)
-    // .. + 31; TMEM column j of the accumulator is row j of the tile.  Each 32-row quarter
-    // is staged in shared memory row-major (the global layout) and written by one bulk
-    // copy: those 32 rows are 16 KB contiguous in the child state. ----
+    // ---- epilogue: two groups of four warps (4..7 and 10..13) take alternate 32-row
+    // quarters of each accumulator.  TMEM lane quarter (warp & 3) holds output
+    // components 32 (warp & 3) .. + 31; TMEM column j of the accumulator is row j of the
+    // tile.  A quarter is staged in shared memory row-major (the global layout), gets the
+    // rest of the level's program, and goes out as one bulk copy (its 32 rows are 16 KB
+    // contiguous in the child state). ----
+    const int grp = warp >= 10 ? 1 : 0;
+    const uint32_t bar_id = 1 + grp;                     // named barrier of the group
     const int q4 = warp & 3;
     const int comp = q4 * 32 + lane;
-    const bool leader = warp == 4 && lane == 0;
+    const bool leader = q4 == 0 && lane == 0;
+    constexpr int kOutPerGroup = kLvlOut / 2;
     int64_t tu = 0, nq = 0;                              // units done, quarters stored
-    // The four warps meet at named barriers, so they decide to stop together: only they
-    // write epi_abort, before a barrier, and all read it after.
+    // The four warps of a group meet at named barriers, so they decide to stop together:
+    // only they write their epi_abort word, before a barrier, and all read it after.
     for (int64_t u = blockIdx.x; u < units; u += gridDim.x, ++tu) {
       const int b = (int)(tu & 1);
       const bool ok = mbar_wait(&tfull[b], (uint32_t)(tu >> 1) & 1u);
-      if (!ok) epi_abort = 1;
-      asm volatile("bar.sync 1, 128;" ::: "memory");
-      if (epi_abort) {
+      if (!ok) epi_abort[grp] = 1;
+      asm volatile("bar.sync %0, 128;" ::"r"(bar_id) : "memory");
+      if (epi_abort[grp]) {
         if (!ok) atomicExch(a.err, 8);
         abort_sh = 1;
         break;
@@ -675,7 +680,7 @@ __global__ void __launch_bounds__(kLvlThreads, 1) level_mma_kernel(const __grid_
       const int64_t g = g_first + (u >> tb) * radix;
       float *dst = a.child + (((uint64_t)(g - a.node_lo) << a.h) + ((uint64_t)(u & ((1 << tb) - 1)) << 13)) * 2;
 #pragma unroll 1
-      for (int qr = 0; qr < 4; ++qr, ++nq) {
+      for (int qr = grp; qr < 4; qr += 2, ++nq) {
         uint32_t v[32];
         const uint32_t taddr = tmem + ((uint32_t)(q4 * 32) << 16) + 256u + (uint32_t)(b * 128 + qr * 32);
         asm volatile(
@@ -687,19 +692,20 @@ __global__ void __launch_bounds__(kLvlThreads, 1) level_mma_kernel(const __grid_
               "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
             : "r"(taddr));
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-        // the staging buffer of this quarter was last read by the bulk copy two quarters ago
-        if (leader && nq >= kLvlOut) asm volatile("cp.async.bulk.wait_group.read %0;" ::"n"(kLvlOut - 1) : "memory");
-        asm volatile("bar.sync 1, 128;" ::: "memory");
-        float *stage = sO + (size_t)(nq % kLvlOut) * 32 * 128;
+        // this group's staging buffer was last read by its bulk copy kOutPerGroup quarters ago
+        if (leader && nq >= kOutPerGroup)
+          asm volatile("cp.async.bulk.wait_group.read %0;" ::"n"(kOutPerGroup - 1) : "memory");
+        asm volatile("bar.sync %0, 128;" ::"r"(bar_id) : "memory");
+        float *stage = sO + (size_t)(grp * kOutPerGroup + nq % kOutPerGroup) * 32 * 128;
 #pragma unroll
         for (int j = 0; j < 32; ++j) stage[j * 128 + comp] = __uint_as_float(v[j]);
         // the rest of the level's program, on storage bits 0..10 of this quarter
         for (int o = 0; o < a.num_post; ++o) {
-          asm volatile("bar.sync 1, 128;" ::: "memory");
+          asm volatile("bar.sync %0, 128;" ::"r"(bar_id) : "memory");
           apply_post_op(stage, reinterpret_cast<const MmaPostOp *>(a.post) + o, comp);
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        asm volatile("bar.sync 1, 128;" ::: "memory");
+        asm volatile("bar.sync %0, 128;" ::"r"(bar_id) : "memory");
         if (leader) {
           asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst + (size_t)qr * 32 * 128),
                        "r"(smem_u32(stage)), "r"(32 * 128 * 4)
