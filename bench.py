@@ -81,12 +81,17 @@ class ClockSampler:
         self.lines = []
 
     def __enter__(self):
+        # nvidia-smi is started, and its first sample awaited, before the caller's timed
+        # region begins: its start-up would otherwise compete with the timed work
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
                  "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
+            t0 = time.time()
+            while not self.lines and time.time() - t0 < 5.0:
+                time.sleep(0.01)
         except Exception:
             self.proc = None
         return self
