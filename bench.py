@@ -525,11 +525,14 @@ def main():
         tr = traffic_per_launch(kind, st.get("bytes", 0.0) / nlk)
         r = {"kernel": kind, "launches": int(st.get("launches", 0)), "avg_launch_ms": k_ms / nlk,
              "share": k_ms / total_kernel_ms if total_kernel_ms else 0.0}
-        if kind == "level_mma":
-            # TF32x3 product: counted flops are the three TF32 products actually issued
-            r.update({"bound": "tensor", "achieved": tfl, "peak": tf32_peak_tflops, "unit": "TFLOP/s",
-                      "frac": tfl / tf32_peak_tflops if tf32_peak_tflops else None,
-                      "peak_source": peak_src + " (bf16 x 1.1/2.25 nominal TF32 ratio)",
+        if kind in ("level_mma", "level_f16"):
+            # three products per level (TF32 parts, or FP16 parts): counted flops are
+            # the three products actually issued; FP16 shares BF16's nominal dense rate
+            peak = tf32_peak_tflops if kind == "level_mma" else bf16_peak
+            src = " (bf16 x 1.1/2.25 nominal TF32 ratio)" if kind == "level_mma" else \
+                " (cuBLAS bf16; fp16 has the same nominal dense rate)"
+            r.update({"bound": "tensor", "achieved": tfl, "peak": peak, "unit": "TFLOP/s",
+                      "frac": tfl / peak if peak else None, "peak_source": peak_src + src,
                       "hbm_gbs": gbs, "hbm_frac": gbs / hbm_peak if hbm_peak else None, "traffic": tr})
         else:
             r.update({"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s",
@@ -554,7 +557,7 @@ def main():
                 "d2h_bytes_per_step": int(S * 16)},
         "roofline": dict(roofline_of(dominant),
                          measured="profiled pass of the same steps, halves on one stream"),
-        "rooflines": {k: roofline_of(k) for k in ("sweep", "level_mma", "leaf") if k in kstats},
+        "rooflines": {k: roofline_of(k) for k in ("sweep", "level_mma", "level_f16", "leaf") if k in kstats},
         "kernels": {k: {"launches": int(v["launches"]), "ms": v["ms"],
                         "share": v["ms"] / total_kernel_ms if total_kernel_ms else 0.0}
                     for k, v in kstats.items() if v["launches"]},

@@ -274,7 +274,9 @@ typedef enum hsf_kernel_kind {
   HSF_KERNEL_WINDOW = 3,     /* window / full path GEMM                      */
   HSF_KERNEL_OTHER = 4,      /* zero-fill, index maps, finalize              */
   HSF_KERNEL_LEAF = 5,       /* leaf level contracted at the bitstrings      */
-  HSF_KERNEL_LEVEL_MMA = 6,  /* tree level as a tensor-core product per digit */
+  HSF_KERNEL_LEVEL_MMA = 6,  /* tree level as a tensor-core product per digit,
+                                TF32 parts (levels with ops after the product) */
+  HSF_KERNEL_LEVEL_F16 = 7,  /* the same with FP16 parts (levels without)    */
   HSF_NUM_KERNEL_KINDS = 8
 } hsf_kernel_kind;
 

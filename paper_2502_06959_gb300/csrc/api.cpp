@@ -235,7 +235,8 @@ int64_t hsf_plan_describe(const hsf_plan *p, char *buf, int64_t cap) {
       const LevelH &lv = sd.levels[k];
       std::snprintf(line, sizeof line, " level %zu: radix %llu, %zu ops, %s\n", k,
                     (unsigned long long)p->radix[k], lv.ops.size(),
-                    ((lv.mma ? std::string("tensor-core product (TF32x3) on the 6 lowest storage bits") +
+                    ((lv.mma ? std::string("tensor-core product (") + (lv.post.empty() ? "FP16x3" : "TF32x3") +
+                                   ") on the 6 lowest storage bits" +
                                    (lv.post.empty() ? std::string()
                                                     : " + " + std::to_string(lv.post.size()) + " ops in its epilogue") +
                                    ", then "
@@ -395,8 +396,8 @@ hsf_status hsf_run(hsf_plan *p, const uint64_t *bits, size_t num, uint64_t windo
           g.num_post = (int32_t)lv.post.size();
           const double amps = (double)(hi - lo) * (double)(1ull << sd.h);
           const double parents = (double)((hi - 1) / g.radix - lo / g.radix + 1) * (double)(1ull << sd.h);
-          // TF32x3: three 128 x 128 x 128 real products per 64-amplitude row
-          LAUNCH(HSF_KERNEL_LEVEL_MMA, (amps + parents) * csz, 3.0 * 2.0 * 128.0 * 128.0 * (amps / 64.0),
+          // three 128 x 128 x 128 real products (FP16 or TF32 parts) per 128 64-amplitude rows
+          LAUNCH(lv.post.empty() ? HSF_KERNEL_LEVEL_F16 : HSF_KERNEL_LEVEL_MMA, (amps + parents) * csz, 3.0 * 2.0 * 128.0 * 128.0 * (amps / 64.0),
                  launch_level_mma(g, st));
         }
         for (size_t pi = 0; pi < lv.passes.size(); ++pi) {

@@ -186,11 +186,14 @@ size_t path_gemm_operand_bytes(int mode, int64_t M, int64_t N, int64_t paths);
 constexpr int kMmaBits = 6;
 constexpr int kMmaMinH = kMmaBits + 7;           // at least one 128-row tile per node
 constexpr int kMmaMinPrefix = 4;                  // ops a partial product must replace
-constexpr size_t kMmaWPartBytes = 128 * 128 * 4;  // one TF32 part of W (64 KB)
+constexpr size_t kMmaWPartBytes = 128 * 128 * 4;       // one TF32 part of W_m (64 KB)
+constexpr size_t kMmaWDigitBytes = 128 * 128 * 2 * 2;  // W_m as FP16 hi then lo, 128 x 128 each
 struct LevelMmaArgs {
   const float *parent;     // previous level buffer, complex64 as float pairs
   float *child;            // this level's buffer
-  const void *w;           // per digit: W hi image then W lo image (kMmaWPartBytes each)
+  const void *w;           // num_post > 0: per digit, TF32 hi then lo (kMmaWPartBytes each);
+                           // num_post = 0: per digit, the FP16 image (kMmaWDigitBytes), then
+                           // radix inverse scales
   int32_t h;
   int32_t radix;
   int64_t node_lo;         // level-global index of the first node held in child
@@ -213,8 +216,11 @@ struct MmaPostOp {
 };
 static_assert(sizeof(MmaPostOp) == 144, "MmaPostOp layout");
 cudaError_t launch_level_mma(const LevelMmaArgs &a, cudaStream_t st);
-// host: the kernel's shared-memory image of W (128 x 128 real, K-major, 128-byte swizzle)
+// host: the kernels' images of W_m (128 x 128 real, row-major [n][k]): TF32 hi and lo
+// parts (levels with ops after the product), or power-of-two scaled FP16 hi and lo parts
+// (kMmaWDigitBytes) with the inverse of the scale (levels without)
 void level_mma_image(const double *w, float *hi, float *lo);
+void level_mma_image_f16(const double *w, void *digit_image, float *inv_scale);
 
 // Adjoint sweep over one pass of one tree level, in reverse op order (adjoint.cu).
 struct AdjointArgs {

@@ -17,9 +17,11 @@
 // records an error code, frees its TMEM and returns.
 #include <cuda.h>
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstdint>
 #include <cstring>
 #include <mutex>
@@ -370,24 +372,22 @@ __global__ void __launch_bounds__(128, 1) gemm_kernel(const __grid_constant__ CU
 // A CTA serves one digit.  W_m's TF32 hi and lo parts sit in tensor memory as the MMA's
 // A operand (lanes = output component n, columns = k), so shared memory holds only the
 // streamed parent rows: 128-row tiles (MMA N = 128) in 32-float K-chunks.  One thread
-// issues TMA loads (128-byte swizzle) into an 8-stage ring and prefetches chunks into L2;
-// four warps compute each chunk's TF32 low part; one thread issues W_hi P_hi + W_hi P_lo +
-// W_lo P_hi (tcgen05.mma kind::tf32, A from TMEM) into one of two TMEM accumulators; four
-// warps read the other back and write the child rows.  Every wait is bounded; on expiry
-// the CTA records an error, drains its MMAs and loads, frees TMEM and returns.
+// issues TMA loads (128-byte swizzle) into a 4-stage ring; four warps compute each
+// chunk's TF32 low part; one thread issues W_hi P_hi + W_hi P_lo + W_lo P_hi
+// (tcgen05.mma kind::tf32, A from TMEM) into one of two TMEM accumulators; two groups of
+// four warps read the other back, stage 32-row quarters in shared memory for the ops that
+// follow the product and write the child rows with bulk copies.  This kernel serves the
+// levels with ops after the product; level_mma_f16_kernel the others.  Every wait is
+// bounded; on expiry the CTA records an error, drains its MMAs and loads, frees TMEM and
+// returns.
 constexpr int kLvlRaw = 4;                      // TMA stages (raw FP32 chunks = the hi parts)
 constexpr int kLvlLo = 4;                       // low-part buffers
 constexpr int kLvlOut = 4;                      // 32-row output staging buffers (16 KB each)
-constexpr int kLvlAhead = 12;                   // chunks prefetched into L2 ahead of the loads
 constexpr int kLvlChunk = 128 * 128;            // bytes: 128 rows x 32 floats
 constexpr int kLvlThreads = 448;                // 4 low-part, 2 x 4 epilogue, 1 MMA, 1 TMA warp
 constexpr uint32_t kLvlTmemCols = 512;          // W hi [0,128), W lo [128,256), D 2 x 128
 constexpr size_t kLvlSmem = (size_t)(kLvlRaw + kLvlLo + kLvlOut) * kLvlChunk + 1024;
 
-__device__ __forceinline__ void tma_prefetch_2d(const CUtensorMap *map, int x, int y) {
-  asm volatile("cp.async.bulk.prefetch.tensor.2d.L2.global.tile [%0, {%1, %2}];" ::"l"((uint64_t)map), "r"(x), "r"(y)
-               : "memory");
-}
 __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
@@ -574,21 +574,17 @@ __global__ void __launch_bounds__(kLvlThreads, 1) level_mma_kernel(const __grid_
     }
   } else if (warp == 9) {
     // ---- TMA: chunk c = chunk c % 4 of unit blockIdx.x + (c / 4) * gridDim.x ----
-    // Chunks kLvlAhead ahead are prefetched into L2 (no shared memory), so the stage
-    // loads, which can only start once a stage frees, see L2 rather than DRAM latency.
     if (lane == 0) {
       auto row_of = [&](int64_t c) {
         const int64_t u = blockIdx.x + (c >> 2) * gridDim.x;
         const int64_t g = g_first + (u >> tb) * radix;
         return ((g / radix - a.parent_lo) << (a.h - kMmaBits)) + ((u & ((1 << tb) - 1)) << 7);
       };
-      for (int64_t c = 0; c < kLvlAhead && c < nchunks; ++c) tma_prefetch_2d(&tmP, (int)(c & 3) * 32, (int)row_of(c));
       int64_t issued = 0;
       for (int64_t it = 0; it < nchunks && !abort_sh; ++it) {
         const int s = (int)(it % kLvlRaw);
         const uint32_t ph = (uint32_t)(it / kLvlRaw) & 1u;
-        if (it + kLvlAhead < nchunks)
-          tma_prefetch_2d(&tmP, (int)((it + kLvlAhead) & 3) * 32, (int)row_of(it + kLvlAhead));
+
         if (!mbar_wait(&raw_empty[s], ph ^ 1)) {
           atomicExch(a.err, 9);
           abort_sh = 1;
@@ -728,6 +724,351 @@ __global__ void __launch_bounds__(kLvlThreads, 1) level_mma_kernel(const __grid_
 }
 
 // ---------------------------------------------------------------------------
+// Tensor-core tree level, FP16 split (levels with no ops after the product)
+// ---------------------------------------------------------------------------
+// Same product as level_mma_kernel, with both operands split into FP16 hi and lo parts:
+// W_hi P_hi + W_hi P_lo + W_lo P_hi (tcgen05.mma kind::f16, FP32 accumulate), twice the
+// tensor rate of TF32.  FP16's exponent range is handled by powers of two: W_m is scaled
+// on the host so that its largest entry lies in [2^14, 2^15), and every 64-amplitude
+// parent row by its own power of two (largest component in [2^14, 2^15)); hi is the
+// scaled value rounded to a multiple of 16 (exact in FP16) and lo the FP16 rounding of
+// the exact rest (|lo| <= 8), so each operand is split within 2^-23 of its row's (or
+// W_m's) largest entry.  The epilogue multiplies each output row by both inverse scales,
+// which is exact.  W_m's parts sit in tensor memory as the MMA's A operand (lanes =
+// output component n, columns = k, two FP16 per column).  Eight split warps stream the raw
+// FP32 parent rows through a shared-memory ring with cp.async (each warp copies the rows
+// it converts) and write the FP16 hi and lo B operands of a 128-row unit (K-major,
+// 128-byte swizzle, two buffers); one thread issues the 24 MMAs of a unit into one of two
+// TMEM accumulators; two groups of four warps read the other back, unscale it and store
+// the child rows from registers.  The split work per element is what bounds this kernel;
+// a level with ops after the product uses the TF32 kernel, whose epilogue stages rows in
+// the shared memory this one spends on the split's operand buffers.  Every wait is
+// bounded; on expiry the CTA records an error, drains its MMAs and copies, frees TMEM and
+// returns.
+constexpr int kHQuarter = 32 * 512;             // bytes: 32 parent rows x 128 floats
+constexpr int kHRaw = 5;                        // raw quarters in the ring
+constexpr int kHOps = 2;                        // FP16 operand buffers (one 128-row unit each)
+constexpr int kHAtom = 128 * 128;               // bytes: 128 rows x 64 FP16 (one swizzle atom column)
+constexpr int kHOpBytes = 4 * kHAtom;           // hi (K 0..63, 64..127) then lo (same)
+constexpr int kHSplit = 8;                      // split warps: 0..3 and 13..16
+constexpr int kHSplitThreads = kHSplit * 32;
+constexpr int kHThreads = (9 + kHSplit) * 32;   // + 2 x 4 epilogue warps and the MMA warp
+constexpr uint32_t kHTmemCols = 512;            // W hi [0,64), W lo [64,128), D 2 x 128 at 256
+constexpr size_t kHSmem = (size_t)kHOps * kHOpBytes + (size_t)kHRaw * kHQuarter + 1024;
+static_assert(kHSmem <= 227 * 1024 - 4096, "FP16 level kernel shared memory");
+
+__device__ __forceinline__ void lvl_cp_async16(uint32_t dst, const void *src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void lvl_cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void lvl_cp_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+// D (TMEM) += A (TMEM) x B (shared-memory descriptor), FP16 operands
+__device__ __forceinline__ void mma_f16_ts(uint32_t d, uint32_t a, uint64_t db, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}\n"
+      ::"r"(d), "r"(a), "l"(db), "r"(idesc), "r"(acc)
+      : "memory");
+}
+// explicit shared-space accesses (the buffers are reached through an aligned generic
+// pointer, which the compiler cannot place in shared memory by itself)
+__device__ __forceinline__ float4 lds128(uint32_t addr) {
+  float4 v;
+  asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "r"(addr));
+  return v;
+}
+__device__ __forceinline__ void sts128(uint32_t addr, uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
+  asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(a), "r"(b), "r"(c), "r"(d) : "memory");
+}
+__device__ __forceinline__ uint32_t h2_bits(__half2 h) {
+  uint32_t u;
+  memcpy(&u, &h, 4);
+  return u;
+}
+
+__global__ void __launch_bounds__(kHThreads, 1) level_mma_f16_kernel(LevelMmaArgs a) {
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+  uint8_t *sOp = smem;                                  // operand buffer o: sOp + o * kHOpBytes
+  uint8_t *sR = sOp + kHOps * kHOpBytes;            // raw quarter r: sR + r * kHQuarter
+  __shared__ __align__(8) uint64_t ops_full[kHOps], ops_empty[kHOps],
+      sc_full[4], tfull[2], tempty[2], drain;
+  __shared__ float row_inv[4][128];                     // per unit (4 in flight): 1 / row scale
+  __shared__ uint32_t tmem_sh;
+  __shared__ volatile int abort_sh, epi_abort[2];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t radix = a.radix;
+  const int m = blockIdx.y;
+  const int64_t g_first = a.node_lo + ((m - a.node_lo % radix) % radix + radix) % radix;
+  const int64_t g_end = a.node_lo + a.num_nodes;
+  const int64_t nchild = g_first < g_end ? (g_end - g_first + radix - 1) / radix : 0;
+  const int tb = a.h - kMmaMinH;                        // 2^tb row units per node
+  const int64_t units = nchild << tb;
+  const int64_t my_units = units > blockIdx.x ? (units - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+  const int64_t nquarters = my_units * 4;
+  const uint8_t *wimg = static_cast<const uint8_t *>(a.w);
+
+  if (threadIdx.x == 0) {
+    epi_abort[0] = epi_abort[1] = 0;
+    for (int s = 0; s < kHOps; ++s) {
+      mbar_init(&ops_full[s], kHSplitThreads);
+      mbar_init(&ops_empty[s], 1);
+    }
+    for (int s = 0; s < 4; ++s) mbar_init(&sc_full[s], kHSplitThreads);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&tfull[b], 1);
+      mbar_init(&tempty[b], 256);
+    }
+    mbar_init(&drain, 1);
+    abort_sh = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 8) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_sh)),
+                 "r"(kHTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_sh;
+  if (warp >= 4 && warp < 8) {
+    // W_m into TMEM: lane n holds row n, two FP16 per column; columns [0,64) the hi part,
+    // [64,128) the lo part (the image holds 128 rows x 64 words per part)
+    const int q4 = warp & 3;
+    const uint32_t *wrow =
+        reinterpret_cast<const uint32_t *>(wimg + (size_t)m * kMmaWDigitBytes) + (size_t)(q4 * 32 + lane) * 64;
+#pragma unroll 1
+    for (int c = 0; c < 4; ++c) {
+      const uint32_t *src = wrow + (size_t)(c >> 1) * 128 * 64 + (c & 1) * 32;
+      uint32_t v[32];
+#pragma unroll
+      for (int j = 0; j < 32; j += 4) {
+        const uint4 x = *reinterpret_cast<const uint4 *>(src + j);
+        v[j] = x.x;
+        v[j + 1] = x.y;
+        v[j + 2] = x.z;
+        v[j + 3] = x.w;
+      }
+      const uint32_t taddr = tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(c * 32);
+      asm volatile(
+          "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,"
+          "%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};" ::"r"(taddr),
+          "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]), "r"(v[8]),
+          "r"(v[9]), "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15]), "r"(v[16]),
+          "r"(v[17]), "r"(v[18]), "r"(v[19]), "r"(v[20]), "r"(v[21]), "r"(v[22]), "r"(v[23]), "r"(v[24]),
+          "r"(v[25]), "r"(v[26]), "r"(v[27]), "r"(v[28]), "r"(v[29]), "r"(v[30]), "r"(v[31])
+          : "memory");
+    }
+    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+
+  if (warp < 4 || warp >= 13) {
+    // ---- split: each 64-amplitude row (128 floats) is scaled by 2^e (largest component
+    // in [2^14, 2^15); exact) and split into hi = fp16(x) and lo = fp16(x - hi).  Thread
+    // t converts 8 consecutive floats (K 8 pc .. 8 pc + 7) of rows t / 16 + R i (R rows
+    // per pass); the 16 threads of a row find its maximum with shuffles.
+    // The parent quarters (quarter c = rows 32 (c % 4) .. + 31 of unit blockIdx.x +
+    // (c / 4) gridDim.x) stream through a kHRaw-stage ring with cp.async: each warp
+    // copies exactly the two rows per pass that it converts (1 KB, coalesced), so a
+    // warp-level sync is all a stage needs. ----
+    const int t = warp < 4 ? (int)threadIdx.x : (int)threadIdx.x - 13 * 32 + 128;
+    constexpr int R = kHSplitThreads / 16;
+    constexpr int kItems = 32 / R;
+    const int pc = t & 15;
+    const int sw = t >> 5;                               // split warp: rows i R + 2 sw, + 1
+    // the parent of child g_first + k radix is parent (g_first / radix + k) - parent_lo
+    const int64_t pbase = g_first / radix - a.parent_lo;
+    auto src_of = [&](int64_t c) {
+      const int64_t u = blockIdx.x + (c >> 2) * gridDim.x;
+      const int64_t row = ((pbase + (u >> tb)) << (a.h - kMmaBits)) + ((u & ((1 << tb) - 1)) << 7) + (c & 3) * 32;
+      return reinterpret_cast<const uint8_t *>(a.parent) + row * 512;
+    };
+    auto issue = [&](int64_t c) {
+      if (c < nquarters) {
+        const uint8_t *src = src_of(c);
+        const uint32_t dst = smem_u32(sR + (int)(c % kHRaw) * kHQuarter);
+#pragma unroll
+        for (int i = 0; i < kItems; ++i)
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const int off = (i * R + 2 * sw + h) * 512 + lane * 16;
+            lvl_cp_async16(dst + off, src + off);
+          }
+      }
+      lvl_cp_commit();                                   // (empty groups keep the count uniform)
+    };
+#pragma unroll
+    for (int c = 0; c < kHRaw - 1; ++c) issue(c);
+    int64_t it = 0;
+    for (int64_t tu = 0; tu < my_units && !abort_sh; ++tu) {
+      const int o = (int)(tu & 1);
+      if (!mbar_wait(&ops_empty[o], ((uint32_t)(tu >> 1) & 1u) ^ 1u)) {
+        atomicExch(a.err, 4);
+        abort_sh = 1;
+        break;
+      }
+      const uint32_t op = smem_u32(sOp + o * kHOpBytes);
+      float *inv = row_inv[tu & 3];
+      for (int q = 0; q < 4; ++q, ++it) {
+        issue(it + kHRaw - 1);                         // into the stage read last iteration
+        lvl_cp_wait<kHRaw - 1>();                      // this thread's copies of quarter it
+        __syncwarp();                                    // ... and the rest of its warp's
+        const uint32_t raw = smem_u32(sR + (int)(it % kHRaw) * kHQuarter);
+        float4 xr[kItems][2];
+#pragma unroll
+        for (int i = 0; i < kItems; ++i) {
+          const int rr = i * R + (t >> 4);
+          xr[i][0] = lds128(raw + rr * 512 + pc * 32);
+          xr[i][1] = lds128(raw + rr * 512 + pc * 32 + 16);
+        }
+        __syncwarp();                                    // read before the stage is refilled
+#pragma unroll
+        for (int i = 0; i < kItems; ++i) {
+          const int rr = i * R + (t >> 4);                 // row within the quarter
+          const int n = q * 32 + rr;                       // row within the unit (MMA N)
+          const float4 x0 = xr[i][0], x1 = xr[i][1];
+          float mx = fmaxf(fmaxf(fmaxf(fabsf(x0.x), fabsf(x0.y)), fmaxf(fabsf(x0.z), fabsf(x0.w))),
+                           fmaxf(fmaxf(fabsf(x1.x), fabsf(x1.y)), fmaxf(fabsf(x1.z), fabsf(x1.w))));
+#pragma unroll
+          for (int sh = 8; sh > 0; sh >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, sh));
+          // scale 2^(141 - eb) for biased exponent eb of the maximum (largest scaled
+          // component in [2^14, 2^15)), capped at 2^126 so that its inverse stays a normal
+          // float (zero rows keep zero).  hi = x s rounded to a multiple of 16 (adding and
+          // removing 1.5 2^27), exact in FP16; lo = x s - hi, exact, |lo| <= 8, rounded to
+          // FP16: the split is within 2^-23 of the row's largest component.
+          const uint32_t eb = __float_as_uint(mx) >> 23;
+          const uint32_t sb = min(268u - min(eb, 254u), 253u);
+          const float sc = __uint_as_float(sb << 23);
+          constexpr float kRound = 201326592.0f;           // 1.5 x 2^27: ulp 16
+          const float xv[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
+          uint32_t hb[4], lb[4];
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            const float h0 = __fsub_rn(__fmaf_rn(xv[2 * j], sc, kRound), kRound);
+            const float h1 = __fsub_rn(__fmaf_rn(xv[2 * j + 1], sc, kRound), kRound);
+            hb[j] = h2_bits(__floats2half2_rn(h0, h1));
+            lb[j] = h2_bits(__floats2half2_rn(__fmaf_rn(xv[2 * j], sc, -h0), __fmaf_rn(xv[2 * j + 1], sc, -h1)));
+          }
+          // K-major, 128-byte swizzle: atom pc / 8, 16-byte piece (pc % 8) ^ (n % 8) of row n
+          const uint32_t off = (uint32_t)(pc >> 3) * kHAtom + (uint32_t)n * 128 + ((uint32_t)((pc & 7) ^ (n & 7)) << 4);
+          sts128(op + off, hb[0], hb[1], hb[2], hb[3]);
+          sts128(op + 2 * kHAtom + off, lb[0], lb[1], lb[2], lb[3]);
+          if (pc == 0) inv[n] = __uint_as_float((254u - sb) << 23);
+        }
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      mbar_arrive(&ops_full[o]);
+      mbar_arrive(&sc_full[tu & 3]);
+    }
+    lvl_cp_wait<0>();                                    // no copy is in flight at exit
+  } else if (warp == 8) {
+    // ---- MMA issuer ----
+    if (lane == 0) {
+      // FP32 accumulate, FP16 A and B, both K-major, N = 128, M = 128
+      const uint32_t idesc = (1u << 4) | ((uint32_t)(128 >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+      for (int64_t tu = 0; tu < my_units && !abort_sh; ++tu) {
+        const int b = (int)(tu & 1);
+        if (!mbar_wait(&tempty[b], ((uint32_t)(tu >> 1) & 1u) ^ 1u)) {
+          atomicExch(a.err, 5);
+          abort_sh = 1;
+          break;
+        }
+        if (!mbar_wait(&ops_full[b], (uint32_t)(tu >> 1) & 1u)) {
+          atomicExch(a.err, 6);
+          abort_sh = 1;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t d = tmem + 256u + (uint32_t)(b * 128);
+        const uint8_t *op = sOp + b * kHOpBytes;
+        // D[n][row] = sum_k W[n][k] parent[row][k]: W (TMEM) is the MMA's A operand
+        // (M = 128 output components), the parent rows its B operand (N = 128 rows)
+#pragma unroll
+        for (int kc = 0; kc < 2; ++kc) {
+          const uint64_t phi = make_desc(op + kc * kHAtom), plo = make_desc(op + (2 + kc) * kHAtom);
+#pragma unroll
+          for (int term = 0; term < 3; ++term) {
+            const uint64_t dp = term == 1 ? plo : phi;
+            const uint32_t wcol = (term == 2 ? 64u : 0u) + (uint32_t)(kc * 32);
+#pragma unroll
+            for (int k = 0; k < 4; ++k)      // 16 FP16 of K per MMA (32 bytes, 8 columns)
+              mma_f16_ts(d, tmem + wcol + 8u * k, dp + 2 * k, idesc, (kc | term | k) ? 1u : 0u);
+          }
+        }
+        mma_commit(&ops_empty[b]);            // the operand buffer is free once these finish
+        mma_commit(&tfull[b]);                // the accumulator is complete
+      }
+      // every MMA issued above has finished before TMEM is released
+      mma_commit(&drain);
+      if (!mbar_wait(&drain, 0)) atomicExch(a.err, 7);
+    }
+    __syncwarp();
+  } else {
+    // ---- epilogue: two groups of four warps (4..7 and 9..12) take alternate 32-row
+    // quarters of each accumulator.  TMEM lane quarter (warp & 3) holds output
+    // components 32 (warp & 3) .. + 31; TMEM column j of the accumulator is row j of the
+    // unit; a quarter is unscaled and stored straight from registers. ----
+    const int grp = warp >= 9 ? 1 : 0;
+    const uint32_t bar_id = 1 + grp;                     // named barrier of the group
+    const int q4 = warp & 3;
+    const int comp = q4 * 32 + lane;
+    const float inv_w = reinterpret_cast<const float *>(wimg + (size_t)radix * kMmaWDigitBytes)[m];
+    int64_t tu = 0;
+    // The four warps of a group meet at named barriers, so they decide to stop together:
+    // only they write their epi_abort word, before a barrier, and all read it after.
+    for (int64_t u = blockIdx.x; u < units; u += gridDim.x, ++tu) {
+      const int b = (int)(tu & 1);
+      const bool ok = mbar_wait(&tfull[b], (uint32_t)(tu >> 1) & 1u) &&
+                      mbar_wait(&sc_full[tu & 3], (uint32_t)(tu >> 2) & 1u);
+      if (!ok) epi_abort[grp] = 1;
+      asm volatile("bar.sync %0, 128;" ::"r"(bar_id) : "memory");
+      if (epi_abort[grp]) {
+        if (!ok) atomicExch(a.err, 8);
+        abort_sh = 1;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const int64_t g = g_first + (u >> tb) * radix;
+      float *dst = a.child + (((uint64_t)(g - a.node_lo) << a.h) + ((uint64_t)(u & ((1 << tb) - 1)) << 13)) * 2;
+      const float *inv = row_inv[tu & 3];
+#pragma unroll 1
+      for (int qr = grp; qr < 4; qr += 2) {
+        uint32_t v[32];
+        const uint32_t taddr = tmem + ((uint32_t)(q4 * 32) << 16) + 256u + (uint32_t)(b * 128 + qr * 32);
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+            "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+              "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
+              "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
+              "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+            : "r"(taddr));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        // row j of the quarter goes out from registers, a warp writing its 32 components
+        // (128 contiguous bytes) per row
+        float *out = dst + (size_t)qr * 32 * 128 + comp;
+#pragma unroll
+        for (int j = 0; j < 32; ++j) out[(size_t)j * 128] = __uint_as_float(v[j]) * inv[qr * 32 + j] * inv_w;
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      mbar_arrive(&tempty[b]);
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 8) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kHTmemCols) : "memory");
+  }
+}
+
+// ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
 PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
@@ -855,6 +1196,25 @@ void level_mma_image(const double *w, float *hi, float *lo) {
   }
 }
 
+void level_mma_image_f16(const double *w, void *digit_image, float *inv_scale) {
+  // scale 2^e with the largest |entry| in [2^14, 2^15); hi = entry rounded to a multiple
+  // of 16 (exact in FP16), lo = fp16(entry - hi), as the kernel splits the parent rows
+  double mx = 0.0;
+  for (int i = 0; i < 128 * 128; ++i) mx = std::max(mx, std::fabs(w[i]));
+  int ex = 0;
+  if (mx > 0.0) std::frexp(mx, &ex);                   // mx = f 2^ex, f in [0.5, 1)
+  const int e = mx > 0.0 ? 15 - ex : 0;
+  // row-major [n][k]: the kernel loads row n into TMEM lane n, two FP16 per column
+  __half *hi = static_cast<__half *>(digit_image), *lo = hi + 128 * 128;
+  for (int i = 0; i < 128 * 128; ++i) {
+    const double xs = std::ldexp(w[i], e);
+    const double h = 16.0 * std::nearbyint(xs / 16.0);
+    hi[i] = __float2half_rn((float)h);
+    lo[i] = __float2half_rn((float)(xs - h));
+  }
+  *inv_scale = std::ldexp(1.0f, -e);
+}
+
 cudaError_t launch_level_mma(const LevelMmaArgs &a, cudaStream_t st) {
   if (a.num_nodes <= 0) return cudaSuccess;
   static int sms = 0;
@@ -863,10 +1223,21 @@ cudaError_t launch_level_mma(const LevelMmaArgs &a, cudaStream_t st) {
     cudaGetDevice(&dev);
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) sms = 148;
   }
+  const int r = a.radix > 0 ? a.radix : 1;
+  if (a.num_post == 0) {
+    // FP16 split kernel (W image: FP16 parts per digit, then the inverse scales)
+    if (a.h < kMmaMinH || (reinterpret_cast<uintptr_t>(a.parent) & 15) || (reinterpret_cast<uintptr_t>(a.child) & 15))
+      return cudaErrorInvalidValue;
+    cudaError_t e = cudaFuncSetAttribute(level_mma_f16_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kHSmem);
+    if (e != cudaSuccess) return e;
+    const int64_t per_digit_units = ((a.num_nodes + r - 1) / r) << (a.h - kMmaMinH);
+    const int64_t gx = std::min<int64_t>(std::max(1, (sms + r - 1) / r), std::max<int64_t>(1, per_digit_units));
+    level_mma_f16_kernel<<<dim3((unsigned)gx, (unsigned)r), kHThreads, kHSmem, st>>>(a);
+    return cudaGetLastError();
+  }
   const size_t smem = kLvlSmem;
   cudaError_t e = cudaFuncSetAttribute(level_mma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  const int r = a.radix > 0 ? a.radix : 1;
   const int64_t per_digit_units = ((a.num_nodes + r - 1) / r) << (a.h - kMmaMinH);
   const int64_t gx = std::min<int64_t>(std::max(1, (sms + r - 1) / r), std::max<int64_t>(1, per_digit_units));
   // the parents as a [rows][128] FP32 matrix (one row = 64 amplitudes); 32 x 128 boxes

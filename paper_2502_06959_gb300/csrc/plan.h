@@ -69,7 +69,8 @@ struct LevelH {
   std::vector<PassH> passes;
   // Tensor-core level (complex64, whole program on the kMmaBits lowest storage bits):
   // per digit, the program as a real 2^(kMmaBits+1)-square matrix W, stored as the
-  // shared-memory image the kernel loads (TF32 hi part, then lo part).
+  // image the kernel loads (per digit TF32 hi then lo part when ops follow the product,
+  // else per digit FP16 hi then lo part, then the inverse scales).
   bool mma = false;
   std::vector<float> wimg;
   size_t w_off = 0;

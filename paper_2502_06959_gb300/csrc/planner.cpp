@@ -640,7 +640,8 @@ void pack_pass(const PassH &ps, std::vector<DevOp> &dops, std::vector<C> &mats, 
 
 // W images of the tensor-core levels: per digit m, the level's program U_m (64 x 64,
 // column by column) in real form W[2i + a][2j + b] (a, b: re / im), split into TF32 hi
-// and lo parts.  The leaf level is left out when it will be contracted at the bitstrings
+// and lo parts (levels with ops after the product) or scaled by a power of two and split
+// into FP16 hi and lo parts (levels without).  The leaf level is left out when it will be contracted at the bitstrings
 // (leaf_c > 0): it is never swept then.
 void compose_mma_levels(hsf_plan &p, int leaf_c) {
   const int B = (int)p.blocks.size();
@@ -674,7 +675,9 @@ void compose_mma_levels(hsf_plan &p, int leaf_c) {
       lv.mma = true;
       const std::vector<OpH> &mops = prefix;
       const int r = (int)p.radix[k];
-      lv.wimg.assign((size_t)r * 2 * (kMmaWPartBytes / 4), 0.f);
+      // a level with ops after the product runs the TF32 kernel, one without the FP16 one
+      const bool f16 = lv.post.empty();
+      lv.wimg.assign(f16 ? (size_t)r * (kMmaWDigitBytes / 4) + (size_t)r : (size_t)r * 2 * (kMmaWPartBytes / 4), 0.f);
       // the ops after the last digit-dependent one are shared by every digit: compose
       // them once (S, column-major), then U_m e_col = S (prefix_m e_col), where the
       // prefix image of a basis vector has few nonzeros
@@ -707,8 +710,13 @@ void compose_mma_levels(hsf_plan &p, int leaf_c) {
             w[(size_t)(2 * row + 1) * K + 2 * col + 1] = v[row].real();
           }
         }
-        float *hi = lv.wimg.data() + (size_t)m * 2 * (kMmaWPartBytes / 4);
-        level_mma_image(w.data(), hi, hi + kMmaWPartBytes / 4);
+        if (f16) {
+          level_mma_image_f16(w.data(), lv.wimg.data() + (size_t)m * (kMmaWDigitBytes / 4),
+                              lv.wimg.data() + (size_t)r * (kMmaWDigitBytes / 4) + m);
+        } else {
+          float *hi = lv.wimg.data() + (size_t)m * 2 * (kMmaWPartBytes / 4);
+          level_mma_image(w.data(), hi, hi + kMmaWPartBytes / 4);
+        }
       }
     }
 }

@@ -115,7 +115,7 @@ SIGNATURES = {
     "hsf_version": (ctypes.c_char_p, []),
 }
 
-KERNEL_KINDS = ("sweep", "gather", "reduce", "window", "other", "leaf", "level_mma")
+KERNEL_KINDS = ("sweep", "gather", "reduce", "window", "other", "leaf", "level_mma", "level_f16")
 
 
 class hsf_kernel_stat(ctypes.Structure):

@@ -1,8 +1,8 @@
 """GPU parity of the tensor-core tree level.
 
 A tree level whose program (Schmidt factor, then the gates it hoists) acts only on the
-6 lowest storage bits of a half state with h >= 13 qubits runs as one TF32x3 tensor-core
-product per Schmidt digit.  These cases check it against the FP64 oracle (complex64
+6 lowest storage bits of a half state with h >= 13 qubits runs as one tensor-core product
+per Schmidt digit (FP16 hi/lo parts of power-of-two scaled operands, three products).  These cases check it against the FP64 oracle (complex64
 bound: 1e-5 max abs and 1e-4 of the largest reference amplitude) and against the same
 plan swept on the CUDA cores, for bitstring and window outputs, over path ranges that
 start and end inside a parent's group of digits.
@@ -65,8 +65,8 @@ def test_tc_level_bitstrings_against_oracle(n, kind, seed):
     ref_cc, desc_cc = run(pr, bits, flags=hsf.FLAG_NO_TC_LEVEL)
     assert "tensor-core product" not in desc_cc
     check(got, ref_cc)
-    # TF32x3 keeps FP32-level accuracy: a hi part one TF32 ulp off (rounded where the
-    # tensor core truncates) would show up as ~5e-4 relative error
+    # the split product keeps FP32-level accuracy: a dropped lo part (one FP16 product)
+    # or a wrong row scale would show up as ~5e-4 relative error or worse
     assert np.max(np.abs(got - ref_cc)) <= 2e-5 * np.max(np.abs(ref_cc))
     plan = hsf.Plan(pr.n, pr.gates, pr.cut, pr.blocks, precision="c64")
     P = int(plan.info["num_paths"])
@@ -104,9 +104,64 @@ def test_tc_level_in_n30_plan():
     plan = hsf.Plan.from_problem(pr)
     desc = hsf.hsf_plan_describe(plan.handle)
     plan.close()
+    # level 7: the whole level is the product (FP16 parts, no ops after it)
     lines = [l for l in desc.splitlines() if l.startswith(" level 7:")]
-    assert len(lines) == 2 and all("tensor-core product" in l and "then 0 passes" in l for l in lines), desc
-    # level 6: its leading ops (factor and the gates on the 6 low bits) as the product,
-    # the rest (on storage bits below 11) applied by the product's epilogue
+    assert len(lines) == 2 and all("product (FP16x3)" in l and "then 0 passes" in l for l in lines), desc
+    # level 6: its leading ops (factor and the gates on the 6 low bits) as the product
+    # (TF32 parts), the rest (on storage bits below 11) applied by the product's epilogue
     lines = [l for l in desc.splitlines() if l.startswith(" level 6:")]
-    assert len(lines) == 2 and all("tensor-core product" in l and "ops in its epilogue" in l for l in lines), desc
+    assert len(lines) == 2 and all("product (TF32x3)" in l and "ops in its epilogue" in l for l in lines), desc
+
+
+def _storage_bits(desc, n, cut):
+    """Global qubit -> storage bit on its side, from the plan description's store lists
+    (side b holds qubits 0..cut, side a the rest)."""
+    import re
+    st = {m.group(1): [int(v) for v in m.group(2).split(",")]
+          for m in re.finditer(r"side ([ab]): h=\d+ store=\[([0-9,]*)\]", desc)}
+    return {q: (st["b"][q] if q <= cut else st["a"][q - cut - 1]) for q in range(n)}
+
+
+def test_fp16_level_keeps_small_amplitudes():
+    """The FP16 split scales every 64-amplitude parent row by its own power of two.
+
+    With near-identity single-qubit rotations the amplitude of a bitstring falls by about
+    three orders of magnitude per 1 it holds.  With the 1s on qubits stored at bit 6 or
+    above, the magnitude changes from row to row (a row is the 64 amplitudes on storage
+    bits 0..5) and the rows span far more than FP16's exponent range (2^29 from its
+    smallest normal to its largest value).  Unscaled FP16 parts would flush the small
+    rows; scaled ones keep those amplitudes to FP32-level relative accuracy, as the
+    CUDA-core sweep does.  (Within a row the split is accurate to about 2^-22 of the
+    row's largest amplitude, an absolute bound, which the standard check covers.)
+    """
+    from paper_2502_06959_gb300 import hsf
+    pr = problem(26, "rzz", 11)
+    theta = 2e-3
+    c, sn = np.cos(theta / 2), np.sin(theta / 2)
+    rx = np.array([[c, -1j * sn], [-1j * sn, c]])
+    for g in pr.gates:
+        if g.kind == "matrix" and len(g.qubits) == 1:
+            g.matrix = rx
+    _, desc = run(pr, np.zeros(1, dtype=np.uint64))
+    assert "product (FP16x3)" in desc, desc
+    sbit = _storage_bits(desc, pr.n, pr.cut)
+    high = [q for q in range(pr.n) if sbit[q] >= 6]
+    rng = np.random.default_rng(11)
+    bits = []
+    for k in range(0, 9):                      # bitstrings with k ones on high storage bits
+        for _ in range(6):
+            b = 0
+            for q in rng.choice(high, size=k, replace=False):
+                b |= 1 << int(q)
+            bits.append(b)
+    extra = W.random_bitstrings(rng, pr.n, 64)  # any bitstrings: absolute accuracy
+    bits = np.concatenate([np.array(bits, dtype=np.uint64), np.asarray(extra, dtype=np.uint64)])
+    got, _ = run(pr, bits)
+    ref, desc_cc = run(pr, bits, flags=hsf.FLAG_NO_TC_LEVEL)
+    assert "tensor-core product" not in desc_cc
+    check(got, ref)
+    nh = 9 * 6
+    mag = np.abs(ref[:nh])
+    assert mag.min() < 1e-12 * mag.max(), (mag.min(), mag.max())   # the range is really there
+    rel = np.abs(got[:nh] - ref[:nh]) / mag
+    assert np.max(rel) <= 1e-4, (np.max(rel), mag[np.argmax(rel)])
