@@ -738,9 +738,10 @@ __global__ void __launch_bounds__(kLvlThreads, 1) level_mma_kernel(const __grid_
 // output component n, columns = k, two FP16 per column).  Eight split warps stream the raw
 // FP32 parent rows through a shared-memory ring with cp.async (each warp copies the rows
 // it converts) and write the FP16 hi and lo B operands of a 128-row unit (K-major,
-// 128-byte swizzle, two buffers); one thread issues the 24 MMAs of a unit into one of two
-// TMEM accumulators; two groups of four warps read the other back, unscale it and store
-// the child rows from registers.  The split work per element is what bounds this kernel;
+// 128-byte swizzle, two buffers).  A CTA serves two Schmidt digits (both W_m in tensor
+// memory), so each parent unit is streamed and split once for two children; one thread
+// issues each digit's 24 MMAs into one of two TMEM accumulators in turn; two groups of
+// four warps read the other back, unscale it and store the child rows from registers.  The split work per element is what bounds this kernel;
 // a level with ops after the product uses the TF32 kernel, whose epilogue stages rows in
 // the shared memory this one spends on the split's operand buffers.  Every wait is
 // bounded; on expiry the CTA records an error, drains its MMAs and copies, frees TMEM and
@@ -750,10 +751,11 @@ constexpr int kHRaw = 5;                        // raw quarters in the ring
 constexpr int kHOps = 2;                        // FP16 operand buffers (one 128-row unit each)
 constexpr int kHAtom = 128 * 128;               // bytes: 128 rows x 64 FP16 (one swizzle atom column)
 constexpr int kHOpBytes = 4 * kHAtom;           // hi (K 0..63, 64..127) then lo (same)
+constexpr int kHDigits = 2;                     // Schmidt digits per CTA (W_m of each in TMEM)
 constexpr int kHSplit = 8;                      // split warps: 0..3 and 13..16
 constexpr int kHSplitThreads = kHSplit * 32;
 constexpr int kHThreads = (9 + kHSplit) * 32;   // + 2 x 4 epilogue warps and the MMA warp
-constexpr uint32_t kHTmemCols = 512;            // W hi [0,64), W lo [64,128), D 2 x 128 at 256
+constexpr uint32_t kHTmemCols = 512;            // W_i hi 128 i + [0,64), lo + [64,128); D 2 x 128 at 256
 constexpr size_t kHSmem = (size_t)kHOps * kHOpBytes + (size_t)kHRaw * kHQuarter + 1024;
 static_assert(kHSmem <= 227 * 1024 - 4096, "FP16 level kernel shared memory");
 
@@ -799,12 +801,15 @@ __global__ void __launch_bounds__(kHThreads, 1) level_mma_f16_kernel(LevelMmaArg
   __shared__ volatile int abort_sh, epi_abort[2];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t radix = a.radix;
-  const int m = blockIdx.y;
-  const int64_t g_first = a.node_lo + ((m - a.node_lo % radix) % radix + radix) % radix;
-  const int64_t g_end = a.node_lo + a.num_nodes;
-  const int64_t nchild = g_first < g_end ? (g_end - g_first + radix - 1) / radix : 0;
+  // A CTA serves kHDigits consecutive digits (one when the radix is odd): each parent unit
+  // is split once and multiplied by every digit's W.  Units run over the parents with a
+  // child in [node_lo, node_lo + num_nodes); children outside are computed, not stored.
+  const int dpc = radix % kHDigits == 0 ? kHDigits : 1;
+  const int m0 = blockIdx.y * dpc;
+  const int64_t p_first = a.node_lo / radix;
+  const int64_t p_last = (a.node_lo + a.num_nodes - 1) / radix;
   const int tb = a.h - kMmaMinH;                        // 2^tb row units per node
-  const int64_t units = nchild << tb;
+  const int64_t units = (p_last - p_first + 1) << tb;
   const int64_t my_units = units > blockIdx.x ? (units - 1 - blockIdx.x) / gridDim.x + 1 : 0;
   const int64_t nquarters = my_units * 4;
   const uint8_t *wimg = static_cast<const uint8_t *>(a.w);
@@ -835,14 +840,15 @@ __global__ void __launch_bounds__(kHThreads, 1) level_mma_f16_kernel(LevelMmaArg
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = tmem_sh;
   if (warp >= 4 && warp < 8) {
-    // W_m into TMEM: lane n holds row n, two FP16 per column; columns [0,64) the hi part,
-    // [64,128) the lo part (the image holds 128 rows x 64 words per part)
+    // W_m into TMEM for each digit i served: lane n holds row n, two FP16 per column;
+    // columns 128 i + [0,64) the hi part, 128 i + [64,128) the lo part (the image holds
+    // 128 rows x 64 words per part)
     const int q4 = warp & 3;
-    const uint32_t *wrow =
-        reinterpret_cast<const uint32_t *>(wimg + (size_t)m * kMmaWDigitBytes) + (size_t)(q4 * 32 + lane) * 64;
 #pragma unroll 1
-    for (int c = 0; c < 4; ++c) {
-      const uint32_t *src = wrow + (size_t)(c >> 1) * 128 * 64 + (c & 1) * 32;
+    for (int c = 0; c < 4 * dpc; ++c) {
+      const uint32_t *wrow = reinterpret_cast<const uint32_t *>(wimg + (size_t)(m0 + (c >> 2)) * kMmaWDigitBytes) +
+                             (size_t)(q4 * 32 + lane) * 64;
+      const uint32_t *src = wrow + (size_t)((c >> 1) & 1) * 128 * 64 + (c & 1) * 32;
       uint32_t v[32];
 #pragma unroll
       for (int j = 0; j < 32; j += 4) {
@@ -882,8 +888,7 @@ __global__ void __launch_bounds__(kHThreads, 1) level_mma_f16_kernel(LevelMmaArg
     constexpr int kItems = 32 / R;
     const int pc = t & 15;
     const int sw = t >> 5;                               // split warp: rows i R + 2 sw, + 1
-    // the parent of child g_first + k radix is parent (g_first / radix + k) - parent_lo
-    const int64_t pbase = g_first / radix - a.parent_lo;
+    const int64_t pbase = p_first - a.parent_lo;        // unit u's parent, in the parent buffer
     auto src_of = [&](int64_t c) {
       const int64_t u = blockIdx.x + (c >> 2) * gridDim.x;
       const int64_t row = ((pbase + (u >> tb)) << (a.h - kMmaBits)) + ((u & ((1 << tb) - 1)) << 7) + (c & 3) * 32;
@@ -973,36 +978,44 @@ __global__ void __launch_bounds__(kHThreads, 1) level_mma_f16_kernel(LevelMmaArg
       // FP32 accumulate, FP16 A and B, both K-major, N = 128, M = 128
       const uint32_t idesc = (1u << 4) | ((uint32_t)(128 >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
       for (int64_t tu = 0; tu < my_units && !abort_sh; ++tu) {
-        const int b = (int)(tu & 1);
-        if (!mbar_wait(&tempty[b], ((uint32_t)(tu >> 1) & 1u) ^ 1u)) {
-          atomicExch(a.err, 5);
-          abort_sh = 1;
-          break;
-        }
-        if (!mbar_wait(&ops_full[b], (uint32_t)(tu >> 1) & 1u)) {
+        const int o = (int)(tu & 1);
+        if (!mbar_wait(&ops_full[o], (uint32_t)(tu >> 1) & 1u)) {
           atomicExch(a.err, 6);
           abort_sh = 1;
           break;
         }
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const uint32_t d = tmem + 256u + (uint32_t)(b * 128);
-        const uint8_t *op = sOp + b * kHOpBytes;
-        // D[n][row] = sum_k W[n][k] parent[row][k]: W (TMEM) is the MMA's A operand
-        // (M = 128 output components), the parent rows its B operand (N = 128 rows)
-#pragma unroll
-        for (int kc = 0; kc < 2; ++kc) {
-          const uint64_t phi = make_desc(op + kc * kHAtom), plo = make_desc(op + (2 + kc) * kHAtom);
-#pragma unroll
-          for (int term = 0; term < 3; ++term) {
-            const uint64_t dp = term == 1 ? plo : phi;
-            const uint32_t wcol = (term == 2 ? 64u : 0u) + (uint32_t)(kc * 32);
-#pragma unroll
-            for (int k = 0; k < 4; ++k)      // 16 FP16 of K per MMA (32 bytes, 8 columns)
-              mma_f16_ts(d, tmem + wcol + 8u * k, dp + 2 * k, idesc, (kc | term | k) ? 1u : 0u);
+        const uint8_t *op = sOp + o * kHOpBytes;
+        bool ok = true;
+        for (int i = 0; i < dpc; ++i) {
+          // output tu dpc + i goes to accumulator b once the epilogue has drained it
+          const int64_t oi = tu * dpc + i;
+          const int b = (int)(oi & 1);
+          if (!mbar_wait(&tempty[b], ((uint32_t)(oi >> 1) & 1u) ^ 1u)) {
+            atomicExch(a.err, 5);
+            abort_sh = 1;
+            ok = false;
+            break;
           }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint32_t d = tmem + 256u + (uint32_t)(b * 128);
+          // D[n][row] = sum_k W[n][k] parent[row][k]: W (TMEM) is the MMA's A operand
+          // (M = 128 output components), the parent rows its B operand (N = 128 rows)
+#pragma unroll
+          for (int kc = 0; kc < 2; ++kc) {
+            const uint64_t phi = make_desc(op + kc * kHAtom), plo = make_desc(op + (2 + kc) * kHAtom);
+#pragma unroll
+            for (int term = 0; term < 3; ++term) {
+              const uint64_t dp = term == 1 ? plo : phi;
+              const uint32_t wcol = (uint32_t)(i * 128) + (term == 2 ? 64u : 0u) + (uint32_t)(kc * 32);
+#pragma unroll
+              for (int kk = 0; kk < 4; ++kk)   // 16 FP16 of K per MMA (32 bytes, 8 columns)
+                mma_f16_ts(d, tmem + wcol + 8u * kk, dp + 2 * kk, idesc, (kc | term | kk) ? 1u : 0u);
+            }
+          }
+          mma_commit(&tfull[b]);              // the accumulator is complete
         }
-        mma_commit(&ops_empty[b]);            // the operand buffer is free once these finish
-        mma_commit(&tfull[b]);                // the accumulator is complete
+        if (!ok) break;
+        mma_commit(&ops_empty[o]);            // the operand buffer is free once these finish
       }
       // every MMA issued above has finished before TMEM is released
       mma_commit(&drain);
@@ -1018,46 +1031,57 @@ __global__ void __launch_bounds__(kHThreads, 1) level_mma_f16_kernel(LevelMmaArg
     const uint32_t bar_id = 1 + grp;                     // named barrier of the group
     const int q4 = warp & 3;
     const int comp = q4 * 32 + lane;
-    const float inv_w = reinterpret_cast<const float *>(wimg + (size_t)radix * kMmaWDigitBytes)[m];
+    const float *inv_ws = reinterpret_cast<const float *>(wimg + (size_t)radix * kMmaWDigitBytes) + m0;
     int64_t tu = 0;
     // The four warps of a group meet at named barriers, so they decide to stop together:
     // only they write their epi_abort word, before a barrier, and all read it after.
     for (int64_t u = blockIdx.x; u < units; u += gridDim.x, ++tu) {
-      const int b = (int)(tu & 1);
-      const bool ok = mbar_wait(&tfull[b], (uint32_t)(tu >> 1) & 1u) &&
-                      mbar_wait(&sc_full[tu & 3], (uint32_t)(tu >> 2) & 1u);
-      if (!ok) epi_abort[grp] = 1;
-      asm volatile("bar.sync %0, 128;" ::"r"(bar_id) : "memory");
-      if (epi_abort[grp]) {
-        if (!ok) atomicExch(a.err, 8);
-        abort_sh = 1;
-        break;
-      }
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const int64_t g = g_first + (u >> tb) * radix;
-      float *dst = a.child + (((uint64_t)(g - a.node_lo) << a.h) + ((uint64_t)(u & ((1 << tb) - 1)) << 13)) * 2;
       const float *inv = row_inv[tu & 3];
+      const int64_t pu = p_first + (u >> tb);           // the unit's parent
+      bool stop = false;
+      for (int i = 0; i < dpc; ++i) {
+        const int64_t oi = tu * dpc + i;
+        const int b = (int)(oi & 1);
+        const bool ok = mbar_wait(&tfull[b], (uint32_t)(oi >> 1) & 1u) &&
+                        mbar_wait(&sc_full[tu & 3], (uint32_t)(tu >> 2) & 1u);
+        if (!ok) epi_abort[grp] = 1;
+        asm volatile("bar.sync %0, 128;" ::"r"(bar_id) : "memory");
+        if (epi_abort[grp]) {
+          if (!ok) atomicExch(a.err, 8);
+          abort_sh = 1;
+          stop = true;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const int64_t g = pu * radix + m0 + i;
+        const bool store = g >= a.node_lo && g < a.node_lo + a.num_nodes;
+        const uint64_t dst_off = store ? (((uint64_t)(g - a.node_lo) << a.h) + ((uint64_t)(u & ((1 << tb) - 1)) << 13)) * 2 : 0;
+        const float inv_w = inv_ws[i];
 #pragma unroll 1
-      for (int qr = grp; qr < 4; qr += 2) {
-        uint32_t v[32];
-        const uint32_t taddr = tmem + ((uint32_t)(q4 * 32) << 16) + 256u + (uint32_t)(b * 128 + qr * 32);
-        asm volatile(
-            "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-            "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-              "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
-              "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
-              "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
-            : "r"(taddr));
-        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-        // row j of the quarter goes out from registers, a warp writing its 32 components
-        // (128 contiguous bytes) per row
-        float *out = dst + (size_t)qr * 32 * 128 + comp;
+        for (int qr = grp; qr < 4; qr += 2) {
+          uint32_t v[32];
+          const uint32_t taddr = tmem + ((uint32_t)(q4 * 32) << 16) + 256u + (uint32_t)(b * 128 + qr * 32);
+          asm volatile(
+              "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+              "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+              : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
+                "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
+                "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+              : "r"(taddr));
+          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+          if (store) {
+            // row j of the quarter goes out from registers, a warp writing its 32
+            // components (128 contiguous bytes) per row
+            float *out = a.child + dst_off + (size_t)qr * 32 * 128 + comp;
 #pragma unroll
-        for (int j = 0; j < 32; ++j) out[(size_t)j * 128] = __uint_as_float(v[j]) * inv[qr * 32 + j] * inv_w;
+            for (int j = 0; j < 32; ++j) out[(size_t)j * 128] = __uint_as_float(v[j]) * inv[qr * 32 + j] * inv_w;
+          }
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        mbar_arrive(&tempty[b]);
       }
-      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-      mbar_arrive(&tempty[b]);
+      if (stop) break;
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -1230,9 +1254,11 @@ cudaError_t launch_level_mma(const LevelMmaArgs &a, cudaStream_t st) {
       return cudaErrorInvalidValue;
     cudaError_t e = cudaFuncSetAttribute(level_mma_f16_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kHSmem);
     if (e != cudaSuccess) return e;
-    const int64_t per_digit_units = ((a.num_nodes + r - 1) / r) << (a.h - kMmaMinH);
-    const int64_t gx = std::min<int64_t>(std::max(1, (sms + r - 1) / r), std::max<int64_t>(1, per_digit_units));
-    level_mma_f16_kernel<<<dim3((unsigned)gx, (unsigned)r), kHThreads, kHSmem, st>>>(a);
+    const int dpc = r % kHDigits == 0 ? kHDigits : 1;
+    const int gy = r / dpc;
+    const int64_t units = ((a.node_lo + a.num_nodes - 1) / r - a.node_lo / r + 1) << (a.h - kMmaMinH);
+    const int64_t gx = std::min<int64_t>(std::max(1, (sms + gy - 1) / gy), std::max<int64_t>(1, units));
+    level_mma_f16_kernel<<<dim3((unsigned)gx, (unsigned)gy), kHThreads, kHSmem, st>>>(a);
     return cudaGetLastError();
   }
   const size_t smem = kLvlSmem;
