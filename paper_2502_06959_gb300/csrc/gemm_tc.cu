@@ -1220,6 +1220,30 @@ void level_mma_image(const double *w, float *hi, float *lo) {
   }
 }
 
+// binary32 -> binary16 bits, round to nearest with ties to even, from the IEEE 754
+// encodings (the host library conversion is a slow call per element)
+static uint16_t f16_bits_rn(float f) {
+  uint32_t x;
+  std::memcpy(&x, &f, 4);
+  const uint32_t sign = (x >> 16) & 0x8000u, ax = x & 0x7fffffffu;
+  if (ax >= 0x7f800000u) return (uint16_t)(sign | (ax > 0x7f800000u ? 0x7e00u : 0x7c00u));   // NaN / Inf
+  if (ax >= 0x477ff000u) return (uint16_t)(sign | 0x7c00u);          // >= 65520 rounds to Inf
+  const uint32_t e = ax >> 23;                                        // biased binary32 exponent
+  if (e >= 113) {                                                     // normal binary16 (>= 2^-14)
+    uint32_t r = ((e - 112) << 10) | ((ax & 0x7fffffu) >> 13);
+    const uint32_t rem = ax & 0x1fffu;
+    r += (rem + (r & 1u)) > 0x1000u;                                 // ties to even; a carry moves to the exponent
+    return (uint16_t)(sign | r);
+  }
+  if (e < 102) return (uint16_t)sign;                                 // below 2^-25: zero
+  // subnormal binary16 in units of 2^-24: m 2^(e - 150) = (m >> (126 - e)) units
+  const uint32_t m = (ax & 0x7fffffu) | 0x800000u, sh = 126 - e;      // sh in 14..24
+  uint32_t r = m >> sh;
+  const uint32_t rem = m & ((1u << sh) - 1u), half = 1u << (sh - 1);
+  r += (rem + (r & 1u)) > half;                                       // ties to even; may reach 0x400 (2^-14)
+  return (uint16_t)(sign | r);
+}
+
 void level_mma_image_f16(const double *w, void *digit_image, float *inv_scale) {
   // scale 2^e with the largest |entry| in [2^14, 2^15); hi = entry rounded to a multiple
   // of 16 (exact in FP16), lo = fp16(entry - hi), as the kernel splits the parent rows
@@ -1228,13 +1252,16 @@ void level_mma_image_f16(const double *w, void *digit_image, float *inv_scale) {
   int ex = 0;
   if (mx > 0.0) std::frexp(mx, &ex);                   // mx = f 2^ex, f in [0.5, 1)
   const int e = mx > 0.0 ? 15 - ex : 0;
+  const double sc = std::ldexp(1.0, e);
+  constexpr double kRound = 6755399441055744.0;        // 1.5 x 2^52: rounds to an integer, ties to even
   // row-major [n][k]: the kernel loads row n into TMEM lane n, two FP16 per column
-  __half *hi = static_cast<__half *>(digit_image), *lo = hi + 128 * 128;
+  uint16_t *hi = static_cast<uint16_t *>(digit_image), *lo = hi + 128 * 128;
   for (int i = 0; i < 128 * 128; ++i) {
-    const double xs = std::ldexp(w[i], e);
-    const double h = 16.0 * std::nearbyint(xs / 16.0);
-    hi[i] = __float2half_rn((float)h);
-    lo[i] = __float2half_rn((float)(xs - h));
+    const double xs = w[i] * sc;                       // exact: a power of two
+    const double t = xs * 0.0625;                      // exact; |t| < 2^11
+    const double h = 16.0 * std::copysign((t + kRound) - kRound, t);   // 16 nearbyint(t)
+    hi[i] = f16_bits_rn((float)h);                     // exact
+    lo[i] = f16_bits_rn((float)(xs - h));
   }
   *inv_scale = std::ldexp(1.0f, -e);
 }
