@@ -135,7 +135,7 @@ PROFILED_TRAFFIC = {
     "sweep": {"ratio": 275.1 / 335.5, "source": "paper_2502_06959_gb300/csrc/sweep.cu",
               "sha256": "a5699515952870e8", "profile": "profiles/sweep_reg_level6_n30.md"},
     "level_f16": {"ratio": 1281.6 / 1342.2, "source": "paper_2502_06959_gb300/csrc/gemm_tc.cu",
-                  "sha256": "f17e3ddda5298ad8", "profile": "profiles/level_f16_level7_n30.md"},
+                  "sha256": "4ea519f013bd5fd7", "profile": "profiles/level_f16_level7_n30.md"},
     "leaf": {"ratio": 1896.7 / 2147.5, "source": "paper_2502_06959_gb300/csrc/accum.cu",
              "sha256": "6aac98c52e3fcafd", "profile": "profiles/leaf_contract_n30.md"},
 }

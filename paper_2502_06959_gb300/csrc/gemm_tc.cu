@@ -741,11 +741,12 @@ __global__ void __launch_bounds__(kLvlThreads, 1) level_mma_kernel(const __grid_
 // 128-byte swizzle, two buffers).  A CTA serves two Schmidt digits (both W_m in tensor
 // memory), so each parent unit is streamed and split once for two children; one thread
 // issues each digit's 24 MMAs into one of two TMEM accumulators in turn; two groups of
-// four warps read the other back, unscale it and store the child rows from registers.  The split work per element is what bounds this kernel;
-// a level with ops after the product uses the TF32 kernel, whose epilogue stages rows in
-// the shared memory this one spends on the split's operand buffers.  Every wait is
-// bounded; on expiry the CTA records an error, drains its MMAs and copies, frees TMEM and
-// returns.
+// four warps read the other back, unscale it and store the child rows from registers.
+// With one digit per CTA the split's input latency bounded the kernel; with two, the
+// level runs close to its read/write pattern's DRAM rate.  A level with ops after the
+// product uses the TF32 kernel, whose epilogue stages rows in the shared memory this one
+// spends on the split's operand buffers.  Every wait is bounded; on expiry the CTA
+// records an error, drains its MMAs and copies, frees TMEM and returns.
 constexpr int kHQuarter = 32 * 512;             // bytes: 32 parent rows x 128 floats
 constexpr int kHRaw = 5;                        // raw quarters in the ring
 constexpr int kHOps = 2;                        // FP16 operand buffers (one 128-row unit each)
