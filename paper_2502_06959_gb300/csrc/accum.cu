@@ -546,12 +546,8 @@ size_t leaf_stream_smem(int r, int64_t per_cta) {
 // bitstrings per CTA; false if S does not fit one wave.
 template <int CB>
 bool leaf_stream_shape(int r, int64_t S, int *grid, int64_t *per_cta) {
-  static int sms = 0;
-  if (!sms) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) return false;
-  }
+  const int sms = device_sm_count();
+  if (sms <= 0) return false;
   for (int per_sm = kStreamPerSm; per_sm >= 1; --per_sm) {
     const int64_t pc = (S + (int64_t)sms * per_sm - 1) / ((int64_t)sms * per_sm);
     const size_t smem = leaf_stream_smem<CB>(r, pc);
@@ -607,9 +603,33 @@ __global__ void range_index_kernel(uint64_t *dst, int64_t count, PermArgs perm) 
   dst[i] = r;
 }
 
-__global__ void finalize_kernel(double *out, const double *comp, int64_t count) {
+// out += comp; a non-finite result sets *numeric (the output canary read by hsf_sync).
+__global__ void finalize_kernel(double *out, const double *comp, int64_t count, int32_t *numeric) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < count) out[i] += comp[i];
+  bool bad = false;
+  if (i < count) {
+    const double v = out[i] + comp[i];
+    out[i] = v;
+    bad = !isfinite(v);
+  }
+  if (__ballot_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0 && numeric) atomicOr(numeric, 1);
+}
+
+// Full-state output: out[i] = state[idx_i] in complex128, idx_i = bits[i] (bitstrings)
+// or i (leading window); a non-finite amplitude sets *numeric.
+template <typename R>
+__global__ void state_gather_kernel(const R *state, const uint64_t *bits, int64_t count, double *out,
+                                    int32_t *numeric) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  bool bad = false;
+  if (i < count) {
+    const uint64_t j = bits ? bits[i] : (uint64_t)i;
+    const double re = (double)state[2 * j], im = (double)state[2 * j + 1];
+    out[2 * i] = re;
+    out[2 * i + 1] = im;
+    bad = !isfinite(re) || !isfinite(im);
+  }
+  if (__ballot_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0 && numeric) atomicOr(numeric, 1);
 }
 
 __global__ void zero_kernel(double *p, int64_t count) {
@@ -745,9 +765,20 @@ cudaError_t launch_range_index(uint64_t *dst, int64_t count, const PermArgs &per
   return cudaGetLastError();
 }
 
-cudaError_t launch_finalize(double *out, const double *comp, int64_t count, cudaStream_t st) {
+cudaError_t launch_finalize(double *out, const double *comp, int64_t count, int32_t *numeric, cudaStream_t st) {
   if (count <= 0) return cudaSuccess;
-  finalize_kernel<<<(unsigned)((count + 255) / 256), 256, 0, st>>>(out, comp, count);
+  finalize_kernel<<<(unsigned)((count + 255) / 256), 256, 0, st>>>(out, comp, count, numeric);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_state_gather(const void *state, int precision, const uint64_t *bits, int64_t count, double *out,
+                                int32_t *numeric, cudaStream_t st) {
+  if (count <= 0) return cudaSuccess;
+  const unsigned grid = (unsigned)((count + 255) / 256);
+  if (precision == 0)
+    state_gather_kernel<float><<<grid, 256, 0, st>>>(static_cast<const float *>(state), bits, count, out, numeric);
+  else
+    state_gather_kernel<double><<<grid, 256, 0, st>>>(static_cast<const double *>(state), bits, count, out, numeric);
   return cudaGetLastError();
 }
 

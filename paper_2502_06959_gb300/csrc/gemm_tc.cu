@@ -912,10 +912,15 @@ __global__ void __launch_bounds__(kHThreads, 1) level_mma_f16_kernel(LevelMmaArg
 #pragma unroll
     for (int c = 0; c < kHRaw - 1; ++c) issue(c);
     int64_t it = 0;
-    for (int64_t tu = 0; tu < my_units && !abort_sh; ++tu) {
+    // A split warp stops as a whole: its lanes meet at __syncwarp and full-mask shuffles
+    // below, so the abort flag and the result of the bounded wait are combined across
+    // the warp before anyone leaves the loop.
+    for (int64_t tu = 0; tu < my_units; ++tu) {
+      if (__any_sync(0xffffffffu, abort_sh != 0)) break;
       const int o = (int)(tu & 1);
-      if (!mbar_wait(&ops_empty[o], ((uint32_t)(tu >> 1) & 1u) ^ 1u)) {
-        atomicExch(a.err, 4);
+      const bool ok = mbar_wait(&ops_empty[o], ((uint32_t)(tu >> 1) & 1u) ^ 1u);
+      if (!__all_sync(0xffffffffu, ok)) {
+        if (lane == 0) atomicExch(a.err, 4);
         abort_sh = 1;
         break;
       }
@@ -1269,12 +1274,8 @@ void level_mma_image_f16(const double *w, void *digit_image, float *inv_scale) {
 
 cudaError_t launch_level_mma(const LevelMmaArgs &a, cudaStream_t st) {
   if (a.num_nodes <= 0) return cudaSuccess;
-  static int sms = 0;
-  if (!sms) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) sms = 148;
-  }
+  int sms = device_sm_count();
+  if (sms <= 0) sms = 148;
   const int r = a.radix > 0 ? a.radix : 1;
   if (a.num_post == 0) {
     // FP16 split kernel (W image: FP16 parts per digit, then the inverse scales)

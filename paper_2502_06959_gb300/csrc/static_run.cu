@@ -15,7 +15,10 @@
 //
 // Host code cannot use the array's name as a device address, so the address is looked
 // up once per device with cudaGetSymbolAddress, with that device current, on the first
-// call made on that device.  Make that first call before any stream capture.
+// call made on that device.  Make that first call before any stream capture.  The cached
+// address does not survive a device reset (cudaDeviceReset, or the primary context being
+// destroyed and created again): the module is then loaded anew and the array may move, so
+// do not call this entry point again in the same process after such a reset.
 #include <mutex>
 
 #include "plan.h"
@@ -51,7 +54,9 @@ extern "C" hsf_status hsf_run_static(hsf_plan *plan, const uint64_t *bitstrings,
     ws = g_static_addr[dev];
   }
   size_t need = 0;
-  if (hsf_workspace_size(plan, num, window, kStaticScratchBytes, &need) != HSF_OK)
+  const hsf_status ws_st = hsf_workspace_size(plan, num, window, kStaticScratchBytes, &need);
+  if (ws_st != HSF_OK && ws_st != HSF_ENOMEM) return ws_st;   // a bad request, not a size limit
+  if (ws_st == HSF_ENOMEM)
     return hsf::set_error(HSF_ENOMEM,
                           "hsf_run_static: this request needs more than the %zu-byte static scratch "
                           "even with the smallest path chunk; use hsf_run with a caller workspace",
