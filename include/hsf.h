@@ -128,6 +128,11 @@ typedef struct hsf_plan_opts {
                                         cores; by default a level whose program acts
                                         only on the 6 lowest storage bits runs as a
                                         TF32x3 tensor-core product per Schmidt digit */
+#define HSF_FLAG_SVD_BLOCKS 128      /* decompose every block by the SVD; by default a
+                                        cascade block (every gate touching the block's
+                                        qubits on one side is diagonal on them: CNOT
+                                        controls, CZ, RZZ, phases; Sec. IV-D, Example 4)
+                                        gets its terms P_z (x) Y_z in closed form */
 
 typedef struct hsf_plan hsf_plan;
 
@@ -144,9 +149,15 @@ typedef struct hsf_plan_info {
   int32_t num_params;       /* 1 + the largest param_id of a rotation gate          */
 } hsf_plan_info;
 
-/* Plan a circuit: validates the circuit, cut and blocks, multiplies every block and
- * Schmidt-decomposes it on the current CUDA device in FP64 (one-sided Jacobi SVD),
- * reads back the ranks (synchronous), and builds the per-level gate programs.
+/* Plan a circuit (Sec. II-B: horizontal cut after qubit l; Sec. III-A: gates crossing
+ * the cut grouped into jointly cut blocks; Sec. IV-A, eq. eq-svd: Schmidt decomposition
+ * of each block unitary through the SVD of its relabelled matrix; Sec. IV-C: the block
+ * product is a chain of matrix multiplications).  Validates the circuit, cut and blocks,
+ * multiplies every block and Schmidt-decomposes it on the current CUDA device in FP64
+ * (one-sided Jacobi SVD), reads back the ranks (synchronous), and builds the per-level
+ * gate programs.  Blocks whose SVD does not converge, or whose kept terms rebuild the
+ * block matrix only to more than 1e-12 * max(1, sigma_0) plus the dropped singular
+ * values, are rejected with HSF_ENUMERIC.
  * cut_l: the cut lies between qubit cut_l and cut_l+1 (Table II "cut pos."),
  * 0 <= cut_l <= n-2.  opts may be NULL (defaults).  On success *out owns all
  * plan-time device tables; release it with hsf_plan_destroy. */
@@ -154,38 +165,104 @@ hsf_status hsf_plan_create(const hsf_circuit *circuit, int32_t cut_l,
                            const hsf_blocks *blocks, const hsf_plan_opts *opts,
                            hsf_plan **out);
 
+/* Sizes of a plan: num_paths is the number of paths n_p, the product of the blocks'
+ * Schmidt ranks (Sec. II-B, Sec. IV-B: n_p^j for joint cuts; Table I "# Paths");
+ * tree_nodes and num_launches describe this library's prefix-sharing schedule, which
+ * the paper does not have.  info is written by the call (host memory). */
 hsf_status hsf_plan_get_info(const hsf_plan *plan, hsf_plan_info *info);
 
+/* Plan a plain Schroedinger simulation of the same circuit (Sec. II-A, Example 1: the
+ * gates applied one after another to the full 2^n statevector from |0...0>; Table I
+ * column S is the method it is compared with).  There is no cut and no block: the
+ * returned plan holds one program of all gates on all n qubits (the same fusion and
+ * tile-pass sweep kernels as the half states) and one path.  hsf_run on it sweeps the
+ * full state in place inside the workspace (hsf_workspace_size: 2^n amplitudes of the
+ * plan's precision, 256-byte rounded) and writes the requested amplitudes (bitstrings,
+ * window or all) as complex128; the path range is ignored.  n <= 34 in complex64 and
+ * n <= 33 in complex128 (a state of at most 128 GB).  HSF_EINVAL for a bad circuit. */
+hsf_status hsf_plan_create_schrodinger(const hsf_circuit *circuit, const hsf_plan_opts *opts,
+                                       hsf_plan **out);
+
 /* Human-readable description of the plan's programs (storage order, tree levels,
- * tile passes, register groups, ops) written to buf (NUL-terminated, at most cap bytes).
- * Returns the size needed including the NUL, or -1 for a NULL plan. */
+ * tile passes, register groups, ops, and per block its rank, Jacobi sweeps and
+ * reconstruction residual) written to buf (NUL-terminated, at most cap bytes).
+ * Returns the size needed including the NUL, or -1 for a NULL plan.  Diagnostic only;
+ * the paper has no counterpart. */
 int64_t hsf_plan_describe(const hsf_plan *plan, char *buf, int64_t cap);
 
-/* Singular values (descending, only the kept ones) and rank of block k; copies at
- * most cap values into sigma (host). */
+/* Singular values sigma_m of block k (eq. eq-svd, Sec. IV-A; descending, only the kept
+ * ones) and its Schmidt rank r; copies at most cap values into sigma (host memory).
+ * HSF_EINVAL for a NULL plan or a block index out of range. */
 hsf_status hsf_plan_get_sigma(const hsf_plan *plan, int32_t block, double *sigma,
                               int32_t cap, int32_t *rank);
 
+/* Automatic joint-cut blocks (Sec. V: cascades of commuting RZZ gates regrouped so that
+ * they can be cut jointly; Sec. IV-D, Example 4: a cascade sharing one qubit has rank 2).
+ * In every maximal run of consecutive diagonal gates (which commute), the crossing
+ * two-qubit gates form a bipartite graph between the qubits of the two halves; a
+ * minimum vertex cover of it (Koenig's theorem, from a maximum matching) gives the hub
+ * qubits, and each hub's gates become one block (at most max_leaves, 1..8, gates per
+ * block; a larger star is split).  Other crossing gates become singleton blocks.  The
+ * run is reordered: in-half gates first, then the blocks.  Host-only, no device work.
+ *   order:    out, num_gates entries: order[i] is the input index of the i-th gate of
+ *             the reordered circuit (the same circuit: only commuting gates move).
+ *   offsets, gate_idx: out, CSR blocks over the REORDERED circuit's gate indices, in
+ *             dependency order; offsets needs cap_blocks + 1 entries, gate_idx
+ *             num_gates entries.
+ *   num_blocks: out; num_hubs: out (may be NULL), the vertex-cover size summed over
+ *             runs (joint paths = 2^num_blocks when every block has rank 2).
+ * HSF_EINVAL for a bad circuit, cut or max_leaves; HSF_ENOMEM if more than cap_blocks
+ * blocks are found. */
+hsf_status hsf_find_blocks(const hsf_circuit *circuit, int32_t cut_l, int32_t max_leaves,
+                           int32_t *order, int32_t *offsets, int32_t *gate_idx, int32_t cap_blocks,
+                           int32_t *num_blocks, int32_t *num_hubs);
+
+/* Release a plan and every device buffer it owns (its tables, and the workspace of
+ * hsf_run calls made with workspace == NULL).  Waits for device work that may still
+ * read them.  NULL is ignored.  The paper has no counterpart. */
 void hsf_plan_destroy(hsf_plan *plan);
 
 /* Device workspace (bytes) that hsf_run needs for the given output request:
  * num_bitstrings > 0 selects bitstring output, else window > 0 selects the first
  * `window` amplitudes, else all 2^n amplitudes.  The library sizes its breadth
- * (paths in flight) to fit `budget_bytes` when it is nonzero. */
+ * (paths in flight, Sec. II-B: the paths are independent and can be simulated in any
+ * grouping) to fit `budget_bytes` when it is nonzero.  HSF_ENOMEM if no path chunk
+ * fits the budget; HSF_EINVAL for a full output of more than 2^34 amplitudes. */
 hsf_status hsf_workspace_size(const hsf_plan *plan, size_t num_bitstrings,
                               uint64_t window, size_t budget_bytes, size_t *bytes);
 
-/* Amplitudes by HSF path sum over paths [path_begin, path_end) (both 0 = all).
+/* Amplitudes by HSF path sum over paths [path_begin, path_end) (both 0 = all):
+ * amp(x) = sum_p psi_a^p(x_a) psi_b^p(x_b) with x = x_a 2^{n_b} + x_b (Sec. II-B, the
+ * Kronecker products of the two halves' states added over all paths; Sec. V computes
+ * a leading window of amplitudes, "the first 10^6").
  *   bitstrings: device array of num uint64 (bit q = qubit q), or NULL.
  *   window:     with bitstrings == NULL: the first `window` amplitudes (0 = all 2^n).
- *   out:        device array of complex128 (re, im interleaved), one per amplitude.
+ *   out:        device array of complex128 (re, im interleaved), one per amplitude,
+ *               caller-owned.
  *   workspace:  device buffer of at least hsf_workspace_size(...) bytes, 256-byte
- *               aligned, caller-owned.  stream: cudaStream_t (NULL = legacy default).
+ *               aligned, caller-owned; or NULL: the plan then owns a workspace sized
+ *               for 60% of the device's free memory, allocated on first use (and grown
+ *               when a larger request needs it) through the allocator registered with
+ *               hsf_set_allocator, freed by hsf_plan_destroy.  Do not pass NULL under
+ *               stream capture.  stream: cudaStream_t (NULL = legacy default).
  * The per-path products are formed in the plan's state precision and summed across
- * path chunks in FP64 with Neumaier compensation. */
+ * path chunks in FP64 with Neumaier compensation.  Asynchronous: errors found on the
+ * device (an expired bounded wait, a NaN / Inf amplitude) are reported by hsf_sync.
+ * Argument errors return HSF_EINVAL before any device work; a workspace that holds no
+ * path chunk returns HSF_ENOMEM. */
 hsf_status hsf_run(hsf_plan *plan, const uint64_t *bitstrings, size_t num,
                    uint64_t window, uint64_t path_begin, uint64_t path_end,
                    void *out, void *workspace, size_t workspace_bytes, void *stream);
+
+/* Device memory for plan-owned workspaces (hsf_run with workspace == NULL):
+ * alloc(ctx, bytes, stream) returns a 256-byte aligned device pointer or NULL, and
+ * release(ctx, ptr, stream) takes it back (a binding can route both to its framework's
+ * caching allocator).  Passing NULL functions restores the default, cudaMalloc and
+ * cudaFree.  Process-wide; a plan releases its workspace with the functions that
+ * allocated it.  The paper has no counterpart. */
+typedef void *(*hsf_alloc_fn)(void *ctx, size_t bytes, void *stream);
+typedef void (*hsf_free_fn)(void *ctx, void *ptr, void *stream);
+void hsf_set_allocator(hsf_alloc_fn alloc, hsf_free_fn release, void *ctx);
 
 /* Same as hsf_run, but for callers that cannot allocate device memory (for example
  * code that runs while another runtime owns all device allocations, or a loop that
@@ -198,13 +275,20 @@ hsf_status hsf_run(hsf_plan *plan, const uint64_t *bitstrings, size_t num,
  * between calls (each run zeroes what it accumulates into); calls that overlap on the
  * GPU race on it, so order them.  The first call on each device looks the array's
  * address up (with that device current); make that first call before any stream
- * capture. */
+ * capture.  That cached address does not survive a device reset (cudaDeviceReset or a
+ * re-created primary context): do not call this again in the process after one.
+ * Requests that are invalid for hsf_run (bad plan, output size, window) return the same
+ * status as hsf_workspace_size would, not HSF_ENOMEM. */
 hsf_status hsf_run_static(hsf_plan *plan, const uint64_t *bitstrings, size_t num,
                           uint64_t window, uint64_t path_begin, uint64_t path_end,
                           void *out, void *stream);
 
 /* Adjoint gradient of a real loss L of the amplitudes at `bitstrings` with respect
- * to the shared angles (gate param_id): grad[j] = dL/dtheta_j, j < num_params.
+ * to the shared angles (gate param_id): grad[j] = dL/dtheta_j, j < num_params.  The
+ * paper computes no gradients; this builds on two of its facts: every path's
+ * contribution is a product of the two halves' states (Sec. II-B), and the amplitude
+ * is linear in each block matrix, whose derivative has a Schmidt decomposition like any
+ * matrix (Sec. III-B: an SVD exists for every matrix; Sec. IV-A).
  *   gout: device complex128 per bitstring, the upstream gradient
  *         g_s = dL/dRe(amp_s) + i dL/dIm(amp_s) (PyTorch's convention; for
  *         L = sum_s |amp_s|^2 it is 2 amp_s).
@@ -223,7 +307,8 @@ hsf_status hsf_grad(hsf_plan *plan, const uint64_t *bitstrings, size_t num, cons
                     void *stream);
 
 /* Batches: many circuits (uneven n, path counts, outputs) recorded once into a CUDA
- * graph and replayed with one launch.  Items run one after another inside the graph
+ * graph and replayed with one launch.  The paper has no counterpart (each circuit's
+ * run is hsf_run, Sec. II-B).  Items run one after another inside the graph
  * and share `workspace` (hsf_batch_workspace_size: the largest item's need); every
  * plan, bitstring array and output must stay alive and at the same address while
  * the batch exists.  Recording happens on `stream` (stream capture); profiling must be
@@ -244,7 +329,8 @@ hsf_status hsf_batch_launch(hsf_batch *batch, void *stream);
 int64_t hsf_batch_nodes(const hsf_batch *batch);
 void hsf_batch_destroy(hsf_batch *batch);
 
-/* Autotuner: for this circuit shape and request, plan and time each candidate
+/* Autotuner (the paper has no counterpart; its preprocessing mentions gate fusion,
+ * Table I caption): for this circuit shape and request, plan and time each candidate
  * sweep configuration (shared-memory tile width 2^tile_bits, register-group fusion on
  * or off) on the current device and write the fastest into opts->tile_bits and
  * opts->flags.  Results are appended to the text file cache_path (may be NULL) keyed by
@@ -257,12 +343,15 @@ hsf_status hsf_tune(const hsf_circuit *circuit, int32_t cut_l, const hsf_blocks 
 
 /* Wait for the stream and report device-side failures of earlier runs of this plan:
  * returns HSF_ETIMEOUT (and clears the flag) if a bounded wait inside a kernel expired,
- * in which case the affected outputs are invalid. */
+ * or HSF_ENUMERIC (and clears it) if an output amplitude was NaN or infinite; the
+ * affected outputs are then invalid.  The paper has no counterpart. */
 hsf_status hsf_sync(hsf_plan *plan, void *stream);
 
+/* Message of the calling thread's last failed call (thread-local, valid until that
+ * thread's next failing call).  The paper has no counterpart. */
 const char *hsf_last_error(void);
 
-/* Per-kernel timing for roofline reporting.  With profiling on, every kernel that
+/* Per-kernel timing for roofline reporting (the paper has no counterpart).  With profiling on, every kernel that
  * hsf_run launches is bracketed by CUDA events on the caller's stream and tagged
  * with its algorithmic bytes and flops; hsf_profile_collect waits for the events,
  * adds them up per kernel kind (HSF_KERNEL_*) into stats[0..cap) and clears the

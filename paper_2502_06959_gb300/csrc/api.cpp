@@ -15,6 +15,7 @@
 #include <functional>
 #include <map>
 #include <memory>
+#include <mutex>
 #include <queue>
 #include <set>
 #include <string>
@@ -27,6 +28,12 @@ using namespace hsf;
 namespace {
 
 std::atomic<int> g_profiling{0};
+
+// Allocator of plan-owned workspaces (hsf_set_allocator); NULL functions: cudaMalloc.
+std::mutex g_alloc_mu;
+hsf_alloc_fn g_alloc = nullptr;
+hsf_free_fn g_release = nullptr;
+void *g_alloc_ctx = nullptr;
 
 #define CUDA_TRY(expr)                                                                   \
   do {                                                                                   \
@@ -140,11 +147,70 @@ hsf_status launch(hsf_plan &p, int kind, double bytes, double flops, cudaStream_
     if (s_ != HSF_OK) return s_;                                                         \
   } while (0)
 
+// Schroedinger plan: the full 2^n state is swept in place in the workspace, pass by pass
+// (the first pass starts every tile from |0...0>), then the requested amplitudes are read
+// out (bit q of a bitstring is qubit q, identity storage order).
+hsf_status run_schrodinger(hsf_plan &pl, const uint64_t *bits, size_t num, uint64_t window, double *outd,
+                           void *workspace, size_t ws_bytes, cudaStream_t st) {
+  hsf_plan *p = &pl;
+  const size_t csz = p->precision == HSF_PREC_C64 ? 8 : 16;
+  const size_t need = ((size_t)1 << p->n) * csz;
+  if (ws_bytes < need) return set_error(HSF_ENOMEM, "workspace of %zu bytes cannot hold the %zu-byte state", ws_bytes, need);
+  const SideH &sd = p->side[0];
+  const LevelH &lv = sd.levels[0];
+  const double amps = (double)(1ull << sd.h);
+  for (size_t pi = 0; pi < lv.passes.size(); ++pi) {
+    const PassH &ps = lv.passes[pi];
+    SweepArgs a{};
+    a.ops = (const DevOp *)((unsigned char *)p->dev_table + ps.ops_off);
+    a.num_ops = ps.num_ops;
+    a.h = sd.h;
+    a.mats = (unsigned char *)p->dev_table + ps.mats_off;
+    a.read_parent = 0;
+    a.init_zero = pi == 0 ? 1 : 0;
+    a.src = workspace;
+    a.dst = workspace;
+    a.active_mask = ps.active;
+    a.t = ps.t;
+    a.radix = 1;
+    a.node_lo = 0;
+    a.parent_lo = 0;
+    a.num_nodes = 1;
+    a.tiles_per_node = (int32_t)(1ll << (sd.h - ps.t));
+    a.groups = ps.groups.empty() ? nullptr : (const DevGroup *)((unsigned char *)p->dev_table + ps.groups_off);
+    a.num_groups = (int32_t)ps.groups.size();
+    a.rbits = p->rbits;
+    const size_t blk = ps.table_end - ps.ops_off;
+    if (!ps.groups.empty() && blk <= (size_t)kMaxStageBytes) {
+      a.stage_src = (unsigned char *)p->dev_table + ps.ops_off;
+      a.stage_bytes = (int32_t)((blk + 15) / 16 * 16);
+      a.stage_mats_off = (int32_t)(ps.mats_off - ps.ops_off);
+      a.stage_groups_off = (int32_t)(ps.groups_off - ps.ops_off);
+    }
+    double fl = 0.0;
+    for (const OpH &op : ps.ops) fl += amps * (op.type == OP_DENSE ? 8.0 * (1 << op.nq) : 6.0);
+    // the first pass only writes (its tiles start from |0...0>)
+    LAUNCH(HSF_KERNEL_SWEEP, (pi == 0 ? 1.0 : 2.0) * amps * csz, fl, launch_sweep(a, p->precision, st));
+  }
+  const int64_t count = num > 0 ? (int64_t)num : (int64_t)(window ? window : (1ull << p->n));
+  LAUNCH(HSF_KERNEL_OTHER, (double)count * (16.0 + csz + (num ? 8.0 : 0.0)), 0.0,
+         launch_state_gather(workspace, p->precision, num > 0 ? bits : nullptr, count, outd,
+                             p->dev_status + kStatusNumeric, st));
+  return HSF_OK;
+}
+
 }  // namespace
 
 extern "C" {
 
 void hsf_set_profiling(int32_t on) { g_profiling.store(on ? 1 : 0); }
+
+void hsf_set_allocator(hsf_alloc_fn alloc, hsf_free_fn release, void *ctx) {
+  std::lock_guard<std::mutex> lock(g_alloc_mu);
+  g_alloc = (alloc && release) ? alloc : nullptr;
+  g_release = (alloc && release) ? release : nullptr;
+  g_alloc_ctx = (alloc && release) ? ctx : nullptr;
+}
 
 uint64_t hsf_launch_count(void) { return g_launches.load(); }
 
@@ -184,6 +250,17 @@ hsf_status hsf_plan_create(const hsf_circuit *circuit, int32_t cut_l, const hsf_
   st = decompose_blocks(*p);
   if (st != HSF_OK) return st;
   st = finish_plan(*p);
+  if (st != HSF_OK) return st;
+  *out = p.release();
+  return HSF_OK;
+}
+
+hsf_status hsf_plan_create_schrodinger(const hsf_circuit *circuit, const hsf_plan_opts *opts, hsf_plan **out) {
+  if (!out) return set_error(HSF_EINVAL, "out must not be NULL");
+  *out = nullptr;
+  std::unique_ptr<hsf_plan> p(new (std::nothrow) hsf_plan());
+  if (!p) return set_error(HSF_ENOMEM, "host allocation failed");
+  hsf_status st = build_schrodinger(*p, circuit, opts);
   if (st != HSF_OK) return st;
   *out = p.release();
   return HSF_OK;
@@ -266,6 +343,16 @@ int64_t hsf_plan_describe(const hsf_plan *p, char *buf, int64_t cap) {
       }
     }
   }
+  for (size_t b = 0; b < p->blocks.size(); ++b) {
+    const BlockH &bk = p->blocks[b];
+    if (bk.closed >= 0)
+      std::snprintf(line, sizeof line, "block %zu: qubits %zu|%zu rank %d closed-form cascade (hub on side %c)\n", b,
+                    bk.qa.size(), bk.qb.size(), bk.rank, bk.closed == 0 ? 'a' : 'b');
+    else
+      std::snprintf(line, sizeof line, "block %zu: qubits %zu|%zu rank %d SVD sweeps %d residual %.3e\n", b,
+                    bk.qa.size(), bk.qb.size(), bk.rank, bk.sweeps, bk.residual);
+    out += line;
+  }
   std::snprintf(line, sizeof line, "leaf_bits=%d paths=%llu\n", p->leaf_c, (unsigned long long)p->num_paths);
   out += line;
   if (buf && cap > 0) {
@@ -279,15 +366,18 @@ int64_t hsf_plan_describe(const hsf_plan *p, char *buf, int64_t cap) {
 hsf_status hsf_sync(hsf_plan *p, void *stream) {
   if (!p) return set_error(HSF_EINVAL, "NULL plan");
   CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
-  int32_t status = 0;
-  CUDA_TRY(cudaMemcpyAsync(&status, p->dev_status, sizeof status, cudaMemcpyDeviceToHost, plan_stream()));
+  int32_t status[2] = {0, 0};
+  CUDA_TRY(cudaMemcpyAsync(status, p->dev_status, sizeof status, cudaMemcpyDeviceToHost, plan_stream()));
   CUDA_TRY(cudaStreamSynchronize(plan_stream()));
-  if (status != 0) {
+  if (status[kStatusWait] != 0 || status[kStatusNumeric] != 0) {
     CUDA_TRY(cudaMemsetAsync(p->dev_status, 0, sizeof status, plan_stream()));
     CUDA_TRY(cudaStreamSynchronize(plan_stream()));
-    return set_error(HSF_ETIMEOUT, "a bounded device-side wait expired (code %d); results of the "
-                                   "affected run are invalid", status);
   }
+  if (status[kStatusWait] != 0)
+    return set_error(HSF_ETIMEOUT, "a bounded device-side wait expired (code %d); results of the "
+                                   "affected run are invalid", status[kStatusWait]);
+  if (status[kStatusNumeric] != 0)
+    return set_error(HSF_ENUMERIC, "an amplitude of an earlier run is NaN or infinite");
   return HSF_OK;
 }
 
@@ -295,6 +385,15 @@ void hsf_plan_destroy(hsf_plan *p) { delete p; }
 
 hsf_status hsf_workspace_size(const hsf_plan *p, size_t num_bits, uint64_t window, size_t budget, size_t *bytes) {
   if (!p || !bytes) return set_error(HSF_EINVAL, "NULL argument");
+  if (p->schrodinger) {
+    const size_t need = align256(((size_t)1 << p->n) * (p->precision == HSF_PREC_C64 ? 8 : 16));
+    if (num_bits == 0 && window == 0 && p->n > 34) return set_error(HSF_EINVAL, "full output of 2^%d amplitudes", p->n);
+    if (budget && need > budget)
+      return set_error(HSF_ENOMEM, "the 2^%d-amplitude state needs %zu bytes, more than the %zu-byte budget", p->n, need,
+                       budget);
+    *bytes = need;
+    return HSF_OK;
+  }
   if (num_bits == 0 && window == 0 && p->n > 34) return set_error(HSF_EINVAL, "full output of 2^%d amplitudes", p->n);
   RunLayout L;
   if (!choose_layout(*p, num_bits, window, budget, L))
@@ -305,7 +404,49 @@ hsf_status hsf_workspace_size(const hsf_plan *p, size_t num_bits, uint64_t windo
 
 hsf_status hsf_run(hsf_plan *p, const uint64_t *bits, size_t num, uint64_t window, uint64_t path_begin,
                    uint64_t path_end, void *out, void *workspace, size_t ws_bytes, void *stream) {
-  if (!p || !out || !workspace) return set_error(HSF_EINVAL, "NULL plan, output or workspace");
+  if (!p || !out) return set_error(HSF_EINVAL, "NULL plan or output");
+  if (!workspace) {
+    // plan-owned workspace, sized for 60% of the free device memory (paths in flight
+    // shrink to fit), made once and grown only when a request needs more
+    if (num == 0 && window == 0 && p->n > 34) return set_error(HSF_EINVAL, "full output of 2^%d amplitudes", p->n);
+    size_t free_b = 0, total_b = 0;
+    CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
+    size_t need = 0;
+    hsf_status ws_st = hsf_workspace_size(p, num, window, (size_t)((double)(free_b + p->own_ws_bytes) * 0.6), &need);
+    if (ws_st != HSF_OK) return ws_st;
+    if (need > p->own_ws_bytes) {
+      if (p->own_ws) {
+        CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
+        if (p->own_release) p->own_release(p->own_ctx, p->own_ws, stream);
+        else CUDA_TRY(cudaFree(p->own_ws));
+        p->own_ws = nullptr;
+        p->own_ws_bytes = 0;
+      }
+      void *mem = nullptr;
+      {
+        std::lock_guard<std::mutex> lock(g_alloc_mu);
+        if (g_alloc) {
+          mem = g_alloc(g_alloc_ctx, need, stream);
+          p->own_release = g_release;
+          p->own_ctx = g_alloc_ctx;
+        } else {
+          if (cudaMalloc(&mem, need) != cudaSuccess) mem = nullptr;
+          p->own_release = nullptr;
+          p->own_ctx = nullptr;
+        }
+      }
+      if (!mem) return set_error(HSF_ENOMEM, "allocating a %zu-byte plan workspace failed", need);
+      if ((uintptr_t)mem % 256) {
+        if (p->own_release) p->own_release(p->own_ctx, mem, stream);
+        else cudaFree(mem);
+        return set_error(HSF_ENOMEM, "the registered allocator returned memory that is not 256-byte aligned");
+      }
+      p->own_ws = mem;
+      p->own_ws_bytes = need;
+    }
+    workspace = p->own_ws;
+    ws_bytes = p->own_ws_bytes;
+  }
   if (num > 0 && !bits) return set_error(HSF_EINVAL, "num > 0 but bitstrings is NULL");
   if ((uintptr_t)workspace % 256) return set_error(HSF_EINVAL, "workspace must be 256-byte aligned");
   if (path_begin == 0 && path_end == 0) path_end = p->num_paths;
@@ -316,6 +457,8 @@ hsf_status hsf_run(hsf_plan *p, const uint64_t *bits, size_t num, uint64_t windo
     if (p->n > 34 && window == 0) return set_error(HSF_EINVAL, "full output of 2^%d amplitudes", p->n);
     if (window > (1ull << std::min(p->n, 62))) return set_error(HSF_EINVAL, "window larger than 2^n");
   }
+  if (p->schrodinger) return run_schrodinger(*p, bits, num, window, (double *)out, workspace, ws_bytes,
+                                             (cudaStream_t)stream);
   RunLayout L;
   if (!choose_layout(*p, num, window, ws_bytes, L))
     return set_error(HSF_ENOMEM, "workspace of %zu bytes is too small for one path chunk", ws_bytes);
@@ -536,7 +679,7 @@ hsf_status hsf_run(hsf_plan *p, const uint64_t *bits, size_t num, uint64_t windo
       }
     }
   }
-  LAUNCH(HSF_KERNEL_OTHER, 48.0 * count, 0.0, launch_finalize(outd, comp, (int64_t)(2 * count), st));
+  LAUNCH(HSF_KERNEL_OTHER, 48.0 * count, 0.0, launch_finalize(outd, comp, (int64_t)(2 * count), p->dev_status + kStatusNumeric, st));
   return HSF_OK;
 }
 

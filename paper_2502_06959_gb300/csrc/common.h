@@ -156,7 +156,8 @@ struct BlockSvdArgs {
   int32_t *rank;                 // [num_blocks]
   double *xf;                    // [num_blocks][64][64][2]  X'_m (scaled by sqrt sigma)
   double *yf;                    // [num_blocks][64][64][2]  Y'_m
-  int32_t *sweeps_used;          // [num_blocks]
+  int32_t *sweeps_used;          // [num_blocks]; == max_sweeps: not converged
+  double *residual;              // [num_blocks] max_e |U_B - sum_m X'_m (x) Y'_m| (kept terms)
 };
 
 // Window / full output on the tensor cores (gemm_tc.cu): complex rank-P product as one
@@ -261,13 +262,25 @@ cudaError_t launch_grad_dot(const double *gout, const double *ampd, int64_t S, d
 cudaError_t launch_zero_bytes(void *p, size_t bytes, cudaStream_t st);
 cudaError_t launch_path_gemm(const PathGemmArgs &g, cudaStream_t st);
 
+// Streaming multiprocessors of the current device, looked up once per device (thread-safe);
+// 0 if the query fails.
+int device_sm_count();
+
 cudaError_t launch_sweep(const SweepArgs &a, int precision, cudaStream_t st);
 cudaError_t launch_gather_dot(const GatherArgs &a, int precision, cudaStream_t st);
 cudaError_t launch_reduce_partials(const double *partial, int32_t num_groups, int64_t S,
                                    double *out, double *comp, cudaStream_t st);
 cudaError_t launch_window(const WindowArgs &a, int precision, cudaStream_t st);
-cudaError_t launch_finalize(double *out, const double *comp, int64_t count, cudaStream_t st);
+// out += comp over count doubles; sets *numeric (if not NULL) when a result is not finite.
+cudaError_t launch_finalize(double *out, const double *comp, int64_t count, int32_t *numeric, cudaStream_t st);
+// Words of a plan's device status block (256 bytes): the code of an expired bounded wait,
+// and the output canary (non-finite amplitude) of the runs since the last hsf_sync.
+constexpr int kStatusWait = 0, kStatusNumeric = 1;
 cudaError_t launch_zero(double *p, int64_t count, cudaStream_t st);
+// out[i] (complex128) = state[bits ? bits[i] : i] for i < count, state complex64
+// (precision 0) or complex128; sets *numeric (if not NULL) on a non-finite amplitude.
+cudaError_t launch_state_gather(const void *state, int precision, const uint64_t *bits, int64_t count, double *out,
+                                int32_t *numeric, cudaStream_t st);
 cudaError_t launch_block_svd(const BlockSvdArgs &a, cudaStream_t st);
 cudaError_t launch_leaf_contract(const LeafArgs &a, int precision, cudaStream_t st);
 // true when launch_leaf_contract uses the one-wave streaming kernel (large bitstring

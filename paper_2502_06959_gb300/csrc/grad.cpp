@@ -11,7 +11,9 @@
 //     matrix A (Sec. IV-A, eq. equ-schmidt-decompostion-res), so d amp / d theta_j is the
 //     HSF sum with A replaced by dA/dtheta_j (product rule over the block's gates tied
 //     to theta_j).  That matrix is Schmidt-decomposed like any block (the SVD exists
-//     for every matrix, Sec. III-B) and run through the ordinary forward path.
+//     for every matrix, Sec. III-B) and run through the ordinary forward path.  A
+//     cascade block's derivative keeps its closed-form terms (Sec. IV-D): the hub
+//     projectors stay, only the other side's factors are differentiated.
 #include <algorithm>
 #include <cstring>
 #include <memory>
@@ -67,6 +69,9 @@ GradLayout grad_layout(const hsf_plan &p, size_t num) {
 
 hsf_status ensure_grad(hsf_plan &p) {
   if (p.grad_ready) return HSF_OK;
+  for (size_t b = 0; b < p.blocks.size(); ++b)
+    if (!p.blocks[b].fops[0].empty() || !p.blocks[b].fops[1].empty())
+      return set_error(HSF_ENOTSUP, "gradients of block %zu (more than 3 qubits on a side) are not supported", b);
   hsf_status st = build_programs(p, true);
   if (st != HSF_OK) return st;
   st = upload_programs(p, true);
@@ -118,9 +123,20 @@ hsf_status ensure_grad(hsf_plan &p) {
       keys.push_back({b, j});
     }
   }
-  std::vector<BlockH> res;
-  st = run_svd_jobs(p, jobs, res);
+  // blocks with closed-form terms get their derivative's terms in closed form too (the
+  // derivative of a gate that is diagonal on the hub is diagonal on it): no SVD
+  std::vector<BlockH> res(jobs.size());
+  std::vector<SvdJob> svd_jobs;
+  std::vector<size_t> svd_of;
+  for (size_t i = 0; i < jobs.size(); ++i) {
+    if (p.blocks[jobs[i].block].closed >= 0 && closed_form_job(p, jobs[i], false, res[i])) continue;
+    svd_jobs.push_back(jobs[i]);
+    svd_of.push_back(i);
+  }
+  std::vector<BlockH> sres;
+  st = run_svd_jobs(p, svd_jobs, sres);
   if (st != HSF_OK) return st;
+  for (size_t j = 0; j < svd_jobs.size(); ++j) res[svd_of[j]] = sres[j];
   for (size_t i = 0; i < jobs.size(); ++i) {
     if (res[i].rank <= 0) continue;                 // the derivative vanishes
     std::unique_ptr<hsf_plan> d(new hsf_plan());

@@ -14,6 +14,9 @@ namespace hsf {
 
 using cd = std::complex<double>;
 
+// A cascade block (closed-form terms) may hold up to this many qubits on its non-hub side.
+constexpr int kMaxCascadeLeaves = 8;
+
 struct GateH {
   int kind = 0;
   int nq = 0;
@@ -27,15 +30,6 @@ struct GateH {
   int side = 0;            // 0 = a (all qubits > l), 1 = b (all <= l), 2 = crossing
 };
 
-struct BlockH {
-  std::vector<int> gates;  // circuit order
-  std::vector<int> qubits; // descending: a-qubits first
-  std::vector<int> qa, qb; // descending
-  int rank = 0;
-  std::vector<double> sigma;
-  std::vector<cd> x, y;    // rank x 4^ka and rank x 4^kb, sqrt(sigma) folded in
-};
-
 // One op of a side program, on side-local logical qubits (q[0] = matrix MSB).
 struct OpH {
   int type = OP_DENSE;
@@ -46,6 +40,22 @@ struct OpH {
   int block = -1;
   int param = -1;          // gradient programs: angle index of an unfused rotation
   std::vector<cd> k;       // its K = (dG/dtheta) G^-1 (same form as m: dense or diagonal)
+};
+
+struct BlockH {
+  std::vector<int> gates;  // circuit order
+  std::vector<int> qubits; // descending: a-qubits first
+  std::vector<int> qa, qb; // descending
+  int rank = 0;
+  std::vector<double> sigma;
+  std::vector<cd> x, y;    // rank x 4^ka and rank x 4^kb, sqrt(sigma) folded in
+  double residual = 0.0;   // max entry of |U_B - sum_m X_m (x) Y_m| (device FP64)
+  int sweeps = 0;          // Jacobi sweeps used
+  int closed = -1;         // >= 0: closed-form cascade terms with the hub on side 0 (a)
+                           // or 1 (b): X_m / Y_m = projector on hub state m (no SVD)
+  // closed-form blocks with more than 3 qubits on a side: each side's factor as a list of
+  // small ops (global qubits, `rank` digits each) instead of one dense op in x / y
+  std::vector<OpH> fops[2];
 };
 
 struct GroupH {
@@ -106,6 +116,9 @@ const char *last_error();
 hsf_status validate_and_load(hsf_plan &p, const hsf_circuit *c, int cut, const hsf_blocks *bl,
                              const hsf_plan_opts *o);
 hsf_status check_order(const hsf_plan &p);
+hsf_status load_gates(hsf_plan &p, const hsf_circuit *c, const hsf_plan_opts *o);
+// Full-state (Schroedinger) plan: one program of all gates on h = n qubits.
+hsf_status build_schrodinger(hsf_plan &p, const hsf_circuit *c, const hsf_plan_opts *o);
 hsf_status decompose_blocks(hsf_plan &p);
 hsf_status build_programs(hsf_plan &p, bool grad = false);
 hsf_status upload_programs(hsf_plan &p, bool grad = false);
@@ -117,6 +130,11 @@ struct SvdJob {
   std::vector<std::vector<int>> terms;
 };
 hsf_status run_svd_jobs(const hsf_plan &p, const std::vector<SvdJob> &jobs, std::vector<BlockH> &out);
+// Closed-form decomposition of a job whose gates, where they touch one side's block qubits
+// (the hub), are all diagonal on them: A = sum_z P_z (x) Y_z.  With need_independent the
+// Y_z must be linearly independent (then 2^{k_hub} is the Schmidt rank); otherwise zero
+// terms are dropped.  Returns false when the block has no such structure.
+bool closed_form_job(const hsf_plan &p, const SvdJob &job, bool need_independent, BlockH &out);
 // Path counts, gate programs, device tables and the status word of a decomposed plan.
 hsf_status finish_plan(hsf_plan &p);
 extern std::atomic<uint64_t> g_launches;
@@ -125,6 +143,7 @@ extern std::atomic<uint64_t> g_launches;
 struct hsf_plan {
   int n = 0, cut = 0, na = 0, nb = 0;
   int precision = 0, gemm_mode = 0, flags = 0, tile_max = 14;
+  bool schrodinger = false;         // full-state plan (hsf_plan_create_schrodinger)
   double rank_tol = 1e-12;
   uint64_t max_paths = 0;
   std::vector<hsf::GateH> gates;
@@ -151,6 +170,12 @@ struct hsf_plan {
   std::vector<DerivPlan> dplans;
   void *dev_factors = nullptr;      // Schmidt factors of every level (gradient pullback)
   std::vector<size_t> factor_off[2];// byte offset of level k's factors (k >= 1)
+  // workspace owned by the plan (hsf_run with workspace == NULL) and the allocator that
+  // made it (release == NULL: cudaMalloc / cudaFree)
+  void *own_ws = nullptr;
+  size_t own_ws_bytes = 0;
+  hsf_free_fn own_release = nullptr;
+  void *own_ctx = nullptr;
 
   hsf_plan() = default;
   hsf_plan(const hsf_plan &) = delete;
@@ -162,5 +187,10 @@ struct hsf_plan {
     if (dev_gtable) cudaFree(dev_gtable);
     if (dev_status) cudaFree(dev_status);
     if (dev_factors) cudaFree(dev_factors);
+    if (own_ws) {
+      cudaDeviceSynchronize();          // no queued run may still use it
+      if (own_release) own_release(own_ctx, own_ws, nullptr);
+      else cudaFree(own_ws);
+    }
   }
 };

@@ -24,6 +24,7 @@
 #include <functional>
 #include <map>
 #include <memory>
+#include <mutex>
 #include <queue>
 #include <set>
 #include <string>
@@ -50,30 +51,47 @@ const char *last_error() { return g_err.c_str(); }
 
 // Plan-time device work (block SVDs, table uploads) runs on a private non-blocking stream
 // of the calling thread, so planning the next circuit on the host overlaps with work the
-// caller has queued on its own streams.
-cudaStream_t plan_stream() {
-  thread_local cudaStream_t st = nullptr;
-  thread_local int dev = -1;
-  int cur = 0;
-  cudaGetDevice(&cur);
-  if (!st || dev != cur) {
+// caller has queued on its own streams.  Each thread keeps one such stream per device it
+// has used (created on first use on that device, kept until the thread exits).
+namespace {
+struct ThreadStreams {
+  std::map<int, cudaStream_t> by_dev;
+  cudaStream_t get() {
+    int cur = 0;
+    cudaGetDevice(&cur);
+    auto it = by_dev.find(cur);
+    if (it != by_dev.end()) return it->second;
+    cudaStream_t st = nullptr;
     cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
-    dev = cur;
+    by_dev[cur] = st;
+    return st;
   }
-  return st;
+};
+}  // namespace
+
+cudaStream_t plan_stream() {
+  thread_local ThreadStreams s;
+  return s.get();
 }
 
 // Second stream of the calling thread on which hsf_run sweeps side b (non-blocking).
 cudaStream_t side_stream() {
-  thread_local cudaStream_t st = nullptr;
-  thread_local int dev = -1;
-  int cur = 0;
-  cudaGetDevice(&cur);
-  if (!st || dev != cur) {
-    cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
-    dev = cur;
-  }
-  return st;
+  thread_local ThreadStreams s;
+  return s.get();
+}
+
+int device_sm_count() {
+  static std::mutex mu;
+  static std::map<int, int> cache;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  std::lock_guard<std::mutex> lock(mu);
+  auto it = cache.find(dev);
+  if (it != cache.end()) return it->second;
+  int sms = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) return 0;
+  cache[dev] = sms;
+  return sms;
 }
 
 #define CUDA_TRY(expr)                                                                   \
@@ -737,6 +755,13 @@ hsf_status build_programs(hsf_plan &p, bool grad) {
     sd.levels.assign(B + 1, LevelH{});
     for (int b = 0; b < B; ++b) {           // Schmidt factors open levels 1..B
       const BlockH &bk = p.blocks[b];
+      if (!bk.fops[s].empty()) {              // a closed-form factor as a list of ops
+        for (OpH op : bk.fops[s]) {
+          for (int j = 0; j < op.nq; ++j) op.q[j] -= sd.offset;
+          sd.levels[b + 1].ops.push_back(op);
+        }
+        continue;
+      }
       const std::vector<int> &qs = s == 0 ? bk.qa : bk.qb;
       OpH op;
       op.type = OP_DENSE;
@@ -870,6 +895,73 @@ hsf_status build_programs(hsf_plan &p, bool grad) {
     }
   }
   compose_mma_levels(p, p.leaf_c);
+  return HSF_OK;
+}
+
+// Schroedinger plan (Sec. II-A, Example 1; Table I column S): the whole circuit as one
+// program on one "side" of h = n qubits with the identity storage order, one tree level,
+// no blocks and a single path.  The same fusion, tile-pass and register-group building as
+// the HSF half states; the passes sweep the full 2^n state in place.
+hsf_status build_schrodinger(hsf_plan &p, const hsf_circuit *c, const hsf_plan_opts *o) {
+  if (!c) return set_error(HSF_EINVAL, "circuit must not be NULL");
+  if (c->num_gates < 0 || (c->num_gates > 0 && !c->gates)) return set_error(HSF_EINVAL, "bad gate array");
+  p.precision = o ? o->precision : HSF_PREC_C64;
+  p.flags = o ? o->flags : 0;
+  if (p.precision != HSF_PREC_C64 && p.precision != HSF_PREC_C128)
+    return set_error(HSF_EINVAL, "precision %d", p.precision);
+  const int nmax = p.precision == HSF_PREC_C64 ? 34 : 33;      // a state of at most 128 GB
+  if (c->n < 1 || c->n > nmax) return set_error(HSF_EINVAL, "n = %d outside 1..%d for a full state", c->n, nmax);
+  p.n = c->n;
+  p.cut = c->n - 1;            // every gate on "side a" below (load_gates' side is unused)
+  p.na = c->n;
+  p.nb = 0;
+  p.schrodinger = true;
+  const int tcap = p.precision == HSF_PREC_C64 ? kRegTileC64 : kRegTileC128;
+  p.tile_max = (o && o->tile_bits) ? o->tile_bits : tcap;
+  if (p.tile_max < 3 || p.tile_max > tcap) return set_error(HSF_EINVAL, "tile_bits %d outside 3..%d", p.tile_max, tcap);
+  p.tile_max = std::min(p.tile_max, p.n);
+  hsf_status st = load_gates(p, c, o);
+  if (st != HSF_OK) return st;
+  p.rbits = p.precision == HSF_PREC_C64
+                ? ((p.flags & HSF_FLAG_REG5) ? 5 : (p.flags & HSF_FLAG_REG3) ? 3 : kRegBitsC64)
+                : kRegBitsC128;
+  p.radix.assign(1, 1);
+  p.below.assign(1, 1);
+  p.num_paths = 1;
+  p.tree_nodes = 1;
+  SideH &sd = p.side[0];
+  sd.h = p.n;
+  sd.offset = 0;
+  sd.store.resize(p.n);
+  for (int q = 0; q < p.n; ++q) sd.store[q] = q;
+  sd.levels.assign(1, LevelH{});
+  LevelH &lv = sd.levels[0];
+  for (const GateH &g : p.gates) {
+    OpH op;
+    op.type = g.diag ? OP_DIAG : OP_DENSE;
+    op.nq = g.nq;
+    for (int j = 0; j < g.nq; ++j) op.q[j] = g.q[j];
+    const int d = 1 << g.nq;
+    if (g.diag) {
+      op.m.resize(d);
+      for (int i = 0; i < d; ++i) op.m[i] = g.m[(size_t)i * d + i];
+    } else {
+      op.m = g.m;
+    }
+    lv.ops.push_back(op);
+  }
+  merge_one_qubit_runs(lv.ops);
+  if (!(p.flags & HSF_FLAG_NO_REGISTER_SWEEP)) absorb_into_two_qubit(lv.ops);
+  split_passes(lv, sd.h, p.tile_max);
+  if (!(p.flags & HSF_FLAG_NO_REGISTER_SWEEP))
+    for (auto &ps : lv.passes) build_groups(ps, p.rbits);
+  p.side[1] = SideH{};
+  st = upload_programs(p);
+  if (st != HSF_OK) return st;
+  p.launches = (int64_t)lv.passes.size();
+  CUDA_TRY(cudaMalloc(&p.dev_status, 256));
+  CUDA_TRY(cudaMemsetAsync(p.dev_status, 0, 256, plan_stream()));
+  CUDA_TRY(cudaStreamSynchronize(plan_stream()));
   return HSF_OK;
 }
 
@@ -1017,7 +1109,8 @@ hsf_status run_svd_jobs(const hsf_plan &p, const std::vector<SvdJob> &jobs, std:
   auto take = [&](size_t bytes) { size_t o = off; off += (bytes + 255) / 256 * 256; return o; };
   const size_t o_bk = take(bk.size() * 4), o_tb = take(tbeg.size() * 4), o_gb = take(gbeg.size() * 4),
                o_gd = take(gdesc.size() * 4 + 4), o_gm = take(gm.size() * 8 + 8), o_sig = take((size_t)J * 64 * 8),
-               o_rank = take((size_t)J * 4), o_x = take(nf * 8), o_y = take(nf * 8), o_sw = take((size_t)J * 4);
+               o_rank = take((size_t)J * 4), o_x = take(nf * 8), o_y = take(nf * 8), o_sw = take((size_t)J * 4),
+               o_res = take((size_t)J * 8);
   cudaStream_t pst = plan_stream();
   unsigned char *d = nullptr;
   CUDA_TRY(cudaMallocAsync((void **)&d, off, pst));
@@ -1042,10 +1135,14 @@ hsf_status run_svd_jobs(const hsf_plan &p, const std::vector<SvdJob> &jobs, std:
   a.xf = (double *)(d + o_x);
   a.yf = (double *)(d + o_y);
   a.sweeps_used = (int32_t *)(d + o_sw);
+  a.residual = (double *)(d + o_res);
   CUDA_TRY(launch_block_svd(a, pst));
   g_launches++;
   std::vector<double> sig((size_t)J * 64), xf(nf), yf(nf);
-  std::vector<int32_t> rank(J);
+  std::vector<int32_t> rank(J), sweeps(J);
+  std::vector<double> resid(J);
+  CUDA_TRY(cudaMemcpyAsync(sweeps.data(), d + o_sw, sweeps.size() * 4, cudaMemcpyDeviceToHost, pst));
+  CUDA_TRY(cudaMemcpyAsync(resid.data(), d + o_res, resid.size() * 8, cudaMemcpyDeviceToHost, pst));
   CUDA_TRY(cudaMemcpyAsync(sig.data(), d + o_sig, sig.size() * 8, cudaMemcpyDeviceToHost, pst));
   CUDA_TRY(cudaMemcpyAsync(rank.data(), d + o_rank, rank.size() * 4, cudaMemcpyDeviceToHost, pst));
   CUDA_TRY(cudaMemcpyAsync(xf.data(), d + o_x, nf * 8, cudaMemcpyDeviceToHost, pst));
@@ -1062,6 +1159,22 @@ hsf_status run_svd_jobs(const hsf_plan &p, const std::vector<SvdJob> &jobs, std:
     r.sigma.assign(sig.begin() + (size_t)j * 64, sig.begin() + (size_t)j * 64 + std::max(0, r.rank));
     for (double sv : r.sigma)
       if (!std::isfinite(sv)) return set_error(HSF_ENUMERIC, "block %d: non-finite singular value", jobs[j].block);
+    // The Jacobi sweeps must have converged, and the kept terms must rebuild the block
+    // matrix (eq. equ-schmidt-decompostion-res) up to FP64 round-off plus what the rank
+    // threshold dropped (each dropped term has unit-norm factors, so it moves an entry by
+    // at most its sigma).
+    if (sweeps[j] >= a.max_sweeps)
+      return set_error(HSF_ENUMERIC, "block %d: Jacobi SVD did not converge in %d sweeps", jobs[j].block,
+                       a.max_sweeps);
+    double dropped = 0.0;
+    for (int m = std::max(0, r.rank); m < 64; ++m) dropped += sig[(size_t)j * 64 + m];
+    const double s0 = r.rank > 0 ? r.sigma[0] : 0.0;
+    const double res_tol = 1e-12 * std::max(1.0, s0) + dropped;
+    if (!(resid[j] <= res_tol))
+      return set_error(HSF_ENUMERIC, "block %d: Schmidt terms rebuild the block matrix only to %.3g (limit %.3g)",
+                       jobs[j].block, resid[j], res_tol);
+    r.residual = resid[j];
+    r.sweeps = sweeps[j];
     const int ea = 1 << (2 * (int)r.qa.size()), eb = 1 << (2 * (int)r.qb.size());
     for (int m = 0; m < r.rank; ++m) {
       for (int e = 0; e < ea; ++e) {
@@ -1077,16 +1190,261 @@ hsf_status run_svd_jobs(const hsf_plan &p, const std::vector<SvdJob> &jobs, std:
   return HSF_OK;
 }
 
+// Closed-form Schmidt terms of cascade blocks (Sec. IV-D, Example 4: a cascade of gates
+// that share one control-like qubit keeps rank 2, C_CNOT,3 = P0 (x) I + P1 (x) X X X).
+// Generalised to a hub H = all block qubits of one side: when every gate that touches H
+// is diagonal on H (block-diagonal in the H basis: CNOT with its control in H, CZ, RZZ,
+// diagonal one-qubit gates), then for every hub basis state z the block acts on the
+// other side as Y_z = prod_g <z|G_g|z>_H (circuit order, later gates on the left), so
+// A = sum_z P_z (x) Y_z with P_z = |z><z| on H.  The P_z are orthogonal; when the Y_z are
+// linearly independent there are exactly 2^{k_H} terms, the Schmidt rank.  A job with
+// several terms (a derivative by the product rule) sums its terms' Y_z.
+static cd m_entry(const GateH &g, int r, int c) { return g.m[(size_t)r * (1 << g.nq) + c]; }
+
+bool closed_form_job(const hsf_plan &p, const SvdJob &job, bool need_independent, BlockH &out) {
+  const BlockH &blk = p.blocks[job.block];
+  for (int hub = 0; hub < 2; ++hub) {
+    const std::vector<int> &H = hub == 0 ? blk.qa : blk.qb;     // descending: H[0] is the MSB of z
+    const std::vector<int> &O = hub == 0 ? blk.qb : blk.qa;
+    const int kh = (int)H.size(), ko = (int)O.size();
+    if (kh == 0 || kh > 3 || ko == 0 || ko > kMaxCascadeLeaves) continue;
+    auto hub_pos = [&](int q) {
+      for (int i = 0; i < kh; ++i)
+        if (H[i] == q) return kh - 1 - i;
+      return -1;
+    };
+    auto other_pos = [&](int q) {
+      for (int i = 0; i < ko; ++i)
+        if (O[i] == q) return ko - 1 - i;
+      return -1;
+    };
+    bool ok = true;
+    for (const auto &term : job.terms) {
+      for (int code : term) {
+        const GateH &g = p.gates[code < 0 ? -1 - code : code];
+        const std::vector<cd> &m = code < 0 ? g.dm : g.m;
+        int hmask = 0;                         // matrix-index bits that are hub qubits
+        for (int x = 0; x < g.nq; ++x)
+          if (hub_pos(g.q[x]) >= 0) hmask |= 1 << (g.nq - 1 - x);
+        if (!hmask) continue;
+        const int d = 1 << g.nq;
+        for (int r = 0; r < d && ok; ++r)
+          for (int c = 0; c < d; ++c)
+            if (((r ^ c) & hmask) && m[(size_t)r * d + c] != cd(0.0)) {
+              ok = false;
+              break;
+            }
+      }
+      if (!ok) break;
+    }
+    if (!ok) continue;
+    const int dz = 1 << kh, dob = 1 << ko;
+    std::vector<std::vector<cd>> Y(dz, std::vector<cd>((size_t)dob * dob, 0.0));
+    std::vector<cd> T((size_t)dob * dob), col(dob);
+    for (int z = 0; z < dz; ++z) {
+      for (const auto &term : job.terms) {
+        std::fill(T.begin(), T.end(), cd(0.0));
+        for (int i = 0; i < dob; ++i) T[(size_t)i * dob + i] = 1.0;
+        for (int code : term) {
+          const GateH &g = p.gates[code < 0 ? -1 - code : code];
+          const std::vector<cd> &m = code < 0 ? g.dm : g.m;
+          const int d = 1 << g.nq;
+          // the gate's matrix restricted to hub state z: its other operands vary
+          int fixed = 0, nv = 0, vbit[3] = {0, 0, 0};
+          OpH op;
+          op.type = OP_DENSE;
+          for (int x = 0; x < g.nq; ++x) {
+            const int hp = hub_pos(g.q[x]);
+            if (hp >= 0) {
+              if ((z >> hp) & 1) fixed |= 1 << (g.nq - 1 - x);
+            } else {
+              vbit[nv] = g.nq - 1 - x;
+              op.q[nv] = other_pos(g.q[x]);
+              ++nv;
+            }
+          }
+          op.nq = nv;
+          const int dv = 1 << nv;
+          auto full_index = [&](int v) {
+            int i = fixed;
+            for (int j = 0; j < nv; ++j)
+              if ((v >> (nv - 1 - j)) & 1) i |= 1 << vbit[j];
+            return i;
+          };
+          if (nv == 0) {
+            const cd sc = m[(size_t)fixed * d + fixed];
+            for (auto &e : T) e *= sc;
+            continue;
+          }
+          op.m.resize((size_t)dv * dv);
+          for (int r = 0; r < dv; ++r)
+            for (int c = 0; c < dv; ++c) op.m[(size_t)r * dv + c] = m[(size_t)full_index(r) * d + full_index(c)];
+          for (int c = 0; c < dob; ++c) {
+            for (int r = 0; r < dob; ++r) col[r] = T[(size_t)r * dob + c];
+            host_apply(col, ko, op, 0);
+            for (int r = 0; r < dob; ++r) T[(size_t)r * dob + c] = col[r];
+          }
+        }
+        for (size_t e = 0; e < T.size(); ++e) Y[z][e] += T[e];
+      }
+    }
+    // norms, and linear independence by Gram-Schmidt on the vectorised Y_z
+    std::vector<double> nrm(dz, 0.0);
+    for (int z = 0; z < dz; ++z) {
+      for (const cd &e : Y[z]) nrm[z] += std::norm(e);
+      nrm[z] = std::sqrt(nrm[z]);
+    }
+    double nmax = 0.0;
+    for (double v : nrm) nmax = std::max(nmax, v);
+    if (need_independent) {
+      if (!(nmax > 0.0)) continue;
+      std::vector<std::vector<cd>> basis;
+      bool indep = true;
+      for (int z = 0; z < dz && indep; ++z) {
+        std::vector<cd> v = Y[z];
+        for (const auto &u : basis) {
+          cd dot = 0.0;
+          for (size_t e = 0; e < v.size(); ++e) dot += std::conj(u[e]) * v[e];
+          for (size_t e = 0; e < v.size(); ++e) v[e] -= dot * u[e];
+        }
+        double r = 0.0;
+        for (const cd &e : v) r += std::norm(e);
+        r = std::sqrt(r);
+        if (!(r > 1e-10 * std::max(nrm[z], 1e-300)) || !(nrm[z] > 1e-12 * nmax)) indep = false;
+        for (auto &e : v) e /= r;
+        basis.push_back(v);
+      }
+      if (!indep) continue;
+    }
+    out = BlockH{};
+    out.gates = blk.gates;
+    out.qubits = blk.qubits;
+    out.qa = blk.qa;
+    out.qb = blk.qb;
+    out.closed = hub;
+    const int ka = (int)blk.qa.size(), kb = (int)blk.qb.size();
+    if (ko > 3) {
+      // more than 3 qubits on the other side: no dense factor; the factor of side O is the
+      // block's gates restricted to the hub state (one small op per gate, a matrix per
+      // digit), and the hub side's factor is the projector (with the hub-only phases and
+      // the balancing scale folded in)
+      if (job.terms.size() != 1 || !need_independent) return false;
+      std::vector<cd> hub_scale(dz, 1.0);
+      for (int z = 0; z < dz; ++z) hub_scale[z] = std::sqrt(nrm[z]);
+      bool first_o = true;
+      for (int code : job.terms[0]) {
+        const GateH &g = p.gates[code];
+        const int d = 1 << g.nq;
+        int nv = 0, vbit[3] = {0, 0, 0}, vq[3] = {0, 0, 0};
+        for (int x = 0; x < g.nq; ++x)
+          if (hub_pos(g.q[x]) < 0) {
+            vbit[nv] = g.nq - 1 - x;
+            vq[nv] = g.q[x];
+            ++nv;
+          }
+        const int dv = 1 << nv;
+        OpH op;
+        op.nq = nv;
+        for (int j = 0; j < nv; ++j) op.q[j] = vq[j];
+        op.digits = dz;
+        op.block = job.block;
+        std::vector<cd> mats;
+        bool diag = true;
+        for (int z = 0; z < dz; ++z) {
+          int fixed = 0;
+          for (int x = 0; x < g.nq; ++x) {
+            const int hp = hub_pos(g.q[x]);
+            if (hp >= 0 && ((z >> hp) & 1)) fixed |= 1 << (g.nq - 1 - x);
+          }
+          auto full_index = [&](int v) {
+            int i = fixed;
+            for (int j = 0; j < nv; ++j)
+              if ((v >> (nv - 1 - j)) & 1) i |= 1 << vbit[j];
+            return i;
+          };
+          if (nv == 0) {
+            hub_scale[z] *= m_entry(g, fixed, fixed);
+            continue;
+          }
+          const double inv = first_o ? 1.0 / std::sqrt(nrm[z]) : 1.0;
+          for (int r = 0; r < dv; ++r)
+            for (int c = 0; c < dv; ++c) {
+              const cd v = g.m[(size_t)full_index(r) * d + full_index(c)] * inv;
+              if (r != c && v != cd(0.0)) diag = false;
+              mats.push_back(v);
+            }
+        }
+        if (nv == 0) continue;
+        first_o = false;
+        if (diag) {
+          op.type = OP_DIAG;
+          for (int z = 0; z < dz; ++z)
+            for (int r = 0; r < dv; ++r) op.m.push_back(mats[(size_t)z * dv * dv + (size_t)r * dv + r]);
+        } else {
+          op.type = OP_DENSE;
+          op.m = mats;
+        }
+        out.fops[1 - hub].push_back(op);
+      }
+      OpH hop;
+      hop.type = OP_DIAG;
+      hop.nq = kh;
+      for (int j = 0; j < kh; ++j) hop.q[j] = H[j];
+      hop.digits = dz;
+      hop.block = job.block;
+      for (int z = 0; z < dz; ++z)
+        for (int e = 0; e < dz; ++e) hop.m.push_back(e == z ? hub_scale[z] : cd(0.0));
+      out.fops[hub].push_back(hop);
+      for (int z = 0; z < dz; ++z) out.sigma.push_back(nrm[z]);
+      out.rank = dz;
+      return true;
+    }
+    const int ea = 1 << (2 * ka), eb = 1 << (2 * kb);
+    for (int z = 0; z < dz; ++z) {
+      if (!(nrm[z] > 1e-300) || (!need_independent && !(nrm[z] > 1e-14 * nmax))) continue;   // a zero term
+      // balanced magnitudes, as the SVD's sqrt(sigma) folding: |X'|_F = |Y'|_F
+      const double c = std::sqrt(nrm[z]);
+      std::vector<cd> proj((size_t)dz * dz, 0.0);
+      proj[(size_t)z * dz + z] = c;
+      std::vector<cd> oth(Y[z]);
+      for (auto &e : oth) e /= c;
+      const std::vector<cd> &xa = hub == 0 ? proj : oth, &yb = hub == 0 ? oth : proj;
+      if ((int)xa.size() != ea || (int)yb.size() != eb) return false;
+      out.x.insert(out.x.end(), xa.begin(), xa.end());
+      out.y.insert(out.y.end(), yb.begin(), yb.end());
+      out.sigma.push_back(nrm[z]);      // |P_z|_F |Y_z|_F
+      ++out.rank;
+    }
+    return true;
+  }
+  return false;
+}
+
 hsf_status decompose_blocks(hsf_plan &p) {
   const int B = (int)p.blocks.size();
-  std::vector<SvdJob> jobs(B);
+  std::vector<SvdJob> jobs;
+  std::vector<int> svd_of;
+  std::vector<BlockH> res(B);
+  std::vector<char> done(B, 0);
   for (int b = 0; b < B; ++b) {
-    jobs[b].block = b;
-    jobs[b].terms = {p.blocks[b].gates};
+    SvdJob job;
+    job.block = b;
+    job.terms = {p.blocks[b].gates};
+    if (!(p.flags & HSF_FLAG_SVD_BLOCKS) && closed_form_job(p, job, true, res[b])) {
+      done[b] = 1;
+      continue;
+    }
+    if (p.blocks[b].qa.size() > 3 || p.blocks[b].qb.size() > 3)
+      return set_error(HSF_ERANK, "block %d spans %zu|%zu qubits: the SVD takes at most 3 per side (only a cascade, "
+                                  "diagonal on one side's block qubits, may have more)", b, p.blocks[b].qa.size(),
+                       p.blocks[b].qb.size());
+    jobs.push_back(job);
+    svd_of.push_back(b);
   }
-  std::vector<BlockH> res;
-  hsf_status st = run_svd_jobs(p, jobs, res);
+  std::vector<BlockH> sres;
+  hsf_status st = run_svd_jobs(p, jobs, sres);
   if (st != HSF_OK) return st;
+  for (size_t j = 0; j < jobs.size(); ++j) res[svd_of[j]] = sres[j];
   for (int b = 0; b < B; ++b) {
     if (res[b].rank <= 0) return set_error(HSF_ENUMERIC, "block %d decomposed to rank 0", b);
     p.blocks[b] = res[b];
@@ -1094,34 +1452,10 @@ hsf_status decompose_blocks(hsf_plan &p) {
   return HSF_OK;
 }
 
-hsf_status validate_and_load(hsf_plan &p, const hsf_circuit *c, int cut, const hsf_blocks *bl,
-                             const hsf_plan_opts *o) {
-  if (!c || !bl) return set_error(HSF_EINVAL, "circuit and blocks must not be NULL");
-  if (c->n < 2 || c->n > 62) return set_error(HSF_EINVAL, "n = %d outside 2..62", c->n);
-  if (cut < 0 || cut > c->n - 2) return set_error(HSF_EINVAL, "cut %d outside 0..n-2", cut);
-  if (c->num_gates < 0 || (c->num_gates > 0 && !c->gates)) return set_error(HSF_EINVAL, "bad gate array");
-  p.n = c->n;
-  p.cut = cut;
-  p.nb = cut + 1;
-  p.na = c->n - cut - 1;
-  p.max_paths = 1ull << 40;
-  if (o) {
-    p.precision = o->precision;
-    p.gemm_mode = o->gemm_mode;
-    p.rank_tol = o->rank_tol > 0 ? o->rank_tol : 1e-12;
-    if (o->max_paths) p.max_paths = o->max_paths;
-    p.flags = o->flags;
-  }
-  if (p.precision != HSF_PREC_C64 && p.precision != HSF_PREC_C128)
-    return set_error(HSF_EINVAL, "precision %d", p.precision);
-  if (p.gemm_mode < 0 || p.gemm_mode > 3) return set_error(HSF_EINVAL, "gemm_mode %d", p.gemm_mode);
-  if (p.gemm_mode != HSF_GEMM_FP32 && p.precision != HSF_PREC_C64)
-    return set_error(HSF_EINVAL, "tensor-core path GEMM modes take complex64 half states");
-  // a shared-memory tile holds at most 2^13 (complex64) or 2^12 (complex128) amplitudes
-  const int tcap = p.precision == HSF_PREC_C64 ? kRegTileC64 : kRegTileC128;
-  p.tile_max = (o && o->tile_bits) ? o->tile_bits : tcap;
-  if (p.tile_max < 3 || p.tile_max > tcap) return set_error(HSF_EINVAL, "tile_bits %d outside 3..%d", p.tile_max, tcap);
-  if (p.na > 40 || p.nb > 40) return set_error(HSF_EINVAL, "half of %d/%d qubits is too large", p.na, p.nb);
+// Gate list of the circuit: matrices (named kinds from their definitions, explicit ones
+// copied and checked finite), rotation derivatives, qubit checks and the side of every
+// gate for the cut p.cut (set by the caller).
+hsf_status load_gates(hsf_plan &p, const hsf_circuit *c, const hsf_plan_opts *o) {
   p.gates.resize(c->num_gates);
   for (int i = 0; i < c->num_gates; ++i) {
     const hsf_gate &g = c->gates[i];
@@ -1172,9 +1506,42 @@ hsf_status validate_and_load(hsf_plan &p, const hsf_circuit *c, int cut, const h
     }
     h.diag = is_diagonal(h.m, 1 << nq);
     bool hi = false, lo = false;
-    for (int j = 0; j < nq; ++j) (h.q[j] > cut ? hi : lo) = true;
+    for (int j = 0; j < nq; ++j) (h.q[j] > p.cut ? hi : lo) = true;
     h.side = (hi && lo) ? 2 : (hi ? 0 : 1);
   }
+  return HSF_OK;
+}
+
+hsf_status validate_and_load(hsf_plan &p, const hsf_circuit *c, int cut, const hsf_blocks *bl,
+                             const hsf_plan_opts *o) {
+  if (!c || !bl) return set_error(HSF_EINVAL, "circuit and blocks must not be NULL");
+  if (c->n < 2 || c->n > 62) return set_error(HSF_EINVAL, "n = %d outside 2..62", c->n);
+  if (cut < 0 || cut > c->n - 2) return set_error(HSF_EINVAL, "cut %d outside 0..n-2", cut);
+  if (c->num_gates < 0 || (c->num_gates > 0 && !c->gates)) return set_error(HSF_EINVAL, "bad gate array");
+  p.n = c->n;
+  p.cut = cut;
+  p.nb = cut + 1;
+  p.na = c->n - cut - 1;
+  p.max_paths = 1ull << 40;
+  if (o) {
+    p.precision = o->precision;
+    p.gemm_mode = o->gemm_mode;
+    p.rank_tol = o->rank_tol > 0 ? o->rank_tol : 1e-12;
+    if (o->max_paths) p.max_paths = o->max_paths;
+    p.flags = o->flags;
+  }
+  if (p.precision != HSF_PREC_C64 && p.precision != HSF_PREC_C128)
+    return set_error(HSF_EINVAL, "precision %d", p.precision);
+  if (p.gemm_mode < 0 || p.gemm_mode > 3) return set_error(HSF_EINVAL, "gemm_mode %d", p.gemm_mode);
+  if (p.gemm_mode != HSF_GEMM_FP32 && p.precision != HSF_PREC_C64)
+    return set_error(HSF_EINVAL, "tensor-core path GEMM modes take complex64 half states");
+  // a shared-memory tile holds at most 2^13 (complex64) or 2^12 (complex128) amplitudes
+  const int tcap = p.precision == HSF_PREC_C64 ? kRegTileC64 : kRegTileC128;
+  p.tile_max = (o && o->tile_bits) ? o->tile_bits : tcap;
+  if (p.tile_max < 3 || p.tile_max > tcap) return set_error(HSF_EINVAL, "tile_bits %d outside 3..%d", p.tile_max, tcap);
+  if (p.na > 40 || p.nb > 40) return set_error(HSF_EINVAL, "half of %d/%d qubits is too large", p.na, p.nb);
+  hsf_status gst = load_gates(p, c, o);
+  if (gst != HSF_OK) return gst;
   if (bl->num_blocks < 0 || bl->num_blocks > 64)
     return set_error(HSF_EINVAL, "num_blocks %d outside 0..64", bl->num_blocks);
   if (bl->num_blocks > 0 && (!bl->offsets || !bl->gate_idx)) return set_error(HSF_EINVAL, "bad block arrays");
@@ -1200,8 +1567,9 @@ hsf_status validate_and_load(hsf_plan &p, const hsf_circuit *c, int cut, const h
     std::sort(blk.gates.begin(), blk.gates.end());
     blk.qubits.assign(qs.rbegin(), qs.rend());
     for (int q : blk.qubits) (q > cut ? blk.qa : blk.qb).push_back(q);
-    if (blk.qa.size() > 3 || blk.qb.size() > 3)
-      return set_error(HSF_ERANK, "block %d spans %zu|%zu qubits; at most 3 per side", b, blk.qa.size(), blk.qb.size());
+    if (std::min(blk.qa.size(), blk.qb.size()) > 3 || std::max(blk.qa.size(), blk.qb.size()) > (size_t)kMaxCascadeLeaves)
+      return set_error(HSF_ERANK, "block %d spans %zu|%zu qubits; at most 3 on one side and %d on the other", b,
+                       blk.qa.size(), blk.qb.size(), kMaxCascadeLeaves);
   }
   for (int i = 0; i < c->num_gates; ++i)
     if (p.gates[i].side == 2 && owner[i] < 0)

@@ -15,6 +15,8 @@
 //   4. Keep sigma_m > rank_tol * sigma_0 and emit the Schmidt factors with sqrt(sigma_m)
 //      folded into both sides: X'_m = sqrt(s) X_m, Y'_m = sqrt(s) Y_m where
 //      X_m[i^a, j^a] = conj(V[(i^a j^a), m]) and Y_m[i^b, j^b] = U[(i^b j^b), m].
+//   5. Reconstruction check: the largest entry of |U_B - sum_m X'_m (x) Y'_m| over the
+//      kept terms (eq. equ-schmidt-decompostion-res), for the host to accept or reject.
 // The sweep count is bounded (max_sweeps); the kernel never waits on anything.
 #include <cstdint>
 
@@ -242,6 +244,28 @@ __global__ void __launch_bounds__(kThreads) block_svd_kernel(BlockSvdArgs a) {
       }
     }
   }
+  // 5. reconstruction residual against the block matrix (U is untouched since step 1)
+  __shared__ unsigned long long res_bits;
+  if (tid == 0) res_bits = 0ull;
+  __syncthreads();
+  const int rda = 1 << ka, rdb = 1 << kb;
+  double worst = 0.0;
+  for (int e = tid; e < D * D; e += blockDim.x) {
+    const int row = e / D, col = e % D;
+    const int ia = row >> kb, ib = row & (rdb - 1), ja = col >> kb, jb = col & (rdb - 1);
+    double2 acc = make_double2(0.0, 0.0);
+    for (int m = 0; m < rank; ++m) {
+      const double2 x = xf[m * kMaxDim + ia * rda + ja], y = yf[m * kMaxDim + ib * rdb + jb];
+      const double2 xy = cmul(x, y);
+      acc.x += xy.x;
+      acc.y += xy.y;
+    }
+    const double2 u = U[e];
+    worst = fmax(worst, hypot(u.x - acc.x, u.y - acc.y));
+  }
+  atomicMax(&res_bits, (unsigned long long)__double_as_longlong(worst));   // non-negative: bit order
+  __syncthreads();
+  if (tid == 0) a.residual[b] = __longlong_as_double((long long)res_bits);
 }
 
 }  // namespace

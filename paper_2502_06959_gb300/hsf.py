@@ -32,6 +32,7 @@ FLAG_IDENTITY_STORAGE = 8
 FLAG_REG5 = 16
 FLAG_REG3 = 32
 FLAG_NO_TC_LEVEL = 64
+FLAG_SVD_BLOCKS = 128
 
 
 class HsfError(RuntimeError):
@@ -83,6 +84,8 @@ SIGNATURES = {
                                        ctypes.POINTER(hsf_blocks), ctypes.POINTER(hsf_plan_opts),
                                        ctypes.POINTER(ctypes.c_void_p)]),
     "hsf_plan_get_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(hsf_plan_info)]),
+    "hsf_plan_create_schrodinger": (ctypes.c_int, [ctypes.POINTER(hsf_circuit), ctypes.POINTER(hsf_plan_opts),
+                                                   ctypes.POINTER(ctypes.c_void_p)]),
     "hsf_plan_get_sigma": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32,
                                           ctypes.POINTER(ctypes.c_double), ctypes.c_int32,
                                           ctypes.POINTER(ctypes.c_int32)]),
@@ -108,6 +111,10 @@ SIGNATURES = {
     "hsf_grad_workspace_size": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]),
     "hsf_grad": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p,
                                 ctypes.c_int32, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
+    "hsf_set_allocator": (None, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "hsf_find_blocks": (ctypes.c_int, [ctypes.POINTER(hsf_circuit), ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p,
+                                       ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
+                                       ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]),
     "hsf_last_error": (ctypes.c_char_p, []),
     "hsf_set_profiling": (None, [ctypes.c_int32]),
     "hsf_profile_collect": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32]),
@@ -213,6 +220,54 @@ def hsf_plan_create(n: int, gates, cut: int, blocks, precision: str = "c64", gem
     return out.value
 
 
+def hsf_plan_create_schrodinger(n: int, gates, precision: str = "c64", tile_bits: int = 0, flags: int = 0,
+                                angles: Optional[Sequence[float]] = None) -> int:
+    """Full-statevector plan of the circuit (no cut, no blocks); run it with hsf_run."""
+    lib = load_library()
+    circ, _, keep = _marshal(n, gates, [])
+    opts = hsf_plan_opts()
+    opts.precision = PREC[precision]
+    opts.tile_bits = tile_bits
+    opts.flags = flags
+    if angles is not None:
+        ang = np.ascontiguousarray(angles, dtype=np.float64)
+        keep.append(ang)
+        opts.angles = ang.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        opts.num_angles = ang.size
+    out = ctypes.c_void_p()
+    _check(lib.hsf_plan_create_schrodinger(ctypes.byref(circ), ctypes.byref(opts), ctypes.byref(out)))
+    return out.value
+
+
+def hsf_find_blocks(n: int, gates, cut: int, max_leaves: int = 8):
+    """Joint-cut blocks found by the library (hsf_find_blocks): returns (order, blocks,
+    hubs) where order[i] is the input index of the i-th gate of the reordered circuit and
+    blocks index the reordered circuit."""
+    lib = load_library()
+    circ, _, keep = _marshal(n, gates, [])
+    G = len(gates)
+    order = np.zeros(max(G, 1), dtype=np.int32)
+    cap = max(G, 1)
+    offs = np.zeros(cap + 1, dtype=np.int32)
+    idx = np.zeros(max(G, 1), dtype=np.int32)
+    nb, hubs = ctypes.c_int32(), ctypes.c_int32()
+    _check(lib.hsf_find_blocks(ctypes.byref(circ), cut, max_leaves, order.ctypes.data, offs.ctypes.data,
+                               idx.ctypes.data, cap, ctypes.byref(nb), ctypes.byref(hubs)))
+    blocks = [[int(x) for x in idx[offs[b]:offs[b + 1]]] for b in range(nb.value)]
+    return [int(x) for x in order[:G]], blocks, int(hubs.value)
+
+
+def problem_with_found_blocks(problem, max_leaves: int = 8):
+    """The problem's circuit reordered and cut into the blocks hsf_find_blocks finds."""
+    import copy
+    order, blocks, hubs = hsf_find_blocks(problem.n, problem.gates, problem.cut, max_leaves)
+    out = copy.copy(problem)
+    out.gates = [problem.gates[i] for i in order]
+    out.blocks = blocks
+    out.meta = dict(problem.meta, hubs=hubs, found_blocks=len(blocks))
+    return out
+
+
 def hsf_plan_get_info(plan: int) -> dict:
     info = hsf_plan_info()
     _check(load_library().hsf_plan_get_info(plan, ctypes.byref(info)))
@@ -239,8 +294,41 @@ def hsf_workspace_size(plan: int, num_bitstrings: int = 0, window: int = 0, budg
 
 def hsf_run(plan: int, bitstrings_ptr: int, num: int, window: int, path_begin: int, path_end: int,
             out_ptr: int, workspace_ptr: int, workspace_bytes: int, stream: int = 0) -> None:
+    """workspace_ptr = 0: the plan owns its workspace (see hsf_set_allocator)."""
     _check(load_library().hsf_run(plan, bitstrings_ptr or None, num, window, path_begin, path_end,
-                                  out_ptr, workspace_ptr, workspace_bytes, stream or None))
+                                  out_ptr, workspace_ptr or None, workspace_bytes, stream or None))
+
+
+_ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+_FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p)
+_allocator_refs = []
+
+
+def use_torch_allocator(on: bool = True) -> None:
+    """Route plan-owned workspaces (hsf_run with workspace 0) through PyTorch's caching
+    allocator (hsf_set_allocator); on=False restores the library's cudaMalloc default."""
+    import torch
+    lib = load_library()
+    if not on:
+        lib.hsf_set_allocator(None, None, None)
+        _allocator_refs.clear()
+        return
+
+    def _alloc(ctx, nbytes, stream):
+        try:
+            return int(torch.cuda.caching_allocator_alloc(int(nbytes), stream=stream or 0))
+        except Exception:
+            return None
+
+    def _free(ctx, ptr, stream):
+        try:
+            torch.cuda.caching_allocator_delete(int(ptr))
+        except Exception:
+            pass
+
+    fa, ff = _ALLOC_FN(_alloc), _FREE_FN(_free)
+    _allocator_refs[:] = [fa, ff]          # the library keeps the function pointers
+    lib.hsf_set_allocator(ctypes.cast(fa, ctypes.c_void_p), ctypes.cast(ff, ctypes.c_void_p), None)
 
 
 def hsf_set_profiling(on: bool) -> None:
@@ -376,6 +464,17 @@ class Plan:
     @classmethod
     def from_problem(cls, problem, **opts):
         return cls(problem.n, problem.gates, problem.cut, problem.blocks, **opts)
+
+    @classmethod
+    def schrodinger(cls, n: int, gates, **opts):
+        """A full-statevector plan of the circuit (hsf_plan_create_schrodinger)."""
+        self = cls.__new__(cls)
+        self.n = n
+        self.cut = -1
+        self.handle = hsf_plan_create_schrodinger(n, gates, **opts)
+        self.info = hsf_plan_get_info(self.handle)
+        self._ws = None
+        return self
 
     def sigma(self, block: int) -> np.ndarray:
         return hsf_plan_get_sigma(self.handle, block)

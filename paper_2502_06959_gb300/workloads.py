@@ -182,6 +182,48 @@ def qaoa_ring(n: int, cut: int, p: int, seed: int, num_bitstrings: int = 0,
                    num_params=2 * p, params=params, meta=dict(seed=seed, p=p))
 
 
+def sbm_graph(sizes: Sequence[int], p_intra: float, p_inter: float, seed: int) -> List[Tuple[int, int]]:
+    """Edges of a two-block stochastic block model graph (Table II: vertices of the two
+    partitions joined with probability p_intra inside a partition and p_inter between
+    them).  Vertices 0..sizes[0]-1 form the first partition; each pair (i < j) is drawn
+    once, in lexicographic order."""
+    rng = np.random.default_rng(seed)
+    n = int(sum(sizes))
+    part = np.concatenate([np.full(int(s), k) for k, s in enumerate(sizes)])
+    edges = []
+    for i in range(n):
+        for j in range(i + 1, n):
+            pr = p_intra if part[i] == part[j] else p_inter
+            if rng.random() < pr:
+                edges.append((i, j))
+    return edges
+
+
+def sbm_qaoa(sizes: Sequence[int] = (15, 15), p_intra: float = 0.8, p_inter: float = 0.1, seed: int = 0,
+             name: str = "") -> Problem:
+    """Single-layer QAOA Max-Cut on a stochastic-block-model graph (Sec. V, Table II):
+    H on every qubit, RZZ(gamma) on every edge (in the generator's edge order, crossing
+    and in-half edges interleaved), RX(beta) on every qubit.  Qubit q is vertex q; the cut
+    lies after the first partition (Table II "cut pos." = sizes[0] - 1).  The angles are
+    drawn from U[0, 2 pi) and shared through param_id (gamma: 0, beta: 1).  The blocks are
+    left empty: ``hsf.problem_with_found_blocks`` (or singleton blocks) fills them."""
+    rng = np.random.default_rng(seed + 7919)
+    gamma, beta = (float(x) for x in rng.uniform(0, 2 * np.pi, size=2))
+    n = int(sum(sizes))
+    edges = sbm_graph(sizes, p_intra, p_inter, seed)
+    gates: List[Gate] = [Gate("h", (q,)) for q in range(n)]
+    for (i, j) in edges:
+        gates.append(Gate("rzz", (j, i), param=gamma, param_id=0))
+    for q in range(n):
+        gates.append(Gate("rx", (q,), param=beta, param_id=1))
+    cut = int(sizes[0]) - 1
+    crossing = sum(1 for (i, j) in edges if i <= cut < j)
+    return Problem(n=n, gates=gates, cut=cut, blocks=[], name=name or f"sbm_q{n}_pinter{p_inter}",
+                   num_params=2, params=np.array([gamma, beta]),
+                   meta=dict(seed=seed, sizes=list(sizes), p_intra=p_intra, p_inter=p_inter,
+                             edges=len(edges), crossing=crossing, two_qubit_gates=len(edges)))
+
+
 # ---------------------------------------------------------------------------
 # The five named workloads (sizes fixed here, seeds fixed per workload).
 # ---------------------------------------------------------------------------
@@ -222,6 +264,19 @@ def workload_c3(seed: int = 3, count: int = 64, n_choices=(20, 22, 24, 26, 28, 3
                               name=f"c3_{i}_n{n}")
         out.append(pr)
     return out
+
+
+def workload_c3_largest(seed: int = 3) -> Problem:
+    """The largest circuit of ``workload_c3`` (most qubits, then most blocks): the one
+    whose window path GEMM is timed on its own."""
+    return max(workload_c3(seed=seed), key=lambda q: (q.n, len(q.blocks)))
+
+
+def window_samples(n: int, window: int, count: int, seed: int) -> np.ndarray:
+    """``count`` distinct seeded indices below min(window, 2^n) (uint64), sorted."""
+    rng = np.random.default_rng(seed)
+    top = min(window, 1 << n)
+    return np.sort(rng.choice(top, size=min(count, top), replace=False)).astype(np.uint64)
 
 
 def workload_c4(seed: int = 4, n: int = 28, p: int = 4, num_bitstrings: int = 1024,
