@@ -197,6 +197,10 @@ def oracle_sample(pr, paths_per_core: int, cores: int, start: int = 0):
     jobs = [(pr.n, pr.gates, pr.cut, pr.blocks, pr.bitstrings, start + i * paths_per_core,
              start + (i + 1) * paths_per_core) for i in range(cores)]
     ctx = mp.get_context("spawn")
+    # one BLAS thread per worker (inherited by the spawned processes): `cores` processes
+    # use `cores` threads
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[v] = "1"
     with ctx.Pool(cores) as pool:
         pool.map(_oracle_slice, jobs[:1])            # start-up outside the timing
         t0 = time.perf_counter()
@@ -774,6 +778,12 @@ def main():
         sch = hsf.Plan.schrodinger(pr.n, pr.gates, precision="c64")
         sch.run(bits, out=out, check=True)
         ws_s = sch.workspace(S, 0)
+        hsf.hsf_set_profiling(True)
+        sch.run(bits, out=out)
+        torch.cuda.synchronize()
+        sst = hsf.hsf_profile_collect(sch.handle)["sweep"]
+        hsf.hsf_set_profiling(False)
+        s_passes = int(sch.info["num_launches"])
         sch.close()
         hs = []
 
@@ -787,8 +797,12 @@ def main():
             hsf.hsf_plan_destroy(h)
         del ws_s
         serr = float(np.max(np.abs(out.cpu().numpy() - gold["amps"]))) if gold is not None else None
+        fp32_peak = 152 * 128 * 2 * peaks()[2] * 1e6 / 1e12
         line["schrodinger"] = {"ms_per_step": ms_s / 2, "s_over_j": (ms_s / 2) / (ms / args.steps),
-                               "err_vs_fp64": serr, "state": "2^30 complex64 (8 GB)",
+                               "err_vs_fp64": serr, "state": "2^30 complex64 (8 GB)", "passes": s_passes,
+                               "sweep_ms": sst["ms"], "sweep_gbs": sst["bytes"] / (sst["ms"] / 1e3) / 1e9,
+                               "sweep_tflops": sst["flops"] / (sst["ms"] / 1e3) / 1e12,
+                               "sweep_alu_frac": sst["flops"] / (sst["ms"] / 1e3) / 1e12 / fp32_peak,
                                "step": "plan + full-state sweep + read-out"}
         line["sbm_table1"] = sbm_leg(hsf, torch, args.steps)
     plan0.close()

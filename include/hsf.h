@@ -297,11 +297,17 @@ hsf_status hsf_run_static(hsf_plan *plan, const uint64_t *bitstrings, size_t num
  * (uncomputing unitary gates, never the Schmidt factors, which are taken from the
  * forward's stored node states); rotations inside a cut block by the HSF sum with
  * the block replaced by its derivative, Schmidt-decomposed on the device (the
- * amplitude is linear in the block matrix, Sec. IV-A).  Supported rotation kinds:
- * RX, RY, RZ, RZZ.  The whole path tree is kept: the workspace must hold every
- * node state twice (hsf_grad_workspace_size).  The first call builds the gradient
- * programs and derivative plans (synchronous). */
-hsf_status hsf_grad_workspace_size(hsf_plan *plan, size_t num_bitstrings, size_t *bytes);
+ * amplitude is linear in the block matrix, Sec. IV-A; cascade blocks keep their
+ * closed-form terms, Sec. IV-D).  Supported rotation kinds: RX, RY, RZ, RZZ.  Forward
+ * states are recomputed rather than stored for the whole tree: levels 0..k0 of the path
+ * tree are held for every node, and each level-k0 node's subtree is recomputed, walked
+ * back and released in turn, k0 being the smallest level whose layout fits the
+ * workspace.  hsf_grad_workspace_size(plan, num, budget, &bytes): bytes needed for the
+ * layout chosen under `budget` (0: the whole tree at once, the fastest); HSF_ENOMEM if
+ * no layout fits.  hsf_grad picks its layout from workspace_bytes the same way.  The
+ * first call builds the gradient programs and derivative plans (synchronous).  Blocks
+ * with more than 3 qubits on a side return HSF_ENOTSUP. */
+hsf_status hsf_grad_workspace_size(hsf_plan *plan, size_t num_bitstrings, size_t budget_bytes, size_t *bytes);
 hsf_status hsf_grad(hsf_plan *plan, const uint64_t *bitstrings, size_t num, const void *gout,
                     double *grad, int32_t num_params, void *workspace, size_t workspace_bytes,
                     void *stream);

@@ -420,6 +420,126 @@ __global__ void __launch_bounds__(128, 4) leaf_contract_async_kernel(LeafArgs a)
   }
 }
 
+// Leaf contraction with one thread per (bitstring, digit, side): the thread keeps only its
+// side's row of L_m (half the registers of one thread per digit), copies and reads only
+// its side's chunk, and the two sides' dot products meet with one shuffle.  Lanes of a
+// warp: bitstring (t / 2RM), side ((t / RM) & 1), digit (t % RM).  Stage row of a
+// bitstring: a chunk, two complex of padding, b chunk, two more: with the row stride of
+// 2^(C+1) + 4 complex the 16-byte reads of a warp's four bitstrings and two sides fall
+// in eight distinct bank groups.
+constexpr int kPairDepth = 4;
+constexpr size_t leaf_pair_ring_bytes(int cb, int rm) {
+  return (size_t)kPairDepth * (128 / (2 * rm)) * ((2u << cb) + 4) * 8;
+}
+
+// Packed FP32 pair FMA (two lanes per instruction): d = a * b + c elementwise.
+__device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) {
+  float2 d;
+  asm("{\n .reg .b64 ra, rb, rc, rd;\n"
+      " mov.b64 ra, {%2, %3};\n mov.b64 rb, {%4, %5};\n mov.b64 rc, {%6, %7};\n"
+      " fma.rn.f32x2 rd, ra, rb, rc;\n mov.b64 {%0, %1}, rd;\n}"
+      : "=f"(d.x), "=f"(d.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+  return d;
+}
+
+template <int CB, int RM>
+__global__ void __launch_bounds__(128, 6) leaf_contract_pair_kernel(LeafArgs a) {
+  using C = float2;
+  constexpr int D = 1 << CB;
+  constexpr int SPB = 128 / (2 * RM);          // bitstrings per CTA
+  constexpr int SB = 2 * D + 4;
+  constexpr int BOFF = D + 2;                  // offset (complex) of the b chunk in a row
+  constexpr int STAGE = SPB * SB;
+  constexpr int HALF = D / 2 > 0 ? D / 2 : 1;  // 16-byte pieces per side
+  extern __shared__ __align__(16) unsigned char leaf_smem[];
+  C(*buf)[STAGE] = reinterpret_cast<C(*)[STAGE]>(leaf_smem);
+  const int m = threadIdx.x % RM;
+  const int side = (threadIdx.x / RM) & 1;
+  const int sl = threadIdx.x / (2 * RM);
+  const int64_t s = (int64_t)blockIdx.x * SPB + sl;
+  const int g = blockIdx.y;
+  const bool on = s < a.S && m < a.r;
+  uint64_t idx = 0;
+  if (s < a.S) idx = side == 0 ? a.ia[s] : a.ib[s];
+  const int rr = (int)(idx & (D - 1));
+  // the row of L_m as broadcast pairs: lr[k] = (Re l_k, Re l_k), li[k] = (Im l_k, Im l_k),
+  // so that with x_k = (Re x_k, Im x_k) as it sits in memory,
+  //   P = sum_k lr[k] * x_k = (sum Re l Re x, sum Re l Im x)
+  //   Q = sum_k li[k] * x_k = (sum Im l Re x, sum Im l Im x)
+  // and l . x = (P.x - Q.y, P.y + Q.x): two packed FMAs per complex term, no shuffling
+  C lr[D], li[D];
+  {
+    const C *gL = reinterpret_cast<const C *>(side == 0 ? a.La : a.Lb) + ((size_t)(on ? m : 0) * D + rr) * D;
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      const C v = gL[k];
+      lr[k] = make_float2(v.x, v.x);
+      li[k] = make_float2(v.y, v.y);
+    }
+  }
+  const int64_t j0 = (int64_t)g * a.parents_per_group;
+  const int64_t j1 = min(a.num_parents, j0 + a.parents_per_group);
+  const int64_t np = j1 - j0;
+  const int hbits = side == 0 ? a.ha : a.hb;
+  const C *src = reinterpret_cast<const C *>(side == 0 ? a.Pa : a.Pb) + (idx - rr);
+  const int roff = sl * SB + side * BOFF;
+  auto issue = [&](int64_t jj, int stage) {
+    if (jj < j1 && s < a.S) {
+      C *row = buf[stage] + roff;
+      const C *sp = src + ((uint64_t)jj << hbits);
+#pragma unroll
+      for (int i = 0; i < (HALF + RM - 1) / RM; ++i) {
+        const int q = m + i * RM;
+        if (q < HALF) cp_async16(row + 2 * q, sp + 2 * q);
+      }
+    }
+    cp_commit();
+  };
+#pragma unroll
+  for (int d = 0; d < kPairDepth - 1; ++d) issue(j0 + d, d);
+  float accr = 0.f, acci = 0.f;
+  for (int64_t t = 0; t < np; ++t) {
+    cp_wait<kPairDepth - 2>();
+    __syncwarp();
+    issue(j0 + t + kPairDepth - 1, (int)((t + kPairDepth - 1) % kPairDepth));
+    const int64_t j = j0 + t;
+    const bool use = on && !((j == 0 && m < a.m_first) || (j == a.num_parents - 1 && m >= a.m_last));
+    float vr = 0.f, vi = 0.f;
+    if (use) {
+      const float4 *x = reinterpret_cast<const float4 *>(buf[t % kPairDepth] + roff);
+      C P = make_float2(0.f, 0.f), Q = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int k2 = 0; k2 < D / 2; ++k2) {
+        const float4 xv = x[k2];
+        const C x0 = make_float2(xv.x, xv.y), x1 = make_float2(xv.z, xv.w);
+        P = ffma2(lr[2 * k2], x0, P);
+        Q = ffma2(li[2 * k2], x0, Q);
+        P = ffma2(lr[2 * k2 + 1], x1, P);
+        Q = ffma2(li[2 * k2 + 1], x1, Q);
+      }
+      vr = P.x - Q.y;
+      vi = P.y + Q.x;
+    }
+    // the other side's value for the same bitstring and digit (all lanes take part)
+    const float wr = __shfl_xor_sync(0xffffffffu, vr, RM);
+    const float wi = __shfl_xor_sync(0xffffffffu, vi, RM);
+    accr = fmaf(vr, wr, fmaf(-vi, wi, accr));
+    acci = fmaf(vr, wi, fmaf(vi, wr, acci));
+  }
+  cp_wait<0>();
+#pragma unroll
+  for (int o = RM / 2; o > 0; o >>= 1) {
+    accr += __shfl_xor_sync(0xffffffffu, accr, o);
+    acci += __shfl_xor_sync(0xffffffffu, acci, o);
+  }
+  if (m == 0 && side == 0 && s < a.S) {
+    double *dst = a.partial + 2 * ((int64_t)g * a.S + s);
+    dst[0] = (double)accr;
+    dst[1] = (double)acci;
+  }
+}
+
 // Leaf contraction for large bitstring counts.  One co-resident wave of CTAs; CTA b
 // owns bitstrings [b * per_cta, (b + 1) * per_cta), and every CTA walks all parents in
 // the same order, so the parents being read at any time are few and stay in L2 however
@@ -681,6 +801,22 @@ cudaError_t leaf_reg_dispatch(const LeafArgs &a, cudaStream_t st) {
       kernel<<<grid, 128, smem, st>>>(a);
       return cudaGetLastError();
     };
+    auto go_pair = [&](auto kernel, int rmv) -> cudaError_t {
+      dim3 gp((unsigned)((a.S * 2 * rmv + 127) / 128), (unsigned)a.num_groups);
+      const size_t smem = leaf_pair_ring_bytes(CB, rmv);
+      cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+      kernel<<<gp, 128, smem, st>>>(a);
+      return cudaGetLastError();
+    };
+    if constexpr (CB >= 2) {
+      switch (rm) {
+        case 1: return go_pair(leaf_contract_pair_kernel<CB, 1>, 1);
+        case 2: return go_pair(leaf_contract_pair_kernel<CB, 2>, 2);
+        case 4: return go_pair(leaf_contract_pair_kernel<CB, 4>, 4);
+        default: return go_pair(leaf_contract_pair_kernel<CB, 8>, 8);
+      }
+    }
     switch (rm) {
       case 1: return go(leaf_contract_async_kernel<CB, 1>, 1);
       case 2: return go(leaf_contract_async_kernel<CB, 2>, 2);

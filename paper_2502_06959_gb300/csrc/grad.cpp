@@ -2,11 +2,14 @@
 // requested bitstrings, given the upstream gradient g_s = dL/dRe amp_s + i dL/dIm amp_s.
 //
 //   * rotations inside one half (Sec. II-B: every path simulates both halves): the
-//     whole path tree is simulated forward with every node state kept, the leaf
-//     cotangents are formed from the other half's leaf states, and the tree is walked
-//     back level by level (adjoint.cu): unitary ops are undone on the stored states,
-//     cotangents are pulled back through G^T, and at every level the children's
-//     cotangents reach their parent through the transposed Schmidt factors;
+//     path tree is simulated forward, the leaf cotangents are formed from the other
+//     half's leaf states, and the tree is walked back level by level (adjoint.cu):
+//     unitary ops are undone on the recomputed states, cotangents are pulled back
+//     through G^T, and at every level the children's cotangents reach their parent
+//     through the transposed Schmidt factors.  Only levels 0..k0 are kept for every
+//     node; the deeper levels are recomputed per chunk (the subtree of one level-k0
+//     node) and walked back before the next chunk, with k0 the smallest level whose
+//     layout fits the caller's workspace, so memory follows the workspace, not the tree;
 //   * rotations inside a jointly cut block: the amplitude is linear in the block
 //     matrix A (Sec. IV-A, eq. equ-schmidt-decompostion-res), so d amp / d theta_j is the
 //     HSF sum with A replaced by dA/dtheta_j (product rule over the block's gates tied
@@ -34,13 +37,24 @@ namespace {
 
 size_t a256(size_t x) { return (x + 255) / 256 * 256; }
 
+// Gradient workspace: levels 0..k0 of the path tree are held for every node (the "upper"
+// tree); each level-k0 node's subtree (levels k0+1..B, a chunk of below[k0] paths) is
+// recomputed forward, contracted with the leaf cotangents and walked back on its own, so
+// only one chunk's deeper levels are held at a time.  k0 = 0 holds the whole tree once.
 struct GradLayout {
+  int k0 = 0;
   std::vector<size_t> psi[2], mu[2];   // per level
   size_t off_index = 0, off_grad = 0, off_amp = 0, off_run = 0, total = 0;
 };
 
-GradLayout grad_layout(const hsf_plan &p, size_t num) {
+// nodes of level k held in the workspace for chunk root level k0
+uint64_t held_nodes(const hsf_plan &p, int k0, int k) {
+  return k <= k0 ? p.num_paths / p.below[k] : p.below[k0] / p.below[k];
+}
+
+GradLayout grad_layout(const hsf_plan &p, size_t num, int k0) {
   GradLayout L;
+  L.k0 = k0;
   const size_t csz = p.precision == HSF_PREC_C64 ? 8 : 16;
   const int B = (int)p.blocks.size();
   size_t off = 0;
@@ -49,7 +63,7 @@ GradLayout grad_layout(const hsf_plan &p, size_t num) {
     L.mu[s].resize(B + 1);
     const size_t sb = ((size_t)1 << p.gside[s].h) * csz;
     for (int k = 0; k <= B; ++k) {
-      const size_t nodes = (size_t)(p.num_paths / p.below[k]);
+      const size_t nodes = (size_t)held_nodes(p, k0, k);
       L.psi[s][k] = off;
       off += a256(nodes * sb);
       L.mu[s][k] = off;
@@ -161,29 +175,42 @@ hsf_status ensure_grad(hsf_plan &p) {
   return HSF_OK;
 }
 
-hsf_status grad_need(hsf_plan &p, size_t num, size_t *bytes) {
+// The layout for a workspace budget (0: the whole tree at once) and the bytes it needs,
+// including the forward-run workspace of the derivative plans of cut-block angles.
+hsf_status grad_plan_layout(hsf_plan &p, size_t num, size_t budget, GradLayout *out, size_t *bytes) {
   hsf_status st = ensure_grad(p);
   if (st != HSF_OK) return st;
-  GradLayout L = grad_layout(p, num);
-  size_t run = 0;
-  for (auto &d : p.dplans) {
-    size_t b = 0;
-    st = hsf_workspace_size(d.plan, num, 0, 0, &b);
-    if (st != HSF_OK) return st;
-    run = std::max(run, b);
+  const int B = (int)p.blocks.size();
+  const int kmax = std::max(0, B - 1);
+  for (int k0 = 0; k0 <= kmax; ++k0) {
+    GradLayout L = grad_layout(p, num, k0);
+    if (budget && L.total > budget) continue;
+    size_t run = 0;
+    bool fits = true;
+    for (auto &d : p.dplans) {
+      size_t b = 0;
+      st = hsf_workspace_size(d.plan, num, 0, budget ? budget - L.total : 0, &b);
+      if (st == HSF_ENOMEM) { fits = false; break; }
+      if (st != HSF_OK) return st;
+      run = std::max(run, b);
+    }
+    if (!fits || (budget && L.total + run > budget)) continue;
+    *out = L;
+    *bytes = L.total + run;
+    return HSF_OK;
   }
-  *bytes = L.total + run;
-  return HSF_OK;
+  return set_error(HSF_ENOMEM, "no gradient layout fits a %zu-byte workspace", budget);
 }
 
 }  // namespace
 
 extern "C" {
 
-hsf_status hsf_grad_workspace_size(hsf_plan *p, size_t num, size_t *bytes) {
+hsf_status hsf_grad_workspace_size(hsf_plan *p, size_t num, size_t budget, size_t *bytes) {
   if (!p || !bytes) return set_error(HSF_EINVAL, "NULL argument");
   if (num == 0) return set_error(HSF_EINVAL, "gradients need at least one bitstring");
-  return grad_need(*p, num, bytes);
+  GradLayout L;
+  return grad_plan_layout(*p, num, budget, &L, bytes);
 }
 
 hsf_status hsf_grad(hsf_plan *p, const uint64_t *bits, size_t num, const void *gout, double *grad,
@@ -194,13 +221,15 @@ hsf_status hsf_grad(hsf_plan *p, const uint64_t *bits, size_t num, const void *g
   if (num_params < p->num_params)
     return set_error(HSF_EINVAL, "num_params %d < %d angles used by the circuit", num_params, p->num_params);
   size_t need = 0;
-  hsf_status st = grad_need(*p, num, &need);
+  GradLayout L;
+  hsf_status st = grad_plan_layout(*p, num, ws_bytes, &L, &need);
   if (st != HSF_OK) return st;
   if (ws_bytes < need) return set_error(HSF_ENOMEM, "gradient workspace needs %zu bytes, got %zu", need, ws_bytes);
-  const GradLayout L = grad_layout(*p, num);
   cudaStream_t stm = (cudaStream_t)stream;
   unsigned char *ws = (unsigned char *)workspace;
   const int B = (int)p->blocks.size();
+  const int k0 = L.k0;
+  const size_t csz = p->precision == HSF_PREC_C64 ? 8 : 16;
   double *gacc = (double *)(ws + L.off_grad);
   CUDA_TRY(launch_zero_bytes(gacc, a256((size_t)std::max(1, p->num_params) * 8), stm));
   // storage indices of the bitstrings under the gradient programs' storage order
@@ -218,102 +247,151 @@ hsf_status hsf_grad(hsf_plan *p, const uint64_t *bits, size_t num, const void *g
     ix.ib = ib;
     CUDA_TRY(launch_index_prep(ix, stm));
   }
-  // forward over the whole tree, every level kept
-  for (int s = 0; s < 2; ++s) {
+  // forward sweep of level k of side s over `nodes` nodes starting at level-global node_lo,
+  // from the parent buffer par whose first node is level-global parent_lo
+  auto forward = [&](int s, int k, void *dst, const void *par, int64_t node_lo, int64_t parent_lo,
+                     int64_t nodes) -> hsf_status {
     const SideH &sd = p->gside[s];
-    for (int k = 0; k <= B; ++k) {
-      const int64_t nodes = (int64_t)(p->num_paths / p->below[k]);
-      void *dst = ws + L.psi[s][k];
-      const void *par = k > 0 ? (const void *)(ws + L.psi[s][k - 1]) : nullptr;
-      const LevelH &lv = sd.levels[k];
-      for (size_t pi = 0; pi < lv.passes.size(); ++pi) {
-        const PassH &ps = lv.passes[pi];
-        SweepArgs a{};
-        a.ops = (const DevOp *)((unsigned char *)p->dev_gtable + ps.ops_off);
-        a.num_ops = ps.num_ops;
-        a.h = sd.h;
-        a.mats = (unsigned char *)p->dev_gtable + ps.mats_off;
-        a.read_parent = (pi == 0 && k > 0) ? 1 : 0;
-        a.init_zero = (pi == 0 && k == 0) ? 1 : 0;
-        a.src = a.read_parent ? par : dst;
-        a.dst = dst;
-        a.active_mask = ps.active;
-        a.t = ps.t;
-        a.radix = (int32_t)p->radix[k];
-        a.node_lo = 0;
-        a.parent_lo = 0;
-        a.num_nodes = nodes;
-        a.tiles_per_node = 1 << (sd.h - ps.t);
-        CUDA_TRY(launch_sweep(a, p->precision, stm));
-        g_launches++;
-      }
+    const LevelH &lv = sd.levels[k];
+    for (size_t pi = 0; pi < lv.passes.size(); ++pi) {
+      const PassH &ps = lv.passes[pi];
+      SweepArgs a{};
+      a.ops = (const DevOp *)((unsigned char *)p->dev_gtable + ps.ops_off);
+      a.num_ops = ps.num_ops;
+      a.h = sd.h;
+      a.mats = (unsigned char *)p->dev_gtable + ps.mats_off;
+      a.read_parent = (pi == 0 && k > 0) ? 1 : 0;
+      a.init_zero = (pi == 0 && k == 0) ? 1 : 0;
+      a.src = a.read_parent ? par : dst;
+      a.dst = dst;
+      a.active_mask = ps.active;
+      a.t = ps.t;
+      a.radix = (int32_t)p->radix[k];
+      a.node_lo = node_lo;
+      a.parent_lo = parent_lo;
+      a.num_nodes = nodes;
+      a.tiles_per_node = 1 << (sd.h - ps.t);
+      CUDA_TRY(launch_sweep(a, p->precision, stm));
+      g_launches++;
     }
-  }
-  // leaf cotangents
-  const size_t csz = p->precision == HSF_PREC_C64 ? 8 : 16;
-  for (int s = 0; s < 2; ++s) {
-    const size_t bytes = (size_t)p->num_paths * ((size_t)1 << p->gside[s].h) * csz;
-    CUDA_TRY(launch_zero_bytes(ws + L.mu[s][B], bytes, stm));
-  }
-  {
+    return HSF_OK;
+  };
+  // reverse sweep of level k (rotation gradients, uncomputing the unitary ops in place)
+  auto backward = [&](int s, int k, void *psi, void *mu, int64_t nodes) -> hsf_status {
+    const SideH &sd = p->gside[s];
+    const LevelH &lv = sd.levels[k];
+    for (int pi = (int)lv.passes.size() - 1; pi >= 0; --pi) {
+      const PassH &ps = lv.passes[pi];
+      AdjointArgs a{};
+      a.ops = (const DevOp *)((unsigned char *)p->dev_gtable + ps.ops_off);
+      a.num_ops = ps.num_ops;
+      a.first_op = (pi == 0 && k > 0) ? 1 : 0;
+      a.mats = (unsigned char *)p->dev_gtable + ps.mats_off;
+      a.psi = psi;
+      a.mu = mu;
+      a.h = sd.h;
+      a.t = ps.t;
+      a.active_mask = ps.active;
+      a.num_nodes = nodes;
+      a.tiles_per_node = 1 << (sd.h - ps.t);
+      a.grad = gacc;
+      CUDA_TRY(launch_adjoint(a, p->precision, stm));
+      g_launches++;
+    }
+    return HSF_OK;
+  };
+  // children (level k, first level-global child_lo) to parents (level k-1)
+  auto pullback = [&](int s, int k, const void *mu_child, void *mu_parent, int64_t parent_lo, int64_t parents,
+                      int64_t child_lo, int64_t children) -> hsf_status {
+    const SideH &sd = p->gside[s];
+    const OpH &f = sd.levels[k].ops[0];
+    PullbackArgs pb{};
+    pb.mu_child = mu_child;
+    pb.mu_parent = mu_parent;
+    pb.factor = (unsigned char *)p->dev_factors + p->factor_off[s][k];
+    pb.h = sd.h;
+    pb.nf = f.nq;
+    for (int x = 0; x < f.nq; ++x) pb.fq[x] = f.q[x];
+    pb.radix = (int32_t)p->radix[k];
+    pb.parent_lo = parent_lo;
+    pb.child_lo = child_lo;
+    pb.num_parents = parents;
+    pb.num_children = children;
+    CUDA_TRY(launch_factor_pullback(pb, p->precision, stm));
+    g_launches++;
+    return HSF_OK;
+  };
+#define GTRY(x)                              \
+  do {                                       \
+    hsf_status s_ = (x);                     \
+    if (s_ != HSF_OK) return s_;             \
+  } while (0)
+  // upper tree, every node: levels 0..k0 (all of it when there is no block)
+  const int top = B == 0 ? 0 : k0;
+  for (int s = 0; s < 2; ++s)
+    for (int k = 0; k <= top; ++k)
+      GTRY(forward(s, k, ws + L.psi[s][k], k > 0 ? ws + L.psi[s][k - 1] : nullptr, 0, 0,
+                   (int64_t)held_nodes(*p, k0, k)));
+  auto leaf_cot = [&](const void *pa, const void *pb_, void *ma, void *mb, int64_t paths) -> hsf_status {
+    for (int s = 0; s < 2; ++s)
+      CUDA_TRY(launch_zero_bytes(s == 0 ? ma : mb, (size_t)paths * ((size_t)1 << p->gside[s].h) * csz, stm));
     LeafCotArgs lc{};
-    lc.psi_a = ws + L.psi[0][B];
-    lc.psi_b = ws + L.psi[1][B];
-    lc.mu_a = ws + L.mu[0][B];
-    lc.mu_b = ws + L.mu[1][B];
+    lc.psi_a = pa;
+    lc.psi_b = pb_;
+    lc.mu_a = ma;
+    lc.mu_b = mb;
     lc.ha = p->na;
     lc.hb = p->nb;
-    lc.paths = (int64_t)p->num_paths;
+    lc.paths = paths;
     lc.ia = ia;
     lc.ib = ib;
     lc.gout = (const double *)gout;
     lc.S = (int64_t)num;
     CUDA_TRY(launch_leaf_cot(lc, p->precision, stm));
     g_launches++;
-  }
-  // backward over the tree
-  for (int k = B; k >= 0; --k) {
-    for (int s = 0; s < 2; ++s) {
-      const SideH &sd = p->gside[s];
-      const int64_t nodes = (int64_t)(p->num_paths / p->below[k]);
-      const LevelH &lv = sd.levels[k];
-      for (int pi = (int)lv.passes.size() - 1; pi >= 0; --pi) {
-        const PassH &ps = lv.passes[pi];
-        AdjointArgs a{};
-        a.ops = (const DevOp *)((unsigned char *)p->dev_gtable + ps.ops_off);
-        a.num_ops = ps.num_ops;
-        a.first_op = (pi == 0 && k > 0) ? 1 : 0;
-        a.mats = (unsigned char *)p->dev_gtable + ps.mats_off;
-        a.psi = ws + L.psi[s][k];
-        a.mu = ws + L.mu[s][k];
-        a.h = sd.h;
-        a.t = ps.t;
-        a.active_mask = ps.active;
-        a.num_nodes = nodes;
-        a.tiles_per_node = 1 << (sd.h - ps.t);
-        a.grad = gacc;
-        CUDA_TRY(launch_adjoint(a, p->precision, stm));
-        g_launches++;
-      }
-      if (k > 0) {
-        const OpH &f = lv.ops[0];
-        PullbackArgs pb{};
-        pb.mu_child = ws + L.mu[s][k];
-        pb.mu_parent = ws + L.mu[s][k - 1];
-        pb.factor = (unsigned char *)p->dev_factors + p->factor_off[s][k];
-        pb.h = sd.h;
-        pb.nf = f.nq;
-        for (int x = 0; x < f.nq; ++x) pb.fq[x] = f.q[x];
-        pb.radix = (int32_t)p->radix[k];
-        pb.parent_lo = 0;
-        pb.child_lo = 0;
-        pb.num_parents = (int64_t)(p->num_paths / p->below[k - 1]);
-        pb.num_children = nodes;
-        CUDA_TRY(launch_factor_pullback(pb, p->precision, stm));
-        g_launches++;
-      }
+    return HSF_OK;
+  };
+  if (B == 0) {
+    GTRY(leaf_cot(ws + L.psi[0][0], ws + L.psi[1][0], ws + L.mu[0][0], ws + L.mu[1][0], 1));
+  } else {
+    // chunks: the subtree of every level-k0 node, levels k0+1..B recomputed from it
+    const int64_t chunks = (int64_t)held_nodes(*p, k0, k0);
+    const size_t sbytes[2] = {((size_t)1 << p->gside[0].h) * csz, ((size_t)1 << p->gside[1].h) * csz};
+    for (int64_t c = 0; c < chunks; ++c) {
+      for (int s = 0; s < 2; ++s)
+        for (int k = k0 + 1; k <= B; ++k) {
+          const int64_t nk = (int64_t)held_nodes(*p, k0, k);
+          const bool from_upper = k == k0 + 1;
+          const int64_t plo = from_upper ? 0 : c * (int64_t)held_nodes(*p, k0, k - 1);
+          GTRY(forward(s, k, ws + L.psi[s][k], ws + L.psi[s][k - 1], c * nk, plo, nk));
+        }
+      GTRY(leaf_cot(ws + L.psi[0][B], ws + L.psi[1][B], ws + L.mu[0][B], ws + L.mu[1][B],
+                    (int64_t)held_nodes(*p, k0, B)));
+      for (int k = B; k > k0; --k)
+        for (int s = 0; s < 2; ++s) {
+          const int64_t nk = (int64_t)held_nodes(*p, k0, k);
+          GTRY(backward(s, k, ws + L.psi[s][k], ws + L.mu[s][k], nk));
+          if (k - 1 > k0) {
+            const int64_t np = (int64_t)held_nodes(*p, k0, k - 1);
+            GTRY(pullback(s, k, ws + L.mu[s][k], ws + L.mu[s][k - 1], c * np, np, c * nk, nk));
+          } else {
+            // into the chunk root's cotangent, held with the upper tree
+            GTRY(pullback(s, k, ws + L.mu[s][k], ws + L.mu[s][k0] + (size_t)c * sbytes[s], c, 1, c * nk, nk));
+          }
+        }
     }
   }
+  // upper tree, backwards
+  for (int k = top; k >= 0; --k)
+    for (int s = 0; s < 2; ++s) {
+      const int64_t nk = (int64_t)held_nodes(*p, k0, k);
+      GTRY(backward(s, k, ws + L.psi[s][k], ws + L.mu[s][k], nk));
+      if (k > 0) {
+        const int64_t np = (int64_t)held_nodes(*p, k0, k - 1);
+        GTRY(pullback(s, k, ws + L.mu[s][k], ws + L.mu[s][k - 1], 0, np, 0, nk));
+      }
+    }
+#undef GTRY
   // angles inside cut blocks: HSF sums with the block replaced by its derivative
   for (auto &d : p->dplans) {
     double *ampd = (double *)(ws + L.off_amp);

@@ -108,7 +108,8 @@ SIGNATURES = {
     "hsf_tune": (ctypes.c_int, [ctypes.POINTER(hsf_circuit), ctypes.c_int32, ctypes.POINTER(hsf_blocks),
                                 ctypes.POINTER(hsf_plan_opts), ctypes.c_size_t, ctypes.c_void_p, ctypes.c_uint64,
                                 ctypes.c_char_p, ctypes.c_void_p, ctypes.c_size_t]),
-    "hsf_grad_workspace_size": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]),
+    "hsf_grad_workspace_size": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_size_t, ctypes.c_size_t,
+                                               ctypes.POINTER(ctypes.c_size_t)]),
     "hsf_grad": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p,
                                 ctypes.c_int32, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
     "hsf_set_allocator": (None, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
@@ -354,9 +355,9 @@ def hsf_run_static(plan: int, bitstrings_ptr: int, num: int, window: int, path_b
                                          path_end, out_ptr, stream or None))
 
 
-def hsf_grad_workspace_size(plan: int, num_bitstrings: int) -> int:
+def hsf_grad_workspace_size(plan: int, num_bitstrings: int, budget: int = 0) -> int:
     out = ctypes.c_size_t()
-    _check(load_library().hsf_grad_workspace_size(plan, num_bitstrings, ctypes.byref(out)))
+    _check(load_library().hsf_grad_workspace_size(plan, num_bitstrings, budget, ctypes.byref(out)))
     return out.value
 
 
@@ -508,13 +509,16 @@ class Plan:
             hsf_sync(self.handle, st.cuda_stream)
         return out
 
-    def grad(self, bitstrings, gout, num_params: int = 0, stream=None):
+    def grad(self, bitstrings, gout, num_params: int = 0, stream=None, budget: int = 0):
         """dL/dtheta (float64 CUDA tensor) for the upstream gradient gout (complex128,
-        one per bitstring)."""
+        one per bitstring).  The workspace is sized for `budget` bytes (0: half the free
+        device memory); the library then recomputes forward states per path chunk."""
         import torch
         num = int(bitstrings.numel())
         num_params = max(num_params, int(self.info["num_params"]))
-        need = hsf_grad_workspace_size(self.handle, num)
+        if budget == 0:
+            budget = int(torch.cuda.mem_get_info()[0] * 0.5)
+        need = hsf_grad_workspace_size(self.handle, num, budget)
         ws = torch.empty(max(need, 256), dtype=torch.uint8, device="cuda")
         g = torch.empty(max(num_params, 1), dtype=torch.float64, device="cuda")
         st = stream if stream is not None else torch.cuda.current_stream()

@@ -48,6 +48,9 @@ def main():
     P = int(np.prod([len(d["sigma"]) for d in dec]))
     cores = os.cpu_count() or 1
     edges = np.linspace(0, P, cores + 1).astype(int)
+    # one BLAS thread per worker process: the pool already uses every core
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[v] = "1"
     t0 = time.time()
     with mp.get_context("spawn").Pool(cores) as pool:
         parts = pool.map(_part, [(int(edges[i]), int(edges[i + 1]), idx) for i in range(cores)])

@@ -119,3 +119,88 @@ def test_c4_qaoa_gradient_full_size():
         tm = pr.params.copy(); tm[j] -= h
         fd = (O.loss_from_amplitudes(amps(tp)) - O.loss_from_amplitudes(amps(tm))) / (2 * h)
         assert abs(g[j] - fd) <= 2e-4 * np.max(np.abs(g)) + 1e-6 * abs(fd), (j, g[j], fd)
+
+
+def gpu_grad_budget(pr, bits, theta, prec, budget):
+    import torch
+    from paper_2502_06959_gb300 import hsf
+    plan = hsf.Plan(pr.n, pr.gates, pr.cut, pr.blocks, precision=prec, angles=theta)
+    b = torch.from_numpy(np.asarray(bits, dtype=np.uint64).view(np.int64)).cuda()
+    amps = plan.run(b)
+    need = hsf.hsf_grad_workspace_size(plan.handle, b.numel(), budget)
+    ws = torch.empty(need, dtype=torch.uint8, device="cuda")
+    g = torch.empty(len(theta), dtype=torch.float64, device="cuda")
+    gout = (2 * amps).contiguous()
+    st = torch.cuda.current_stream()
+    hsf.hsf_grad(plan.handle, b.data_ptr(), b.numel(), gout.data_ptr(), g.data_ptr(), len(theta), ws.data_ptr(),
+                 need, st.cuda_stream)
+    hsf.hsf_sync(plan.handle, st.cuda_stream)
+    out = g.cpu().numpy()
+    plan.close()
+    return out, need
+
+
+def test_chunked_adjoint_equals_whole_tree_and_fd():
+    """Forward states recomputed per subtree chunk (small workspace) give the gradient of
+    the whole-tree layout, and both match the oracle's central differences."""
+    pr = mixed_circuit(12, 5, 4)
+    bits = W.random_bitstrings(np.random.default_rng(4), pr.n, 50)
+    g0, full = gpu_grad_budget(pr, bits, pr.params, "c128", 0)
+    g1, small = gpu_grad_budget(pr, bits, pr.params, "c128", full // 3)
+    assert small < full
+    assert np.max(np.abs(g1 - g0)) <= 1e-12 * np.max(np.abs(g0))
+    ref = fd_grad(pr, bits, pr.params, schrodinger_at(pr, bits))
+    assert np.max(np.abs(g1 - ref)) <= 1e-7 * np.max(np.abs(ref))
+
+
+def test_c4_all_angles_against_stored_fd():
+    """All 8 angles of the n = 28 QAOA workload (1024 bitstrings): the complex128 adjoint
+    within 1e-6 of max|g| of the stored FP64 central differences (oracle HSF path sum,
+    tests/golden/c4_fd_gradient.json), the complex64 adjoint within 1e-4."""
+    import json
+    import os
+    rec = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "c4_fd_gradient.json")))
+    pr = W.workload_c4()
+    assert np.allclose(rec["theta"], pr.params, rtol=0, atol=0)
+    ref = np.array(rec["grad_richardson"])
+    assert rec["fd_error_bound"] <= 1e-3 * np.max(np.abs(ref))
+    scale = np.max(np.abs(ref))
+    g128 = gpu_grad(pr, pr.bitstrings, pr.params, "c128")
+    assert np.max(np.abs(g128 - ref)) <= 1e-6 * scale, (g128, ref)
+    g64 = gpu_grad(pr, pr.bitstrings, pr.params, "c64")
+    assert np.max(np.abs(g64 - ref)) <= 1e-4 * scale, (g64, ref)
+
+
+def test_c2_shaped_gradient_in_the_run_workspace():
+    """n = 30, 8 jointly cut blocks, 65536 paths: angles on every block's RZZ gates (one
+    shared angle) and on in-half RY rotations.  The gradient runs in a workspace no
+    larger than the forward run's (the whole tree would need ~90 GB in complex64), and
+    matches central differences of the library's own complex128 forward."""
+    import torch
+    from paper_2502_06959_gb300 import hsf
+    pr = W.workload_c2(num_bitstrings=256)
+    gates = list(pr.gates)
+    for gi in sorted(set(i for b in pr.blocks for i in b)):
+        if gates[gi].kind == "rzz":
+            gates[gi] = Gate("rzz", gates[gi].qubits, param=gates[gi].param, param_id=0)
+    ry = [i for i, g in enumerate(gates) if g.kind == "matrix" and len(g.qubits) == 1
+          and not any(i in b for b in pr.blocks)]
+    rng = np.random.default_rng(5)
+    for j, gi in enumerate(rng.choice(ry, size=6, replace=False)):
+        gates[gi] = Gate("ry", gates[gi].qubits, param=0.0, param_id=1 + j % 2)
+    theta = np.array([0.7, 1.3, -0.4])
+    q = W.Problem(pr.n, gates, pr.cut, pr.blocks, num_params=3, params=theta, bitstrings=pr.bitstrings)
+    plan = hsf.Plan(q.n, q.gates, q.cut, q.blocks, precision="c128", angles=theta)
+    run_ws = hsf.hsf_workspace_size(plan.handle, 256, 0, int(torch.cuda.mem_get_info()[0] * 0.25))
+    plan.close()
+    g, need = gpu_grad_budget(q, q.bitstrings, theta, "c128", run_ws)
+    assert need <= run_ws
+
+    def loss(th):
+        p = hsf.Plan(q.n, q.gates, q.cut, q.blocks, precision="c128", angles=th)
+        b = torch.from_numpy(q.bitstrings.view(np.int64)).cuda()
+        v = float((p.run(b).abs() ** 2).sum())
+        p.close()
+        return v
+    fd = O.fd_gradient(loss, theta, h=1e-5)
+    assert np.max(np.abs(g - fd)) <= 1e-6 * np.max(np.abs(fd)), (g, fd)

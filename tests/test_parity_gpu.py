@@ -110,7 +110,9 @@ def test_block_svd_matches_lapack():
     for pr, blocks in _sigma_cases():
         blocks = pr.blocks if blocks is None else blocks
         dec = O.decompose_blocks(pr.n, pr.gates, pr.cut, blocks)
-        plan = H().Plan(pr.n, pr.gates, pr.cut, blocks, precision="c128")
+        # the device SVD itself: cascade blocks would otherwise get closed-form terms,
+        # whose weights are not the singular values
+        plan = H().Plan(pr.n, pr.gates, pr.cut, blocks, precision="c128", flags=H().FLAG_SVD_BLOCKS)
         for k, d in enumerate(dec):
             s = plan.sigma(k)
             assert len(s) == len(d["sigma"])
