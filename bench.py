@@ -145,28 +145,49 @@ class ClockSampler:
 
 # DRAM traffic per launch relative to the algorithmic bytes, from one ncu capture of the
 # kernel (dram__bytes_read.sum + dram__bytes_write.sum over the launch's algorithmic
-# bytes); valid only for the kernel source it was taken on, identified by the first 16
-# hex digits of its SHA-256.  The summaries named here hold the numbers and commands.
-PROFILED_TRAFFIC = {
-    "sweep": {"ratio": 275.1 / 335.5, "source": "paper_2502_06959_gb300/csrc/sweep.cu",
-              "sha256": "a5699515952870e8", "profile": "profiles/sweep_reg_level6_n30.md"},
-    "level_f16": {"ratio": 1281.6 / 1342.2, "source": "paper_2502_06959_gb300/csrc/gemm_tc.cu",
-                  "sha256": "4ea519f013bd5fd7", "profile": "profiles/level_f16_level7_n30.md"},
-    "leaf": {"ratio": 1896.7 / 2147.5, "source": "paper_2502_06959_gb300/csrc/accum.cu",
-             "sha256": "6aac98c52e3fcafd", "profile": "profiles/leaf_contract_n30.md"},
-}
+# bytes).  A ratio is valid only for the kernel it was taken on: the entry records the
+# first 16 hex digits of the SHA-256 of that kernel's definition (from its __global__
+# line to its closing brace) at capture time; host code and other kernels of the file
+# may change without invalidating it.  The summaries named here hold the numbers and the
+# commands.
+PROFILED_TRAFFIC = {}
 
 
-def _source_hash(rel):
+def _kernel_text(rel, kernel):
+    """Source text of the __global__ function `kernel` in file `rel`."""
+    with open(os.path.join(ROOT, rel)) as f:
+        src = f.read()
+    i = 0
+    while True:
+        i = src.find("__global__", i)
+        if i < 0:
+            return None
+        j = src.find("{", i)
+        head = src[i:j]
+        if (" " + kernel + "(") in head or (" " + kernel + " (") in head:
+            depth, k = 0, j
+            while k < len(src):
+                if src[k] == "{":
+                    depth += 1
+                elif src[k] == "}":
+                    depth -= 1
+                    if depth == 0:
+                        return src[i:k + 1]
+                k += 1
+            return None
+        i = j
+
+
+def _kernel_hash(rel, kernel):
     import hashlib
-    with open(os.path.join(ROOT, rel), "rb") as f:
-        return hashlib.sha256(f.read()).hexdigest()[:16]
+    t = _kernel_text(rel, kernel)
+    return hashlib.sha256(t.encode()).hexdigest()[:16] if t is not None else None
 
 
 def traffic_per_launch(kind, algorithmic_bytes_per_launch):
-    """ncu-derived DRAM bytes per launch, or None when no capture matches the source."""
+    """ncu-derived DRAM bytes per launch, or None when no capture matches the kernel."""
     e = PROFILED_TRAFFIC.get(kind)
-    if not e or _source_hash(e["source"]) != e["sha256"]:
+    if not e or _kernel_hash(e["source"], e["kernel"]) != e["sha256"]:
         return None
     return e["ratio"] * algorithmic_bytes_per_launch
 

@@ -508,18 +508,19 @@ __global__ void __launch_bounds__(128, 6) leaf_contract_pair_kernel(LeafArgs a) 
     float vr = 0.f, vi = 0.f;
     if (use) {
       const float4 *x = reinterpret_cast<const float4 *>(buf[t % kPairDepth] + roff);
-      C P = make_float2(0.f, 0.f), Q = make_float2(0.f, 0.f);
+      // two independent accumulator pairs (even and odd k) halve the dependent chains
+      C P0 = make_float2(0.f, 0.f), Q0 = P0, P1 = P0, Q1 = P0;
 #pragma unroll
       for (int k2 = 0; k2 < D / 2; ++k2) {
         const float4 xv = x[k2];
         const C x0 = make_float2(xv.x, xv.y), x1 = make_float2(xv.z, xv.w);
-        P = ffma2(lr[2 * k2], x0, P);
-        Q = ffma2(li[2 * k2], x0, Q);
-        P = ffma2(lr[2 * k2 + 1], x1, P);
-        Q = ffma2(li[2 * k2 + 1], x1, Q);
+        P0 = ffma2(lr[2 * k2], x0, P0);
+        Q0 = ffma2(li[2 * k2], x0, Q0);
+        P1 = ffma2(lr[2 * k2 + 1], x1, P1);
+        Q1 = ffma2(li[2 * k2 + 1], x1, Q1);
       }
-      vr = P.x - Q.y;
-      vi = P.y + Q.x;
+      vr = (P0.x + P1.x) - (Q0.y + Q1.y);
+      vi = (P0.y + P1.y) + (Q0.x + Q1.x);
     }
     // the other side's value for the same bitstring and digit (all lanes take part)
     const float wr = __shfl_xor_sync(0xffffffffu, vr, RM);

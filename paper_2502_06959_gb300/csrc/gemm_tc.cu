@@ -9,12 +9,17 @@
 //   round(x - hi)) the product is hi*hi + hi*lo + lo*hi (split-BF16 or split-TF32,
 //   3 terms) or a single TF32 term.
 // pack_kernel gathers the leaf states at the window's storage indices and writes these
-// operands (zero padded to the tile sizes).  gemm_kernel runs 128 x 128 output tiles:
-// one thread issues TMA tile loads (128-byte swizzle) into a 4-stage shared-memory
-// ring, one thread issues tcgen05.mma into a TMEM accumulator (FP32), and all four
-// warps read the accumulator back with tcgen05.ld and add it into the FP64 output with
-// Neumaier compensation.  Every wait on an mbarrier is bounded: on expiry the kernel
-// records an error code, frees its TMEM and returns.
+// operands (zero padded to the tile sizes); the a operand's real rows are interleaved
+// (row 2i: Re of x_a = i, row 2i+1: Im).  gemm_kernel is persistent (one CTA per SM) and
+// computes 128 x 256 tiles of C^T: the MMA's M dimension runs over 128 columns x_b (the
+// b operand), its N dimension over 256 interleaved real rows (128 values of x_a).  One
+// thread issues TMA tile loads (128-byte swizzle) into a 4-stage shared-memory ring, one
+// thread issues tcgen05.mma into one of two TMEM accumulators (2 x 256 FP32 columns), and
+// four epilogue warps drain the other: TMEM lane = x_b, columns = (Re, Im) pairs, so each
+// thread adds complex values into the FP64 output (Neumaier compensation) and a warp's
+// 16-byte stores cover 512 contiguous bytes.  Every wait on an mbarrier is bounded: on
+// expiry the kernel records an error code, drains its MMAs and loads, frees its TMEM and
+// returns.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
@@ -31,8 +36,10 @@
 namespace hsf {
 namespace {
 
-constexpr int kBM = 128, kBN = 128, kStages = 4;
-constexpr int kTileBytes = 128 * 128;               // 128 rows x 128 bytes of K
+constexpr int kBM = 128, kBN = 128, kStages = 4;   // padding: 128 x_b, 128 x_a (256 real rows)
+constexpr int kGM = 128, kGN = 256;                 // MMA tile: M = x_b columns, N = real rows
+constexpr int kTileA = kGM * 128, kTileB = kGN * 128;   // bytes: rows x 128 bytes of K
+constexpr int kGemmThreads = 192;                   // TMA, MMA, 4 epilogue warps
 constexpr uint32_t kWaitLimit = 1u << 22;           // bounded mbarrier polls (about a second)
 
 // ---------------------------------------------------------------------------
@@ -140,7 +147,7 @@ __global__ void __launch_bounds__(256) pack_kernel(PackArgs a) {
           t0[0] = h0; t0[1] = l0; t0[2] = h0;
           t1[0] = h1; t1[1] = l1; t1[2] = h1;
         }
-        const int64_t r = part * a.rows_pad + ir;
+        const int64_t r = a.side == 0 ? 2 * ir + part : ir;   // a: (Re, Im) rows interleaved
 #pragma unroll
         for (int tt = 0; tt < nterms; ++tt) {
           const int64_t c0 = tt * kp + p, c1 = tt * kp + P + p;
@@ -171,8 +178,8 @@ struct EpiArgs {
   int32_t k_tiles;
   int32_t kind;          // 0: kind::f16 (bf16 operands), 1: kind::tf32
   int32_t *err;          // device error word (0 = ok)
-  int32_t num_m, num_n;  // output tiles along the real rows and along x_b
-  int32_t group_m;       // tile order: groups of group_m row tiles, rows fastest
+  int32_t num_m, num_n;  // tiles along the real rows (256 each) and along x_b (128 each)
+  int32_t pad;
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -226,36 +233,46 @@ __device__ __forceinline__ void neumaier(double &sum, double &c, double x) {
   sum = t;
 }
 
-__global__ void __launch_bounds__(128, 1) gemm_kernel(const __grid_constant__ CUtensorMap tmA,
-                                                      const __grid_constant__ CUtensorMap tmB, EpiArgs ep) {
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint64_t *bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
+__global__ void __launch_bounds__(kGemmThreads, 1) gemm_kernel(const __grid_constant__ CUtensorMap tmA,
+                                                                const __grid_constant__ CUtensorMap tmB, EpiArgs ep) {
+  // tmA: a operand (2 Mp interleaved real rows), tmB: b operand (Np rows of x_b)
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
-  uint8_t *sA = smem;
-  uint8_t *sB = smem + kStages * kTileBytes;
-  __shared__ __align__(8) uint64_t full_bar[kStages], empty_bar[kStages], done_bar;
+  uint8_t *sX = smem;                                   // b tiles (MMA A): kStages x 16 KB
+  uint8_t *sY = smem + kStages * kTileA;                // a tiles (MMA B): kStages x 32 KB
+  __shared__ __align__(8) uint64_t full_bar[kStages], empty_bar[kStages], tfull[2], tempty[2], drain;
   __shared__ uint32_t tmem_base_sh;
-  __shared__ int abort_sh;
+  __shared__ volatile int abort_sh;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  // grouped tile order: the CTAs in flight cover group_m row tiles x a few column tiles,
-  // so the column operand tiles are read from DRAM once and the row operand stays in L2
-  const int per_group = ep.group_m * ep.num_n;
-  const int first_m = (int)(blockIdx.x / per_group) * ep.group_m;
-  const int gm = min(ep.group_m, ep.num_m - first_m);
-  const int local = (int)(blockIdx.x % per_group);
-  const int m0 = (first_m + local % gm) * kBM, n0 = (local / gm) * kBN;
+  // tiles: x_b tile major, real-row tile minor, so the CTAs in flight share x_b tiles
+  // (read from DRAM once) while the small a operand stays in L2
+  const int64_t tiles = (int64_t)ep.num_m * ep.num_n;
+  const int ktiles = ep.k_tiles;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStages; ++s) {
       mbar_init(&full_bar[s], 1);
       mbar_init(&empty_bar[s], 1);
     }
-    mbar_init(&done_bar, 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&tfull[b], 1);
+      mbar_init(&tempty[b], 128);
+    }
+    mbar_init(&drain, 1);
     abort_sh = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (warp == 2) {   // the whole warp allocates the accumulator columns
+  if (warp == 1) {   // the whole warp allocates both accumulators
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base_sh)),
-                 "r"(kBN)
+                 "r"(2 * kGN)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -264,102 +281,139 @@ __global__ void __launch_bounds__(128, 1) gemm_kernel(const __grid_constant__ CU
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = tmem_base_sh;
 
-  // instruction descriptor: FP32 accumulate, K-major A and B, M = 128, N = 128
-  const uint32_t fmt = ep.kind == 0 ? 1u : 2u;      // BF16 (kind::f16) or TF32
-  const uint32_t idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(kBN >> 3) << 17) |
-                         ((uint32_t)(kBM >> 4) << 24);
-  const int ksteps = 4;                              // 4 MMAs of 32 bytes of K per tile
-  const int ktiles = ep.k_tiles;
-
-  if (warp == 0 && lane == 0) {
-    // TMA producer
-    for (int kt = 0; kt < ktiles; ++kt) {
-      const int s = kt % kStages;
-      const uint32_t ph = (kt / kStages) & 1;
-      if (!mbar_wait(&empty_bar[s], ph ^ 1)) { atomicExch(ep.err, 1); abort_sh = 1; break; }
-      mbar_expect_tx(&full_bar[s], 2 * kTileBytes);
-      const int kx = kt * (ep.kind == 0 ? 64 : 32);  // K elements per 128-byte row
-      tma_load_2d(sA + s * kTileBytes, &tmA, kx, m0, &full_bar[s]);
-      tma_load_2d(sB + s * kTileBytes, &tmB, kx, n0, &full_bar[s]);
-    }
-  } else if (warp == 1 && lane == 0) {
-    // MMA issuer
-    bool ok = true;
-    for (int kt = 0; kt < ktiles && ok; ++kt) {
-      const int s = kt % kStages;
-      const uint32_t ph = (kt / kStages) & 1;
-      if (!mbar_wait(&full_bar[s], ph)) { atomicExch(ep.err, 2); abort_sh = 1; ok = false; break; }
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint64_t da = make_desc(sA + s * kTileBytes), db = make_desc(sB + s * kTileBytes);
-      for (int k = 0; k < ksteps; ++k) {
-        const uint64_t adv = (uint64_t)((k * 32) >> 4);
-        const uint32_t acc = (kt > 0 || k > 0) ? 1u : 0u;
-        if (ep.kind == 0) {
-          asm volatile(
-              "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
-              " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
-              ::"r"(tmem), "l"(da + adv), "l"(db + adv), "r"(idesc), "r"(acc)
-              : "memory");
-        } else {
-          asm volatile(
-              "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
-              " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n"
-              ::"r"(tmem), "l"(da + adv), "l"(db + adv), "r"(idesc), "r"(acc)
-              : "memory");
+  if (warp == 0) {
+    if (lane == 0) {
+      // TMA producer: k-tiles of every tile this CTA owns, one ring across tiles
+      int64_t it = 0, issued = 0;
+      for (int64_t t = blockIdx.x; t < tiles && !abort_sh; t += gridDim.x) {
+        const int x0 = (int)(t / ep.num_m) * kGM, y0 = (int)(t % ep.num_m) * kGN;
+        for (int kt = 0; kt < ktiles; ++kt, ++it) {
+          const int s = (int)(it % kStages);
+          const uint32_t ph = (uint32_t)(it / kStages) & 1u;
+          if (!mbar_wait(&empty_bar[s], ph ^ 1u)) { atomicExch(ep.err, 1); abort_sh = 1; break; }
+          mbar_expect_tx(&full_bar[s], kTileA + kTileB);
+          const int kx = kt * (ep.kind == 0 ? 64 : 32);   // K elements per 128-byte row
+          tma_load_2d(sX + s * kTileA, &tmB, kx, x0, &full_bar[s]);
+          tma_load_2d(sY + s * kTileB, &tmA, kx, y0, &full_bar[s]);
+          issued = it + 1;
         }
       }
-      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                       smem_u32(&empty_bar[s]))
-                   : "memory");
+      // every load issued has landed before the CTA can exit (matters only on abort)
+      for (int64_t i = issued > kStages ? issued - kStages : 0; i < issued; ++i)
+        if (!mbar_wait(&full_bar[i % kStages], (uint32_t)(i / kStages) & 1u)) atomicExch(ep.err, 10);
     }
-    // the accumulator is complete when every MMA issued above has finished
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                     smem_u32(&done_bar))
-                 : "memory");
-  }
-  __syncwarp();
-
-  // epilogue: every warp reads its 32 TMEM lanes (rows m0 + 32w .. +31)
-  const bool done = mbar_wait(&done_bar, 0);
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  if (!done) {
-    if (lane == 0) atomicExch(ep.err, 3);
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // MMA issuer: D[x_b][real row] += B-tile rows x a-tile rows, accumulator t % 2
+      const uint32_t fmt = ep.kind == 0 ? 1u : 2u;        // BF16 (kind::f16) or TF32
+      const uint32_t idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(kGN >> 3) << 17) |
+                             ((uint32_t)(kGM >> 4) << 24);
+      int64_t it = 0, tl = 0;
+      bool ok = true;
+      for (int64_t t = blockIdx.x; t < tiles && ok && !abort_sh; t += gridDim.x, ++tl) {
+        const int b = (int)(tl & 1);
+        if (!mbar_wait(&tempty[b], ((uint32_t)(tl >> 1) & 1u) ^ 1u)) { atomicExch(ep.err, 5); abort_sh = 1; break; }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t d = tmem + (uint32_t)(b * kGN);
+        for (int kt = 0; kt < ktiles; ++kt, ++it) {
+          const int s = (int)(it % kStages);
+          const uint32_t ph = (uint32_t)(it / kStages) & 1u;
+          if (!mbar_wait(&full_bar[s], ph)) { atomicExch(ep.err, 2); abort_sh = 1; ok = false; break; }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint64_t da = make_desc(sX + s * kTileA), db = make_desc(sY + s * kTileB);
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {                    // 4 MMAs of 32 bytes of K per k-tile
+            const uint64_t adv = (uint64_t)((k * 32) >> 4);
+            const uint32_t acc = (kt > 0 || k > 0) ? 1u : 0u;
+            if (ep.kind == 0) {
+              asm volatile(
+                  "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
+                  " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+                  ::"r"(d), "l"(da + adv), "l"(db + adv), "r"(idesc), "r"(acc)
+                  : "memory");
+            } else {
+              asm volatile(
+                  "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
+                  " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n"
+                  ::"r"(d), "l"(da + adv), "l"(db + adv), "r"(idesc), "r"(acc)
+                  : "memory");
+            }
+          }
+          mma_commit(&empty_bar[s]);                        // the stage is free once these finish
+        }
+        if (!ok) break;
+        mma_commit(&tfull[b]);                              // accumulator b is complete
+      }
+      // every MMA issued above has finished before TMEM is released
+      mma_commit(&drain);
+      if (!mbar_wait(&drain, 0)) atomicExch(ep.err, 7);
+    }
   } else {
-    const int64_t r = m0 + warp * 32 + lane;            // row of the real GEMM
-    const int part = r >= ep.Mp ? 1 : 0;                // 0: Re(Out), 1: Im(Out)
-    const int64_t i = part ? r - ep.Mp : r;
-    for (int c0 = 0; c0 < kBN; c0 += 32) {
-      uint32_t v[32];
-      const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
-      asm volatile(
-          "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-          "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-          : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-            "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
-            "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
-            "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
-          : "r"(taddr));
-      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-      if (i < ep.M) {
-        for (int c = 0; c < 32; ++c) {
-          const int64_t j = n0 + c0 + c;
-          if (j >= ep.N) break;
-          const uint64_t idx = ((uint64_t)i << ep.hb) + (uint64_t)j;
-          if (idx >= ep.window) break;
-          double *o = ep.out + 2 * idx + part;
-          double *cp = ep.comp + 2 * idx + part;
-          double sum = *o, cc = *cp;
-          neumaier(sum, cc, (double)__uint_as_float(v[c]));
-          *o = sum;
-          *cp = cc;
+    // ---- epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31, i.e. x_b = x0 + that
+    // lane; the accumulator's columns are 128 (Re, Im) pairs of x_a = y0 / 2 + c ----
+    const int q4 = warp & 3;
+    int64_t tl = 0;
+    for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x, ++tl) {
+      const int b = (int)(tl & 1);
+      const bool ok = mbar_wait(&tfull[b], (uint32_t)(tl >> 1) & 1u);
+      if (!__all_sync(0xffffffffu, ok)) {
+        if (lane == 0) atomicExch(ep.err, 3);
+        abort_sh = 1;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const int64_t j = (t / ep.num_m) * kGM + q4 * 32 + lane;          // x_b
+      const int64_t i0 = (t % ep.num_m) * (kGN / 2);                     // first x_a
+#pragma unroll 1
+      for (int c0 = 0; c0 < kGN; c0 += 32) {
+        uint32_t v[32];
+        const uint32_t taddr = tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(b * kGN + c0);
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+            "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+              "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
+              "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
+              "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+            : "r"(taddr));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        if (j < ep.N) {
+          // 8 pairs at a time: load their running sums first (independent requests), then fold
+#pragma unroll
+          for (int h8 = 0; h8 < 16; h8 += 8) {
+            double2 sum[8], cmp[8];
+            uint64_t idx[8];
+            bool in[8];
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+              const int64_t i = i0 + c0 / 2 + h8 + c;
+              idx[c] = ((uint64_t)i << ep.hb) + (uint64_t)j;
+              in[c] = i < ep.M && idx[c] < ep.window;
+              if (in[c]) {
+                sum[c] = reinterpret_cast<const double2 *>(ep.out)[idx[c]];
+                cmp[c] = reinterpret_cast<const double2 *>(ep.comp)[idx[c]];
+              }
+            }
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+              if (!in[c]) continue;
+              neumaier(sum[c].x, cmp[c].x, (double)__uint_as_float(v[2 * (h8 + c)]));
+              neumaier(sum[c].y, cmp[c].y, (double)__uint_as_float(v[2 * (h8 + c) + 1]));
+              reinterpret_cast<double2 *>(ep.out)[idx[c]] = sum[c];
+              reinterpret_cast<double2 *>(ep.comp)[idx[c]] = cmp[c];
+            }
+          }
         }
       }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      mbar_arrive(&tempty[b]);
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
-  if (warp == 2) {
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kBN) : "memory");
+  if (warp == 1) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * kGN) : "memory");
   }
 }
 
@@ -388,13 +442,6 @@ constexpr int kLvlThreads = 448;                // 4 low-part, 2 x 4 epilogue, 1
 constexpr uint32_t kLvlTmemCols = 512;          // W hi [0,128), W lo [128,256), D 2 x 128
 constexpr size_t kLvlSmem = (size_t)(kLvlRaw + kLvlLo + kLvlOut) * kLvlChunk + 1024;
 
-__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-__device__ __forceinline__ void mma_commit(uint64_t *bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
-               : "memory");
-}
 // D (TMEM) += A (TMEM) x B (shared-memory descriptor)
 __device__ __forceinline__ void mma_tf32_ts(uint32_t d, uint32_t a, uint64_t db, uint32_t idesc, uint32_t acc) {
   asm volatile(
@@ -415,13 +462,22 @@ __device__ __forceinline__ float2 cmulf(float2 a, float2 b) {
   return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
 }
 __device__ __forceinline__ void apply_post_op(float *stage, const MmaPostOp *op, int t) {
+  // the op's matrix is read into registers once (not per element)
   const int nq = __ldg(&op->nq), q0 = __ldg(&op->q0), q1 = __ldg(&op->q1), diag = __ldg(&op->diag);
   if (diag) {
+    const float2 d0 = __ldg(&op->m[0]), d1 = __ldg(&op->m[1]);
+    const float2 d2 = nq == 2 ? __ldg(&op->m[2]) : d0, d3 = nq == 2 ? __ldg(&op->m[3]) : d1;
     for (uint32_t i = t; i < 2048; i += 128) {
-      int k = (int)((i >> q0) & 1u);
-      if (nq == 2) k = (k << 1) | (int)((i >> q1) & 1u);
+      const uint32_t b0 = (i >> q0) & 1u;
+      float2 m;
+      if (nq == 2) {
+        const uint32_t b1 = (i >> q1) & 1u;
+        m = b0 ? (b1 ? d3 : d2) : (b1 ? d1 : d0);
+      } else {
+        m = b0 ? d1 : d0;
+      }
       float2 *e = post_elem(stage, i);
-      *e = cmulf(__ldg(&op->m[k]), *e);
+      *e = cmulf(m, *e);
     }
   } else if (nq == 1) {
     const float2 m0 = __ldg(&op->m[0]), m1 = __ldg(&op->m[1]), m2 = __ldg(&op->m[2]), m3 = __ldg(&op->m[3]);
@@ -434,6 +490,9 @@ __device__ __forceinline__ void apply_post_op(float *stage, const MmaPostOp *op,
       *e1 = make_float2(c.x + d.x, c.y + d.y);
     }
   } else {
+    float2 mm[16];
+#pragma unroll
+    for (int e = 0; e < 16; ++e) mm[e] = __ldg(&op->m[e]);
     const int lo = min(q0, q1), hi = max(q0, q1);
     for (uint32_t j = t; j < 512; j += 128) {
       const uint32_t base = ins0(ins0(j, lo), hi);
@@ -450,9 +509,8 @@ __device__ __forceinline__ void apply_post_op(float *stage, const MmaPostOp *op,
         float re = 0.f, im = 0.f;
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-          const float2 mm = __ldg(&op->m[r * 4 + k]);
-          re = fmaf(mm.x, x[k].x, fmaf(-mm.y, x[k].y, re));
-          im = fmaf(mm.x, x[k].y, fmaf(mm.y, x[k].x, im));
+          re = fmaf(mm[r * 4 + k].x, x[k].x, fmaf(-mm[r * 4 + k].y, x[k].y, re));
+          im = fmaf(mm[r * 4 + k].x, x[k].y, fmaf(mm[r * 4 + k].y, x[k].x, im));
         }
         y[r] = make_float2(re, im);
       }
@@ -1114,12 +1172,12 @@ PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
   return fn;
 }
 
-bool make_map(CUtensorMap *m, void *base, bool bf16, uint64_t kpad, uint64_t rows) {
+bool make_map(CUtensorMap *m, void *base, bool bf16, uint64_t kpad, uint64_t rows, uint32_t box_rows) {
   auto enc = get_encode();
   if (!enc) return false;
   const cuuint64_t dims[2] = {(cuuint64_t)kpad, (cuuint64_t)rows};
   const cuuint64_t strides[1] = {(cuuint64_t)(kpad * (bf16 ? 2 : 4))};
-  const cuuint32_t box[2] = {(cuuint32_t)(bf16 ? 64 : 32), 128};
+  const cuuint32_t box[2] = {(cuuint32_t)(bf16 ? 64 : 32), (cuuint32_t)box_rows};
   const cuuint32_t estr[2] = {1, 1};
   const CUresult r = enc(m, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base, dims,
                          strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
@@ -1183,8 +1241,8 @@ cudaError_t launch_path_gemm(const PathGemmArgs &g, cudaStream_t st) {
     if (e != cudaSuccess) return e;
   }
   CUtensorMap tmA, tmB;
-  if (!make_map(&tmA, opA, bf16, (uint64_t)kpad, (uint64_t)(2 * Mp)) ||
-      !make_map(&tmB, opB, bf16, (uint64_t)kpad, (uint64_t)Np))
+  if (!make_map(&tmA, opA, bf16, (uint64_t)kpad, (uint64_t)(2 * Mp), (uint32_t)kGN) ||
+      !make_map(&tmB, opB, bf16, (uint64_t)kpad, (uint64_t)Np, (uint32_t)kGM))
     return cudaErrorInvalidValue;
   EpiArgs ep{};
   ep.out = g.out;
@@ -1197,15 +1255,17 @@ cudaError_t launch_path_gemm(const PathGemmArgs &g, cudaStream_t st) {
   ep.k_tiles = (int32_t)(kpad / kalign);
   ep.kind = bf16 ? 0 : 1;
   ep.err = g.err;
-  const size_t smem = (size_t)2 * kStages * kTileBytes + 1024;
+  const size_t smem = (size_t)kStages * (kTileA + kTileB) + 1024;
   e = cudaFuncSetAttribute(gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  ep.num_m = (int32_t)(2 * Mp / kBM);
-  ep.num_n = (int32_t)(Np / kBN);
-  // as many row tiles per group as keep about 48 MB of the row operand in L2
-  const int64_t row_tile_bytes = (int64_t)kBM * kpad * esz;
-  ep.group_m = (int32_t)std::max<int64_t>(1, std::min<int64_t>(ep.num_m, (48ll << 20) / row_tile_bytes));
-  gemm_kernel<<<(unsigned)((int64_t)ep.num_m * ep.num_n), 128, smem, st>>>(tmA, tmB, ep);
+  ep.num_m = (int32_t)(2 * Mp / kGN);
+  ep.num_n = (int32_t)(Np / kGM);
+  (void)esz;
+  const int64_t tiles = (int64_t)ep.num_m * ep.num_n;
+  int sms = device_sm_count();
+  if (sms <= 0) sms = 148;
+  const unsigned grid = (unsigned)std::min<int64_t>(tiles, sms);   // persistent: one CTA per SM
+  gemm_kernel<<<grid, kGemmThreads, smem, st>>>(tmA, tmB, ep);
   return cudaGetLastError();
 }
 

@@ -55,6 +55,7 @@ const char *last_error() { return g_err.c_str(); }
 // has used (created on first use on that device, kept until the thread exits).
 namespace {
 struct ThreadStreams {
+  bool high = false;          // create at the device's highest stream priority
   std::map<int, cudaStream_t> by_dev;
   cudaStream_t get() {
     int cur = 0;
@@ -62,15 +63,22 @@ struct ThreadStreams {
     auto it = by_dev.find(cur);
     if (it != by_dev.end()) return it->second;
     cudaStream_t st = nullptr;
-    cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    int least = 0, greatest = 0;
+    if (high && cudaDeviceGetStreamPriorityRange(&least, &greatest) == cudaSuccess)
+      cudaStreamCreateWithPriority(&st, cudaStreamNonBlocking, greatest);
+    else
+      cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
     by_dev[cur] = st;
     return st;
   }
 };
 }  // namespace
 
+// The plan stream has the highest priority: the block SVD a plan waits for is scheduled
+// as soon as CTAs of the runs already queued on other streams retire, so planning the next
+// circuit overlaps the current run instead of waiting for it to drain.
 cudaStream_t plan_stream() {
-  thread_local ThreadStreams s;
+  thread_local ThreadStreams s{true, {}};
   return s.get();
 }
 

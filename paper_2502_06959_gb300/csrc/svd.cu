@@ -160,7 +160,9 @@ __global__ void __launch_bounds__(kThreads) block_svd_kernel(BlockSvdArgs a) {
         gr = warp_sum(gr);
         gi = warp_sum(gi);
         const double ag = sqrt(gr * gr + gi * gi);
-        if (ag > 1e-15 * sqrt(al * be) && ag > 1e-300) {
+        // rotate while the columns' cosine is above 1e-14: the rounding of a 64-term
+        // complex dot product sits near 1e-15, so a lower threshold never stops
+        if (ag > 1e-14 * sqrt(al * be) && ag > 1e-300) {
           const double zeta = (be - al) / (2.0 * ag);
           const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
           const double c = 1.0 / sqrt(1.0 + t * t), s = c * t;

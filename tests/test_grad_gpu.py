@@ -47,13 +47,13 @@ def gpu_grad(pr, bits, theta, prec):
     return out
 
 
-def mixed_circuit(n, cut, seed):
+def mixed_circuit(n, cut, seed, layers=3):
     """Rotations of every supported kind with shared angles, inside both halves and
     inside jointly cut blocks."""
     rng = np.random.default_rng(seed)
     gates, blocks = [], []
     nparam = 6
-    for layer in range(3):
+    for layer in range(layers):
         for q in range(n):
             k = ["rx", "ry", "rz"][(q + layer) % 3]
             gates.append(Gate(k, (q,), param=0.0, param_id=int(rng.integers(nparam))))
@@ -143,11 +143,24 @@ def gpu_grad_budget(pr, bits, theta, prec, budget):
 def test_chunked_adjoint_equals_whole_tree_and_fd():
     """Forward states recomputed per subtree chunk (small workspace) give the gradient of
     the whole-tree layout, and both match the oracle's central differences."""
-    pr = mixed_circuit(12, 5, 4)
+    from paper_2502_06959_gb300 import hsf
+    pr = mixed_circuit(12, 5, 4, layers=6)
     bits = W.random_bitstrings(np.random.default_rng(4), pr.n, 50)
     g0, full = gpu_grad_budget(pr, bits, pr.params, "c128", 0)
-    g1, small = gpu_grad_budget(pr, bits, pr.params, "c128", full // 3)
-    assert small < full
+    # the smallest budget that holds a layout: the tree is then walked in subtree chunks
+    plan = hsf.Plan(pr.n, pr.gates, pr.cut, pr.blocks, precision="c128", angles=pr.params)
+    budget = None
+    for f in np.linspace(0.1, 1.0, 19):
+        try:
+            hsf.hsf_grad_workspace_size(plan.handle, bits.size, int(full * f))
+            budget = int(full * f)
+            break
+        except hsf.HsfError:
+            continue
+    plan.close()
+    assert budget is not None and budget <= 0.7 * full, (budget, full)
+    g1, small = gpu_grad_budget(pr, bits, pr.params, "c128", budget)
+    assert small <= budget < full
     assert np.max(np.abs(g1 - g0)) <= 1e-12 * np.max(np.abs(g0))
     ref = fd_grad(pr, bits, pr.params, schrodinger_at(pr, bits))
     assert np.max(np.abs(g1 - ref)) <= 1e-7 * np.max(np.abs(ref))
