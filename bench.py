@@ -482,12 +482,14 @@ def path_gemm_leg(hsf, torch, g3):
         st = hsf.hsf_profile_collect(plan.handle)
         hsf.hsf_set_profiling(False)
         w = st["window"]
+        pk = st.get("pack", {"ms": 0.0})
         P = int(plan.info["num_paths"])
         M, N = -(-window // (1 << (pr.cut + 1))), min(window, 1 << (pr.cut + 1))
         useful = 8.0 * M * N * P
         err = float(np.max(np.abs(out[idx].cpu().numpy() - g3["amps"])))
         tfl = w["flops"] / (w["ms"] / 1e3) / 1e12 if w["ms"] else 0.0
-        r = {"ms": w["ms"], "paths": P, "M": M, "N": N, "useful_complex_tflops": useful / (w["ms"] / 1e3) / 1e12,
+        r = {"ms": w["ms"], "pack_ms": pk["ms"], "paths": P, "M": M, "N": N,
+             "useful_complex_tflops": useful / (w["ms"] / 1e3) / 1e12,
              "err_vs_fp64": err, "err_samples": int(idx.numel())}
         if gemm == "bf16x3":
             r.update({"bound": "tensor", "achieved": tfl, "peak": bf16_peak, "unit": "TFLOP/s",

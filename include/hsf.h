@@ -372,7 +372,8 @@ typedef enum hsf_kernel_kind {
   HSF_KERNEL_LEVEL_MMA = 6,  /* tree level as a tensor-core product per digit,
                                 TF32 parts (levels with ops after the product) */
   HSF_KERNEL_LEVEL_F16 = 7,  /* the same with FP16 parts (levels without)    */
-  HSF_NUM_KERNEL_KINDS = 8
+  HSF_KERNEL_PACK = 8,       /* split-operand packing of the tensor-core path GEMM */
+  HSF_NUM_KERNEL_KINDS = 9
 } hsf_kernel_kind;
 
 typedef struct hsf_kernel_stat {

@@ -671,7 +671,13 @@ hsf_status hsf_run(hsf_plan *p, const uint64_t *bits, size_t num, uint64_t windo
         g.mode = p->gemm_mode;
         g.err = p->dev_status;
         const double terms = p->gemm_mode == HSF_GEMM_TF32 ? 1.0 : 3.0;
-        LAUNCH(HSF_KERNEL_WINDOW, (double)np * (w.M + w.N) * csz + 64.0 * w.M * w.N,
+        const double esz = p->gemm_mode == HSF_GEMM_BF16X3 ? 2.0 : 4.0;
+        const double kcols = terms * 2.0 * (double)np;
+        // packing: the leaf rows read once, the split operands written once
+        LAUNCH(HSF_KERNEL_PACK, (double)np * (w.M + w.N) * csz + (2.0 * w.M + w.N) * kcols * esz, 0.0,
+               launch_path_pack(g, st));
+        // the GEMM: its operands read once, the FP64 output and compensation updated
+        LAUNCH(HSF_KERNEL_WINDOW, (2.0 * w.M + w.N) * kcols * esz + 64.0 * w.M * w.N,
                8.0 * terms * (double)np * w.M * w.N, launch_path_gemm(g, st));
       } else {
         LAUNCH(HSF_KERNEL_WINDOW, (double)np * (w.M + w.N) * csz + 64.0 * w.M * w.N,

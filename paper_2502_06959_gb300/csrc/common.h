@@ -158,6 +158,9 @@ struct BlockSvdArgs {
   double *yf;                    // [num_blocks][64][64][2]  Y'_m
   int32_t *sweeps_used;          // [num_blocks]; == max_sweeps: not converged
   double *residual;              // [num_blocks] max_e |U_B - sum_m X'_m (x) Y'_m| (kept terms)
+  // shared-memory layout for the launch's largest block (complex elements): U at 0, the
+  // working matrix at off_w, V at off_v; max_nw = the largest min(4^k_a, 4^k_b)
+  int32_t off_w, off_v, max_nw;
 };
 
 // Window / full output on the tensor cores (gemm_tc.cu): complex rank-P product as one
@@ -179,6 +182,9 @@ struct PathGemmArgs {
   int32_t *err;                    // device status word (bounded waits)
 };
 size_t path_gemm_operand_bytes(int mode, int64_t M, int64_t N, int64_t paths);
+// The path GEMM in two launches: the operand packing (zeroing of the padding and the
+// pack kernels), then the tcgen05 GEMM that reads the packed operands.
+cudaError_t launch_path_pack(const PathGemmArgs &g, cudaStream_t st);
 
 // Tensor-core tree level (gemm_tc.cu): child node g (digit m = g % radix) =
 // U_m (x) I applied to its parent, where U_m acts on the kMmaBits lowest storage bits.

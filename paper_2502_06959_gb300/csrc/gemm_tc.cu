@@ -1196,17 +1196,24 @@ size_t path_gemm_operand_bytes(int mode, int64_t M, int64_t N, int64_t paths) {
   return (size_t)(2 * Mp + Np) * (size_t)kpad * esz + 256;
 }
 
-cudaError_t launch_path_gemm(const PathGemmArgs &g, cudaStream_t st) {
+cudaError_t launch_path_pack(const PathGemmArgs &g, cudaStream_t st) {
   const int64_t Mp = (g.M + kBM - 1) / kBM * kBM, Np = (g.N + kBN - 1) / kBN * kBN;
   const int nterms = g.mode == 3 ? 1 : 3;
   const bool bf16 = g.mode == 1;
   const int kalign = bf16 ? 64 : 32;
-  const int64_t kpad = (nterms * 2 * g.paths + kalign - 1) / kalign * kalign;
+  const int64_t kcols = (int64_t)nterms * 2 * g.paths;
+  const int64_t kpad = (kcols + kalign - 1) / kalign * kalign;
   const int esz = bf16 ? 2 : 4;
   uint8_t *opA = reinterpret_cast<uint8_t *>(g.scratch);
   uint8_t *opB = opA + (size_t)2 * Mp * kpad * esz;
-  // zero the padded operands (padding columns and rows must contribute nothing)
-  cudaError_t e = cudaMemsetAsync(opA, 0, (size_t)(2 * Mp + Np) * kpad * esz, st);
+  // zero only the padding (rows past M or N, columns past the K'' used), which must
+  // contribute nothing; the pack kernels write every other entry
+  cudaError_t e = cudaSuccess;
+  if (Mp > g.M) e = cudaMemsetAsync(opA + (size_t)2 * g.M * kpad * esz, 0, (size_t)2 * (Mp - g.M) * kpad * esz, st);
+  if (e == cudaSuccess && Np > g.N) e = cudaMemsetAsync(opB + (size_t)g.N * kpad * esz, 0, (size_t)(Np - g.N) * kpad * esz, st);
+  if (e == cudaSuccess && kpad > kcols)
+    e = cudaMemset2DAsync(opA + (size_t)kcols * esz, (size_t)kpad * esz, 0, (size_t)(kpad - kcols) * esz,
+                          (size_t)(2 * Mp + Np), st);
   if (e != cudaSuccess) return e;
   for (int side = 0; side < 2; ++side) {
     PackArgs pa{};
@@ -1240,6 +1247,19 @@ cudaError_t launch_path_gemm(const PathGemmArgs &g, cudaStream_t st) {
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
+  return cudaSuccess;
+}
+
+cudaError_t launch_path_gemm(const PathGemmArgs &g, cudaStream_t st) {
+  const int64_t Mp = (g.M + kBM - 1) / kBM * kBM, Np = (g.N + kBN - 1) / kBN * kBN;
+  const int nterms = g.mode == 3 ? 1 : 3;
+  const bool bf16 = g.mode == 1;
+  const int kalign = bf16 ? 64 : 32;
+  const int64_t kpad = (nterms * 2 * g.paths + kalign - 1) / kalign * kalign;
+  const int esz = bf16 ? 2 : 4;
+  uint8_t *opA = reinterpret_cast<uint8_t *>(g.scratch);
+  uint8_t *opB = opA + (size_t)2 * Mp * kpad * esz;
+  cudaError_t e = cudaSuccess;
   CUtensorMap tmA, tmB;
   if (!make_map(&tmA, opA, bf16, (uint64_t)kpad, (uint64_t)(2 * Mp), (uint32_t)kGN) ||
       !make_map(&tmB, opB, bf16, (uint64_t)kpad, (uint64_t)Np, (uint32_t)kGM))

@@ -1144,6 +1144,19 @@ hsf_status run_svd_jobs(const hsf_plan &p, const std::vector<SvdJob> &jobs, std:
   a.yf = (double *)(d + o_y);
   a.sweeps_used = (int32_t *)(d + o_sw);
   a.residual = (double *)(d + o_res);
+  {
+    int dmax = 1, wmax = 1, nwmax = 1;
+    for (int j = 0; j < J; ++j) {
+      const int k = bk[3 * j], ka = bk[3 * j + 1], kb = bk[3 * j + 2];
+      const int Mw = std::max(1 << (2 * ka), 1 << (2 * kb)), Nw = std::min(1 << (2 * ka), 1 << (2 * kb));
+      dmax = std::max(dmax, 1 << k);
+      wmax = std::max(wmax, Mw * Nw);
+      nwmax = std::max(nwmax, Nw);
+    }
+    a.off_w = dmax * dmax;
+    a.off_v = a.off_w + wmax;
+    a.max_nw = nwmax;
+  }
   CUDA_TRY(launch_block_svd(a, pst));
   g_launches++;
   std::vector<double> sig((size_t)J * 64), xf(nf), yf(nf);

@@ -18,6 +18,7 @@
 //   5. Reconstruction check: the largest entry of |U_B - sum_m X'_m (x) Y'_m| over the
 //      kept terms (eq. equ-schmidt-decompostion-res), for the host to accept or reject.
 // The sweep count is bounded (max_sweeps); the kernel never waits on anything.
+#include <algorithm>
 #include <cstdint>
 
 #include "common.h"
@@ -40,12 +41,15 @@ __device__ __forceinline__ double warp_sum(double v) {
 
 __global__ void __launch_bounds__(kThreads) block_svd_kernel(BlockSvdArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  // sized by the launch for its largest block (a small block needs a few hundred bytes,
+  // so the CTA fits beside other kernels' CTAs on a busy SM)
   double2 *U = reinterpret_cast<double2 *>(smem_raw);          // D x D, row-major
-  double2 *W = U + kMaxDim * kMaxDim;                           // Mw x Nw, column-major
-  double2 *V = W + kMaxDim * kMaxDim;                           // Nw x Nw, column-major
+  double2 *W = U + a.off_w;                                     // Mw x Nw, column-major
+  double2 *V = U + a.off_v;                                     // Nw x Nw, column-major
   __shared__ double sig[kMaxDim];
   __shared__ int order[kMaxDim];
   __shared__ int rotated;
+  __shared__ double fro2;
 
   const int b = blockIdx.x;
   const int k = a.block_k[3 * b], ka = a.block_k[3 * b + 1], kb = a.block_k[3 * b + 2];
@@ -128,6 +132,11 @@ __global__ void __launch_bounds__(kThreads) block_svd_kernel(BlockSvdArgs a) {
   }
   for (int e = tid; e < Nw * Nw; e += blockDim.x)
     V[e] = make_double2((e / Nw) == (e % Nw) ? 1.0 : 0.0, 0.0);
+  if (tid == 0) {
+    double f = 0.0;
+    for (int e = 0; e < Mw * Nw; ++e) f += W[e].x * W[e].x + W[e].y * W[e].y;
+    fro2 = f;
+  }
   __syncthreads();
 
   // 3. one-sided Jacobi
@@ -160,9 +169,12 @@ __global__ void __launch_bounds__(kThreads) block_svd_kernel(BlockSvdArgs a) {
         gr = warp_sum(gr);
         gi = warp_sum(gi);
         const double ag = sqrt(gr * gr + gi * gi);
-        // rotate while the columns' cosine is above 1e-14: the rounding of a 64-term
-        // complex dot product sits near 1e-15, so a lower threshold never stops
-        if (ag > 1e-14 * sqrt(al * be) && ag > 1e-300) {
+        // rotate while the columns' cosine is above 1e-14 (the rounding of a 64-term
+        // complex dot product sits near 1e-15, so a lower threshold never stops) and both
+        // columns are above round-off of the whole matrix: a column of norm below
+        // 1e-14 |A~|_F is numerically zero (its sigma is dropped by any rank threshold
+        // above 1e-14), and its noise would otherwise keep rotating
+        if (ag > 1e-14 * sqrt(al * be) && fmin(al, be) > 1e-28 * fro2 && ag > 1e-300) {
           const double zeta = (be - al) / (2.0 * ag);
           const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
           const double c = 1.0 / sqrt(1.0 + t * t), s = c * t;
@@ -274,10 +286,14 @@ __global__ void __launch_bounds__(kThreads) block_svd_kernel(BlockSvdArgs a) {
 
 cudaError_t launch_block_svd(const BlockSvdArgs &a, cudaStream_t st) {
   if (a.num_blocks <= 0) return cudaSuccess;
-  const size_t smem = (size_t)3 * kMaxDim * kMaxDim * sizeof(double2);
+  // shared memory and threads for the largest block of the launch: U is D x D, the
+  // working matrix Mw x Nw, V Nw x Nw; a Jacobi round uses Nw / 2 warps
+  const size_t elems = (size_t)a.off_v + (size_t)a.max_nw * a.max_nw;
+  const size_t smem = elems * sizeof(double2);
+  const int threads = std::min(kThreads, std::max(128, 32 * (a.max_nw / 2)));
   cudaError_t e = cudaFuncSetAttribute(block_svd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  block_svd_kernel<<<a.num_blocks, kThreads, smem, st>>>(a);
+  block_svd_kernel<<<a.num_blocks, threads, smem, st>>>(a);
   return cudaGetLastError();
 }
 

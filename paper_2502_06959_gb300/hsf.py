@@ -123,7 +123,7 @@ SIGNATURES = {
     "hsf_version": (ctypes.c_char_p, []),
 }
 
-KERNEL_KINDS = ("sweep", "gather", "reduce", "window", "other", "leaf", "level_mma", "level_f16")
+KERNEL_KINDS = ("sweep", "gather", "reduce", "window", "other", "leaf", "level_mma", "level_f16", "pack")
 
 
 class hsf_kernel_stat(ctypes.Structure):
@@ -337,8 +337,8 @@ def hsf_set_profiling(on: bool) -> None:
 
 
 def hsf_profile_collect(plan: int) -> dict:
-    arr = (hsf_kernel_stat * 8)()
-    _check(load_library().hsf_profile_collect(plan, arr, 8))
+    arr = (hsf_kernel_stat * len(KERNEL_KINDS))()
+    _check(load_library().hsf_profile_collect(plan, arr, len(KERNEL_KINDS)))
     return {k: dict(launches=arr[i].launches, ms=arr[i].ms, bytes=arr[i].bytes, flops=arr[i].flops)
             for i, k in enumerate(KERNEL_KINDS)}
 

@@ -42,11 +42,16 @@ def subtree_size(ranks: Sequence[int], world: int) -> int:
 
 
 def allreduce_amplitudes(partial, group=None):
-    """Sum complex128 partial amplitudes over the ranks (in place, returned)."""
+    """Sum complex128 partial amplitudes over the ranks (in place, returned).  With a
+    gloo group a device tensor is reduced through a host copy."""
     import torch
     import torch.distributed as dist
-    view = torch.view_as_real(partial)
-    dist.all_reduce(view, op=dist.ReduceOp.SUM, group=group)
+    t = partial
+    if partial.device.type != "cpu" and dist.get_backend(group) != "nccl":
+        t = partial.cpu()
+    dist.all_reduce(torch.view_as_real(t), op=dist.ReduceOp.SUM, group=group)
+    if t is not partial:
+        partial.copy_(t)
     return partial
 
 
