@@ -150,7 +150,17 @@ class ClockSampler:
 # line to its closing brace) at capture time; host code and other kernels of the file
 # may change without invalidating it.  The summaries named here hold the numbers and the
 # commands.
-PROFILED_TRAFFIC = {}
+PROFILED_TRAFFIC = {
+    "sweep": {"ratio": 275.1 / 335.5, "source": "paper_2502_06959_gb300/csrc/sweep.cu",
+              "kernel": "sweep_reg_kernel", "sha256": "1a9bade5309e94b9",
+              "profile": "profiles/sweep_reg_level6_n30.md"},
+    "level_f16": {"ratio": 1289.7 / 1342.2, "source": "paper_2502_06959_gb300/csrc/gemm_tc.cu",
+                  "kernel": "level_mma_f16_kernel", "sha256": "5fafb56a20723142",
+                  "profile": "profiles/level_f16_level7_n30.md"},
+    "leaf": {"ratio": 1868.7 / 2151.7, "source": "paper_2502_06959_gb300/csrc/accum.cu",
+             "kernel": "leaf_contract_pair_kernel", "sha256": "6679c458867f2c10",
+             "profile": "profiles/leaf_contract_pair_n30.md"},
+}
 
 
 def _kernel_text(rel, kernel):
@@ -712,6 +722,13 @@ def main():
             r.update({"bound": "tensor", "achieved": tfl, "peak": peak, "unit": "TFLOP/s",
                       "frac": tfl / peak if peak else None, "peak_source": peak_src + src,
                       "hbm_gbs": gbs, "hbm_frac": gbs / hbm_peak if hbm_peak else None, "traffic": tr})
+        elif kind == "leaf":
+            # 33 FLOP per algorithmic byte, above the FP32 machine balance (80.5 TFLOP/s over
+            # the measured HBM bandwidth, about 12 FLOP/B): the FP32 ALU roof binds
+            r.update({"bound": "alu", "achieved": tfl, "peak": fp32_peak_tflops, "unit": "TFLOP/s",
+                      "frac": tfl / fp32_peak_tflops, "traffic": tr,
+                      "peak_source": "152 SMs x 128 FP32 lanes x 2 x max SM clock",
+                      "hbm_gbs": gbs, "hbm_frac": gbs / hbm_peak if hbm_peak else None})
         else:
             r.update({"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s",
                       "frac": gbs / hbm_peak if hbm_peak else None, "traffic": tr, "peak_source": peak_src,

@@ -111,7 +111,8 @@ hsf_status ensure_grad(hsf_plan &p) {
     }
   }
   if (host.empty()) host.resize(256);
-  CUDA_TRY(cudaMalloc(&p.dev_factors, host.size()));
+  p.dev_factors = table_alloc(host.size());
+  if (!p.dev_factors) return set_error(HSF_ENOMEM, "gradient factor tables of %zu bytes", host.size());
   CUDA_TRY(cudaMemcpyAsync(p.dev_factors, host.data(), host.size(), cudaMemcpyHostToDevice, plan_stream()));
   CUDA_TRY(cudaStreamSynchronize(plan_stream()));
   // derivative blocks: one SVD job per (block, angle) pair

@@ -112,6 +112,10 @@ namespace hsf {
 cudaStream_t plan_stream();   // the calling thread's private non-blocking stream for plan work
 cudaStream_t side_stream();   // the calling thread's second stream for side b of hsf_run
 hsf_status set_error(hsf_status code, const char *fmt, ...);
+// Plan-table device memory from a per-device arena (no cudaMalloc on the common path).
+// table_free returns a block at once: the caller makes sure no kernel still reads it.
+void *table_alloc(size_t bytes);
+void table_free(void *p);
 const char *last_error();
 hsf_status validate_and_load(hsf_plan &p, const hsf_circuit *c, int cut, const hsf_blocks *bl,
                              const hsf_plan_opts *o);
@@ -183,10 +187,12 @@ struct hsf_plan {
   ~hsf_plan() {
     for (auto &r : prof) { cudaEventDestroy(r.e0); cudaEventDestroy(r.e1); }
     for (auto &d : dplans) delete d.plan;
-    if (dev_table) cudaFree(dev_table);
-    if (dev_gtable) cudaFree(dev_gtable);
-    if (dev_status) cudaFree(dev_status);
-    if (dev_factors) cudaFree(dev_factors);
+    // every kernel that may read the plan's tables has finished before they are reused
+    if (dev_table || dev_gtable || dev_status || dev_factors) cudaDeviceSynchronize();
+    hsf::table_free(dev_table);
+    hsf::table_free(dev_gtable);
+    hsf::table_free(dev_status);
+    hsf::table_free(dev_factors);
     if (own_ws) {
       cudaDeviceSynchronize();          // no queued run may still use it
       if (own_release) own_release(own_ctx, own_ws, nullptr);

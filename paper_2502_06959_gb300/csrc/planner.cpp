@@ -88,6 +88,79 @@ cudaStream_t side_stream() {
   return s.get();
 }
 
+// Device memory of plan tables.  cudaMalloc implicitly synchronises the streams of the
+// device, so a plan created while another circuit runs must not call it: its tables
+// (and the SVD scratch) are carved first-fit from slabs kept per device, and a slab is
+// allocated only when none has room.  Freed blocks merge with their free neighbours.
+namespace {
+struct Arena {
+  std::vector<std::pair<char *, size_t>> slabs;
+  std::map<char *, size_t> free_blocks;   // address -> bytes
+  std::map<char *, size_t> used;
+};
+std::mutex g_arena_mu;
+std::map<int, Arena> g_arenas;
+constexpr size_t kSlabBytes = (size_t)64 << 20;
+}  // namespace
+
+void *table_alloc(size_t bytes) {
+  bytes = (bytes + 255) / 256 * 256;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+  std::lock_guard<std::mutex> lock(g_arena_mu);
+  Arena &A = g_arenas[dev];
+  for (auto it = A.free_blocks.begin(); it != A.free_blocks.end(); ++it) {
+    if (it->second < bytes) continue;
+    char *ptr = it->first;
+    const size_t rest = it->second - bytes;
+    A.free_blocks.erase(it);
+    if (rest) A.free_blocks[ptr + bytes] = rest;
+    A.used[ptr] = bytes;
+    return ptr;
+  }
+  const size_t slab = std::max(kSlabBytes, bytes);
+  char *mem = nullptr;
+  if (cudaMalloc((void **)&mem, slab) != cudaSuccess) return nullptr;
+  A.slabs.push_back({mem, slab});
+  if (slab > bytes) A.free_blocks[mem + bytes] = slab - bytes;
+  A.used[mem] = bytes;
+  return mem;
+}
+
+void table_free(void *p) {
+  if (!p) return;
+  std::lock_guard<std::mutex> lock(g_arena_mu);
+  for (auto &kv : g_arenas) {
+    Arena &A = kv.second;
+    auto u = A.used.find((char *)p);
+    if (u == A.used.end()) continue;
+    char *ptr = u->first;
+    size_t bytes = u->second;
+    A.used.erase(u);
+    // merge with the free neighbours inside the same slab
+    auto next = A.free_blocks.lower_bound(ptr);
+    if (next != A.free_blocks.end() && next->first == ptr + bytes) {
+      bool same = false;
+      for (auto &sl : A.slabs) same |= ptr >= sl.first && next->first < sl.first + sl.second;
+      if (same) {
+        bytes += next->second;
+        next = A.free_blocks.erase(next);
+      }
+    }
+    if (next != A.free_blocks.begin()) {
+      auto prev = std::prev(next);
+      bool same = false;
+      for (auto &sl : A.slabs) same |= prev->first >= sl.first && ptr < sl.first + sl.second && prev->first < ptr;
+      if (same && prev->first + prev->second == ptr) {
+        prev->second += bytes;
+        return;
+      }
+    }
+    A.free_blocks[ptr] = bytes;
+    return;
+  }
+}
+
 int device_sm_count() {
   static std::mutex mu;
   static std::map<int, int> cache;
@@ -967,7 +1040,8 @@ hsf_status build_schrodinger(hsf_plan &p, const hsf_circuit *c, const hsf_plan_o
   st = upload_programs(p);
   if (st != HSF_OK) return st;
   p.launches = (int64_t)lv.passes.size();
-  CUDA_TRY(cudaMalloc(&p.dev_status, 256));
+  p.dev_status = (int32_t *)table_alloc(256);
+  if (!p.dev_status) return set_error(HSF_ENOMEM, "device status words");
   CUDA_TRY(cudaMemsetAsync(p.dev_status, 0, 256, plan_stream()));
   CUDA_TRY(cudaStreamSynchronize(plan_stream()));
   return HSF_OK;
@@ -1035,9 +1109,10 @@ hsf_status upload_programs(hsf_plan &p, bool grad) {
   align(256);
   if (host.empty()) host.resize(256);
   void *&table = grad ? p.dev_gtable : p.dev_table;
-  // plain cudaMalloc: hsf_plan_destroy's cudaFree then waits for every kernel that may
-  // still read the table (a stream-ordered pool allocation could be unmapped under them)
-  CUDA_TRY(cudaMalloc(&table, host.size()));
+  // from the table arena (no implicit stream synchronisation); hsf_plan_destroy waits
+  // for the device before returning the block, so no queued kernel can still read it
+  table = table_alloc(host.size());
+  if (!table) return set_error(HSF_ENOMEM, "device table of %zu bytes", host.size());
   if (!grad) p.dev_table_bytes = host.size();
   CUDA_TRY(cudaMemcpyAsync(table, host.data(), host.size(), cudaMemcpyHostToDevice, plan_stream()));
   CUDA_TRY(cudaStreamSynchronize(plan_stream()));
@@ -1065,7 +1140,8 @@ hsf_status finish_plan(hsf_plan &p) {
   if (st != HSF_OK) return st;
   st = upload_programs(p);
   if (st != HSF_OK) return st;
-  CUDA_TRY(cudaMalloc(&p.dev_status, 256));
+  p.dev_status = (int32_t *)table_alloc(256);
+  if (!p.dev_status) return set_error(HSF_ENOMEM, "device status words");
   CUDA_TRY(cudaMemsetAsync(p.dev_status, 0, 256, plan_stream()));
   CUDA_TRY(cudaStreamSynchronize(plan_stream()));
   return HSF_OK;
@@ -1121,9 +1197,14 @@ hsf_status run_svd_jobs(const hsf_plan &p, const std::vector<SvdJob> &jobs, std:
                o_res = take((size_t)J * 8);
   cudaStream_t pst = plan_stream();
   unsigned char *d = nullptr;
-  CUDA_TRY(cudaMallocAsync((void **)&d, off, pst));
-  std::unique_ptr<unsigned char, void (*)(unsigned char *)> guard(
-      d, [](unsigned char *q) { cudaFreeAsync(q, plan_stream()); });
+  // scratch from the table arena; it is returned only after the stream sync below (or,
+  // on an early error, after waiting for the plan stream)
+  d = (unsigned char *)table_alloc(off);
+  if (!d) return set_error(HSF_ENOMEM, "SVD scratch of %zu bytes", off);
+  std::unique_ptr<unsigned char, void (*)(unsigned char *)> guard(d, [](unsigned char *q) {
+    cudaStreamSynchronize(plan_stream());
+    table_free(q);
+  });
   CUDA_TRY(cudaMemcpyAsync(d + o_bk, bk.data(), bk.size() * 4, cudaMemcpyHostToDevice, pst));
   CUDA_TRY(cudaMemcpyAsync(d + o_tb, tbeg.data(), tbeg.size() * 4, cudaMemcpyHostToDevice, pst));
   CUDA_TRY(cudaMemcpyAsync(d + o_gb, gbeg.data(), gbeg.size() * 4, cudaMemcpyHostToDevice, pst));
