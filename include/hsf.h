@@ -336,16 +336,23 @@ int64_t hsf_batch_nodes(const hsf_batch *batch);
 void hsf_batch_destroy(hsf_batch *batch);
 
 /* Autotuner (the paper has no counterpart; its preprocessing mentions gate fusion,
- * Table I caption): for this circuit shape and request, plan and time each candidate
- * sweep configuration (shared-memory tile width 2^tile_bits, register-group fusion on
- * or off) on the current device and write the fastest into opts->tile_bits and
- * opts->flags.  Results are appended to the text file cache_path (may be NULL) keyed by
- * a hash of the circuit structure and request, and reused on later calls.  Timing
- * runs use `workspace` (hsf_workspace_size bytes for the request) and synchronise. */
+ * Table I caption): for this circuit shape and request, plan and time candidate
+ * configurations on the current device by a coordinate search (each dimension in turn,
+ * the others held at the best so far): shared-memory tile width 2^tile_bits, register-
+ * group fusion on or off and its width (8 / 16 / 32 amplitudes per thread), tensor-core
+ * tree levels on or off, the path-GEMM form for window output (split-BF16, split-TF32 or
+ * FP32; never the inexact plain TF32) and the path batch (workspace budget: the full
+ * workspace, a quarter or a sixteenth, which sets the path-chunk size).  The fastest is
+ * written into opts->tile_bits, opts->flags (HSF_FLAG_NO_REGISTER_SWEEP, _REG3, _REG5,
+ * _NO_TC_LEVEL) and opts->gemm_mode, and its workspace budget into *best_budget (may be
+ * NULL; pass it to hsf_workspace_size).  Results are appended to the text file
+ * cache_path (may be NULL) keyed by a hash of the circuit structure and request, and
+ * reused on later calls.  Timing runs use `workspace` (hsf_workspace_size bytes for the
+ * request) and synchronise. */
 hsf_status hsf_tune(const hsf_circuit *circuit, int32_t cut_l, const hsf_blocks *blocks,
                     hsf_plan_opts *opts, size_t num_bitstrings, const uint64_t *bitstrings,
                     uint64_t window, const char *cache_path, void *workspace,
-                    size_t workspace_bytes);
+                    size_t workspace_bytes, size_t *best_budget);
 
 /* Wait for the stream and report device-side failures of earlier runs of this plan:
  * returns HSF_ETIMEOUT (and clears the flag) if a bounded wait inside a kernel expired,

@@ -427,7 +427,7 @@ __global__ void __launch_bounds__(128, 4) leaf_contract_async_kernel(LeafArgs a)
 // bitstring: a chunk, two complex of padding, b chunk, two more: with the row stride of
 // 2^(C+1) + 4 complex the 16-byte reads of a warp's four bitstrings and two sides fall
 // in eight distinct bank groups.
-constexpr int kPairDepth = 6;          // stage ring: three pairs of parents
+constexpr int kPairDepth = 4;
 constexpr size_t leaf_pair_ring_bytes(int cb, int rm) {
   return (size_t)kPairDepth * (128 / (2 * rm)) * ((2u << cb) + 4) * 8;
 }
@@ -496,21 +496,15 @@ __global__ void __launch_bounds__(128, 6) leaf_contract_pair_kernel(LeafArgs a) 
     }
     cp_commit();
   };
-  // two parents per iteration (independent loads and FMA chains); the ring holds three
-  // pairs: the pair being computed, the next one landing, and the one being issued
 #pragma unroll
-  for (int d = 0; d < kPairDepth - 2; ++d) issue(j0 + d, d);
+  for (int d = 0; d < kPairDepth - 1; ++d) issue(j0 + d, d);
   float accr = 0.f, acci = 0.f;
-  for (int64_t t0 = 0; t0 < np; t0 += 2) {
-    cp_wait<2>();                              // parents t0 and t0 + 1 have landed
+  for (int64_t t = 0; t < np; ++t) {
+    cp_wait<kPairDepth - 2>();
     __syncwarp();
-    issue(j0 + t0 + kPairDepth - 2, (int)((t0 + kPairDepth - 2) % kPairDepth));
-    issue(j0 + t0 + kPairDepth - 1, (int)((t0 + kPairDepth - 1) % kPairDepth));
-#pragma unroll
-    for (int u = 0; u < 2; ++u) {
-    const int64_t t = t0 + u;
+    issue(j0 + t + kPairDepth - 1, (int)((t + kPairDepth - 1) % kPairDepth));
     const int64_t j = j0 + t;
-    const bool use = t < np && on && !((j == 0 && m < a.m_first) || (j == a.num_parents - 1 && m >= a.m_last));
+    const bool use = on && !((j == 0 && m < a.m_first) || (j == a.num_parents - 1 && m >= a.m_last));
     float vr = 0.f, vi = 0.f;
     if (use) {
       const float4 *x = reinterpret_cast<const float4 *>(buf[t % kPairDepth] + roff);
@@ -533,7 +527,6 @@ __global__ void __launch_bounds__(128, 6) leaf_contract_pair_kernel(LeafArgs a) 
     const float wi = __shfl_xor_sync(0xffffffffu, vi, RM);
     accr = fmaf(vr, wr, fmaf(-vi, wi, accr));
     acci = fmaf(vr, wi, fmaf(vi, wr, acci));
-    }
   }
   cp_wait<0>();
 #pragma unroll

@@ -321,6 +321,15 @@ int64_t hsf_plan_describe(const hsf_plan *p, char *buf, int64_t cap) {
                      std::to_string(lv.passes.size()) + " passes")
                         .c_str());
       out += line;
+      if (!lv.post.empty()) {
+        out += "  epilogue ops:";
+        for (const OpH &op : lv.post) {
+          std::snprintf(line, sizeof line, " %s%d(%d%s%s)", op.type == OP_DENSE ? "D" : "d", op.nq, op.q[0],
+                        op.nq > 1 ? "," : "", op.nq > 1 ? std::to_string(op.q[1]).c_str() : "");
+          out += line;
+        }
+        out += "\n";
+      }
       for (size_t pi = 0; pi < lv.passes.size(); ++pi) {
         const PassH &ps = lv.passes[pi];
         std::snprintf(line, sizeof line, "  pass %zu: active=0x%llx t=%d ops=%zu groups=%zu\n", pi,

@@ -69,30 +69,41 @@ uint64_t shape_key(const hsf_circuit *c, int cut, const hsf_blocks *b, const hsf
   return h;
 }
 
-bool cache_lookup(const char *path, uint64_t key, int *tile, int *flags) {
+// One tuned configuration: plan options and the workspace budget (path batch).
+struct TuneCfg {
+  int tile = 0, flags = 0, gemm = 0;
+  size_t budget = 0;
+};
+
+bool cache_lookup(const char *path, uint64_t key, TuneCfg *c) {
   if (!path || !*path) return false;
   FILE *f = std::fopen(path, "r");
   if (!f) return false;
-  unsigned long long k;
-  int t, fl;
+  char line[256];
   bool found = false;
-  while (std::fscanf(f, "%llx %d %d", &k, &t, &fl) == 3)
+  while (std::fgets(line, sizeof line, f)) {
+    unsigned long long k, b = 0;
+    int t, fl, g = 0;
+    if (std::sscanf(line, "%llx %d %d %d %llu", &k, &t, &fl, &g, &b) != 5) continue;
     if (k == key) {
-      *tile = t;
-      *flags = fl;
+      *c = TuneCfg{t, fl, g, (size_t)b};
       found = true;
     }
+  }
   std::fclose(f);
   return found;
 }
 
-void cache_store(const char *path, uint64_t key, int tile, int flags) {
+void cache_store(const char *path, uint64_t key, const TuneCfg &c) {
   if (!path || !*path) return;
   FILE *f = std::fopen(path, "a");
   if (!f) return;
-  std::fprintf(f, "%016llx %d %d\n", (unsigned long long)key, tile, flags);
+  std::fprintf(f, "%016llx %d %d %d %llu\n", (unsigned long long)key, c.tile, c.flags, c.gemm,
+               (unsigned long long)c.budget);
   std::fclose(f);
 }
+
+constexpr int kTunedFlags = HSF_FLAG_NO_REGISTER_SWEEP | HSF_FLAG_REG3 | HSF_FLAG_REG5 | HSF_FLAG_NO_TC_LEVEL;
 
 }  // namespace
 
@@ -100,14 +111,19 @@ extern "C" {
 
 hsf_status hsf_tune(const hsf_circuit *circuit, int32_t cut_l, const hsf_blocks *blocks, hsf_plan_opts *opts,
                     size_t num_bitstrings, const uint64_t *bitstrings, uint64_t window, const char *cache_path,
-                    void *workspace, size_t workspace_bytes) {
+                    void *workspace, size_t workspace_bytes, size_t *best_budget) {
   if (!circuit || !blocks || !opts || !workspace) return set_error(HSF_EINVAL, "NULL argument");
   std::lock_guard<std::mutex> lock(g_tune_mu);
   const uint64_t key = shape_key(circuit, cut_l, blocks, opts, num_bitstrings, window);
-  int tile = 0, flags = 0;
-  if (cache_lookup(cache_path, key, &tile, &flags)) {
-    opts->tile_bits = tile;
-    opts->flags = (opts->flags & ~HSF_FLAG_NO_REGISTER_SWEEP) | flags;
+  TuneCfg best_cfg;
+  auto apply = [&](const TuneCfg &c) {
+    opts->tile_bits = c.tile;
+    opts->flags = (opts->flags & ~kTunedFlags) | c.flags;
+    opts->gemm_mode = c.gemm;
+    if (best_budget) *best_budget = c.budget;
+  };
+  if (cache_lookup(cache_path, key, &best_cfg)) {
+    apply(best_cfg);
     return HSF_OK;
   }
   const int tmax = opts->precision == HSF_PREC_C64 ? kRegTileC64 : kRegTileC128;
@@ -118,8 +134,6 @@ hsf_status hsf_tune(const hsf_circuit *circuit, int32_t cut_l, const hsf_blocks 
   cudaEvent_t e0, e1;
   CUDA_TRY(cudaEventCreate(&e0));
   CUDA_TRY(cudaEventCreate(&e1));
-  float best = 1e30f;
-  int best_tile = tmax, best_flags = 0;
   const uint64_t count = num_bitstrings ? num_bitstrings : (window ? window : (1ull << circuit->n));
   void *out = nullptr;
   if (cudaMalloc(&out, count * 16) != cudaSuccess) {
@@ -127,45 +141,78 @@ hsf_status hsf_tune(const hsf_circuit *circuit, int32_t cut_l, const hsf_blocks 
     cudaEventDestroy(e1);
     return set_error(HSF_ENOMEM, "hsf_tune: output buffer");
   }
-  hsf_status result = HSF_OK;
-  for (int t = std::min(tmax, half); t >= std::max(3, std::min(tmax, half) - 3) && result == HSF_OK; --t) {
-    for (int reg = 0; reg < 2; ++reg) {
-      hsf_plan_opts o = *opts;
-      o.tile_bits = t;
-      o.flags = (opts->flags & ~HSF_FLAG_NO_REGISTER_SWEEP) | (reg ? 0 : HSF_FLAG_NO_REGISTER_SWEEP);
-      hsf_plan *p = nullptr;
-      if (hsf_plan_create(circuit, cut_l, blocks, &o, &p) != HSF_OK) continue;
-      size_t need = 0;
-      if (hsf_workspace_size(p, num_bitstrings, window, workspace_bytes, &need) != HSF_OK) {
-        hsf_plan_destroy(p);
-        continue;
-      }
-      float ms = 1e30f;
-      bool ok = hsf_run(p, bitstrings, num_bitstrings, window, 0, 0, out, workspace, workspace_bytes, st) == HSF_OK;
-      for (int rep = 0; rep < 2 && ok; ++rep) {
-        cudaEventRecord(e0, st);
-        ok = hsf_run(p, bitstrings, num_bitstrings, window, 0, 0, out, workspace, workspace_bytes, st) == HSF_OK;
-        cudaEventRecord(e1, st);
-        if (cudaEventSynchronize(e1) != cudaSuccess) ok = false;
-        float m = 0.f;
-        cudaEventElapsedTime(&m, e0, e1);
-        ms = std::min(ms, m);
-      }
+  // time one configuration: plan, one warm run, best of two timed runs (ms; 1e30 if it
+  // does not run)
+  auto time_cfg = [&](const TuneCfg &c) -> float {
+    hsf_plan_opts o = *opts;
+    o.tile_bits = c.tile;
+    o.flags = (opts->flags & ~kTunedFlags) | c.flags;
+    o.gemm_mode = c.gemm;
+    hsf_plan *p = nullptr;
+    if (hsf_plan_create(circuit, cut_l, blocks, &o, &p) != HSF_OK) return 1e30f;
+    size_t need = 0;
+    const size_t budget = c.budget ? std::min(c.budget, workspace_bytes) : workspace_bytes;
+    if (hsf_workspace_size(p, num_bitstrings, window, budget, &need) != HSF_OK) {
       hsf_plan_destroy(p);
-      if (ok && ms < best) {
-        best = ms;
-        best_tile = t;
-        best_flags = reg ? 0 : HSF_FLAG_NO_REGISTER_SWEEP;
-      }
+      return 1e30f;
     }
+    float ms = 1e30f;
+    bool ok = hsf_run(p, bitstrings, num_bitstrings, window, 0, 0, out, workspace, need, st) == HSF_OK;
+    for (int rep = 0; rep < 2 && ok; ++rep) {
+      cudaEventRecord(e0, st);
+      ok = hsf_run(p, bitstrings, num_bitstrings, window, 0, 0, out, workspace, need, st) == HSF_OK;
+      cudaEventRecord(e1, st);
+      if (cudaEventSynchronize(e1) != cudaSuccess) ok = false;
+      float m = 0.f;
+      cudaEventElapsedTime(&m, e0, e1);
+      ms = std::min(ms, m);
+    }
+    if (hsf_sync(p, st) != HSF_OK) ok = false;
+    hsf_plan_destroy(p);
+    return ok ? ms : 1e30f;
+  };
+  // coordinate search: each dimension in turn, the others held at the best so far
+  best_cfg = TuneCfg{std::min(tmax, half), opts->flags & kTunedFlags, opts->gemm_mode, 0};
+  float best = time_cfg(best_cfg);
+  auto try_cfg = [&](TuneCfg c) {
+    const float ms = time_cfg(c);
+    if (ms < best) {
+      best = ms;
+      best_cfg = c;
+    }
+  };
+  {  // shared-memory tile width
+    const TuneCfg base = best_cfg;
+    for (int t = std::min(tmax, half) - 1; t >= std::max(3, std::min(tmax, half) - 3); --t) try_cfg({t, base.flags, base.gemm, base.budget});
+  }
+  {  // register-group fusion off, and the register block width (8 / 16 / 32 amplitudes)
+    const TuneCfg base = best_cfg;
+    const int keep = base.flags & ~(HSF_FLAG_NO_REGISTER_SWEEP | HSF_FLAG_REG3 | HSF_FLAG_REG5);
+    try_cfg({base.tile, keep | HSF_FLAG_NO_REGISTER_SWEEP, base.gemm, base.budget});
+    if (opts->precision == HSF_PREC_C64) {
+      try_cfg({base.tile, keep | HSF_FLAG_REG3, base.gemm, base.budget});
+      try_cfg({base.tile, keep | HSF_FLAG_REG5, base.gemm, base.budget});
+    }
+  }
+  if (opts->precision == HSF_PREC_C64) {  // tensor-core tree levels off
+    const TuneCfg base = best_cfg;
+    try_cfg({base.tile, base.flags ^ HSF_FLAG_NO_TC_LEVEL, base.gemm, base.budget});
+  }
+  if (num_bitstrings == 0 && opts->precision == HSF_PREC_C64) {  // path-GEMM form (the accurate ones)
+    const TuneCfg base = best_cfg;
+    for (int g : {HSF_GEMM_BF16X3, HSF_GEMM_TF32X3, HSF_GEMM_FP32})
+      if (g != base.gemm) try_cfg({base.tile, base.flags, g, base.budget});
+  }
+  {  // path batch: the workspace budget (smaller budgets = smaller path chunks)
+    const TuneCfg base = best_cfg;
+    for (size_t div : {4, 16}) try_cfg({base.tile, base.flags, base.gemm, workspace_bytes / div});
   }
   cudaFree(out);
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (best >= 1e29f) return set_error(HSF_ENOTSUP, "hsf_tune: no candidate configuration ran");
-  opts->tile_bits = best_tile;
-  opts->flags = (opts->flags & ~HSF_FLAG_NO_REGISTER_SWEEP) | best_flags;
-  cache_store(cache_path, key, best_tile, best_flags);
+  apply(best_cfg);
+  cache_store(cache_path, key, best_cfg);
   return HSF_OK;
 }
 

@@ -461,12 +461,23 @@ __device__ __forceinline__ float2 *post_elem(float *stage, uint32_t i) {
 __device__ __forceinline__ float2 cmulf(float2 a, float2 b) {
   return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
 }
+// Packed FP32 pair FMA (two lanes per instruction): d = a * b + c elementwise.
+__device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) {
+  float2 d;
+  asm("{\n .reg .b64 ra, rb, rc, rd;\n"
+      " mov.b64 ra, {%2, %3};\n mov.b64 rb, {%4, %5};\n mov.b64 rc, {%6, %7};\n"
+      " fma.rn.f32x2 rd, ra, rb, rc;\n mov.b64 {%0, %1}, rd;\n}"
+      : "=f"(d.x), "=f"(d.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+  return d;
+}
+
 __device__ __forceinline__ void apply_post_op(float *stage, const MmaPostOp *op, int t) {
-  // the op's matrix is read into registers once (not per element)
-  const int nq = __ldg(&op->nq), q0 = __ldg(&op->q0), q1 = __ldg(&op->q1), diag = __ldg(&op->diag);
+  // the op (staged in shared memory) is read into registers once, not per element
+  const int nq = op->nq, q0 = op->q0, q1 = op->q1, diag = op->diag;
   if (diag) {
-    const float2 d0 = __ldg(&op->m[0]), d1 = __ldg(&op->m[1]);
-    const float2 d2 = nq == 2 ? __ldg(&op->m[2]) : d0, d3 = nq == 2 ? __ldg(&op->m[3]) : d1;
+    const float2 d0 = op->m[0], d1 = op->m[1];
+    const float2 d2 = nq == 2 ? op->m[2] : d0, d3 = nq == 2 ? op->m[3] : d1;
     for (uint32_t i = t; i < 2048; i += 128) {
       const uint32_t b0 = (i >> q0) & 1u;
       float2 m;
@@ -480,7 +491,7 @@ __device__ __forceinline__ void apply_post_op(float *stage, const MmaPostOp *op,
       *e = cmulf(m, *e);
     }
   } else if (nq == 1) {
-    const float2 m0 = __ldg(&op->m[0]), m1 = __ldg(&op->m[1]), m2 = __ldg(&op->m[2]), m3 = __ldg(&op->m[3]);
+    const float2 m0 = op->m[0], m1 = op->m[1], m2 = op->m[2], m3 = op->m[3];
     for (uint32_t j = t; j < 1024; j += 128) {
       const uint32_t i0 = ins0(j, q0), i1 = i0 | (1u << q0);
       float2 *e0 = post_elem(stage, i0), *e1 = post_elem(stage, i1);
@@ -490,9 +501,16 @@ __device__ __forceinline__ void apply_post_op(float *stage, const MmaPostOp *op,
       *e1 = make_float2(c.x + d.x, c.y + d.y);
     }
   } else {
-    float2 mm[16];
+    // two-qubit dense op: the matrix as broadcast pairs (Re m, Re m) and (Im m, Im m), so
+    // that with x_k = (Re x_k, Im x_k) as it sits in the stage, P = sum mr * x and
+    // Q = sum mi * x are packed FMAs and (m x)_r = (P.x - Q.y, P.y + Q.x)
+    float2 mr[16], mi[16];
 #pragma unroll
-    for (int e = 0; e < 16; ++e) mm[e] = __ldg(&op->m[e]);
+    for (int e = 0; e < 16; ++e) {
+      const float2 v = op->m[e];
+      mr[e] = make_float2(v.x, v.x);
+      mi[e] = make_float2(v.y, v.y);
+    }
     const int lo = min(q0, q1), hi = max(q0, q1);
     for (uint32_t j = t; j < 512; j += 128) {
       const uint32_t base = ins0(ins0(j, lo), hi);
@@ -506,13 +524,13 @@ __device__ __forceinline__ void apply_post_op(float *stage, const MmaPostOp *op,
       float2 y[4];
 #pragma unroll
       for (int r = 0; r < 4; ++r) {
-        float re = 0.f, im = 0.f;
+        float2 P = make_float2(0.f, 0.f), Q = P;
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-          re = fmaf(mm[r * 4 + k].x, x[k].x, fmaf(-mm[r * 4 + k].y, x[k].y, re));
-          im = fmaf(mm[r * 4 + k].x, x[k].y, fmaf(mm[r * 4 + k].y, x[k].x, im));
+          P = ffma2(mr[r * 4 + k], x[k], P);
+          Q = ffma2(mi[r * 4 + k], x[k], Q);
         }
-        y[r] = make_float2(re, im);
+        y[r] = make_float2(P.x - Q.y, P.y + Q.x);
       }
 #pragma unroll
       for (int k = 0; k < 4; ++k) *e[k] = y[k];
@@ -531,9 +549,16 @@ __global__ void __launch_bounds__(kLvlThreads, 1) level_mma_kernel(const __grid_
       tempty[2], drain;
   __shared__ uint32_t tmem_sh;
   __shared__ volatile int abort_sh, epi_abort[2];
+  __shared__ __align__(16) MmaPostOp post_sh[kMmaMaxPost];   // the epilogue's ops, staged once
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t radix = a.radix;
   const int m = blockIdx.y;
+  {
+    constexpr int kWords = (int)(sizeof(MmaPostOp) / 16);
+    const int n = min(a.num_post, kMmaMaxPost) * kWords;
+    for (int e = threadIdx.x; e < n; e += blockDim.x)
+      reinterpret_cast<int4 *>(post_sh)[e] = reinterpret_cast<const int4 *>(a.post)[e];
+  }
   const int64_t g_first = a.node_lo + ((m - a.node_lo % radix) % radix + radix) % radix;
   const int64_t g_end = a.node_lo + a.num_nodes;
   const int64_t nchild = g_first < g_end ? (g_end - g_first + radix - 1) / radix : 0;
@@ -756,7 +781,7 @@ __global__ void __launch_bounds__(kLvlThreads, 1) level_mma_kernel(const __grid_
         // the rest of the level's program, on storage bits 0..10 of this quarter
         for (int o = 0; o < a.num_post; ++o) {
           asm volatile("bar.sync %0, 128;" ::"r"(bar_id) : "memory");
-          apply_post_op(stage, reinterpret_cast<const MmaPostOp *>(a.post) + o, comp);
+          apply_post_op(stage, post_sh + o, comp);
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         asm volatile("bar.sync %0, 128;" ::"r"(bar_id) : "memory");

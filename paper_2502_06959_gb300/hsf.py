@@ -107,7 +107,7 @@ SIGNATURES = {
     "hsf_batch_destroy": (None, [ctypes.c_void_p]),
     "hsf_tune": (ctypes.c_int, [ctypes.POINTER(hsf_circuit), ctypes.c_int32, ctypes.POINTER(hsf_blocks),
                                 ctypes.POINTER(hsf_plan_opts), ctypes.c_size_t, ctypes.c_void_p, ctypes.c_uint64,
-                                ctypes.c_char_p, ctypes.c_void_p, ctypes.c_size_t]),
+                                ctypes.c_char_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]),
     "hsf_grad_workspace_size": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_size_t, ctypes.c_size_t,
                                                ctypes.POINTER(ctypes.c_size_t)]),
     "hsf_grad": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p,
@@ -198,11 +198,26 @@ def _marshal(n: int, gates, blocks: Sequence[Sequence[int]]):
     return circ, bl, keep
 
 
+class Marshalled:
+    """A circuit and its blocks in the C ABI's structs, built once: planning the same
+    circuit again (new angles, or every step of a benchmark) then skips the Python-side
+    conversion of the gate list."""
+
+    def __init__(self, n: int, gates, blocks):
+        self.n = n
+        self.circ, self.bl, self._keep = _marshal(n, gates, blocks)
+
+
 def hsf_plan_create(n: int, gates, cut: int, blocks, precision: str = "c64", gemm: str = "fp32",
                     rank_tol: float = 0.0, max_paths: int = 0, tile_bits: int = 0, flags: int = 0,
-                    angles: Optional[Sequence[float]] = None) -> int:
+                    angles: Optional[Sequence[float]] = None, marshalled: Optional[Marshalled] = None) -> int:
+    """hsf_plan_create; `marshalled` (from Marshalled(n, gates, blocks)) reuses the C
+    structs of an earlier conversion of the same circuit."""
     lib = load_library()
-    circ, bl, keep = _marshal(n, gates, blocks)
+    if marshalled is not None:
+        circ, bl, keep = marshalled.circ, marshalled.bl, []
+    else:
+        circ, bl, keep = _marshal(n, gates, blocks)
     opts = hsf_plan_opts()
     opts.precision = PREC[precision]
     opts.gemm_mode = GEMM[gemm]
@@ -370,8 +385,9 @@ def hsf_grad(plan: int, bitstrings_ptr: int, num: int, gout_ptr: int, grad_ptr: 
 def hsf_tune(n: int, gates, cut: int, blocks, num: int = 0, bitstrings_ptr: int = 0, window: int = 0,
              cache_path: Optional[str] = None, precision: str = "c64", gemm: str = "fp32",
              budget: int = 0) -> dict:
-    """Autotune the sweep configuration for this circuit shape; returns the plan options
-    (tile_bits, flags) to pass to hsf_plan_create."""
+    """Autotune the configuration for this circuit shape and request; returns the plan
+    options (tile_bits, flags, gemm) to pass to hsf_plan_create and the workspace budget
+    ("budget") that sets the path batch."""
     import torch
     lib = load_library()
     circ, bl, keep = _marshal(n, gates, blocks)
@@ -384,10 +400,13 @@ def hsf_tune(n: int, gates, cut: int, blocks, num: int = 0, bitstrings_ptr: int 
     need = hsf_workspace_size(probe, num, window, budget)
     hsf_plan_destroy(probe)
     ws = torch.empty(need, dtype=torch.uint8, device="cuda")
+    best_budget = ctypes.c_size_t()
     _check(lib.hsf_tune(ctypes.byref(circ), cut, ctypes.byref(bl), ctypes.byref(opts), num,
                         bitstrings_ptr or None, window, cache_path.encode() if cache_path else None,
-                        ws.data_ptr(), need))
-    return {"tile_bits": opts.tile_bits, "flags": opts.flags}
+                        ws.data_ptr(), need, ctypes.byref(best_budget)))
+    inv = {v: k for k, v in GEMM.items()}
+    return {"tile_bits": opts.tile_bits, "flags": opts.flags, "gemm": inv.get(opts.gemm_mode, gemm),
+            "budget": int(best_budget.value)}
 
 
 class Batch:
