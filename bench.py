@@ -372,6 +372,7 @@ def bench_other(args):
             "config": {"workload": "c3_64_uneven_n20to32_window2^24", "circuits": len(items),
                        "n_range": [min(ns), max(ns)], "paths_range": [min(paths), max(paths)],
                        "graph_kernel_nodes": batch.nodes, "tuned": bool(args.tune),
+                       "tuned_choices": {str(k): v for k, v in tuned.items()},
                        "step": "one graph replay of hsf_run for all 64 plans"},
             "gpu_launches": int(launches),
             "roofline": {"bound": "tensor", "kernel": "path_gemm (largest circuit)", "achieved": tf,

@@ -28,6 +28,7 @@
 #include <queue>
 #include <set>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "plan.h"
@@ -745,8 +746,17 @@ void pack_pass(const PassH &ps, std::vector<DevOp> &dops, std::vector<C> &mats, 
 void compose_mma_levels(hsf_plan &p, int leaf_c) {
   const int B = (int)p.blocks.size();
   const int dim = 1 << kMmaBits, K = 2 * dim;
-  std::vector<double> w((size_t)K * K);
-  std::vector<cd> v(dim);
+  // One composition task per (level, digit); the levels' shared parts (the ops after the
+  // last digit-dependent one, composed once as S) are prepared first, serially.
+  struct LevelJob {
+    LevelH *lv;
+    std::vector<OpH> prefix;
+    size_t split;
+    std::vector<cd> S;       // column-major dim x dim
+    bool f16;
+    int r;
+  };
+  std::vector<LevelJob> jobs;
   for (int s = 0; s < 2; ++s)
     for (int k = 1; k <= B; ++k) {
       LevelH &lv = p.side[s].levels[k];
@@ -772,52 +782,81 @@ void compose_mma_levels(hsf_plan &p, int leaf_c) {
           for (auto &ps : lv.passes) build_groups(ps, p.rbits);
       }
       lv.mma = true;
-      const std::vector<OpH> &mops = prefix;
-      const int r = (int)p.radix[k];
+      LevelJob job;
+      job.lv = &lv;
+      job.prefix = prefix;
+      job.r = (int)p.radix[k];
       // a level with ops after the product runs the TF32 kernel, one without the FP16 one
-      const bool f16 = lv.post.empty();
-      lv.wimg.assign(f16 ? (size_t)r * (kMmaWDigitBytes / 4) + (size_t)r : (size_t)r * 2 * (kMmaWPartBytes / 4), 0.f);
+      job.f16 = lv.post.empty();
+      lv.wimg.assign(job.f16 ? (size_t)job.r * (kMmaWDigitBytes / 4) + (size_t)job.r
+                             : (size_t)job.r * 2 * (kMmaWPartBytes / 4),
+                     0.f);
       // the ops after the last digit-dependent one are shared by every digit: compose
       // them once (S, column-major), then U_m e_col = S (prefix_m e_col), where the
       // prefix image of a basis vector has few nonzeros
-      size_t split = 0;
-      for (size_t o = 0; o < mops.size(); ++o)
-        if (mops[o].digits > 1) split = o + 1;
-      std::vector<cd> S((size_t)dim * dim);
+      job.split = 0;
+      for (size_t o = 0; o < prefix.size(); ++o)
+        if (prefix[o].digits > 1) job.split = o + 1;
+      job.S.assign((size_t)dim * dim, cd(0.0));
+      std::vector<cd> v(dim);
       for (int col = 0; col < dim; ++col) {
         std::fill(v.begin(), v.end(), cd(0.0));
         v[col] = 1.0;
-        for (size_t o = split; o < mops.size(); ++o) host_apply(v, kMmaBits, mops[o], 0);
-        std::copy(v.begin(), v.end(), S.begin() + (size_t)col * dim);
+        for (size_t o = job.split; o < prefix.size(); ++o) host_apply(v, kMmaBits, prefix[o], 0);
+        std::copy(v.begin(), v.end(), job.S.begin() + (size_t)col * dim);
       }
-      std::vector<cd> u(dim);
-      for (int m = 0; m < r; ++m) {
-        for (int col = 0; col < dim; ++col) {
-          std::fill(u.begin(), u.end(), cd(0.0));
-          u[col] = 1.0;
-          for (size_t o = 0; o < split; ++o) host_apply(u, kMmaBits, mops[o], m);
-          std::fill(v.begin(), v.end(), cd(0.0));
-          for (int j = 0; j < dim; ++j) {
-            if (u[j] == cd(0.0)) continue;
-            const cd *sj = S.data() + (size_t)j * dim;
-            for (int row = 0; row < dim; ++row) cmac(v[row], sj[row], u[j]);
-          }
-          for (int row = 0; row < dim; ++row) {
-            w[(size_t)(2 * row) * K + 2 * col] = v[row].real();
-            w[(size_t)(2 * row) * K + 2 * col + 1] = -v[row].imag();
-            w[(size_t)(2 * row + 1) * K + 2 * col] = v[row].imag();
-            w[(size_t)(2 * row + 1) * K + 2 * col + 1] = v[row].real();
-          }
-        }
-        if (f16) {
-          level_mma_image_f16(w.data(), lv.wimg.data() + (size_t)m * (kMmaWDigitBytes / 4),
-                              lv.wimg.data() + (size_t)r * (kMmaWDigitBytes / 4) + m);
-        } else {
-          float *hi = lv.wimg.data() + (size_t)m * 2 * (kMmaWPartBytes / 4);
-          level_mma_image(w.data(), hi, hi + kMmaWPartBytes / 4);
-        }
+      jobs.push_back(std::move(job));
+    }
+  std::vector<std::pair<int, int>> tasks;     // (job, digit)
+  for (int j = 0; j < (int)jobs.size(); ++j)
+    for (int m = 0; m < jobs[j].r; ++m) tasks.push_back({j, m});
+  auto run_task = [&](const std::pair<int, int> &t, std::vector<double> &w, std::vector<cd> &u, std::vector<cd> &v) {
+    const LevelJob &job = jobs[t.first];
+    const int m = t.second;
+    for (int col = 0; col < dim; ++col) {
+      std::fill(u.begin(), u.end(), cd(0.0));
+      u[col] = 1.0;
+      for (size_t o = 0; o < job.split; ++o) host_apply(u, kMmaBits, job.prefix[o], m);
+      std::fill(v.begin(), v.end(), cd(0.0));
+      for (int j = 0; j < dim; ++j) {
+        if (u[j] == cd(0.0)) continue;
+        const cd *sj = job.S.data() + (size_t)j * dim;
+        for (int row = 0; row < dim; ++row) cmac(v[row], sj[row], u[j]);
+      }
+      for (int row = 0; row < dim; ++row) {
+        w[(size_t)(2 * row) * K + 2 * col] = v[row].real();
+        w[(size_t)(2 * row) * K + 2 * col + 1] = -v[row].imag();
+        w[(size_t)(2 * row + 1) * K + 2 * col] = v[row].imag();
+        w[(size_t)(2 * row + 1) * K + 2 * col + 1] = v[row].real();
       }
     }
+    LevelH &lv = *job.lv;
+    if (job.f16) {
+      level_mma_image_f16(w.data(), lv.wimg.data() + (size_t)m * (kMmaWDigitBytes / 4),
+                          lv.wimg.data() + (size_t)job.r * (kMmaWDigitBytes / 4) + m);
+    } else {
+      float *hi = lv.wimg.data() + (size_t)m * 2 * (kMmaWPartBytes / 4);
+      level_mma_image(w.data(), hi, hi + kMmaWPartBytes / 4);
+    }
+  };
+  // the digits' compositions write disjoint parts of their level's image: a few host
+  // threads take them in turn
+  const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+  const int nthreads = (int)std::min<size_t>(tasks.size(), std::min(8u, hw));
+  std::atomic<size_t> next{0};
+  auto worker = [&]() {
+    std::vector<double> w((size_t)K * K);
+    std::vector<cd> u(dim), v(dim);
+    for (size_t i = next++; i < tasks.size(); i = next++) run_task(tasks[i], w, u, v);
+  };
+  if (nthreads <= 1) {
+    worker();
+  } else {
+    std::vector<std::thread> pool;
+    for (int i = 1; i < nthreads; ++i) pool.emplace_back(worker);
+    worker();
+    for (auto &th : pool) th.join();
+  }
 }
 
 hsf_status build_programs(hsf_plan &p, bool grad) {
