@@ -157,6 +157,11 @@ PROFILED_TRAFFIC = {
     "level_f16": {"ratio": 1289.7 / 1342.2, "source": "paper_2502_06959_gb300/csrc/gemm_tc.cu",
                   "kernel": "level_mma_f16_kernel", "sha256": "5fafb56a20723142",
                   "profile": "profiles/level_f16_level7_n30.md"},
+    # level 6 of the small n=30 case (levels 5 and 6 share the kernel; level 5's output
+    # stayed in L2 there, so the larger launch's ratio stands for both)
+    "level_mma": {"ratio": 275.4 / 335.5, "source": "paper_2502_06959_gb300/csrc/gemm_tc.cu",
+                  "kernel": "level_mma_kernel", "sha256": "1aa361be73ac7e76",
+                  "profile": "profiles/level_mma_levels56_n30.md"},
     "leaf": {"ratio": 1868.7 / 2151.7, "source": "paper_2502_06959_gb300/csrc/accum.cu",
              "kernel": "leaf_contract_pair_kernel", "sha256": "6679c458867f2c10",
              "profile": "profiles/leaf_contract_pair_n30.md"},
@@ -303,6 +308,15 @@ def _timed(torch, stream, fn, steps):
     return e0.elapsed_time(e1)
 
 
+def _tuned_summary(tuned):
+    """How often each tuned choice was taken over the circuits."""
+    out = {}
+    for v in tuned.values():
+        key = f"tile{v['tile_bits']}/flags{v['flags']}/{v['gemm']}/budget={v['budget'] or 'full'}"
+        out[key] = out.get(key, 0) + 1
+    return out
+
+
 def bench_other(args):
     """Secondary workloads (one GPU): c3 batched graph, c4 gradients, c5 n=36, c1 parity."""
     import torch
@@ -329,18 +343,19 @@ def bench_other(args):
             return
         tuned = {}
         if args.tune:
+            # one tuning per circuit shape (the cache key is the circuit's structure: the
+            # same qubit count with another block count is another shape, and the best
+            # path-GEMM form depends on the path count)
             import tempfile
             cache = os.path.join(tempfile.gettempdir(), "hsf_tune_cache.txt")
             for pr in probs:
-                if pr.n in tuned:
-                    continue
                 window = min(1 << pr.n, 1 << 24)
-                tuned[pr.n] = hsf.hsf_tune(pr.n, pr.gates, pr.cut, pr.blocks, window=window, cache_path=cache,
-                                           gemm=args.gemm)
+                tuned[pr.name] = hsf.hsf_tune(pr.n, pr.gates, pr.cut, pr.blocks, window=window, cache_path=cache,
+                                              gemm=args.gemm)
         items = []
         for pr in probs:
             window = min(1 << pr.n, 1 << 24)
-            opts = dict(tuned.get(pr.n, {}))
+            opts = dict(tuned.get(pr.name, {}))
             opts.pop("budget", None)             # the batch shares one workspace
             gemm = opts.pop("gemm", args.gemm)
             plan = hsf.Plan.from_problem(pr, precision="c64", gemm=gemm, **opts)
@@ -372,7 +387,7 @@ def bench_other(args):
             "config": {"workload": "c3_64_uneven_n20to32_window2^24", "circuits": len(items),
                        "n_range": [min(ns), max(ns)], "paths_range": [min(paths), max(paths)],
                        "graph_kernel_nodes": batch.nodes, "tuned": bool(args.tune),
-                       "tuned_choices": {str(k): v for k, v in tuned.items()},
+                       "tuned_choices": _tuned_summary(tuned),
                        "step": "one graph replay of hsf_run for all 64 plans"},
             "gpu_launches": int(launches),
             "roofline": {"bound": "tensor", "kernel": "path_gemm (largest circuit)", "achieved": tf,

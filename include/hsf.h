@@ -217,6 +217,27 @@ hsf_status hsf_find_blocks(const hsf_circuit *circuit, int32_t cut_l, int32_t ma
                            int32_t *order, int32_t *offsets, int32_t *gate_idx, int32_t cap_blocks,
                            int32_t *num_blocks, int32_t *num_hubs);
 
+/* Qubit-reordering search for a better cut (Sec. VI: reordering the qubits to find
+ * better blocks is named as future work; no method is given there).  Searches the
+ * bipartitions of the qubits with n_b = cut_l + 1 qubits on side b for the one whose
+ * hsf_find_blocks blocks give the fewest joint paths: cost = log2 of the path count,
+ * with rank 2 for a cascade of two or more gates (Sec. IV-D, Example 4) and the
+ * operator-Schmidt rank of the relabeled matrix for a single crossing gate (Sec. IV-A).
+ * Local search: Kernighan-Lin passes of swaps of one a-qubit with one b-qubit (the
+ * best swap among qubits not yet moved in the pass, kept only up to the pass's best
+ * point), repeated while a pass improves, from the input bipartition and from
+ * `restarts` random ones drawn with splitmix64(seed).  Deterministic for a given seed.  Host-only, no device work.
+ *   perm:   out, n entries: new label of qubit q (side-b qubits get 0..cut_l, side-a
+ *           qubits cut_l+1..n-1, each side in ascending old label).  Relabeling every
+ *           gate's qubits by perm (and bit q of a bitstring to bit perm[q]) gives the
+ *           same circuit with the better cut after qubit cut_l.
+ *   log2_paths_before / _after: out (may be NULL), the cost of the input and of the
+ *           returned bipartition.
+ * HSF_EINVAL for a bad circuit, cut, max_leaves (1..8) or restarts < 0. */
+hsf_status hsf_search_cut(const hsf_circuit *circuit, int32_t cut_l, int32_t max_leaves,
+                          int32_t restarts, uint64_t seed, int32_t *perm,
+                          double *log2_paths_before, double *log2_paths_after);
+
 /* Release a plan and every device buffer it owns (its tables, and the workspace of
  * hsf_run calls made with workspace == NULL).  Waits for device work that may still
  * read them.  NULL is ignored.  The paper has no counterpart. */

@@ -472,125 +472,69 @@ __device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) {
   return d;
 }
 
-// Register-resident application of a group of epilogue ops whose qubits lie in three
-// storage bits b0 < b1 < b2 (< 11): a thread holds an octet (the 8 elements of a quarter
-// that differ only in those bits, register c = bit b0 + 2 bit b1 + 4 bit b2) and applies
-// the group's ops to it in registers, so a group costs one shared-memory load and store
-// per element instead of one per op.  Register positions are template parameters (no
-// local memory).
-template <int P0, int P1>
-__device__ __forceinline__ void oct_dense2(float2 (&x)[8], const float2 (&mr)[16], const float2 (&mi)[16]) {
-  constexpr int P2 = 3 - P0 - P1;
+__device__ __forceinline__ void apply_post_op(float *stage, const MmaPostOp *op, int t) {
+  // the op (staged in shared memory) is read into registers once, not per element
+  const int nq = op->nq, q0 = op->q0, q1 = op->q1, diag = op->diag;
+  if (diag) {
+    const float2 d0 = op->m[0], d1 = op->m[1];
+    const float2 d2 = nq == 2 ? op->m[2] : d0, d3 = nq == 2 ? op->m[3] : d1;
+    for (uint32_t i = t; i < 2048; i += 128) {
+      const uint32_t b0 = (i >> q0) & 1u;
+      float2 m;
+      if (nq == 2) {
+        const uint32_t b1 = (i >> q1) & 1u;
+        m = b0 ? (b1 ? d3 : d2) : (b1 ? d1 : d0);
+      } else {
+        m = b0 ? d1 : d0;
+      }
+      float2 *e = post_elem(stage, i);
+      *e = cmulf(m, *e);
+    }
+  } else if (nq == 1) {
+    const float2 m0 = op->m[0], m1 = op->m[1], m2 = op->m[2], m3 = op->m[3];
+    for (uint32_t j = t; j < 1024; j += 128) {
+      const uint32_t i0 = ins0(j, q0), i1 = i0 | (1u << q0);
+      float2 *e0 = post_elem(stage, i0), *e1 = post_elem(stage, i1);
+      const float2 x0 = *e0, x1 = *e1;
+      const float2 a = cmulf(m0, x0), b = cmulf(m1, x1), c = cmulf(m2, x0), d = cmulf(m3, x1);
+      *e0 = make_float2(a.x + b.x, a.y + b.y);
+      *e1 = make_float2(c.x + d.x, c.y + d.y);
+    }
+  } else {
+    // two-qubit dense op: the matrix as broadcast pairs (Re m, Re m) and (Im m, Im m), so
+    // that with x_k = (Re x_k, Im x_k) as it sits in the stage, P = sum mr * x and
+    // Q = sum mi * x are packed FMAs and (m x)_r = (P.x - Q.y, P.y + Q.x)
+    float2 mr[16], mi[16];
 #pragma unroll
-  for (int t = 0; t < 2; ++t) {
-    float2 v[4];
-#pragma unroll
-    for (int k = 0; k < 4; ++k) v[k] = x[((k >> 1) << P0) | ((k & 1) << P1) | (t << P2)];
-#pragma unroll
-    for (int r = 0; r < 4; ++r) {
-      float2 P = make_float2(0.f, 0.f), Q = P;
+    for (int e = 0; e < 16; ++e) {
+      const float2 v = op->m[e];
+      mr[e] = make_float2(v.x, v.x);
+      mi[e] = make_float2(v.y, v.y);
+    }
+    const int lo = min(q0, q1), hi = max(q0, q1);
+    for (uint32_t j = t; j < 512; j += 128) {
+      const uint32_t base = ins0(ins0(j, lo), hi);
+      float2 *e[4];
+      float2 x[4];
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
-        P = ffma2(mr[r * 4 + k], v[k], P);
-        Q = ffma2(mi[r * 4 + k], v[k], Q);
+        e[k] = post_elem(stage, base | ((uint32_t)(k >> 1) << q0) | ((uint32_t)(k & 1) << q1));
+        x[k] = *e[k];
       }
-      x[((r >> 1) << P0) | ((r & 1) << P1) | (t << P2)] = make_float2(P.x - Q.y, P.y + Q.x);
-    }
-  }
-}
-template <int P0, int P1>
-__device__ __forceinline__ void oct_diag2(float2 (&x)[8], const float2 (&d)[4]) {
+      float2 y[4];
 #pragma unroll
-  for (int c = 0; c < 8; ++c) x[c] = cmulf(d[(((c >> P0) & 1) << 1) | ((c >> P1) & 1)], x[c]);
-}
-template <int P>
-__device__ __forceinline__ void oct_dense1(float2 (&x)[8], const float2 (&m)[4]) {
+      for (int r = 0; r < 4; ++r) {
+        float2 P = make_float2(0.f, 0.f), Q = P;
 #pragma unroll
-  for (int c = 0; c < 8; ++c) {
-    if (c & (1 << P)) continue;
-    const float2 x0 = x[c], x1 = x[c | (1 << P)];
-    const float2 a = cmulf(m[0], x0), b = cmulf(m[1], x1), e = cmulf(m[2], x0), f = cmulf(m[3], x1);
-    x[c] = make_float2(a.x + b.x, a.y + b.y);
-    x[c | (1 << P)] = make_float2(e.x + f.x, e.y + f.y);
-  }
-}
-template <int P>
-__device__ __forceinline__ void oct_diag1(float2 (&x)[8], const float2 (&d)[4]) {
-#pragma unroll
-  for (int c = 0; c < 8; ++c) x[c] = cmulf(d[(c >> P) & 1], x[c]);
-}
-
-// Apply ops [o0, o1) of the staged list to a quarter; `bits` holds their storage bits
-// (at most three; padded with the lowest unused bits to exactly three).  Each thread
-// takes its two octets one after the other.
-__device__ __forceinline__ void apply_post_group(float *stage, const MmaPostOp *ops, int o0, int o1, uint32_t bits,
-                                                 int t) {
-  uint32_t pad = bits;
-  while (__popc(pad) < 3) pad |= ~pad & (pad + 1u);
-  uint32_t rest = pad;
-  const int b0 = __ffs(rest) - 1;
-  rest &= rest - 1u;
-  const int b1 = __ffs(rest) - 1;
-  rest &= rest - 1u;
-  const int b2 = __ffs(rest) - 1;
-  auto pos = [&](int q) { return __popc(pad & ((1u << q) - 1u)); };
-#pragma unroll 1
-  for (int h = 0; h < 2; ++h) {
-    const uint32_t j = (uint32_t)t + 128u * h;
-    const uint32_t base = ins0(ins0(ins0(j, b0), b1), b2);
-    float2 x[8];
-#pragma unroll
-    for (int c = 0; c < 8; ++c)
-      x[c] = *post_elem(stage, base | ((uint32_t)(c & 1) << b0) | ((uint32_t)((c >> 1) & 1) << b1) |
-                                   ((uint32_t)((c >> 2) & 1) << b2));
-#pragma unroll 1
-    for (int o = o0; o < o1; ++o) {
-      const MmaPostOp *op = ops + o;
-      const int nq = op->nq, diag = op->diag;
-      const int p0 = pos(op->q0), p1 = nq == 2 ? pos(op->q1) : 0;
-      if (nq == 2 && !diag) {
-        float2 mr[16], mi[16];
-#pragma unroll
-        for (int k = 0; k < 16; ++k) {
-          const float2 v = op->m[k];
-          mr[k] = make_float2(v.x, v.x);
-          mi[k] = make_float2(v.y, v.y);
+        for (int k = 0; k < 4; ++k) {
+          P = ffma2(mr[r * 4 + k], x[k], P);
+          Q = ffma2(mi[r * 4 + k], x[k], Q);
         }
-        switch (p0 * 3 + p1) {
-          case 1: oct_dense2<0, 1>(x, mr, mi); break;
-          case 2: oct_dense2<0, 2>(x, mr, mi); break;
-          case 3: oct_dense2<1, 0>(x, mr, mi); break;
-          case 5: oct_dense2<1, 2>(x, mr, mi); break;
-          case 6: oct_dense2<2, 0>(x, mr, mi); break;
-          default: oct_dense2<2, 1>(x, mr, mi); break;
-        }
-      } else if (nq == 2) {
-        const float2 d[4] = {op->m[0], op->m[1], op->m[2], op->m[3]};
-        switch (p0 * 3 + p1) {
-          case 1: oct_diag2<0, 1>(x, d); break;
-          case 2: oct_diag2<0, 2>(x, d); break;
-          case 3: oct_diag2<1, 0>(x, d); break;
-          case 5: oct_diag2<1, 2>(x, d); break;
-          case 6: oct_diag2<2, 0>(x, d); break;
-          default: oct_diag2<2, 1>(x, d); break;
-        }
-      } else {
-        const float2 m[4] = {op->m[0], op->m[1], diag ? op->m[0] : op->m[2], diag ? op->m[1] : op->m[3]};
-        if (diag) {
-          if (p0 == 0) oct_diag1<0>(x, m);
-          else if (p0 == 1) oct_diag1<1>(x, m);
-          else oct_diag1<2>(x, m);
-        } else {
-          if (p0 == 0) oct_dense1<0>(x, m);
-          else if (p0 == 1) oct_dense1<1>(x, m);
-          else oct_dense1<2>(x, m);
-        }
+        y[r] = make_float2(P.x - Q.y, P.y + Q.x);
       }
-    }
 #pragma unroll
-    for (int c = 0; c < 8; ++c)
-      *post_elem(stage, base | ((uint32_t)(c & 1) << b0) | ((uint32_t)((c >> 1) & 1) << b1) |
-                            ((uint32_t)((c >> 2) & 1) << b2)) = x[c];
+      for (int k = 0; k < 4; ++k) *e[k] = y[k];
+    }
   }
 }
 
@@ -834,22 +778,10 @@ __global__ void __launch_bounds__(kLvlThreads, 1) level_mma_kernel(const __grid_
         float *stage = sO + (size_t)(grp * kOutPerGroup + nq % kOutPerGroup) * 32 * 128;
 #pragma unroll
         for (int j = 0; j < 32; ++j) stage[j * 128 + comp] = __uint_as_float(v[j]);
-        // the rest of the level's program, on storage bits 0..10 of this quarter: runs of
-        // consecutive ops within three storage bits go through registers in one pass
-        for (int o = 0; o < a.num_post;) {
-          uint32_t bits = 1u << post_sh[o].q0;
-          if (post_sh[o].nq == 2) bits |= 1u << post_sh[o].q1;
-          int o1 = o + 1;
-          while (o1 < a.num_post) {
-            uint32_t more = bits | (1u << post_sh[o1].q0);
-            if (post_sh[o1].nq == 2) more |= 1u << post_sh[o1].q1;
-            if (__popc(more) > 3) break;
-            bits = more;
-            ++o1;
-          }
+        // the rest of the level's program, on storage bits 0..10 of this quarter
+        for (int o = 0; o < a.num_post; ++o) {
           asm volatile("bar.sync %0, 128;" ::"r"(bar_id) : "memory");
-          apply_post_group(stage, post_sh, o, o1, bits, comp);
-          o = o1;
+          apply_post_op(stage, post_sh + o, comp);
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         asm volatile("bar.sync %0, 128;" ::"r"(bar_id) : "memory");

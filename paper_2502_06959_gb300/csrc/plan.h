@@ -5,6 +5,7 @@
 #include <complex>
 #include <cstdint>
 #include <string>
+#include <functional>
 #include <vector>
 
 #include "../../include/hsf.h"
@@ -114,6 +115,17 @@ cudaStream_t side_stream();   // the calling thread's second stream for side b o
 hsf_status set_error(hsf_status code, const char *fmt, ...);
 // Plan-table device memory from a per-device arena (no cudaMalloc on the common path).
 // table_free returns a block at once: the caller makes sure no kernel still reads it.
+// Page-locked host staging buffer (planner.cpp): taken for one upload, given back after
+// its copy has completed.
+struct StagingBuf {
+  unsigned char *p = nullptr;
+  size_t size = 0, cap = 0;
+};
+StagingBuf staging_take();
+void staging_give(StagingBuf s);
+bool staging_reserve(StagingBuf &s, size_t need);
+// fn(0..n-1) on a persistent pool of host threads and the caller (planner.cpp).
+void host_parallel_for(size_t n, const std::function<void(size_t)> &fn);
 void *table_alloc(size_t bytes);
 void table_free(void *p);
 const char *last_error();

@@ -17,7 +17,9 @@
 //     program as one small operator per Schmidt digit, so the leaf level is contracted
 //     directly at the requested bitstrings instead of being simulated.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
+#include <condition_variable>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -160,6 +162,113 @@ void table_free(void *p) {
     A.free_blocks[ptr] = bytes;
     return;
   }
+}
+
+// Page-locked host staging for the table uploads: a few buffers reused across plans (one
+// is taken for an upload and given back once its copy has completed), so the copy runs
+// at DMA speed and nothing is allocated once the buffers have grown.
+namespace {
+std::mutex g_stage_mu;
+std::vector<StagingBuf> g_stage_free;
+}  // namespace
+
+StagingBuf staging_take() {
+  std::lock_guard<std::mutex> lock(g_stage_mu);
+  if (g_stage_free.empty()) return StagingBuf{};
+  StagingBuf s = g_stage_free.back();
+  g_stage_free.pop_back();
+  s.size = 0;
+  return s;
+}
+
+void staging_give(StagingBuf s) {
+  if (!s.p) return;
+  std::lock_guard<std::mutex> lock(g_stage_mu);
+  g_stage_free.push_back(s);
+}
+
+bool staging_reserve(StagingBuf &s, size_t need) {
+  if (need <= s.cap) return true;
+  const size_t cap = std::max(need, std::max(2 * s.cap, (size_t)1 << 20));
+  unsigned char *q = nullptr;
+  if (cudaHostAlloc((void **)&q, cap, cudaHostAllocPortable) != cudaSuccess) return false;
+  if (s.size) std::memcpy(q, s.p, s.size);
+  if (s.p) cudaFreeHost(s.p);
+  s.p = q;
+  s.cap = cap;
+  return true;
+}
+
+// A persistent pool of host threads for the plan's independent composition tasks (no
+// thread start per plan).  run(n, fn) calls fn(0..n-1) on the pool and the caller and
+// returns when all are done; a call made while the pool is busy (another host thread
+// planning) runs its tasks on the caller alone.
+namespace {
+class HostPool {
+ public:
+  explicit HostPool(int workers) {
+    for (int i = 0; i < workers; ++i) th_.emplace_back([this] { loop(); });
+    for (auto &t : th_) t.detach();       // the pool lives until the process exits
+  }
+  void run(size_t n, const std::function<void(size_t)> &fn) {
+    std::unique_lock<std::mutex> busy(run_mu_, std::try_to_lock);
+    if (!busy.owns_lock() || th_.empty() || n <= 1) {
+      for (size_t i = 0; i < n; ++i) fn(i);
+      return;
+    }
+    {
+      std::lock_guard<std::mutex> lk(mu_);
+      fn_ = &fn;
+      n_ = n;
+      next_ = 0;
+      active_ = (int)th_.size();
+      ++gen_;
+    }
+    cv_.notify_all();
+    work(fn, n);
+    std::unique_lock<std::mutex> lk(mu_);
+    done_cv_.wait(lk, [&] { return active_ == 0; });
+    fn_ = nullptr;
+  }
+
+ private:
+  void work(const std::function<void(size_t)> &fn, size_t n) {
+    for (size_t i = next_++; i < n; i = next_++) fn(i);
+  }
+  void loop() {
+    uint64_t seen = 0;
+    for (;;) {
+      const std::function<void(size_t)> *fn;
+      size_t n;
+      {
+        std::unique_lock<std::mutex> lk(mu_);
+        cv_.wait(lk, [&] { return gen_ != seen; });
+        seen = gen_;
+        fn = fn_;
+        n = n_;
+      }
+      work(*fn, n);
+      std::lock_guard<std::mutex> lk(mu_);
+      if (--active_ == 0) done_cv_.notify_all();
+    }
+  }
+  std::vector<std::thread> th_;
+  std::mutex run_mu_, mu_;
+  std::condition_variable cv_, done_cv_;
+  const std::function<void(size_t)> *fn_ = nullptr;
+  size_t n_ = 0;
+  std::atomic<size_t> next_{0};
+  int active_ = 0;
+  uint64_t gen_ = 0;
+};
+}  // namespace
+
+void host_parallel_for(size_t n, const std::function<void(size_t)> &fn) {
+  static HostPool *pool = [] {
+    const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+    return new HostPool((int)std::min(7u, hw > 1 ? hw - 1 : 0u));
+  }();
+  pool->run(n, fn);
 }
 
 int device_sm_count() {
@@ -747,7 +856,7 @@ void compose_mma_levels(hsf_plan &p, int leaf_c) {
   const int B = (int)p.blocks.size();
   const int dim = 1 << kMmaBits, K = 2 * dim;
   // One composition task per (level, digit); the levels' shared parts (the ops after the
-  // last digit-dependent one, composed once as S) are prepared first, serially.
+  // last digit-dependent one, composed once as S) are prepared first, one task per level.
   struct LevelJob {
     LevelH *lv;
     std::vector<OpH> prefix;
@@ -797,16 +906,20 @@ void compose_mma_levels(hsf_plan &p, int leaf_c) {
       job.split = 0;
       for (size_t o = 0; o < prefix.size(); ++o)
         if (prefix[o].digits > 1) job.split = o + 1;
-      job.S.assign((size_t)dim * dim, cd(0.0));
-      std::vector<cd> v(dim);
-      for (int col = 0; col < dim; ++col) {
-        std::fill(v.begin(), v.end(), cd(0.0));
-        v[col] = 1.0;
-        for (size_t o = job.split; o < prefix.size(); ++o) host_apply(v, kMmaBits, prefix[o], 0);
-        std::copy(v.begin(), v.end(), job.S.begin() + (size_t)col * dim);
-      }
       jobs.push_back(std::move(job));
     }
+  // the shared parts S, one task per level
+  host_parallel_for(jobs.size(), [&](size_t j) {
+    LevelJob &job = jobs[j];
+    job.S.assign((size_t)dim * dim, cd(0.0));
+    std::vector<cd> v(dim);
+    for (int col = 0; col < dim; ++col) {
+      std::fill(v.begin(), v.end(), cd(0.0));
+      v[col] = 1.0;
+      for (size_t o = job.split; o < job.prefix.size(); ++o) host_apply(v, kMmaBits, job.prefix[o], 0);
+      std::copy(v.begin(), v.end(), job.S.begin() + (size_t)col * dim);
+    }
+  });
   std::vector<std::pair<int, int>> tasks;     // (job, digit)
   for (int j = 0; j < (int)jobs.size(); ++j)
     for (int m = 0; m < jobs[j].r; ++m) tasks.push_back({j, m});
@@ -839,24 +952,16 @@ void compose_mma_levels(hsf_plan &p, int leaf_c) {
       level_mma_image(w.data(), hi, hi + kMmaWPartBytes / 4);
     }
   };
-  // the digits' compositions write disjoint parts of their level's image: a few host
-  // threads take them in turn
-  const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
-  const int nthreads = (int)std::min<size_t>(tasks.size(), std::min(8u, hw));
-  std::atomic<size_t> next{0};
-  auto worker = [&]() {
-    std::vector<double> w((size_t)K * K);
-    std::vector<cd> u(dim), v(dim);
-    for (size_t i = next++; i < tasks.size(); i = next++) run_task(tasks[i], w, u, v);
-  };
-  if (nthreads <= 1) {
-    worker();
-  } else {
-    std::vector<std::thread> pool;
-    for (int i = 1; i < nthreads; ++i) pool.emplace_back(worker);
-    worker();
-    for (auto &th : pool) th.join();
-  }
+  // the digits' compositions write disjoint parts of their level's image: the host pool
+  // takes them in turn
+  host_parallel_for(tasks.size(), [&](size_t i) {
+    thread_local std::vector<double> w;
+    thread_local std::vector<cd> u, v;
+    w.resize((size_t)K * K);
+    u.resize(dim);
+    v.resize(dim);
+    run_task(tasks[i], w, u, v);
+  });
 }
 
 hsf_status build_programs(hsf_plan &p, bool grad) {
@@ -1087,11 +1192,27 @@ hsf_status build_schrodinger(hsf_plan &p, const hsf_circuit *c, const hsf_plan_o
 }
 
 hsf_status upload_programs(hsf_plan &p, bool grad) {
-  std::vector<unsigned char> host;
-  auto align = [&](size_t a) { while (host.size() % a) host.push_back(0); };
-  auto append = [&](const void *ptr, size_t bytes) {
-    host.insert(host.end(), (const unsigned char *)ptr, (const unsigned char *)ptr + bytes);
-  };
+  // the table is assembled in page-locked staging and copied with one DMA
+  struct HostTable {
+    StagingBuf s = staging_take();
+    bool ok = true;
+    ~HostTable() { staging_give(s); }
+    size_t size() const { return s.size; }
+    bool empty() const { return s.size == 0; }
+    const unsigned char *data() const { return s.p; }
+    void put(const void *ptr, size_t bytes, bool zero) {
+      if (!bytes || !ok) return;
+      if (!staging_reserve(s, s.size + bytes)) {
+        ok = false;
+        return;
+      }
+      if (zero) std::memset(s.p + s.size, 0, bytes);
+      else std::memcpy(s.p + s.size, ptr, bytes);
+      s.size += bytes;
+    }
+  } host;
+  auto align = [&](size_t a) { host.put(nullptr, (a - host.size() % a) % a, true); };
+  auto append = [&](const void *ptr, size_t bytes) { host.put(ptr, bytes, false); };
   int64_t launches = 0;
   for (int s = 0; s < 2; ++s) {
     for (auto &lv : (grad ? p.gside[s] : p.side[s]).levels)
@@ -1146,7 +1267,8 @@ hsf_status upload_programs(hsf_plan &p, bool grad) {
     }
   }
   align(256);
-  if (host.empty()) host.resize(256);
+  if (host.empty()) host.put(nullptr, 256, true);
+  if (!host.ok) return set_error(HSF_ENOMEM, "page-locked staging of %zu bytes", host.size());
   void *&table = grad ? p.dev_gtable : p.dev_table;
   // from the table arena (no implicit stream synchronisation); hsf_plan_destroy waits
   // for the device before returning the block, so no queued kernel can still read it
@@ -1279,15 +1401,25 @@ hsf_status run_svd_jobs(const hsf_plan &p, const std::vector<SvdJob> &jobs, std:
   }
   CUDA_TRY(launch_block_svd(a, pst));
   g_launches++;
-  std::vector<double> sig((size_t)J * 64), xf(nf), yf(nf);
+  std::vector<double> sig((size_t)J * 64);
   std::vector<int32_t> rank(J), sweeps(J);
   std::vector<double> resid(J);
+  // the factors are read back only up to the widest factor row (4^|q_a| or 4^|q_b|
+  // entries of the 64 the device layout reserves per term)
+  int wx = 1, wy = 1;
+  for (int j = 0; j < J; ++j) {
+    wx = std::max(wx, 1 << (2 * bk[3 * j + 1]));
+    wy = std::max(wy, 1 << (2 * bk[3 * j + 2]));
+  }
+  std::vector<double> xf((size_t)J * 64 * wx * 2), yf((size_t)J * 64 * wy * 2);
   CUDA_TRY(cudaMemcpyAsync(sweeps.data(), d + o_sw, sweeps.size() * 4, cudaMemcpyDeviceToHost, pst));
   CUDA_TRY(cudaMemcpyAsync(resid.data(), d + o_res, resid.size() * 8, cudaMemcpyDeviceToHost, pst));
   CUDA_TRY(cudaMemcpyAsync(sig.data(), d + o_sig, sig.size() * 8, cudaMemcpyDeviceToHost, pst));
   CUDA_TRY(cudaMemcpyAsync(rank.data(), d + o_rank, rank.size() * 4, cudaMemcpyDeviceToHost, pst));
-  CUDA_TRY(cudaMemcpyAsync(xf.data(), d + o_x, nf * 8, cudaMemcpyDeviceToHost, pst));
-  CUDA_TRY(cudaMemcpyAsync(yf.data(), d + o_y, nf * 8, cudaMemcpyDeviceToHost, pst));
+  CUDA_TRY(cudaMemcpy2DAsync(xf.data(), (size_t)wx * 16, d + o_x, 64 * 16, (size_t)wx * 16, (size_t)J * 64,
+                             cudaMemcpyDeviceToHost, pst));
+  CUDA_TRY(cudaMemcpy2DAsync(yf.data(), (size_t)wy * 16, d + o_y, 64 * 16, (size_t)wy * 16, (size_t)J * 64,
+                             cudaMemcpyDeviceToHost, pst));
   CUDA_TRY(cudaStreamSynchronize(pst));
   for (int j = 0; j < J; ++j) {
     BlockH &r = out[j];
@@ -1319,11 +1451,11 @@ hsf_status run_svd_jobs(const hsf_plan &p, const std::vector<SvdJob> &jobs, std:
     const int ea = 1 << (2 * (int)r.qa.size()), eb = 1 << (2 * (int)r.qb.size());
     for (int m = 0; m < r.rank; ++m) {
       for (int e = 0; e < ea; ++e) {
-        const size_t i = (((size_t)j * 64 + m) * 64 + e) * 2;
+        const size_t i = (((size_t)j * 64 + m) * wx + e) * 2;
         r.x.push_back(cd(xf[i], xf[i + 1]));
       }
       for (int e = 0; e < eb; ++e) {
-        const size_t i = (((size_t)j * 64 + m) * 64 + e) * 2;
+        const size_t i = (((size_t)j * 64 + m) * wy + e) * 2;
         r.y.push_back(cd(yf[i], yf[i + 1]));
       }
     }

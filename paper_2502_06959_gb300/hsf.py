@@ -116,6 +116,9 @@ SIGNATURES = {
     "hsf_find_blocks": (ctypes.c_int, [ctypes.POINTER(hsf_circuit), ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p,
                                        ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
                                        ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]),
+    "hsf_search_cut": (ctypes.c_int, [ctypes.POINTER(hsf_circuit), ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                      ctypes.c_uint64, ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
+                                      ctypes.POINTER(ctypes.c_double)]),
     "hsf_last_error": (ctypes.c_char_p, []),
     "hsf_set_profiling": (None, [ctypes.c_int32]),
     "hsf_profile_collect": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32]),
@@ -281,6 +284,46 @@ def problem_with_found_blocks(problem, max_leaves: int = 8):
     out.gates = [problem.gates[i] for i in order]
     out.blocks = blocks
     out.meta = dict(problem.meta, hubs=hubs, found_blocks=len(blocks))
+    return out
+
+
+def hsf_search_cut(n: int, gates, cut: int, max_leaves: int = 8, restarts: int = 4, seed: int = 1):
+    """Qubit-reordering search (hsf_search_cut): returns (perm, log2_paths_before,
+    log2_paths_after) where perm[q] is the new label of qubit q."""
+    lib = load_library()
+    circ, _, keep = _marshal(n, gates, [])
+    perm = np.zeros(n, dtype=np.int32)
+    before, after = ctypes.c_double(), ctypes.c_double()
+    _check(lib.hsf_search_cut(ctypes.byref(circ), cut, max_leaves, restarts, seed, perm.ctypes.data,
+                              ctypes.byref(before), ctypes.byref(after)))
+    return [int(x) for x in perm], float(before.value), float(after.value)
+
+
+def relabel_problem(problem, perm):
+    """The same circuit with qubit q renamed perm[q] (gates, bitstrings); blocks are
+    dropped (find them again on the relabeled circuit)."""
+    import copy
+    from . import workloads as W
+    out = copy.copy(problem)
+    out.gates = [W.Gate(g.kind, tuple(perm[q] for q in g.qubits), g.param, g.param_id, g.matrix)
+                 for g in problem.gates]
+    out.blocks = []
+    if problem.bitstrings is not None:
+        src = problem.bitstrings.astype(np.uint64)
+        dst = np.zeros_like(src)
+        for q, t in enumerate(perm):
+            dst |= ((src >> np.uint64(q)) & np.uint64(1)) << np.uint64(t)
+        out.bitstrings = dst
+    out.meta = dict(problem.meta, perm=list(perm))
+    return out
+
+
+def problem_with_searched_cut(problem, max_leaves: int = 8, restarts: int = 4, seed: int = 1):
+    """hsf_search_cut, then the relabeled circuit cut into the blocks hsf_find_blocks
+    finds (the cut position stays problem.cut)."""
+    perm, before, after = hsf_search_cut(problem.n, problem.gates, problem.cut, max_leaves, restarts, seed)
+    out = problem_with_found_blocks(relabel_problem(problem, perm), max_leaves)
+    out.meta = dict(out.meta, log2_paths_before=before, log2_paths_after=after)
     return out
 
 

@@ -191,3 +191,29 @@ def test_sbm_qaoa_found_blocks_joint_plain_schrodinger():
     got = plan.run(window=100000, check=True).cpu().numpy()
     plan.close()
     assert np.max(np.abs(got - ref)) <= 1e-5
+
+
+def test_searched_cut_of_scrambled_sbm_qaoa():
+    """A q20-shaped SBM-QAOA instance with scrambled qubit labels: hsf_search_cut
+    relabels it, the planner runs the blocks found on the relabeled circuit with exactly
+    2^(reported log2 paths) paths, and the amplitudes equal the oracle's Schroedinger
+    amplitudes of the input circuit under the bit permutation."""
+    from paper_2502_06959_gb300 import hsf
+    pr = W.sbm_qaoa((10, 10), 0.8, 0.2, seed=22)
+    rng = np.random.default_rng(4)
+    ps = hsf.relabel_problem(pr, [int(x) for x in rng.permutation(pr.n)])
+    q = hsf.problem_with_searched_cut(ps)
+    assert q.meta["log2_paths_after"] < q.meta["log2_paths_before"]
+    perm = q.meta["perm"]
+    ref = O.schrodinger(ps.n, ps.gates)
+    x = np.arange(1 << ps.n, dtype=np.int64)
+    xp = np.zeros_like(x)
+    for a, b in enumerate(perm):
+        xp |= ((x >> a) & 1) << b
+    ref_new = np.empty_like(ref)
+    ref_new[xp] = ref                           # amplitudes of the relabeled circuit
+    plan = hsf.Plan.from_problem(q, precision="c64", gemm="fp32")
+    assert plan.info["num_paths"] == round(2 ** q.meta["log2_paths_after"])
+    got = plan.run(window=1 << 16, check=True).cpu().numpy()
+    plan.close()
+    assert np.max(np.abs(got - ref_new[:1 << 16])) <= 1e-5
