@@ -541,6 +541,131 @@ __global__ void __launch_bounds__(128, 6) leaf_contract_pair_kernel(LeafArgs a) 
   }
 }
 
+// Leaf contraction with the chunk split over the digit lanes: the RM lanes of one
+// (bitstring, side) each read only their D / RM entries of the chunk and form the partial
+// products of ALL RM digits over them; a reduce-scatter across the RM lanes (log2 RM
+// shuffle rounds, halving the digits each round) leaves lane q with digit q summed over
+// the whole chunk.  The same FMAs as one lane per digit over the whole chunk, but each
+// chunk entry is read from shared memory once instead of RM times (broadcast).  Lane
+// layout and stage rows as in leaf_contract_pair_kernel.
+template <int CB, int RM>
+__global__ void __launch_bounds__(128, 5) leaf_contract_split_kernel(LeafArgs a) {
+  using C = float2;
+  constexpr int D = 1 << CB;
+  constexpr int KQ = D / RM;                   // complex chunk entries per lane
+  static_assert(KQ >= 2 && KQ % 2 == 0, "a lane reads whole 16-byte pieces");
+  constexpr int SPB = 128 / (2 * RM);
+  constexpr int SB = 2 * D + 4;
+  constexpr int BOFF = D + 2;
+  constexpr int STAGE = SPB * SB;
+  constexpr int HALF = D / 2;
+  extern __shared__ __align__(16) unsigned char leaf_smem[];
+  C(*buf)[STAGE] = reinterpret_cast<C(*)[STAGE]>(leaf_smem);
+  const int q = threadIdx.x % RM;              // chunk part; after the reduce-scatter, the digit
+  const int side = (threadIdx.x / RM) & 1;
+  const int sl = threadIdx.x / (2 * RM);
+  const int64_t s = (int64_t)blockIdx.x * SPB + sl;
+  const int g = blockIdx.y;
+  uint64_t idx = 0;
+  if (s < a.S) idx = side == 0 ? a.ia[s] : a.ib[s];
+  const int rr = (int)(idx & (D - 1));
+  // entries k = q KQ + i of row rr of every L_m, as broadcast pairs (see the pair kernel)
+  C lr[RM][KQ], li[RM][KQ];
+  {
+    const C *gL = reinterpret_cast<const C *>(side == 0 ? a.La : a.Lb);
+#pragma unroll
+    for (int m = 0; m < RM; ++m) {
+      const bool mv = s < a.S && m < a.r;
+      const C *row = gL + ((size_t)(mv ? m : 0) * D + rr) * D + q * KQ;
+#pragma unroll
+      for (int i = 0; i < KQ; ++i) {
+        const C v = mv ? row[i] : make_float2(0.f, 0.f);
+        lr[m][i] = make_float2(v.x, v.x);
+        li[m][i] = make_float2(v.y, v.y);
+      }
+    }
+  }
+  const bool on = s < a.S && q < a.r;
+  const int64_t j0 = (int64_t)g * a.parents_per_group;
+  const int64_t j1 = min(a.num_parents, j0 + a.parents_per_group);
+  const int64_t np = j1 - j0;
+  const int hbits = side == 0 ? a.ha : a.hb;
+  const C *src = reinterpret_cast<const C *>(side == 0 ? a.Pa : a.Pb) + (idx - rr);
+  const int roff = sl * SB + side * BOFF;
+  auto issue = [&](int64_t jj, int stage) {
+    if (jj < j1 && s < a.S) {
+      C *row = buf[stage] + roff;
+      const C *sp = src + ((uint64_t)jj << hbits);
+#pragma unroll
+      for (int i = 0; i < (HALF + RM - 1) / RM; ++i) {
+        const int p = q + i * RM;
+        if (p < HALF) cp_async16(row + 2 * p, sp + 2 * p);
+      }
+    }
+    cp_commit();
+  };
+#pragma unroll
+  for (int d = 0; d < kPairDepth - 1; ++d) issue(j0 + d, d);
+  float accr = 0.f, acci = 0.f;
+  for (int64_t t = 0; t < np; ++t) {
+    cp_wait<kPairDepth - 2>();
+    __syncwarp();
+    issue(j0 + t + kPairDepth - 1, (int)((t + kPairDepth - 1) % kPairDepth));
+    const int64_t j = j0 + t;
+    const float4 *x = reinterpret_cast<const float4 *>(buf[t % kPairDepth] + roff + q * KQ);
+    C xk[KQ];
+#pragma unroll
+    for (int i = 0; i < KQ / 2; ++i) {
+      const float4 v = x[i];
+      xk[2 * i] = make_float2(v.x, v.y);
+      xk[2 * i + 1] = make_float2(v.z, v.w);
+    }
+    float vr[RM], vi[RM];
+#pragma unroll
+    for (int m = 0; m < RM; ++m) {
+      C P = make_float2(0.f, 0.f), Q = P;
+#pragma unroll
+      for (int i = 0; i < KQ; ++i) {
+        P = ffma2(lr[m][i], xk[i], P);
+        Q = ffma2(li[m][i], xk[i], Q);
+      }
+      vr[m] = P.x - Q.y;
+      vi[m] = P.y + Q.x;
+    }
+    // reduce-scatter: each round the lanes with bit o set keep the upper half of their
+    // digit range and send the lower half to lane ^ o, which does the opposite
+#pragma unroll
+    for (int o = RM / 2; o > 0; o >>= 1) {
+      const bool up = (q & o) != 0;
+#pragma unroll
+      for (int i = 0; i < o; ++i) {
+        const float sr = up ? vr[i] : vr[i + o], si = up ? vi[i] : vi[i + o];
+        const float kr = up ? vr[i + o] : vr[i], ki = up ? vi[i + o] : vi[i];
+        vr[i] = kr + __shfl_xor_sync(0xffffffffu, sr, o);
+        vi[i] = ki + __shfl_xor_sync(0xffffffffu, si, o);
+      }
+    }
+    const bool use = on && !((j == 0 && q < a.m_first) || (j == a.num_parents - 1 && q >= a.m_last));
+    const float ur = use ? vr[0] : 0.f, ui = use ? vi[0] : 0.f;
+    // the other side's value for the same bitstring and digit
+    const float wr = __shfl_xor_sync(0xffffffffu, ur, RM);
+    const float wi = __shfl_xor_sync(0xffffffffu, ui, RM);
+    accr = fmaf(ur, wr, fmaf(-ui, wi, accr));
+    acci = fmaf(ur, wi, fmaf(ui, wr, acci));
+  }
+  cp_wait<0>();
+#pragma unroll
+  for (int o = RM / 2; o > 0; o >>= 1) {
+    accr += __shfl_xor_sync(0xffffffffu, accr, o);
+    acci += __shfl_xor_sync(0xffffffffu, acci, o);
+  }
+  if (q == 0 && side == 0 && s < a.S) {
+    double *dst = a.partial + 2 * ((int64_t)g * a.S + s);
+    dst[0] = (double)accr;
+    dst[1] = (double)acci;
+  }
+}
+
 // Leaf contraction for large bitstring counts.  One co-resident wave of CTAs; CTA b
 // owns bitstrings [b * per_cta, (b + 1) * per_cta), and every CTA walks all parents in
 // the same order, so the parents being read at any time are few and stay in L2 however
@@ -811,6 +936,14 @@ cudaError_t leaf_reg_dispatch(const LeafArgs &a, cudaStream_t st) {
       return cudaGetLastError();
     };
     if constexpr (CB >= 2) {
+      // chunk split over the digit lanes where every lane gets whole 16-byte pieces
+      if (rm >= 2 && (1 << CB) >= 2 * rm) {
+        switch (rm) {
+          case 2: return go_pair(leaf_contract_split_kernel<CB, (CB >= 2 ? 2 : 1)>, 2);
+          case 4: return go_pair(leaf_contract_split_kernel<CB, (CB >= 3 ? 4 : 1)>, 4);
+          default: return go_pair(leaf_contract_split_kernel<CB, (CB >= 4 ? 8 : 1)>, 8);
+        }
+      }
       switch (rm) {
         case 1: return go_pair(leaf_contract_pair_kernel<CB, 1>, 1);
         case 2: return go_pair(leaf_contract_pair_kernel<CB, 2>, 2);

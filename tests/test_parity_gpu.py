@@ -417,3 +417,22 @@ def test_c5_n36_sampled_paths(path_range):
     got, ginfo = gpu_amps(pr, "c64", bitstrings=pr.bitstrings, path_range=path_range)
     assert ginfo["num_paths"] == 4 ** 12
     check(got, want, "c64")
+
+
+def test_leaf_kernel_shapes_covered():
+    """The (leaf width, operator count) pairs that the leaf-rank problems above reach:
+    they must include chunk-split shapes (2^width >= 2 x operators, 2 or more operators)
+    at two widths, so that the split kernel's reduce-scatter over 2 and 4 lanes is
+    checked against the oracle there."""
+    from paper_2502_06959_gb300 import hsf
+    shapes = set()
+    for rank in (1, 2, 4, 8):
+        for tail in (0, 1, 2):
+            pr = _leaf_rank_problem(rank, tail, seed=70 + rank + 10 * tail)
+            plan = hsf.Plan.from_problem(pr, precision="c64")
+            info = plan.info
+            plan.close()
+            if info["leaf_bits"] > 0:
+                shapes.add((int(info["leaf_bits"]), rank))
+    split = {(c, r) for (c, r) in shapes if r >= 2 and (1 << c) >= 2 * r}
+    assert len({r for (_, r) in split}) >= 2, shapes
