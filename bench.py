@@ -162,9 +162,6 @@ PROFILED_TRAFFIC = {
     "level_mma": {"ratio": 275.4 / 335.5, "source": "paper_2502_06959_gb300/csrc/gemm_tc.cu",
                   "kernel": "level_mma_kernel", "sha256": "1aa361be73ac7e76",
                   "profile": "profiles/level_mma_levels56_n30.md"},
-    "leaf": {"ratio": 1868.7 / 2151.7, "source": "paper_2502_06959_gb300/csrc/accum.cu",
-             "kernel": "leaf_contract_pair_kernel", "sha256": "6679c458867f2c10",
-             "profile": "profiles/leaf_contract_pair_n30.md"},
 }
 
 

@@ -569,19 +569,22 @@ __global__ void __launch_bounds__(128, 5) leaf_contract_split_kernel(LeafArgs a)
   uint64_t idx = 0;
   if (s < a.S) idx = side == 0 ? a.ia[s] : a.ib[s];
   const int rr = (int)(idx & (D - 1));
-  // entries k = q KQ + i of row rr of every L_m, as broadcast pairs (see the pair kernel)
+  // entries k = q KQ + i of row rr of every L_m, as broadcast pairs (see the pair kernel);
+  // slot j holds digit j ^ q, so that in every reduce-scatter round the values a lane
+  // keeps and the ones it sends sit at fixed slots (no selects)
   C lr[RM][KQ], li[RM][KQ];
   {
     const C *gL = reinterpret_cast<const C *>(side == 0 ? a.La : a.Lb);
 #pragma unroll
-    for (int m = 0; m < RM; ++m) {
+    for (int jm = 0; jm < RM; ++jm) {
+      const int m = jm ^ q;
       const bool mv = s < a.S && m < a.r;
       const C *row = gL + ((size_t)(mv ? m : 0) * D + rr) * D + q * KQ;
 #pragma unroll
       for (int i = 0; i < KQ; ++i) {
         const C v = mv ? row[i] : make_float2(0.f, 0.f);
-        lr[m][i] = make_float2(v.x, v.x);
-        li[m][i] = make_float2(v.y, v.y);
+        lr[jm][i] = make_float2(v.x, v.x);
+        li[jm][i] = make_float2(v.y, v.y);
       }
     }
   }
@@ -632,17 +635,15 @@ __global__ void __launch_bounds__(128, 5) leaf_contract_split_kernel(LeafArgs a)
       vr[m] = P.x - Q.y;
       vi[m] = P.y + Q.x;
     }
-    // reduce-scatter: each round the lanes with bit o set keep the upper half of their
-    // digit range and send the lower half to lane ^ o, which does the opposite
+    // reduce-scatter: in the round over lane bit o a lane keeps slots [0, o) and sends
+    // slots [o, 2o); slot i + o of lane q ^ o holds the digit of slot i of lane q, since
+    // (i + o) ^ (q ^ o) = i ^ q for i < o.  Slot 0 ends with digit q summed over the RM lanes.
 #pragma unroll
     for (int o = RM / 2; o > 0; o >>= 1) {
-      const bool up = (q & o) != 0;
 #pragma unroll
       for (int i = 0; i < o; ++i) {
-        const float sr = up ? vr[i] : vr[i + o], si = up ? vi[i] : vi[i + o];
-        const float kr = up ? vr[i + o] : vr[i], ki = up ? vi[i + o] : vi[i];
-        vr[i] = kr + __shfl_xor_sync(0xffffffffu, sr, o);
-        vi[i] = ki + __shfl_xor_sync(0xffffffffu, si, o);
+        vr[i] += __shfl_xor_sync(0xffffffffu, vr[i + o], o);
+        vi[i] += __shfl_xor_sync(0xffffffffu, vi[i + o], o);
       }
     }
     const bool use = on && !((j == 0 && q < a.m_first) || (j == a.num_parents - 1 && q >= a.m_last));
@@ -660,6 +661,166 @@ __global__ void __launch_bounds__(128, 5) leaf_contract_split_kernel(LeafArgs a)
     acci += __shfl_xor_sync(0xffffffffu, acci, o);
   }
   if (q == 0 && side == 0 && s < a.S) {
+    double *dst = a.partial + 2 * ((int64_t)g * a.S + s);
+    dst[0] = (double)accr;
+    dst[1] = (double)acci;
+  }
+}
+
+// Factored leaf contraction.  When every leaf operator is L_m = S (F_m (x) I) with F_m a
+// one-qubit factor on chunk bit PF (both sides), a parent's contribution at a bitstring
+// is the bilinear form sum_{al, be} G[al][be] d_a[al] d_b[be] (see factor_leaf): d holds
+// the four dots d[(i, j)] = sum_k w[(i, k)] x[(j, k)] of the row w = S[rr] with the
+// bitstring's chunk x (i, j the factor bit, k the other chunk bits), and G the digit sum
+// of F^a (x) F^b.  One thread per (bitstring, side): lanes t (side a) and t ^ 1 (side b)
+// swap their d with one shuffle per value, and each adds half of the form (rows al of
+// its own side's pair).  Stage rows as in leaf_contract_pair_kernel.
+constexpr int kFactDepth = 4;
+constexpr int kFactSpb = 64;                   // bitstrings per 128-thread CTA
+constexpr size_t leaf_fact_ring_bytes(int cb) { return (size_t)kFactDepth * kFactSpb * ((2u << cb) + 4) * 8; }
+
+template <int CB, int PF>
+__global__ void __launch_bounds__(128, 3) leaf_contract_fact_kernel(LeafArgs a) {
+  using C = float2;
+  constexpr int D = 1 << CB;
+  constexpr int H = D / 2;
+  constexpr int SB = 2 * D + 4;
+  constexpr int BOFF = D + 2;
+  constexpr int STAGE = kFactSpb * SB;
+  static_assert(PF < CB, "the factor bit lies in the chunk");
+  extern __shared__ __align__(16) unsigned char leaf_smem[];
+  C(*buf)[STAGE] = reinterpret_cast<C(*)[STAGE]>(leaf_smem);
+  const int side = threadIdx.x & 1;
+  const int sl = threadIdx.x >> 1;
+  const int64_t s = (int64_t)blockIdx.x * kFactSpb + sl;
+  const int g = blockIdx.y;
+  uint64_t idx = 0;
+  if (s < a.S) idx = side == 0 ? a.ia[s] : a.ib[s];
+  const int rr = (int)(idx & (D - 1));
+  // w = S[rr] as broadcast pairs (see the pair kernel)
+  C wr[D], wi[D];
+  {
+    const C *row = reinterpret_cast<const C *>(side == 0 ? a.Sa : a.Sb) + (size_t)rr * D;
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      const C v = row[k];
+      wr[k] = make_float2(v.x, v.x);
+      wi[k] = make_float2(v.y, v.y);
+    }
+  }
+  // rows al = 2 side, 2 side + 1 of G over all digits
+  const C *Gt = reinterpret_cast<const C *>(a.G);
+  const int r1 = a.r + 1;
+  C g0[4], g1[4];
+  {
+    const C *G = Gt + (size_t)a.r * 16;        // [m0 = 0][m1 = r]
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      g0[b] = G[(2 * side) * 4 + b];
+      g1[b] = G[(2 * side + 1) * 4 + b];
+    }
+  }
+  const int64_t j0 = (int64_t)g * a.parents_per_group;
+  const int64_t j1 = min(a.num_parents, j0 + a.parents_per_group);
+  const int64_t np = j1 - j0;
+  const int hbits = side == 0 ? a.ha : a.hb;
+  const C *src = reinterpret_cast<const C *>(side == 0 ? a.Pa : a.Pb) + (idx - rr);
+  const int roff = sl * SB + side * BOFF;
+  auto issue = [&](int64_t jj, int stage) {
+    if (jj < j1 && s < a.S) {
+      C *row = buf[stage] + roff;
+      const C *sp = src + ((uint64_t)jj << hbits);
+#pragma unroll
+      for (int q = 0; q < H; ++q) cp_async16(row + 2 * q, sp + 2 * q);
+    }
+    cp_commit();
+  };
+#pragma unroll
+  for (int d = 0; d < kFactDepth - 1; ++d) issue(j0 + d, d);
+  float accr = 0.f, acci = 0.f;
+  for (int64_t t = 0; t < np; ++t) {
+    cp_wait<kFactDepth - 2>();
+    __syncwarp();
+    issue(j0 + t + kFactDepth - 1, (int)((t + kFactDepth - 1) % kFactDepth));
+    const int64_t j = j0 + t;
+    const float4 *x4 = reinterpret_cast<const float4 *>(buf[t % kFactDepth] + roff);
+    C x[D];
+#pragma unroll
+    for (int q = 0; q < H; ++q) {
+      const float4 v = x4[q];
+      x[2 * q] = make_float2(v.x, v.y);
+      x[2 * q + 1] = make_float2(v.z, v.w);
+    }
+    // the four dots, al = 2 i + j
+    C P[4], Q[4];
+#pragma unroll
+    for (int al = 0; al < 4; ++al) P[al] = Q[al] = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int k = 0; k < H; ++k) {
+      constexpr int lo = (1 << PF) - 1;
+      const int e0 = ((k & ~lo) << 1) | (k & lo), e1 = e0 | (1 << PF);   // factor bit 0 / 1
+      P[0] = ffma2(wr[e0], x[e0], P[0]);
+      Q[0] = ffma2(wi[e0], x[e0], Q[0]);
+      P[1] = ffma2(wr[e0], x[e1], P[1]);
+      Q[1] = ffma2(wi[e0], x[e1], Q[1]);
+      P[2] = ffma2(wr[e1], x[e0], P[2]);
+      Q[2] = ffma2(wi[e1], x[e0], Q[2]);
+      P[3] = ffma2(wr[e1], x[e1], P[3]);
+      Q[3] = ffma2(wi[e1], x[e1], Q[3]);
+    }
+    float dr[4], di[4], er[4], ei[4];
+#pragma unroll
+    for (int al = 0; al < 4; ++al) {
+      dr[al] = P[al].x - Q[al].y;
+      di[al] = P[al].y + Q[al].x;
+      er[al] = __shfl_xor_sync(0xffffffffu, dr[al], 1);
+      ei[al] = __shfl_xor_sync(0xffffffffu, di[al], 1);
+    }
+    // d_a and d_b of this bitstring
+    float ar[4], ai[4], br[4], bi[4];
+#pragma unroll
+    for (int al = 0; al < 4; ++al) {
+      ar[al] = side == 0 ? dr[al] : er[al];
+      ai[al] = side == 0 ? di[al] : ei[al];
+      br[al] = side == 0 ? er[al] : dr[al];
+      bi[al] = side == 0 ? ei[al] : di[al];
+    }
+    C h0[4], h1[4];
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      h0[b] = g0[b];
+      h1[b] = g1[b];
+    }
+    if ((j == 0 && a.m_first > 0) || (j == a.num_parents - 1 && a.m_last < a.r)) {
+      // a parent with only part of its digits in the path range
+      const int m0 = j == 0 ? a.m_first : 0, m1 = j == a.num_parents - 1 ? a.m_last : a.r;
+      const C *G = Gt + ((size_t)m0 * r1 + m1) * 16;
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        h0[b] = G[(2 * side) * 4 + b];
+        h1[b] = G[(2 * side + 1) * 4 + b];
+      }
+    }
+    // this lane's half: sum over al = 2 side + {0, 1} of d_a[al] (G[al] . d_b)
+    float u0r = 0.f, u0i = 0.f, u1r = 0.f, u1i = 0.f;
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      u0r = fmaf(h0[b].x, br[b], fmaf(-h0[b].y, bi[b], u0r));
+      u0i = fmaf(h0[b].x, bi[b], fmaf(h0[b].y, br[b], u0i));
+      u1r = fmaf(h1[b].x, br[b], fmaf(-h1[b].y, bi[b], u1r));
+      u1i = fmaf(h1[b].x, bi[b], fmaf(h1[b].y, br[b], u1i));
+    }
+    const float a0r = side == 0 ? ar[0] : ar[2], a0i = side == 0 ? ai[0] : ai[2];
+    const float a1r = side == 0 ? ar[1] : ar[3], a1i = side == 0 ? ai[1] : ai[3];
+    accr = fmaf(a0r, u0r, fmaf(-a0i, u0i, accr));
+    acci = fmaf(a0r, u0i, fmaf(a0i, u0r, acci));
+    accr = fmaf(a1r, u1r, fmaf(-a1i, u1i, accr));
+    acci = fmaf(a1r, u1i, fmaf(a1i, u1r, acci));
+  }
+  cp_wait<0>();
+  accr += __shfl_xor_sync(0xffffffffu, accr, 1);
+  acci += __shfl_xor_sync(0xffffffffu, acci, 1);
+  if (side == 0 && s < a.S) {
     double *dst = a.partial + 2 * ((int64_t)g * a.S + s);
     dst[0] = (double)accr;
     dst[1] = (double)acci;
@@ -1011,8 +1172,38 @@ bool leaf_streams(const LeafArgs &a, int precision) {
   }
 }
 
+bool leaf_factored(const LeafArgs &a, int precision) {
+  return precision == 0 && a.pf >= 0 && a.pf < a.c && a.c >= 2 && a.c <= 4 && a.r >= 3 && a.r <= 4 &&
+         !leaf_streams(a, precision);
+}
+
+template <int CB>
+cudaError_t leaf_fact_launch(const LeafArgs &a, cudaStream_t st) {
+  auto go = [&](auto kernel) -> cudaError_t {
+    const size_t smem = leaf_fact_ring_bytes(CB);
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    dim3 grid((unsigned)((a.S + kFactSpb - 1) / kFactSpb), (unsigned)a.num_groups);
+    kernel<<<grid, 128, smem, st>>>(a);
+    return cudaGetLastError();
+  };
+  switch (a.pf) {
+    case 0: return go(leaf_contract_fact_kernel<CB, 0>);
+    case 1: return go(leaf_contract_fact_kernel<CB, (CB > 1 ? 1 : 0)>);
+    case 2: return go(leaf_contract_fact_kernel<CB, (CB > 2 ? 2 : 0)>);
+    default: return go(leaf_contract_fact_kernel<CB, (CB > 3 ? 3 : 0)>);
+  }
+}
+
 cudaError_t launch_leaf_contract(const LeafArgs &a, int precision, cudaStream_t st) {
   if (a.S <= 0 || a.num_parents <= 0) return cudaSuccess;
+  if (leaf_factored(a, precision)) {
+    switch (a.c) {
+      case 2: return leaf_fact_launch<2>(a, st);
+      case 3: return leaf_fact_launch<3>(a, st);
+      default: return leaf_fact_launch<4>(a, st);
+    }
+  }
   if (leaf_streams(a, precision)) {
     switch (a.c) {
       case 1: return leaf_stream_launch<1>(a, st);

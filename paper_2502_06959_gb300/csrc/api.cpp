@@ -362,7 +362,8 @@ int64_t hsf_plan_describe(const hsf_plan *p, char *buf, int64_t cap) {
                     bk.qa.size(), bk.qb.size(), bk.rank, bk.sweeps, bk.residual);
     out += line;
   }
-  std::snprintf(line, sizeof line, "leaf_bits=%d paths=%llu\n", p->leaf_c, (unsigned long long)p->num_paths);
+  std::snprintf(line, sizeof line, "leaf_bits=%d paths=%llu%s\n", p->leaf_c, (unsigned long long)p->num_paths,
+                p->leaf_pf >= 0 ? " leaf=factored" : "");
   out += line;
   if (buf && cap > 0) {
     const int64_t n = std::min<int64_t>(cap - 1, (int64_t)out.size());
@@ -616,7 +617,14 @@ hsf_status hsf_run(hsf_plan *p, const uint64_t *bits, size_t num, uint64_t windo
       la.partial = (double *)(ws + L.off_partial);
       la.sync = (uint32_t *)(ws + L.off_sync);
       la.err = p->dev_status;
-      if (leaf_streams(la, p->precision)) {
+      la.pf = p->leaf_pf;
+      if (p->leaf_pf >= 0) {
+        la.Sa = (unsigned char *)p->dev_table + p->side[0].leaf_s_off;
+        la.Sb = (unsigned char *)p->dev_table + p->side[1].leaf_s_off;
+        la.G = (unsigned char *)p->dev_table + p->leaf_g_off;
+      }
+      const bool streams = leaf_streams(la, p->precision);
+      if (streams) {
         la.parents_per_group = (int32_t)la.num_parents;
         la.num_groups = 1;
       }
@@ -625,8 +633,12 @@ hsf_status hsf_run(hsf_plan *p, const uint64_t *bits, size_t num, uint64_t windo
       // chunks, when the bitstrings touch few of them) plus the FP64 partials
       const double gathered = units * 2.0 * (1 << la.c) * csz;
       const double states = (double)la.num_parents * (double)((1ull << la.ha) + (1ull << la.hb)) * csz;
-      LAUNCH(HSF_KERNEL_LEAF, std::min(gathered, states) + 16.0 * la.num_groups * num,
-             units * la.r * (8.0 * 2.0 * (1 << la.c) + 8.0), launch_leaf_contract(la, p->precision, st));
+      // FLOP per (bitstring, parent): r digits x (two dots of 2^c terms + the product), or
+      // factored: four dots of 2^(c-1) terms per side + the 4 x 4 bilinear form
+      const double fl = leaf_factored(la, p->precision) ? 8.0 * (4.0 * (1 << la.c) + 20.0)
+                                                         : la.r * (8.0 * 2.0 * (1 << la.c) + 8.0);
+      LAUNCH(HSF_KERNEL_LEAF, std::min(gathered, states) + 16.0 * la.num_groups * num, units * fl,
+             launch_leaf_contract(la, p->precision, st));
       LAUNCH(HSF_KERNEL_REDUCE, 16.0 * la.num_groups * num + 64.0 * num, 0.0,
              launch_reduce_partials(la.partial, la.num_groups, la.S, outd, comp, st));
     } else if (num > 0) {

@@ -99,6 +99,9 @@ struct LeafArgs {
   const uint64_t *ia, *ib;   // storage index of every bitstring on each side
   int64_t S;
   int32_t parents_per_group, num_groups;
+  int32_t pf;            // >= 0: factored leaf operators (L_m = S (F_m (x) I), factor on chunk bit pf)
+  const void *Sa, *Sb;   // factored: S of each side, [2^c][2^c] row-major
+  const void *G;         // factored: [(r+1)][(r+1)][4][4], G over digits [m0, m1)
   double *partial;       // [num_groups][S][2]
   uint32_t *sync;        // 2 words of device scratch (grid barrier of the streaming kernel)
   int32_t *err;          // device status word
@@ -292,6 +295,8 @@ cudaError_t launch_leaf_contract(const LeafArgs &a, int precision, cudaStream_t 
 // true when launch_leaf_contract uses the one-wave streaming kernel (large bitstring
 // counts); it then writes a single partial per bitstring (num_groups = 1)
 bool leaf_streams(const LeafArgs &a, int precision);
+// the factored leaf kernel runs for this launch (FP32, factored operators, 3-4 digits)
+bool leaf_factored(const LeafArgs &a, int precision);
 cudaError_t launch_index_prep(const IndexArgs &a, cudaStream_t st);
 // dst[i] = storage index of local index i, i < count.
 cudaError_t launch_range_index(uint64_t *dst, int64_t count, const PermArgs &perm, cudaStream_t st);

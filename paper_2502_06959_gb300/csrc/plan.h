@@ -104,6 +104,9 @@ struct SideH {
   // storage bits (padded to the plan-wide leaf_c)
   std::vector<cd> leaf_ops;     // r x 2^c x 2^c
   size_t leaf_off = 0;
+  std::vector<OpH> leaf_pre;    // the leaf level's ops before fusion (storage bits)
+  std::vector<cd> leaf_S;       // factored leaf: L_m = S (F_m (x) I), S as 2^c x 2^c
+  size_t leaf_s_off = 0;
 };
 
 }  // namespace hsf
@@ -178,6 +181,9 @@ struct hsf_plan {
   int64_t tree_nodes = 0;
   int64_t launches = 0;
   int leaf_c = 0;                   // > 0: the leaf level can be contracted at bitstrings
+  int leaf_pf = -1;                 // >= 0: factored leaf, the factor's storage bit in the chunk
+  std::vector<hsf::cd> leaf_G;      // [(r+1)][(r+1)][4][4]: sum over digits [m0, m1) of F^a (x) F^b
+  size_t leaf_g_off = 0;
   int rbits = 4;                    // register slots of the register-resident sweep
   struct ProfRec { int kind; cudaEvent_t e0, e1; double bytes, flops; };
   std::vector<ProfRec> prof;

@@ -964,6 +964,68 @@ void compose_mma_levels(hsf_plan &p, int leaf_c) {
   });
 }
 
+// Factored leaf operators.  The leaf level opens with the last block's Schmidt factor
+// (Sec. IV-A: the factors X_m, Y_m start the branch of digit m), so before fusion its
+// program is [F_m, rest]; when F_m is a one-qubit operator on the same storage bit of
+// the chunk on both sides and the rest is digit-independent, L_m = S (F_m (x) I) with S
+// the rest's matrix.  Then, with w = row x of S and d[(i, j)] = sum_k w[(i, k)] x[(j, k)]
+// (i, j: the factor bit of the output and of the input),
+//   sum_m (L^a_m x_a)(L^b_m x_b) = sum_{al, be} G[al][be] d_a[al] d_b[be],
+//   G[(i, j)][(i', j')] = sum_m F^a_m[i][j] F^b_m[i'][j'],
+// which is what the factored leaf kernel evaluates; the digit sum is done here once (for
+// every digit range [m0, m1), so that partial path ranges need no other operator).  Only
+// worth it for 3 or 4 digits on chunks of 4..16 amplitudes.
+void factor_leaf(hsf_plan &p) {
+  p.leaf_pf = -1;
+  const int B = (int)p.blocks.size(), r = (int)p.radix[B], c = p.leaf_c, dim = 1 << c;
+  if (p.precision != HSF_PREC_C64 || r < 3 || r > 4 || c < 2 || c > 4) return;
+  int pf = -1;
+  std::vector<cd> F[2];
+  for (int s = 0; s < 2; ++s) {
+    const std::vector<OpH> &pre = p.side[s].leaf_pre;
+    if (pre.empty() || pre[0].type != OP_DENSE || pre[0].nq != 1 || pre[0].digits != r ||
+        pre[0].block != B - 1 || pre[0].m.size() != (size_t)4 * r)
+      return;
+    if (s == 1 && pre[0].q[0] != pf) return;
+    pf = pre[0].q[0];
+    if (pf >= c) return;
+    for (size_t o = 1; o < pre.size(); ++o)
+      if (pre[o].digits != 1) return;
+    F[s] = pre[0].m;
+    std::vector<cd> S((size_t)dim * dim, 0.0);
+    for (int col = 0; col < dim; ++col) {
+      std::vector<cd> v(dim, 0.0);
+      v[col] = 1.0;
+      for (size_t o = 1; o < pre.size(); ++o) host_apply(v, c, pre[o], 0);
+      for (int row = 0; row < dim; ++row) S[(size_t)row * dim + col] = v[row];
+    }
+    // check S (F_m (x) I) against the fused operators
+    double err = 0.0, mx = 0.0;
+    for (int m = 0; m < r; ++m)
+      for (int row = 0; row < dim; ++row)
+        for (int col = 0; col < dim; ++col) {
+          const int jf = (col >> pf) & 1;
+          cd z = 0.0;
+          for (int kf = 0; kf < 2; ++kf)
+            z += S[(size_t)row * dim + ((col & ~(1 << pf)) | (kf << pf))] * F[s][(size_t)m * 4 + kf * 2 + jf];
+          const cd L = p.side[s].leaf_ops[((size_t)m * dim + row) * dim + col];
+          err = std::max(err, std::abs(z - L));
+          mx = std::max(mx, std::abs(L));
+        }
+    if (!(err <= 1e-10 * std::max(1.0, mx))) return;
+    p.side[s].leaf_S = S;
+  }
+  p.leaf_G.assign((size_t)(r + 1) * (r + 1) * 16, 0.0);
+  for (int m0 = 0; m0 < r; ++m0)
+    for (int m1 = m0 + 1; m1 <= r; ++m1) {
+      cd *G = p.leaf_G.data() + ((size_t)m0 * (r + 1) + m1) * 16;
+      for (int m = m0; m < m1; ++m)
+        for (int al = 0; al < 4; ++al)
+          for (int be = 0; be < 4; ++be) G[al * 4 + be] += F[0][(size_t)m * 4 + al] * F[1][(size_t)m * 4 + be];
+    }
+  p.leaf_pf = pf;
+}
+
 hsf_status build_programs(hsf_plan &p, bool grad) {
   const int B = (int)p.blocks.size();
   std::vector<std::pair<bool, int>> order;
@@ -1055,6 +1117,7 @@ hsf_status build_programs(hsf_plan &p, bool grad) {
     for (auto &lv : sd.levels)
       for (auto &op : lv.ops)
         for (int j = 0; j < op.nq; ++j) op.q[j] = sd.store[op.q[j]];
+    if (!grad) sd.leaf_pre = sd.levels[B].ops;
     for (auto &lv : sd.levels) {
       merge_one_qubit_runs(lv.ops);
       if (!grad && !(p.flags & HSF_FLAG_NO_REGISTER_SWEEP)) absorb_into_two_qubit(lv.ops);
@@ -1118,6 +1181,7 @@ hsf_status build_programs(hsf_plan &p, bool grad) {
           for (int row = 0; row < dim; ++row) sd.leaf_ops[((size_t)m * dim + row) * dim + col] = v[row];
         }
     }
+    factor_leaf(p);
   }
   compose_mma_levels(p, p.leaf_c);
   return HSF_OK;
@@ -1264,6 +1328,22 @@ hsf_status upload_programs(hsf_plan &p, bool grad) {
         double2 c = make_double2(z.real(), z.imag());
         append(&c, sizeof c);
       }
+    }
+    if (!grad && p.leaf_pf >= 0) {
+      align(256);
+      sd.leaf_s_off = host.size();
+      for (auto &z : sd.leaf_S) {
+        float2 c = make_float2((float)z.real(), (float)z.imag());
+        append(&c, sizeof c);
+      }
+    }
+  }
+  if (!grad && p.leaf_pf >= 0) {
+    align(256);
+    p.leaf_g_off = host.size();
+    for (auto &z : p.leaf_G) {
+      float2 c = make_float2((float)z.real(), (float)z.imag());
+      append(&c, sizeof c);
     }
   }
   align(256);
