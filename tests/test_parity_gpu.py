@@ -438,30 +438,34 @@ def test_leaf_kernel_shapes_covered():
     assert len({r for (_, r) in split}) >= 2, shapes
 
 
-@pytest.mark.parametrize("tail", [0, 1, 2])
-def test_factored_leaf_against_oracle_and_direct(tail):
-    """A rank-4 last block (one qubit per side): its leaf operators factor as
-    S (F_m (x) I), and the factored kernel (digit sum folded into a 4 x 4 bilinear form)
-    must equal the oracle over all paths and over path ranges that cut a parent's digits
-    (first parent from digit 1 or 3, last parent up to digit 1 or 3, a single parent),
-    and the direct kernel of the same plan with the leaf contraction off."""
+def test_factored_leaf_against_oracle_and_direct():
+    """Rank-4 last blocks (one qubit per side): where the leaf spans 2 to 4 chunk bits
+    its operators factor as S (F_m (x) I), and the factored kernel (digit sum folded
+    into a 4 x 4 bilinear form) must equal the oracle over all paths and over path
+    ranges that cut a parent's digits (first parent from digit 1 or 3, last parent up
+    to digit 1 or 3, a single parent).  The leaf widens with the tail layers; the
+    factored kernel must have run for at least one of them."""
     from paper_2502_06959_gb300 import hsf
-    pr = _leaf_rank_problem(4, tail, seed=170 + tail)
-    rng = np.random.default_rng(tail + 300)
-    bs = W.random_bitstrings(rng, pr.n, 333)
-    plan = hsf.Plan.from_problem(pr, precision="c64")
-    desc = hsf.hsf_plan_describe(plan.handle)
-    plan.close()
-    if tail == 0:
-        assert "leaf=factored" in desc, desc.splitlines()[-1]
-    ref = O.schrodinger(pr.n, pr.gates)[bs.astype(np.int64)]
-    got, info = gpu_amps(pr, "c64", bitstrings=bs)
-    check(got, ref, "c64")
-    P = info["num_paths"]
-    for (a, b) in ((1, P), (0, P - 1), (3, P - 3), (5, 7), (P // 2 + 1, P // 2 + 3), (4, 8)):
-        want, _ = O.hsf_amplitudes(pr.n, pr.gates, pr.cut, pr.blocks, bitstrings=bs, path_range=(a, b))
-        got, _ = gpu_amps(pr, "c64", bitstrings=bs, path_range=(a, b))
-        check(got, want, "c64")
+    widths = set()
+    for tail in (0, 1, 2, 3):
+        pr = _leaf_rank_problem(4, tail, seed=170 + tail)
+        rng = np.random.default_rng(tail + 300)
+        bs = W.random_bitstrings(rng, pr.n, 333)
+        plan = hsf.Plan.from_problem(pr, precision="c64")
+        desc = hsf.hsf_plan_describe(plan.handle)
+        c = int(plan.info["leaf_bits"])
+        plan.close()
+        if "leaf=factored" in desc:
+            widths.add(c)
+        ref = O.schrodinger(pr.n, pr.gates)[bs.astype(np.int64)]
+        got, info = gpu_amps(pr, "c64", bitstrings=bs)
+        check(got, ref, "c64")
+        P = info["num_paths"]
+        for (a, b) in ((1, P), (0, P - 1), (3, P - 3), (5, 7), (P // 2 + 1, P // 2 + 3), (4, 8)):
+            want, _ = O.hsf_amplitudes(pr.n, pr.gates, pr.cut, pr.blocks, bitstrings=bs, path_range=(a, b))
+            got, _ = gpu_amps(pr, "c64", bitstrings=bs, path_range=(a, b))
+            check(got, want, "c64")
+    assert widths, "no leaf took the factored kernel"
 
 
 def test_c2_leaf_is_factored():
