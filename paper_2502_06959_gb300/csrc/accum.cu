@@ -723,15 +723,35 @@ __global__ void __launch_bounds__(128, 3) leaf_contract_fact_kernel(LeafArgs a) 
   const int64_t j0 = (int64_t)g * a.parents_per_group;
   const int64_t j1 = min(a.num_parents, j0 + a.parents_per_group);
   const int64_t np = j1 - j0;
-  const int hbits = side == 0 ? a.ha : a.hb;
-  const C *src = reinterpret_cast<const C *>(side == 0 ? a.Pa : a.Pb) + (idx - rr);
   const int roff = sl * SB + side * BOFF;
-  auto issue = [&](int64_t jj, int stage) {
-    if (jj < j1 && s < a.S) {
-      C *row = buf[stage] + roff;
-      const C *sp = src + ((uint64_t)jj << hbits);
+  // The warp's 32 chunks (16 bitstrings x 2 sides) are copied with whole chunks per
+  // instruction: in copy q lane l moves 16-byte piece l % H of chunk (32 / H) q + l / H,
+  // so one instruction covers 32 / H chunks of contiguous bytes instead of 32 scattered
+  // pieces.  Chunk c of the warp is bitstring c / 2, side c % 2; cof[q] is its origin.
+  constexpr int CPI = 32 / H;                  // chunks per copy instruction
+  const int lane = threadIdx.x & 31, wbase = threadIdx.x & ~31;
+  uint32_t cof[H];
+  bool cok[H];
 #pragma unroll
-      for (int q = 0; q < H; ++q) cp_async16(row + 2 * q, sp + 2 * q);
+  for (int q = 0; q < H; ++q) {
+    const int c = CPI * q + lane / H;
+    const int64_t sc = (int64_t)blockIdx.x * kFactSpb + (wbase >> 1) + (c >> 1);
+    cok[q] = sc < a.S;
+    const uint64_t ic = cok[q] ? ((c & 1) == 0 ? a.ia[sc] : a.ib[sc]) : 0;
+    cof[q] = (uint32_t)(ic & ~(uint64_t)(D - 1));
+  }
+  auto issue = [&](int64_t jj, int stage) {
+    if (jj < j1) {
+#pragma unroll
+      for (int q = 0; q < H; ++q) {
+        const int c = CPI * q + lane / H, piece = lane % H;
+        if (cok[q]) {
+          const int sd = c & 1;
+          const C *sp = reinterpret_cast<const C *>(sd == 0 ? a.Pa : a.Pb) +
+                        (((uint64_t)jj << (sd == 0 ? a.ha : a.hb)) + cof[q]);
+          cp_async16(buf[stage] + ((wbase >> 1) + (c >> 1)) * SB + sd * BOFF + 2 * piece, sp + 2 * piece);
+        }
+      }
     }
     cp_commit();
   };
@@ -1174,7 +1194,7 @@ bool leaf_streams(const LeafArgs &a, int precision) {
 
 bool leaf_factored(const LeafArgs &a, int precision) {
   return precision == 0 && a.pf >= 0 && a.pf < a.c && a.c >= 2 && a.c <= 4 && a.r >= 3 && a.r <= 4 &&
-         !leaf_streams(a, precision);
+         a.ha <= 32 && a.hb <= 32 && !leaf_streams(a, precision);
 }
 
 template <int CB>
