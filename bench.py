@@ -157,6 +157,9 @@ PROFILED_TRAFFIC = {
     "level_f16": {"ratio": 1289.7 / 1342.2, "source": "paper_2502_06959_gb300/csrc/gemm_tc.cu",
                   "kernel": "level_mma_f16_kernel", "sha256": "5fafb56a20723142",
                   "profile": "profiles/level_f16_level7_n30.md"},
+    "leaf": {"ratio": (1896.2 + 7.5) / 2151.7, "source": "paper_2502_06959_gb300/csrc/accum.cu",
+             "kernel": "leaf_contract_fact_kernel", "sha256": "50afedbb5f9cb3f9",
+             "profile": "profiles/leaf_contract_fact_n30.md"},
     # level 6 of the small n=30 case (levels 5 and 6 share the kernel; level 5's output
     # stayed in L2 there, so the larger launch's ratio stands for both)
     "level_mma": {"ratio": 275.4 / 335.5, "source": "paper_2502_06959_gb300/csrc/gemm_tc.cu",
@@ -759,6 +762,10 @@ def main():
     total_kernel_ms = sum(v["ms"] for v in kstats.values())
 
     def roofline_of(kind):
+        """The kernel against the roof that binds its algorithmic work: the HBM roof when
+        its bytes take longer at the measured bandwidth than its FLOP at the compute
+        peak of its unit (FP32 ALU; TF32 or FP16 tensor pipe), else that compute roof.
+        The other roof's fraction is reported beside it."""
         st = kstats.get(kind, {})
         k_ms, nlk = st.get("ms", 0.0), max(1, st.get("launches", 1))
         gbs = st.get("bytes", 0.0) / (k_ms / 1e3) / 1e9 if k_ms else 0.0
@@ -766,26 +773,25 @@ def main():
         tr = traffic_per_launch(kind, st.get("bytes", 0.0) / nlk)
         r = {"kernel": kind, "launches": int(st.get("launches", 0)), "avg_launch_ms": k_ms / nlk,
              "share": k_ms / total_kernel_ms if total_kernel_ms else 0.0}
-        if kind in ("level_mma", "level_f16"):
-            # three products per level (TF32 parts, or FP16 parts): counted flops are
-            # the three products actually issued; FP16 shares BF16's nominal dense rate
-            peak = tf32_peak_tflops if kind == "level_mma" else bf16_peak
-            src = " (bf16 x 1.1/2.25 nominal TF32 ratio)" if kind == "level_mma" else \
-                " (cuBLAS bf16; fp16 has the same nominal dense rate)"
-            r.update({"bound": "tensor", "achieved": tfl, "peak": peak, "unit": "TFLOP/s",
-                      "frac": tfl / peak if peak else None, "peak_source": peak_src + src,
-                      "hbm_gbs": gbs, "hbm_frac": gbs / hbm_peak if hbm_peak else None, "traffic": tr})
-        elif kind == "leaf":
-            # 33 FLOP per algorithmic byte, above the FP32 machine balance (80.5 TFLOP/s over
-            # the measured HBM bandwidth, about 12 FLOP/B): the FP32 ALU roof binds
-            r.update({"bound": "alu", "achieved": tfl, "peak": fp32_peak_tflops, "unit": "TFLOP/s",
-                      "frac": tfl / fp32_peak_tflops, "traffic": tr,
-                      "peak_source": "152 SMs x 128 FP32 lanes x 2 x max SM clock",
-                      "hbm_gbs": gbs, "hbm_frac": gbs / hbm_peak if hbm_peak else None})
+        if kind == "level_mma":
+            # three TF32 products per level: counted flops are the products issued
+            cpeak, cunit, csrc = tf32_peak_tflops, "tensor", peak_src + " (bf16 x 1.1/2.25 nominal TF32 ratio)"
+        elif kind == "level_f16":
+            cpeak, cunit, csrc = bf16_peak, "tensor", peak_src + " (cuBLAS bf16; fp16 has the same nominal dense rate)"
         else:
-            r.update({"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s",
-                      "frac": gbs / hbm_peak if hbm_peak else None, "traffic": tr, "peak_source": peak_src,
-                      "alu_tflops": tfl, "alu_peak_tflops": fp32_peak_tflops, "alu_frac": tfl / fp32_peak_tflops})
+            cpeak, cunit, csrc = fp32_peak_tflops, "alu", "152 SMs x 128 FP32 lanes x 2 x max SM clock"
+        intensity = st.get("flops", 0.0) / st.get("bytes", 1.0) if st.get("bytes") else 0.0
+        balance = cpeak * 1e12 / (hbm_peak * 1e9) if hbm_peak else 0.0
+        hbm = {"achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak if hbm_peak else None,
+               "peak_source": peak_src}
+        comp = {"achieved": tfl, "peak": cpeak, "unit": "TFLOP/s", "frac": tfl / cpeak if cpeak else None,
+                "peak_source": csrc}
+        if intensity < balance:
+            r.update({"bound": "hbm", **hbm, "traffic": tr, "flop_per_byte": intensity, "balance": balance,
+                      cunit: comp})
+        else:
+            r.update({"bound": cunit, **comp, "traffic": tr, "flop_per_byte": intensity, "balance": balance,
+                      "hbm": hbm})
         return r
 
     dominant = max(kstats, key=lambda k: kstats[k]["ms"]) if kstats else "sweep"
