@@ -910,8 +910,9 @@ __global__ void __launch_bounds__(kStreamThreads) leaf_stream_kernel(LeafArgs a,
     bs[i].ob = (uint32_t)(ib - rb);
     bs[i].rr = ra | (rb << 8);
     bs[i].acc = make_float2(0.f, 0.f);
-    a.partial[2 * (s0 + i)] = 0.0;
-    a.partial[2 * (s0 + i) + 1] = 0.0;
+    const int64_t o = a.perm ? a.perm[s0 + i] : s0 + i;
+    a.partial[2 * o] = 0.0;
+    a.partial[2 * o + 1] = 0.0;
   }
   __syncthreads();
   for (int64_t j0 = 0; j0 < a.num_parents; j0 += kStreamBatch) {
@@ -957,33 +958,119 @@ __global__ void __launch_bounds__(kStreamThreads) leaf_stream_kernel(LeafArgs a,
     // every thread only ever touches its own bitstrings i = tid + k * blockDim.x
     for (int i = threadIdx.x; i < ns; i += blockDim.x) {
       const float2 c = bs[i].acc;
-      a.partial[2 * (s0 + i)] += (double)c.x;
-      a.partial[2 * (s0 + i) + 1] += (double)c.y;
+      const int64_t o = a.perm ? a.perm[s0 + i] : s0 + i;
+      a.partial[2 * o] += (double)c.x;
+      a.partial[2 * o + 1] += (double)c.y;
       bs[i].acc = make_float2(0.f, 0.f);
     }
   }
 }
 
+// The streaming kernel with the digit sum folded into the pair form: each (bitstring,
+// parent) adds x_a^T H[i][i'] x_b (see pair_leaf), H[i][i'] of the full digit range
+// from shared memory, of a partial range (the first or last parent of a path range)
+// from the table in global memory.
 template <int CB>
+__global__ void __launch_bounds__(kStreamThreads) leaf_stream_pair_kernel(LeafArgs a, int64_t per_cta) {
+  using C = float2;
+  constexpr int D = 1 << CB;
+  constexpr int PER = D * D * D * D;
+  extern __shared__ __align__(16) unsigned char leaf_smem[];
+  C *sH = reinterpret_cast<C *>(leaf_smem);
+  StreamBits *bs = reinterpret_cast<StreamBits *>(sH + PER);
+  const C *gH = reinterpret_cast<const C *>(a.H);
+  const int r1 = a.r + 1;
+  const int64_t s0 = (int64_t)blockIdx.x * per_cta;
+  const int ns = (int)(min(a.S, s0 + per_cta) - s0);
+  for (int e = threadIdx.x; e < PER; e += blockDim.x) sH[e] = gH[(size_t)a.r * PER + e];   // [0][r]
+  for (int i = threadIdx.x; i < ns; i += blockDim.x) {
+    const uint64_t ia = a.ia[s0 + i], ib = a.ib[s0 + i];
+    const uint32_t ra = (uint32_t)(ia & (D - 1)), rb = (uint32_t)(ib & (D - 1));
+    bs[i].oa = (uint32_t)(ia - ra);
+    bs[i].ob = (uint32_t)(ib - rb);
+    bs[i].rr = ra | (rb << 8);
+    bs[i].acc = make_float2(0.f, 0.f);
+    const int64_t o = a.perm ? a.perm[s0 + i] : s0 + i;
+    a.partial[2 * o] = 0.0;
+    a.partial[2 * o + 1] = 0.0;
+  }
+  __syncthreads();
+  for (int64_t j0 = 0; j0 < a.num_parents; j0 += kStreamBatch) {
+    const int64_t j1 = min(a.num_parents, j0 + kStreamBatch);
+    for (int64_t j = j0; j < j1; ++j) {
+      if (j % kStreamSync == 0 && j > 0) stream_barrier(a.sync, a.sync + 1, gridDim.x, a.err);
+      const int mlo = j == 0 ? a.m_first : 0;
+      const int mhi = j == a.num_parents - 1 ? a.m_last : a.r;
+      const bool full = mlo == 0 && mhi == a.r;
+      const C *Ht = full ? sH : gH + ((size_t)mlo * r1 + mhi) * PER;
+      const C *Pa = reinterpret_cast<const C *>(a.Pa) + ((uint64_t)j << a.ha);
+      const C *Pb = reinterpret_cast<const C *>(a.Pb) + ((uint64_t)j << a.hb);
+      for (int i = threadIdx.x; i < ns; i += blockDim.x) {
+        const StreamBits st = bs[i];
+        C xa[D], xb[D];
+#pragma unroll
+        for (int k2 = 0; k2 < D / 2; ++k2) {
+          const float4 u = __ldg(reinterpret_cast<const float4 *>(Pa + st.oa) + k2);
+          const float4 v = __ldg(reinterpret_cast<const float4 *>(Pb + st.ob) + k2);
+          xa[2 * k2] = make_float2(u.x, u.y);
+          xa[2 * k2 + 1] = make_float2(u.z, u.w);
+          xb[2 * k2] = make_float2(v.x, v.y);
+          xb[2 * k2 + 1] = make_float2(v.z, v.w);
+        }
+        const int ra = (int)(st.rr & 255u), rb = (int)(st.rr >> 8);
+        const C *h = Ht + (size_t)(ra * D + rb) * D * D;
+        float sr = 0.f, si = 0.f;
+#pragma unroll
+        for (int jj = 0; jj < D; ++jj) {
+          float ur = 0.f, ui = 0.f;       // (H[i][i'] x_b)[jj]
+#pragma unroll
+          for (int j2 = 0; j2 < D; ++j2) {
+            const C hv = h[jj * D + j2];
+            ur = fmaf(hv.x, xb[j2].x, fmaf(-hv.y, xb[j2].y, ur));
+            ui = fmaf(hv.x, xb[j2].y, fmaf(hv.y, xb[j2].x, ui));
+          }
+          sr = fmaf(xa[jj].x, ur, fmaf(-xa[jj].y, ui, sr));
+          si = fmaf(xa[jj].x, ui, fmaf(xa[jj].y, ur, si));
+        }
+        bs[i].acc = make_float2(st.acc.x + sr, st.acc.y + si);
+      }
+    }
+    for (int i = threadIdx.x; i < ns; i += blockDim.x) {
+      const float2 c = bs[i].acc;
+      const int64_t o = a.perm ? a.perm[s0 + i] : s0 + i;
+      a.partial[2 * o] += (double)c.x;
+      a.partial[2 * o + 1] += (double)c.y;
+      bs[i].acc = make_float2(0.f, 0.f);
+    }
+  }
+}
+
+template <int CB, bool PAIR>
 size_t leaf_stream_smem(int r, int64_t per_cta) {
-  return (size_t)2 * r * (1 << CB) * ((1 << CB) + 2) * sizeof(float2) + (size_t)per_cta * sizeof(StreamBits);
+  const size_t ops = PAIR ? (size_t)(1 << (4 * CB)) * sizeof(float2)
+                          : (size_t)2 * r * (1 << CB) * ((1 << CB) + 2) * sizeof(float2);
+  return ops + (size_t)per_cta * sizeof(StreamBits);
+}
+template <int CB, bool PAIR>
+constexpr auto stream_kernel() {
+  if constexpr (PAIR) return leaf_stream_pair_kernel<CB>;
+  else return leaf_stream_kernel<CB>;
 }
 
 // Launch shape of the one-wave kernel for S bitstrings: CTAs (all co-resident) and
 // bitstrings per CTA; false if S does not fit one wave.
-template <int CB>
+template <int CB, bool PAIR>
 bool leaf_stream_shape(int r, int64_t S, int *grid, int64_t *per_cta) {
   const int sms = device_sm_count();
   if (sms <= 0) return false;
+  const auto kernel = stream_kernel<CB, PAIR>();
   for (int per_sm = kStreamPerSm; per_sm >= 1; --per_sm) {
     const int64_t pc = (S + (int64_t)sms * per_sm - 1) / ((int64_t)sms * per_sm);
-    const size_t smem = leaf_stream_smem<CB>(r, pc);
+    const size_t smem = leaf_stream_smem<CB, PAIR>(r, pc);
     if (smem > 200 * 1024) continue;
     int occ = 0;
-    if (cudaFuncSetAttribute(leaf_stream_kernel<CB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-            cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, leaf_stream_kernel<CB>, kStreamThreads, smem) !=
-            cudaSuccess)
+    if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, kStreamThreads, smem) != cudaSuccess)
       return false;
     if (occ >= per_sm) {
       *per_cta = pc;
@@ -994,18 +1081,18 @@ bool leaf_stream_shape(int r, int64_t S, int *grid, int64_t *per_cta) {
   return false;
 }
 
-template <int CB>
+template <int CB, bool PAIR>
 cudaError_t leaf_stream_launch(const LeafArgs &a, cudaStream_t st) {
   int grid = 0;
   int64_t per_cta = 0;
-  if (!leaf_stream_shape<CB>(a.r, a.S, &grid, &per_cta)) return cudaErrorInvalidConfiguration;
+  if (!leaf_stream_shape<CB, PAIR>(a.r, a.S, &grid, &per_cta)) return cudaErrorInvalidConfiguration;
   // the barrier words start at zero (and return there after every barrier)
   cudaError_t e = cudaMemsetAsync(a.sync, 0, 2 * sizeof(uint32_t), st);
   if (e != cudaSuccess) return e;
   LeafArgs args = a;
   void *params[] = {&args, &per_cta};
-  return cudaLaunchCooperativeKernel((const void *)leaf_stream_kernel<CB>, dim3(grid), dim3(kStreamThreads), params,
-                                     leaf_stream_smem<CB>(a.r, per_cta), st);
+  return cudaLaunchCooperativeKernel((const void *)stream_kernel<CB, PAIR>(), dim3(grid), dim3(kStreamThreads),
+                                     params, leaf_stream_smem<CB, PAIR>(a.r, per_cta), st);
 }
 
 __global__ void index_prep_kernel(IndexArgs a) {
@@ -1186,9 +1273,9 @@ bool leaf_streams(const LeafArgs &a, int precision) {
   int grid = 0;
   int64_t pc = 0;
   switch (a.c) {
-    case 1: return leaf_stream_shape<1>(a.r, a.S, &grid, &pc);
-    case 2: return leaf_stream_shape<2>(a.r, a.S, &grid, &pc);
-    default: return leaf_stream_shape<3>(a.r, a.S, &grid, &pc);
+    case 1: return a.H ? leaf_stream_shape<1, true>(a.r, a.S, &grid, &pc) : leaf_stream_shape<1, false>(a.r, a.S, &grid, &pc);
+    case 2: return a.H ? leaf_stream_shape<2, true>(a.r, a.S, &grid, &pc) : leaf_stream_shape<2, false>(a.r, a.S, &grid, &pc);
+    default: return leaf_stream_shape<3, false>(a.r, a.S, &grid, &pc);
   }
 }
 
@@ -1226,12 +1313,71 @@ cudaError_t launch_leaf_contract(const LeafArgs &a, int precision, cudaStream_t 
   }
   if (leaf_streams(a, precision)) {
     switch (a.c) {
-      case 1: return leaf_stream_launch<1>(a, st);
-      case 2: return leaf_stream_launch<2>(a, st);
-      default: return leaf_stream_launch<3>(a, st);
+      case 1: return a.H ? leaf_stream_launch<1, true>(a, st) : leaf_stream_launch<1, false>(a, st);
+      case 2: return a.H ? leaf_stream_launch<2, true>(a, st) : leaf_stream_launch<2, false>(a, st);
+      default: return leaf_stream_launch<3, false>(a, st);
     }
   }
   return precision == 0 ? leaf_dispatch<float>(a, st) : leaf_dispatch<double>(a, st);
+}
+
+// Counting sort of the bitstrings by the high bits of their side-a storage index (the
+// streaming leaf kernel then gives each CTA bitstrings whose side-a chunks lie close
+// together, so those gathers hit in L1).  Buckets are filled with atomics: the order
+// inside a bucket varies, the results do not (every bitstring's sum is formed alone).
+__global__ void sort_count_kernel(const uint64_t *ia, int64_t S, int shift, uint32_t *counts) {
+  const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s < S) atomicAdd(&counts[ia[s] >> shift], 1u);
+}
+__global__ void __launch_bounds__(1024) sort_scan_kernel(uint32_t *counts, int nb) {
+  // exclusive prefix sum of nb <= 4096 counters by one CTA (each thread a run of 4)
+  __shared__ uint32_t part[1024];
+  const int t = threadIdx.x;
+  uint32_t v[4], sum = 0;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const int i = 4 * t + k;
+    v[k] = i < nb ? counts[i] : 0u;
+    sum += v[k];
+  }
+  part[t] = sum;
+  __syncthreads();
+  for (int o = 1; o < 1024; o <<= 1) {
+    const uint32_t x = t >= o ? part[t - o] : 0u;
+    __syncthreads();
+    part[t] += x;
+    __syncthreads();
+  }
+  uint32_t run = part[t] - sum;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const int i = 4 * t + k;
+    if (i < nb) counts[i] = run;
+    run += v[k];
+  }
+}
+__global__ void sort_scatter_kernel(const uint64_t *ia, const uint64_t *ib, int64_t S, int shift,
+                                    uint32_t *offsets, uint64_t *ia_s, uint64_t *ib_s, int64_t *perm) {
+  const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= S) return;
+  const uint64_t a = ia[s];
+  const uint32_t pos = atomicAdd(&offsets[a >> shift], 1u);
+  ia_s[pos] = a;
+  ib_s[pos] = ib[s];
+  perm[pos] = s;
+}
+
+cudaError_t launch_bitstring_sort(const uint64_t *ia, const uint64_t *ib, int64_t S, int ha, uint32_t *counts,
+                                  uint64_t *ia_s, uint64_t *ib_s, int64_t *perm, cudaStream_t st) {
+  if (S <= 0) return cudaSuccess;
+  const int bits = ha < kSortBits ? ha : kSortBits, shift = ha - bits, nb = 1 << bits;
+  cudaError_t e = cudaMemsetAsync(counts, 0, (size_t)nb * sizeof(uint32_t), st);
+  if (e != cudaSuccess) return e;
+  const unsigned grid = (unsigned)((S + 255) / 256);
+  sort_count_kernel<<<grid, 256, 0, st>>>(ia, S, shift, counts);
+  sort_scan_kernel<<<1, 1024, 0, st>>>(counts, nb);
+  sort_scatter_kernel<<<grid, 256, 0, st>>>(ia, ib, S, shift, counts, ia_s, ib_s, perm);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_index_prep(const IndexArgs &a, cudaStream_t st) {

@@ -47,7 +47,7 @@ struct RunLayout {
   bool leaf = false;           // leaf level contracted at the bitstrings
   bool tc = false;             // window output on the tensor cores
   size_t off_buf[2][2] = {{0, 0}, {0, 0}};
-  size_t off_partial = 0, off_sync = 0, off_comp = 0, off_index = 0, off_gemm = 0, total = 0;
+  size_t off_partial = 0, off_sync = 0, off_comp = 0, off_index = 0, off_gemm = 0, off_sort = 0, total = 0;
   int32_t ppg = 64, groups = 0;
 };
 
@@ -88,6 +88,10 @@ RunLayout layout_for(const hsf_plan &p, size_t num_bits, uint64_t window, uint64
     off += align256(num_bits * 16);
     L.off_comp = off;
     off += align256(num_bits * 16);
+    if (L.leaf && num_bits >= 65536) {       // the streaming leaf's sorted bitstrings
+      L.off_sort = off;
+      off += align256(num_bits * 24) + align256(((size_t)1 << kSortBits) * 4);
+    }
   } else {
     const uint64_t count = window ? window : (1ull << p.n);
     const uint64_t nbw = 1ull << p.nb;
@@ -482,6 +486,7 @@ hsf_status hsf_run(hsf_plan *p, const uint64_t *bits, size_t num, uint64_t windo
   LAUNCH(HSF_KERNEL_OTHER, 16.0 * count, 0.0, launch_zero(comp, (int64_t)(2 * count), st));
   // storage index of every requested amplitude on each side
   uint64_t *ia = nullptr, *ib = nullptr;
+  bool sorted = false;                         // streaming leaf: bitstrings sorted once per run
   const uint64_t nbw = 1ull << p->nb;
   const int64_t M = (int64_t)((count + nbw - 1) / nbw), N = (int64_t)std::min<uint64_t>(count, nbw);
   if (num > 0) {
@@ -618,6 +623,7 @@ hsf_status hsf_run(hsf_plan *p, const uint64_t *bits, size_t num, uint64_t windo
       la.sync = (uint32_t *)(ws + L.off_sync);
       la.err = p->dev_status;
       la.pf = p->leaf_pf;
+      la.H = p->leaf_H.empty() ? nullptr : (unsigned char *)p->dev_table + p->leaf_h_off;
       if (p->leaf_pf >= 0) {
         la.Sa = (unsigned char *)p->dev_table + p->side[0].leaf_s_off;
         la.Sb = (unsigned char *)p->dev_table + p->side[1].leaf_s_off;
@@ -627,6 +633,20 @@ hsf_status hsf_run(hsf_plan *p, const uint64_t *bits, size_t num, uint64_t windo
       if (streams) {
         la.parents_per_group = (int32_t)la.num_parents;
         la.num_groups = 1;
+        if (L.off_sort) {
+          // once per run: the bitstrings sorted by their side-a storage index
+          int64_t *perm = (int64_t *)(ws + L.off_sort);
+          uint64_t *ia_s = (uint64_t *)(perm + num), *ib_s = ia_s + num;
+          uint32_t *counts = (uint32_t *)(ws + L.off_sort + align256(num * 24));
+          if (!sorted) {
+            LAUNCH(HSF_KERNEL_OTHER, 64.0 * num, 0.0,
+                   launch_bitstring_sort(ia, ib, (int64_t)num, p->na, counts, ia_s, ib_s, perm, st));
+            sorted = true;
+          }
+          la.ia = ia_s;
+          la.ib = ib_s;
+          la.perm = perm;
+        }
       }
       const double units = (double)la.num_parents * (double)num;
       // algorithmic DRAM bytes: every parent state read once (at most: the gathered
@@ -635,8 +655,10 @@ hsf_status hsf_run(hsf_plan *p, const uint64_t *bits, size_t num, uint64_t windo
       const double states = (double)la.num_parents * (double)((1ull << la.ha) + (1ull << la.hb)) * csz;
       // FLOP per (bitstring, parent): r digits x (two dots of 2^c terms + the product), or
       // factored: four dots of 2^(c-1) terms per side + the 4 x 4 bilinear form
+      // or, streaming with the pair form, the D x D bilinear form
       const double fl = leaf_factored(la, p->precision) ? 8.0 * (4.0 * (1 << la.c) + 20.0)
-                                                         : la.r * (8.0 * 2.0 * (1 << la.c) + 8.0);
+                        : (streams && la.H) ? 8.0 * ((1 << (2 * la.c)) + (1 << la.c))
+                                            : la.r * (8.0 * 2.0 * (1 << la.c) + 8.0);
       LAUNCH(HSF_KERNEL_LEAF, std::min(gathered, states) + 16.0 * la.num_groups * num, units * fl,
              launch_leaf_contract(la, p->precision, st));
       LAUNCH(HSF_KERNEL_REDUCE, 16.0 * la.num_groups * num + 64.0 * num, 0.0,

@@ -102,6 +102,8 @@ struct LeafArgs {
   int32_t pf;            // >= 0: factored leaf operators (L_m = S (F_m (x) I), factor on chunk bit pf)
   const void *Sa, *Sb;   // factored: S of each side, [2^c][2^c] row-major
   const void *G;         // factored: [(r+1)][(r+1)][4][4], G over digits [m0, m1)
+  const void *H;         // chunks of <= 4 amplitudes: [(r+1)][(r+1)][D^2][D][D] or NULL
+  const int64_t *perm;   // streaming kernels: bitstring i of ia / ib is output perm[i] (NULL: i)
   double *partial;       // [num_groups][S][2]
   uint32_t *sync;        // 2 words of device scratch (grid barrier of the streaming kernel)
   int32_t *err;          // device status word
@@ -295,6 +297,11 @@ cudaError_t launch_leaf_contract(const LeafArgs &a, int precision, cudaStream_t 
 // true when launch_leaf_contract uses the one-wave streaming kernel (large bitstring
 // counts); it then writes a single partial per bitstring (num_groups = 1)
 bool leaf_streams(const LeafArgs &a, int precision);
+// counting sort of S bitstrings by the high bits of ia (2^kSortBits buckets at most):
+// ia_s, ib_s in sorted order, perm[i] = the input position of sorted bitstring i
+constexpr int kSortBits = 12;
+cudaError_t launch_bitstring_sort(const uint64_t *ia, const uint64_t *ib, int64_t S, int ha, uint32_t *counts,
+                                  uint64_t *ia_s, uint64_t *ib_s, int64_t *perm, cudaStream_t st);
 // the factored leaf kernel runs for this launch (FP32, factored operators, 3-4 digits)
 bool leaf_factored(const LeafArgs &a, int precision);
 cudaError_t launch_index_prep(const IndexArgs &a, cudaStream_t st);

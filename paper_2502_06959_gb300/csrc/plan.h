@@ -183,6 +183,8 @@ struct hsf_plan {
   int leaf_c = 0;                   // > 0: the leaf level can be contracted at bitstrings
   int leaf_pf = -1;                 // >= 0: factored leaf, the factor's storage bit in the chunk
   std::vector<hsf::cd> leaf_G;      // [(r+1)][(r+1)][4][4]: sum over digits [m0, m1) of F^a (x) F^b
+  std::vector<hsf::cd> leaf_H;      // leaf chunks of 2 or 4 amplitudes: [(r+1)][(r+1)][D^2][D][D], H over digits [m0, m1)
+  size_t leaf_h_off = 0;
   size_t leaf_g_off = 0;
   int rbits = 4;                    // register slots of the register-resident sweep
   struct ProfRec { int kind; cudaEvent_t e0, e1; double bytes, flops; };

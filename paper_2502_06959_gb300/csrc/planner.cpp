@@ -1026,6 +1026,32 @@ void factor_leaf(hsf_plan &p) {
   p.leaf_pf = pf;
 }
 
+// Leaf digit sums for short chunks.  For a bitstring whose chunk rows are i on side a and
+// i' on side b, the parent's contribution sum_m (L^a_m x_a)[i] (L^b_m x_b)[i'] is the
+// bilinear form x_a^T H[i][i'] x_b with H[i][i'][j][j'] = sum_m L^a_m[i][j] L^b_m[i'][j']:
+// D^2 + D complex products per (bitstring, parent) instead of r (2D + 1), whatever the
+// operators.  Built for chunks of 2 and 4 amplitudes (complex64) and every digit range
+// [m0, m1), for the streaming leaf kernel.
+void pair_leaf(hsf_plan &p) {
+  p.leaf_H.clear();
+  const int B = (int)p.blocks.size(), r = (int)p.radix[B], c = p.leaf_c, D = 1 << c;
+  if (p.precision != HSF_PREC_C64 || c < 1 || c > 2) return;
+  const size_t per = (size_t)D * D * D * D;
+  p.leaf_H.assign((size_t)(r + 1) * (r + 1) * per, 0.0);
+  const std::vector<cd> &La = p.side[0].leaf_ops, &Lb = p.side[1].leaf_ops;
+  for (int m0 = 0; m0 < r; ++m0)
+    for (int m1 = m0 + 1; m1 <= r; ++m1) {
+      cd *H = p.leaf_H.data() + ((size_t)m0 * (r + 1) + m1) * per;
+      for (int m = m0; m < m1; ++m)
+        for (int i = 0; i < D; ++i)
+          for (int i2 = 0; i2 < D; ++i2)
+            for (int j = 0; j < D; ++j)
+              for (int j2 = 0; j2 < D; ++j2)
+                H[((size_t)(i * D + i2) * D + j) * D + j2] +=
+                    La[((size_t)m * D + i) * D + j] * Lb[((size_t)m * D + i2) * D + j2];
+    }
+}
+
 hsf_status build_programs(hsf_plan &p, bool grad) {
   const int B = (int)p.blocks.size();
   std::vector<std::pair<bool, int>> order;
@@ -1182,6 +1208,7 @@ hsf_status build_programs(hsf_plan &p, bool grad) {
         }
     }
     factor_leaf(p);
+    pair_leaf(p);
   }
   compose_mma_levels(p, p.leaf_c);
   return HSF_OK;
@@ -1336,6 +1363,14 @@ hsf_status upload_programs(hsf_plan &p, bool grad) {
         float2 c = make_float2((float)z.real(), (float)z.imag());
         append(&c, sizeof c);
       }
+    }
+  }
+  if (!grad && !p.leaf_H.empty()) {
+    align(256);
+    p.leaf_h_off = host.size();
+    for (auto &z : p.leaf_H) {
+      float2 c = make_float2((float)z.real(), (float)z.imag());
+      append(&c, sizeof c);
     }
   }
   if (!grad && p.leaf_pf >= 0) {
