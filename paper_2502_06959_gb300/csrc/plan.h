@@ -134,7 +134,7 @@ void table_free(void *p);
 const char *last_error();
 hsf_status validate_and_load(hsf_plan &p, const hsf_circuit *c, int cut, const hsf_blocks *bl,
                              const hsf_plan_opts *o);
-hsf_status check_order(const hsf_plan &p);
+hsf_status check_order(hsf_plan &p);
 hsf_status load_gates(hsf_plan &p, const hsf_circuit *c, const hsf_plan_opts *o);
 // Full-state (Schroedinger) plan: one program of all gates on h = n qubits.
 hsf_status build_schrodinger(hsf_plan &p, const hsf_circuit *c, const hsf_plan_opts *o);
@@ -181,6 +181,7 @@ struct hsf_plan {
   int64_t tree_nodes = 0;
   int64_t launches = 0;
   int leaf_c = 0;                   // > 0: the leaf level can be contracted at bitstrings
+  std::vector<std::pair<bool, int>> order;   // execution order (block?, index), set by check_order
   int leaf_pf = -1;                 // >= 0: factored leaf, the factor's storage bit in the chunk
   std::vector<hsf::cd> leaf_G;      // [(r+1)][(r+1)][4][4]: sum over digits [m0, m1) of F^a (x) F^b
   std::vector<hsf::cd> leaf_H;      // leaf chunks of 2 or 4 amplitudes: [(r+1)][(r+1)][D^2][D][D], H over digits [m0, m1)

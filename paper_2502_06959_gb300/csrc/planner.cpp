@@ -369,36 +369,33 @@ int popcount64(uint64_t x) { return __builtin_popcountll(x); }
 // DAG with blocks contracted to single nodes; Kahn's algorithm with the smallest
 // gate index first.  The listed block order is enforced as extra edges.
 // ---------------------------------------------------------------------------
-struct Node {
-  bool is_block = false;
-  int id = 0;
-  int key = 0;
-  std::vector<int> succ;
-  int indeg = 0;
-};
-
 hsf_status execution_order(const hsf_plan &p, std::vector<std::pair<bool, int>> &order) {
+  if (!p.order.empty()) {                      // computed once when the plan was checked
+    order = p.order;
+    return HSF_OK;
+  }
+  // Kahn's algorithm over the gate DAG with every block contracted to one node; among the
+  // ready nodes the one with the smallest first gate index goes first
   const int G = (int)p.gates.size();
   const int B = (int)p.blocks.size();
+  const int V = B + G;
   std::vector<int> owner(G, -1);
   for (int b = 0; b < B; ++b)
     for (int gi : p.blocks[b].gates) owner[gi] = b;
-  std::vector<Node> nodes(B + G);
-  std::vector<char> used(B + G, 0);
+  std::vector<int> key(V, 0);
+  std::vector<char> used(V, 0);
   for (int b = 0; b < B; ++b) {
-    nodes[b].is_block = true;
-    nodes[b].id = b;
-    nodes[b].key = *std::min_element(p.blocks[b].gates.begin(), p.blocks[b].gates.end());
+    key[b] = *std::min_element(p.blocks[b].gates.begin(), p.blocks[b].gates.end());
     used[b] = 1;
   }
   for (int gi = 0; gi < G; ++gi)
     if (owner[gi] < 0) {
-      nodes[B + gi].id = gi;
-      nodes[B + gi].key = gi;
+      key[B + gi] = gi;
       used[B + gi] = 1;
     }
   auto nid = [&](int gi) { return owner[gi] >= 0 ? owner[gi] : B + gi; };
-  std::set<std::pair<int, int>> edges;
+  std::vector<uint64_t> edges;                 // (u << 32) | v, deduplicated below
+  edges.reserve((size_t)2 * G + B);
   std::vector<int> last(p.n, -1);
   for (int gi = 0; gi < G; ++gi) {
     const int v = nid(gi);
@@ -406,30 +403,38 @@ hsf_status execution_order(const hsf_plan &p, std::vector<std::pair<bool, int>> 
       const int q = p.gates[gi].q[j];
       if (last[q] >= 0) {
         const int u = nid(last[q]);
-        if (u != v) edges.insert({u, v});
+        if (u != v) edges.push_back(((uint64_t)u << 32) | (uint32_t)v);
       }
       last[q] = gi;
     }
   }
-  for (int b = 0; b + 1 < B; ++b) edges.insert({b, b + 1});
-  for (auto &e : edges) {
-    nodes[e.first].succ.push_back(e.second);
-    nodes[e.second].indeg++;
+  for (int b = 0; b + 1 < B; ++b) edges.push_back(((uint64_t)b << 32) | (uint32_t)(b + 1));
+  std::sort(edges.begin(), edges.end());
+  edges.erase(std::unique(edges.begin(), edges.end()), edges.end());
+  // successor lists in CSR form (edges are sorted by source)
+  std::vector<int> start(V + 1, 0), succ(edges.size()), indeg(V, 0);
+  for (size_t e = 0; e < edges.size(); ++e) {
+    const int u = (int)(edges[e] >> 32), v = (int)(uint32_t)edges[e];
+    start[u + 1]++;
+    succ[e] = v;
+    indeg[v]++;
   }
+  for (int v = 0; v < V; ++v) start[v + 1] += start[v];
   using QE = std::pair<int, int>;
   std::priority_queue<QE, std::vector<QE>, std::greater<QE>> pq;
   int total = 0;
-  for (int v = 0; v < B + G; ++v) {
+  for (int v = 0; v < V; ++v) {
     total += used[v];
-    if (used[v] && nodes[v].indeg == 0) pq.push({nodes[v].key, v});
+    if (used[v] && indeg[v] == 0) pq.push({key[v], v});
   }
   order.clear();
+  order.reserve(total);
   while (!pq.empty()) {
     const int v = pq.top().second;
     pq.pop();
-    order.push_back({nodes[v].is_block, nodes[v].id});
-    for (int w : nodes[v].succ)
-      if (--nodes[w].indeg == 0) pq.push({nodes[w].key, w});
+    order.push_back({v < B, v < B ? v : v - B});
+    for (int e = start[v]; e < start[v + 1]; ++e)
+      if (--indeg[succ[e]] == 0) pq.push({key[succ[e]], succ[e]});
   }
   if ((int)order.size() != total)
     return set_error(HSF_EBLOCK, "a block is not convex in the circuit DAG, or the blocks are not "
@@ -740,6 +745,60 @@ void host_apply(std::vector<cd> &v, int c, const OpH &op, int digit) {
   }
 }
 
+// M <- op M for a 2^c x 2^c matrix stored row-major as separate real and imaginary
+// parts: the op acts on the row index and every column gets the same op, so the inner
+// loop runs over contiguous columns (the product of a level's shared ops, composed
+// once for all digits).
+void host_apply_rows(std::vector<double> &re, std::vector<double> &im, int c, const OpH &op) {
+  const int dim = 1 << c, nq = op.nq, d = 1 << nq;
+  const cd *m = op.m.data();
+  if (op.type == OP_DIAG) {
+    for (int i = 0; i < dim; ++i) {
+      int idx = 0;
+      for (int x = 0; x < nq; ++x) idx |= ((i >> op.q[x]) & 1) << (nq - 1 - x);
+      const double mr = m[idx].real(), mi = m[idx].imag();
+      double *r = re.data() + (size_t)i * dim, *q = im.data() + (size_t)i * dim;
+      for (int col = 0; col < dim; ++col) {
+        const double a = r[col], b = q[col];
+        r[col] = mr * a - mi * b;
+        q[col] = mr * b + mi * a;
+      }
+    }
+    return;
+  }
+  int mask = 0;
+  for (int x = 0; x < nq; ++x) mask |= 1 << op.q[x];
+  std::vector<double> tr((size_t)d * dim), ti((size_t)d * dim);
+  for (int i = 0; i < dim; ++i) {
+    if (i & mask) continue;
+    int addr[8];
+    for (int k = 0; k < d; ++k) {
+      int a = i;
+      for (int x = 0; x < nq; ++x)
+        if ((k >> (nq - 1 - x)) & 1) a |= 1 << op.q[x];
+      addr[k] = a;
+    }
+    for (int r = 0; r < d; ++r) {
+      double *orr = tr.data() + (size_t)r * dim, *oi = ti.data() + (size_t)r * dim;
+      std::fill(orr, orr + dim, 0.0);
+      std::fill(oi, oi + dim, 0.0);
+      for (int k = 0; k < d; ++k) {
+        const double mr = m[r * d + k].real(), mi = m[r * d + k].imag();
+        if (mr == 0.0 && mi == 0.0) continue;
+        const double *xr = re.data() + (size_t)addr[k] * dim, *xi = im.data() + (size_t)addr[k] * dim;
+        for (int col = 0; col < dim; ++col) {
+          orr[col] += mr * xr[col] - mi * xi[col];
+          oi[col] += mr * xi[col] + mi * xr[col];
+        }
+      }
+    }
+    for (int r = 0; r < d; ++r) {
+      std::copy(tr.data() + (size_t)r * dim, tr.data() + (size_t)(r + 1) * dim, re.data() + (size_t)addr[r] * dim);
+      std::copy(ti.data() + (size_t)r * dim, ti.data() + (size_t)(r + 1) * dim, im.data() + (size_t)addr[r] * dim);
+    }
+  }
+}
+
 template <typename C>
 void pack_pass(const PassH &ps, std::vector<DevOp> &dops, std::vector<C> &mats, std::vector<DevGroup> &dgroups) {
   int tile_bit[64];
@@ -911,14 +970,13 @@ void compose_mma_levels(hsf_plan &p, int leaf_c) {
   // the shared parts S, one task per level
   host_parallel_for(jobs.size(), [&](size_t j) {
     LevelJob &job = jobs[j];
-    job.S.assign((size_t)dim * dim, cd(0.0));
-    std::vector<cd> v(dim);
-    for (int col = 0; col < dim; ++col) {
-      std::fill(v.begin(), v.end(), cd(0.0));
-      v[col] = 1.0;
-      for (size_t o = job.split; o < job.prefix.size(); ++o) host_apply(v, kMmaBits, job.prefix[o], 0);
-      std::copy(v.begin(), v.end(), job.S.begin() + (size_t)col * dim);
-    }
+    std::vector<double> re((size_t)dim * dim, 0.0), im((size_t)dim * dim, 0.0);
+    for (int i = 0; i < dim; ++i) re[(size_t)i * dim + i] = 1.0;
+    for (size_t o = job.split; o < job.prefix.size(); ++o) host_apply_rows(re, im, kMmaBits, job.prefix[o]);
+    job.S.assign((size_t)dim * dim, cd(0.0));              // column-major
+    for (int row = 0; row < dim; ++row)
+      for (int col = 0; col < dim; ++col)
+        job.S[(size_t)col * dim + row] = cd(re[(size_t)row * dim + col], im[(size_t)row * dim + col]);
   });
   std::vector<std::pair<int, int>> tasks;     // (job, digit)
   for (int j = 0; j < (int)jobs.size(); ++j)
@@ -1423,9 +1481,12 @@ hsf_status finish_plan(hsf_plan &p) {
   return HSF_OK;
 }
 
-hsf_status check_order(const hsf_plan &p) {
+hsf_status check_order(hsf_plan &p) {
   std::vector<std::pair<bool, int>> order;
-  return execution_order(p, order);
+  p.order.clear();
+  hsf_status st = execution_order(p, order);
+  if (st == HSF_OK) p.order = order;
+  return st;
 }
 
 // Multiply and decompose blocks on the device (svd.cu); read back ranks and factors.
