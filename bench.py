@@ -457,6 +457,23 @@ def bench_other(args):
     print(json.dumps(line), flush=True)
 
 
+def read_segment_fraction(desc, n, nb, bits):
+    """Fraction of the 16-amplitude segments of each half state that the bitstrings'
+    chunks fall in (the segments the FP16 level before the leaf contraction stores),
+    from the storage order the plan description prints ("side a: h=.. store=[..]")."""
+    import re
+    fr = []
+    for side, m in zip(("a", "b"), re.finditer(r"side ([ab]): h=(\d+) store=\[([0-9,]*)\]", desc)):
+        h = int(m.group(2))
+        store = [int(x) for x in m.group(3).split(",")]
+        x = (bits >> np.uint64(nb)) if m.group(1) == "a" else (bits & np.uint64((1 << nb) - 1))
+        idx = np.zeros_like(x)
+        for q, t in enumerate(store):
+            idx |= ((x >> np.uint64(q)) & np.uint64(1)) << np.uint64(t)
+        fr.append(len(np.unique(idx >> np.uint64(4))) / float(1 << (h - 4)))
+    return fr
+
+
 def form_leg(hsf, torch, pr, bits, S, stream, steps, flags, gold, budget):
     """Plan + run of the whole circuit `steps` times with the given plan flags: circuits/s,
     run-only circuits/s and the max error of the output against the stored FP64 values."""
@@ -814,6 +831,8 @@ def main():
         "roofline": dict(roofline_of(dominant),
                          measured="profiled pass of the same steps, halves on one stream"),
         "rooflines": {k: roofline_of(k) for k in ("sweep", "level_mma", "level_f16", "leaf") if k in kstats},
+        "leaf_level_segments_read": read_segment_fraction(hsf.hsf_plan_describe(plan0.handle), pr.n, pr.cut + 1,
+                                                          bits_np.astype(np.uint64)),
         "kernels": {k: {"launches": int(v["launches"]), "ms": v["ms"],
                         "share": v["ms"] / total_kernel_ms if total_kernel_ms else 0.0}
                     for k, v in kstats.items() if v["launches"]},

@@ -1380,6 +1380,33 @@ cudaError_t launch_bitstring_sort(const uint64_t *ia, const uint64_t *ib, int64_
   return cudaGetLastError();
 }
 
+// Which 16-amplitude segments of the deepest stored level the leaf contraction reads:
+// the segments covered by each bitstring's chunk on either side.
+__global__ void chunk_mask_kernel(const uint64_t *ia, const uint64_t *ib, int64_t S, int c, uint32_t *mask_a,
+                                  uint32_t *mask_b) {
+  const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= S) return;
+  const uint64_t D = 1ull << c;
+  for (int side = 0; side < 2; ++side) {
+    const uint64_t first = (side == 0 ? ia[s] : ib[s]) & ~(D - 1);
+    uint32_t *mask = side == 0 ? mask_a : mask_b;
+    for (uint64_t seg = first >> 4; seg <= (first + D - 1) >> 4; ++seg)
+      atomicOr(&mask[seg >> 5], 1u << (seg & 31));
+  }
+}
+
+cudaError_t launch_chunk_mask(const uint64_t *ia, const uint64_t *ib, int64_t S, int c, int ha, int hb,
+                              uint32_t *mask_a, uint32_t *mask_b, cudaStream_t st) {
+  if (S <= 0) return cudaSuccess;
+  // at least one word per mask (a half state below 2^9 amplitudes has fewer than 32 bits)
+  const size_t ba = ((((size_t)1 << (ha - 4)) + 31) / 32) * 4, bb = ((((size_t)1 << (hb - 4)) + 31) / 32) * 4;
+  cudaError_t e = cudaMemsetAsync(mask_a, 0, ba, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(mask_b, 0, bb, st);
+  if (e != cudaSuccess) return e;
+  chunk_mask_kernel<<<(unsigned)((S + 255) / 256), 256, 0, st>>>(ia, ib, S, c, mask_a, mask_b);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_index_prep(const IndexArgs &a, cudaStream_t st) {
   if (a.S <= 0) return cudaSuccess;
   index_prep_kernel<<<(unsigned)((a.S + 255) / 256), 256, 0, st>>>(a);

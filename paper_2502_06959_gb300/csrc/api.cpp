@@ -48,6 +48,7 @@ struct RunLayout {
   bool tc = false;             // window output on the tensor cores
   size_t off_buf[2][2] = {{0, 0}, {0, 0}};
   size_t off_partial = 0, off_sync = 0, off_comp = 0, off_index = 0, off_gemm = 0, off_sort = 0, total = 0;
+  size_t off_mask[2] = {0, 0};   // leaf contraction: segments of the deepest level that bitstrings read
   int32_t ppg = 64, groups = 0;
 };
 
@@ -88,6 +89,12 @@ RunLayout layout_for(const hsf_plan &p, size_t num_bits, uint64_t window, uint64
     off += align256(num_bits * 16);
     L.off_comp = off;
     off += align256(num_bits * 16);
+    if (L.leaf && p.side[0].h >= 5 && p.side[1].h >= 5 && p.side[0].h <= 28 && p.side[1].h <= 28) {
+      for (int s = 0; s < 2; ++s) {
+        L.off_mask[s] = off;
+        off += align256(std::max<size_t>(4, ((size_t)1 << (p.side[s].h - 4)) / 8));
+      }
+    }
     if (L.leaf && num_bits >= 65536) {       // the streaming leaf's sorted bitstrings
       L.off_sort = off;
       off += align256(num_bits * 24) + align256(((size_t)1 << kSortBits) * 4);
@@ -503,6 +510,10 @@ hsf_status hsf_run(hsf_plan *p, const uint64_t *bits, size_t num, uint64_t windo
     ix.ia = ia;
     ix.ib = ib;
     LAUNCH(HSF_KERNEL_OTHER, 24.0 * num, 0.0, launch_index_prep(ix, st));
+    if (L.off_mask[0])
+      LAUNCH(HSF_KERNEL_OTHER, 16.0 * num, 0.0,
+             launch_chunk_mask(ia, ib, (int64_t)num, p->leaf_c, p->na, p->nb, (uint32_t *)(ws + L.off_mask[0]),
+                               (uint32_t *)(ws + L.off_mask[1]), st));
   } else {
     ia = (uint64_t *)(ws + L.off_index);
     ib = ia + M;
@@ -552,6 +563,9 @@ hsf_status hsf_run(hsf_plan *p, const uint64_t *bits, size_t num, uint64_t windo
           g.err = p->dev_status;
           g.post = (unsigned char *)p->dev_table + lv.post_off;
           g.num_post = (int32_t)lv.post.size();
+          // the level the leaf contraction reads: store only the segments bitstrings read
+          if (L.leaf && k == top && L.off_mask[s] && lv.post.empty())
+            g.store_mask = (const uint32_t *)(ws + L.off_mask[s]);
           const double amps = (double)(hi - lo) * (double)(1ull << sd.h);
           const double parents = (double)((hi - 1) / g.radix - lo / g.radix + 1) * (double)(1ull << sd.h);
           // three 128 x 128 x 128 real products (FP16 or TF32 parts) per 128 64-amplitude rows

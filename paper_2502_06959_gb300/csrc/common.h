@@ -215,6 +215,10 @@ struct LevelMmaArgs {
   const void *post;        // ops applied in the epilogue after the product (MmaPostOp[])
   int32_t num_post;
   int32_t pad;
+  // FP16 kernel, deepest level before a leaf contraction: bit 4 R + s set when 16-amplitude
+  // segment s of row R is read by some bitstring; other segments are not stored (NULL:
+  // every segment is stored)
+  const uint32_t *store_mask;
 };
 // A one- or two-qubit op on storage bits < kMmaPostBits, applied by the tensor-core
 // level's epilogue to each staged 32-row quarter (amplitude bits 0..5, row bits 0..4).
@@ -300,6 +304,10 @@ bool leaf_streams(const LeafArgs &a, int precision);
 // counting sort of S bitstrings by the high bits of ia (2^kSortBits buckets at most):
 // ia_s, ib_s in sorted order, perm[i] = the input position of sorted bitstring i
 constexpr int kSortBits = 12;
+// bit (ia >> 4) of mask_a (and of mask_b for ib) for every 16-amplitude segment that a
+// bitstring's 2^c-amplitude chunk covers; the masks hold 2^(ha-4) and 2^(hb-4) bits
+cudaError_t launch_chunk_mask(const uint64_t *ia, const uint64_t *ib, int64_t S, int c, int ha, int hb,
+                              uint32_t *mask_a, uint32_t *mask_b, cudaStream_t st);
 cudaError_t launch_bitstring_sort(const uint64_t *ia, const uint64_t *ib, int64_t S, int ha, uint32_t *counts,
                                   uint64_t *ia_s, uint64_t *ib_s, int64_t *perm, cudaStream_t st);
 // the factored leaf kernel runs for this launch (FP32, factored operators, 3-4 digits)

@@ -873,6 +873,8 @@ __device__ __forceinline__ uint32_t h2_bits(__half2 h) {
   return u;
 }
 
+constexpr int kHMaskWords = (1 << (17 - 4)) / 32;   // store mask of a half state of up to 2^17 amplitudes
+
 __global__ void __launch_bounds__(kHThreads, 1) level_mma_f16_kernel(LevelMmaArgs a) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
@@ -883,8 +885,15 @@ __global__ void __launch_bounds__(kHThreads, 1) level_mma_f16_kernel(LevelMmaArg
   __shared__ float row_inv[4][128];                     // per unit (4 in flight): 1 / row scale
   __shared__ uint32_t tmem_sh;
   __shared__ volatile int abort_sh, epi_abort[2];
+  __shared__ uint32_t mask_sh[kHMaskWords];             // the store mask, when it fits
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t radix = a.radix;
+  // 2^(h-4) mask bits; staged in shared memory for h <= 17 (visible after the first
+  // __syncthreads below)
+  const bool mask_in_smem = a.store_mask && a.h <= 17;
+  if (mask_in_smem)
+    for (int e = threadIdx.x; e < (1 << (a.h - 4)) / 32; e += blockDim.x) mask_sh[e] = a.store_mask[e];
+  const uint32_t *smask = mask_in_smem ? mask_sh : a.store_mask;
   // A CTA serves kHDigits consecutive digits (one when the radix is odd): each parent unit
   // is split once and multiplied by every digit's W.  Units run over the parents with a
   // child in [node_lo, node_lo + num_nodes); children outside are computed, not stored.
@@ -1161,10 +1170,25 @@ __global__ void __launch_bounds__(kHThreads, 1) level_mma_f16_kernel(LevelMmaArg
           asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
           if (store) {
             // row j of the quarter goes out from registers, a warp writing its 32
-            // components (128 contiguous bytes) per row
+            // components (128 contiguous bytes: segment q4 of the row) per row; with a
+            // store mask, segments no bitstring reads are skipped (the bit is the same
+            // for the whole warp)
             float *out = a.child + dst_off + (size_t)qr * 32 * 128 + comp;
+            uint32_t keep = 0xffffffffu;
+            if (smask) {
+              const uint64_t r0 = ((uint64_t)(u & ((1 << tb) - 1)) << 7) + (uint64_t)qr * 32;   // first row
+              const uint32_t *mw = smask + (r0 >> 3);                  // 8 rows (4 bits each) per word
+              keep = 0;
 #pragma unroll
-            for (int j = 0; j < 32; ++j) out[(size_t)j * 128] = __uint_as_float(v[j]) * inv[qr * 32 + j] * inv_w;
+              for (int w4 = 0; w4 < 4; ++w4) {
+                const uint32_t word = mw[w4];
+#pragma unroll
+                for (int jj = 0; jj < 8; ++jj) keep |= ((word >> (4 * jj + q4)) & 1u) << (8 * w4 + jj);
+              }
+            }
+#pragma unroll
+            for (int j = 0; j < 32; ++j)
+              if ((keep >> j) & 1u) out[(size_t)j * 128] = __uint_as_float(v[j]) * inv[qr * 32 + j] * inv_w;
           }
         }
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
