@@ -156,8 +156,8 @@ PROFILED_TRAFFIC = {
     "sweep": {"ratio": 275.1 / 335.5, "source": "paper_2502_06959_gb300/csrc/sweep.cu",
               "kernel": "sweep_reg_kernel", "sha256": "1a9bade5309e94b9",
               "profile": "profiles/sweep_reg_level6_n30.md"},
-    "level_f16": {"ratio": 1289.7 / 1342.2, "source": "paper_2502_06959_gb300/csrc/gemm_tc.cu",
-                  "kernel": "level_mma_f16_kernel", "sha256": "5fafb56a20723142",
+    "level_f16": {"ratio": (268.7 + 877.8) / 1342.2, "source": "paper_2502_06959_gb300/csrc/gemm_tc.cu",
+                  "kernel": "level_mma_f16_kernel", "sha256": "b73929fba14e31a5",
                   "profile": "profiles/level_f16_level7_n30.md"},
     "leaf": {"ratio": (1896.2 + 7.5) / 2151.7, "source": "paper_2502_06959_gb300/csrc/accum.cu",
              "kernel": "leaf_contract_fact_kernel", "sha256": "50afedbb5f9cb3f9",
