@@ -435,10 +435,10 @@ __global__ void __launch_bounds__(kGemmThreads, 1) gemm_kernel(const __grid_cons
 // bounded; on expiry the CTA records an error, drains its MMAs and loads, frees TMEM and
 // returns.
 constexpr int kLvlRaw = 4;                      // TMA stages (raw FP32 chunks = the hi parts)
-constexpr int kLvlLo = 4;                       // low-part buffers
-constexpr int kLvlOut = 4;                      // 32-row output staging buffers (16 KB each)
+constexpr int kLvlLo = 3;                       // low-part buffers
+constexpr int kLvlOut = 6;                      // 32-row output staging buffers (16 KB each)
 constexpr int kLvlChunk = 128 * 128;            // bytes: 128 rows x 32 floats
-constexpr int kLvlThreads = 448;                // 4 low-part, 2 x 4 epilogue, 1 MMA, 1 TMA warp
+constexpr int kLvlThreads = 576;                // 4 low-part, 3 x 4 epilogue, 1 MMA, 1 TMA warp
 constexpr uint32_t kLvlTmemCols = 512;          // W hi [0,128), W lo [128,256), D 2 x 128
 constexpr size_t kLvlSmem = (size_t)(kLvlRaw + kLvlLo + kLvlOut) * kLvlChunk + 1024;
 
@@ -544,11 +544,11 @@ __global__ void __launch_bounds__(kLvlThreads, 1) level_mma_kernel(const __grid_
   uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
   uint8_t *sR = smem;                                   // raw stage r (hi part): sR + r * kLvlChunk
   uint8_t *sL = sR + kLvlRaw * kLvlChunk;               // low-part buffer l: sL + l * kLvlChunk
-  float *sO = reinterpret_cast<float *>(sL + kLvlLo * kLvlChunk);   // output staging: [2][32 rows][128]
+  float *sO = reinterpret_cast<float *>(sL + kLvlLo * kLvlChunk);   // output staging: [6][32 rows][128]
   __shared__ __align__(8) uint64_t loaded[kLvlRaw], raw_empty[kLvlRaw], full_bar[kLvlLo], lo_empty[kLvlLo], tfull[2],
       tempty[2], drain;
   __shared__ uint32_t tmem_sh;
-  __shared__ volatile int abort_sh, epi_abort[2];
+  __shared__ volatile int abort_sh, epi_abort[3];
   __shared__ __align__(16) MmaPostOp post_sh[kMmaMaxPost];   // the epilogue's ops, staged once
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t radix = a.radix;
@@ -567,7 +567,7 @@ __global__ void __launch_bounds__(kLvlThreads, 1) level_mma_kernel(const __grid_
   const int64_t nchunks = units > blockIdx.x ? ((units - 1 - blockIdx.x) / gridDim.x + 1) * 4 : 0;
 
   if (threadIdx.x == 0) {
-    epi_abort[0] = epi_abort[1] = 0;
+    epi_abort[0] = epi_abort[1] = epi_abort[2] = 0;
     for (int s = 0; s < kLvlRaw; ++s) {
       mbar_init(&loaded[s], 1);
       mbar_init(&raw_empty[s], 1);
@@ -578,7 +578,7 @@ __global__ void __launch_bounds__(kLvlThreads, 1) level_mma_kernel(const __grid_
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&tfull[b], 1);
-      mbar_init(&tempty[b], 256);
+      mbar_init(&tempty[b], 384);
     }
     mbar_init(&drain, 1);
     abort_sh = 0;
@@ -730,18 +730,19 @@ __global__ void __launch_bounds__(kLvlThreads, 1) level_mma_kernel(const __grid_
     }
     __syncwarp();
   } else {
-    // ---- epilogue: two groups of four warps (4..7 and 10..13) take alternate 32-row
-    // quarters of each accumulator.  TMEM lane quarter (warp & 3) holds output
+    // ---- epilogue: three groups of four warps (4..7, 10..13 and 14..17) take the 32-row
+    // quarters of the accumulators round-robin (quarter q of unit tu goes to group
+    // (4 tu + q) mod 3), so up to three quarters get their ops at once.  TMEM lane quarter (warp & 3) holds output
     // components 32 (warp & 3) .. + 31; TMEM column j of the accumulator is row j of the
     // tile.  A quarter is staged in shared memory row-major (the global layout), gets the
     // rest of the level's program, and goes out as one bulk copy (its 32 rows are 16 KB
     // contiguous in the child state). ----
-    const int grp = warp >= 10 ? 1 : 0;
+    const int grp = warp >= 14 ? 2 : (warp >= 10 ? 1 : 0);
     const uint32_t bar_id = 1 + grp;                     // named barrier of the group
     const int q4 = warp & 3;
     const int comp = q4 * 32 + lane;
     const bool leader = q4 == 0 && lane == 0;
-    constexpr int kOutPerGroup = kLvlOut / 2;
+    constexpr int kOutPerGroup = kLvlOut / 3;
     int64_t tu = 0, nq = 0;                              // units done, quarters stored
     // The four warps of a group meet at named barriers, so they decide to stop together:
     // only they write their epi_abort word, before a barrier, and all read it after.
@@ -759,7 +760,8 @@ __global__ void __launch_bounds__(kLvlThreads, 1) level_mma_kernel(const __grid_
       const int64_t g = g_first + (u >> tb) * radix;
       float *dst = a.child + (((uint64_t)(g - a.node_lo) << a.h) + ((uint64_t)(u & ((1 << tb) - 1)) << 13)) * 2;
 #pragma unroll 1
-      for (int qr = grp; qr < 4; qr += 2, ++nq) {
+      for (int qr = 0; qr < 4; ++qr) {
+        if ((int)((tu * 4 + qr) % 3) != grp) continue;
         uint32_t v[32];
         const uint32_t taddr = tmem + ((uint32_t)(q4 * 32) << 16) + 256u + (uint32_t)(b * 128 + qr * 32);
         asm volatile(
@@ -791,6 +793,7 @@ __global__ void __launch_bounds__(kLvlThreads, 1) level_mma_kernel(const __grid_
                        : "memory");
           asm volatile("cp.async.bulk.commit_group;" ::: "memory");
         }
+        ++nq;
       }
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       mbar_arrive(&tempty[b]);
