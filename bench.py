@@ -164,8 +164,8 @@ PROFILED_TRAFFIC = {
              "profile": "profiles/leaf_contract_fact_n30.md"},
     # level 6 of the small n=30 case (levels 5 and 6 share the kernel; level 5's output
     # stayed in L2 there, so the larger launch's ratio stands for both)
-    "level_mma": {"ratio": 275.4 / 335.5, "source": "paper_2502_06959_gb300/csrc/gemm_tc.cu",
-                  "kernel": "level_mma_kernel", "sha256": "1aa361be73ac7e76",
+    "level_mma": {"ratio": (67.7 + 207.6) / 335.5, "source": "paper_2502_06959_gb300/csrc/gemm_tc.cu",
+                  "kernel": "level_mma_kernel", "sha256": "5846d163ab97848f",
                   "profile": "profiles/level_mma_levels56_n30.md"},
 }
 
