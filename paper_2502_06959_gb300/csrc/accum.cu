@@ -728,30 +728,32 @@ __global__ void __launch_bounds__(128, 3) leaf_contract_fact_kernel(LeafArgs a) 
   // instruction: in copy q lane l moves 16-byte piece l % H of chunk (32 / H) q + l / H,
   // so one instruction covers 32 / H chunks of contiguous bytes instead of 32 scattered
   // pieces.  Chunk c of the warp is bitstring c / 2, side c % 2; cof[q] is its origin.
+  // CPI is even, so the side of every chunk a lane copies is (lane / H) & 1: the lane's
+  // source base, shift and destination column are fixed, and copy q only adds its
+  // chunk's origin and row.
   constexpr int CPI = 32 / H;                  // chunks per copy instruction
+  static_assert(CPI % 2 == 0, "a lane copies chunks of one side");
   const int lane = threadIdx.x & 31, wbase = threadIdx.x & ~31;
+  const int csd = (lane / H) & 1, piece = lane % H;
+  const C *cbase = reinterpret_cast<const C *>(csd == 0 ? a.Pa : a.Pb) + 2 * piece;
+  const int chb = csd == 0 ? a.ha : a.hb;
   uint32_t cof[H];
-  bool cok[H];
+  int crow[H];                                 // destination offset (complex) of copy q
 #pragma unroll
   for (int q = 0; q < H; ++q) {
     const int c = CPI * q + lane / H;
     const int64_t sc = (int64_t)blockIdx.x * kFactSpb + (wbase >> 1) + (c >> 1);
-    cok[q] = sc < a.S;
-    const uint64_t ic = cok[q] ? ((c & 1) == 0 ? a.ia[sc] : a.ib[sc]) : 0;
+    const bool ok = sc < a.S;
+    const uint64_t ic = ok ? (csd == 0 ? a.ia[sc] : a.ib[sc]) : 0;
     cof[q] = (uint32_t)(ic & ~(uint64_t)(D - 1));
+    crow[q] = ok ? ((wbase >> 1) + (c >> 1)) * SB + csd * BOFF + 2 * piece : -1;
   }
   auto issue = [&](int64_t jj, int stage) {
     if (jj < j1) {
+      const C *pj = cbase + ((uint64_t)jj << chb);
 #pragma unroll
-      for (int q = 0; q < H; ++q) {
-        const int c = CPI * q + lane / H, piece = lane % H;
-        if (cok[q]) {
-          const int sd = c & 1;
-          const C *sp = reinterpret_cast<const C *>(sd == 0 ? a.Pa : a.Pb) +
-                        (((uint64_t)jj << (sd == 0 ? a.ha : a.hb)) + cof[q]);
-          cp_async16(buf[stage] + ((wbase >> 1) + (c >> 1)) * SB + sd * BOFF + 2 * piece, sp + 2 * piece);
-        }
-      }
+      for (int q = 0; q < H; ++q)
+        if (crow[q] >= 0) cp_async16(buf[stage] + crow[q], pj + cof[q]);
     }
     cp_commit();
   };
