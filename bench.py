@@ -159,8 +159,8 @@ PROFILED_TRAFFIC = {
     "level_f16": {"ratio": (268.7 + 877.8) / 1342.2, "source": "paper_2502_06959_gb300/csrc/gemm_tc.cu",
                   "kernel": "level_mma_f16_kernel", "sha256": "b73929fba14e31a5",
                   "profile": "profiles/level_f16_level7_n30.md"},
-    "leaf": {"ratio": (1896.2 + 7.5) / 2151.7, "source": "paper_2502_06959_gb300/csrc/accum.cu",
-             "kernel": "leaf_contract_fact_kernel", "sha256": "50afedbb5f9cb3f9",
+    "leaf": {"ratio": (1883.1 + 7.0) / 2151.7, "source": "paper_2502_06959_gb300/csrc/accum.cu",
+             "kernel": "leaf_contract_fact_kernel", "sha256": "f449d346010749b5",
              "profile": "profiles/leaf_contract_fact_n30.md"},
     # level 6 of the small n=30 case (levels 5 and 6 share the kernel; level 5's output
     # stayed in L2 there, so the larger launch's ratio stands for both)
