@@ -196,10 +196,56 @@ __device__ __forceinline__ void ap1(C (&v)[NR], const C *__restrict__ m) {
   }
 }
 
+// Packed FP32 pair FMA (two lanes per instruction): d = a * b + c elementwise.
+__device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) {
+  float2 d;
+  asm("{\n .reg .b64 ra, rb, rc, rd;\n"
+      " mov.b64 ra, {%2, %3};\n mov.b64 rb, {%4, %5};\n mov.b64 rc, {%6, %7};\n"
+      " fma.rn.f32x2 rd, ra, rb, rc;\n mov.b64 {%0, %1}, rd;\n}"
+      : "=f"(d.x), "=f"(d.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+  return d;
+}
+
 template <int J, int K, int NR, typename C>
 __device__ __forceinline__ void ap2(C (&v)[NR], const C *m0) {
-  if constexpr (sizeof(C) == 8) {
-    // complex64: the 4x4 matrix is loaded once and stays in registers for every quad
+  if constexpr (sizeof(C) == 8 && NR >= 16) {
+    // complex64: the 4x4 matrix is loaded once as broadcast pairs (Re m, Re m) and
+    // (Im m, Im m) and stays in registers for every quad; with x = (Re x, Im x) as it
+    // sits in registers, P = sum mr x and Q = sum mi x are packed FMAs and
+    // (m x)_r = (P.x - Q.y, P.y + Q.x)
+    C mr[16], mi[16];
+#pragma unroll
+    for (int e = 0; e < 16; e += 2) {
+      C a0, a1;
+      ld2(m0 + e, a0, a1);
+      mr[e] = make_float2(a0.x, a0.x);
+      mi[e] = make_float2(a0.y, a0.y);
+      mr[e + 1] = make_float2(a1.x, a1.x);
+      mi[e + 1] = make_float2(a1.y, a1.y);
+    }
+#pragma unroll
+    for (int i = 0; i < NR; ++i) {
+      if (i & ((1 << J) | (1 << K))) continue;
+      const int id[4] = {i, i | (1 << K), i | (1 << J), i | (1 << J) | (1 << K)};
+      C x[4];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) x[c] = v[id[c]];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        C P = make_float2(0.f, 0.f), Q = P;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          P = ffma2(mr[4 * r + c], x[c], P);
+          Q = ffma2(mi[4 * r + c], x[c], Q);
+        }
+        v[id[r]] = make_float2(P.x - Q.y, P.y + Q.x);
+      }
+    }
+    return;
+  } else if constexpr (sizeof(C) == 8) {
+    // complex64 with 8-amplitude register blocks (64 registers a thread): the matrix as
+    // plain complex values, to stay in registers
     C mm[16];
 #pragma unroll
     for (int e = 0; e < 16; e += 2) ld2(m0 + e, mm[e], mm[e + 1]);
