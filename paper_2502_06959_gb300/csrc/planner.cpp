@@ -266,7 +266,7 @@ class HostPool {
 void host_parallel_for(size_t n, const std::function<void(size_t)> &fn) {
   static HostPool *pool = [] {
     const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
-    return new HostPool((int)std::min(7u, hw > 1 ? hw - 1 : 0u));
+    return new HostPool((int)std::min(15u, hw > 1 ? hw - 1 : 0u));
   }();
   pool->run(n, fn);
 }
