@@ -3,6 +3,8 @@
 
 #include <atomic>
 #include <complex>
+#include <memory>
+#include <utility>
 #include <cstdint>
 #include <string>
 #include <functional>
@@ -17,6 +19,27 @@ using cd = std::complex<double>;
 
 // A cascade block (closed-form terms) may hold up to this many qubits on its non-hub side.
 constexpr int kMaxCascadeLeaves = 8;
+
+// Allocator whose default construction leaves trivial elements uninitialised (a vector
+// resized with it is not zero-filled first: for buffers that are written in full).
+template <typename T>
+struct NoInitAlloc : std::allocator<T> {
+  template <typename U>
+  struct rebind {
+    using other = NoInitAlloc<U>;
+  };
+  NoInitAlloc() = default;
+  template <typename U>
+  NoInitAlloc(const NoInitAlloc<U> &) noexcept {}
+  template <typename U>
+  void construct(U *p) noexcept {
+    ::new (static_cast<void *>(p)) U;
+  }
+  template <typename U, typename... Args>
+  void construct(U *p, Args &&...args) {
+    ::new (static_cast<void *>(p)) U(std::forward<Args>(args)...);
+  }
+};
 
 struct GateH {
   int kind = 0;
@@ -83,7 +106,7 @@ struct LevelH {
   // image the kernel loads (per digit TF32 hi then lo part when ops follow the product,
   // else per digit FP16 hi then lo part, then the inverse scales).
   bool mma = false;
-  std::vector<float> wimg;
+  std::vector<float, NoInitAlloc<float>> wimg;   // every entry is written by the composition
   size_t w_off = 0;
   // candidate: the first mma_prefix ops act on the kMmaBits lowest storage bits (the
   // whole program when mma_prefix == ops.size()); once chosen, those ops are composed

@@ -956,9 +956,9 @@ void compose_mma_levels(hsf_plan &p, int leaf_c) {
       job.r = (int)p.radix[k];
       // a level with ops after the product runs the TF32 kernel, one without the FP16 one
       job.f16 = lv.post.empty();
-      lv.wimg.assign(job.f16 ? (size_t)job.r * (kMmaWDigitBytes / 4) + (size_t)job.r
-                             : (size_t)job.r * 2 * (kMmaWPartBytes / 4),
-                     0.f);
+      lv.wimg.clear();        // every entry is written below, so no zero fill
+      lv.wimg.resize(job.f16 ? (size_t)job.r * (kMmaWDigitBytes / 4) + (size_t)job.r
+                             : (size_t)job.r * 2 * (kMmaWPartBytes / 4));
       // the ops after the last digit-dependent one are shared by every digit: compose
       // them once (S, column-major), then U_m e_col = S (prefix_m e_col), where the
       // prefix image of a basis vector has few nonzeros
