@@ -151,14 +151,118 @@ __device__ double kdot_tile(const typename CT<R>::T *psi, const typename CT<R>::
   return tot;
 }
 
+// One op of at most two qubits undone on both tiles in a single pass, with the
+// gradient term first: g += Re sum_u mu(u) (K psi)(u), then psi <- G^dagger psi and
+// mu <- G^T mu (the same three steps as kdot_tile + two apply_tile, one sweep over the
+// tile and one barrier).  The op's G^dagger, G^T and K are staged in shared memory
+// first.  Dense ops act on tile bits; a diagonal op's bits may be fixed bits of the tile.
+template <typename R, int NQ, bool DIAG>
+__device__ double fused_op(typename CT<R>::T *psi, typename CT<R>::T *mu, uint32_t tile_elems, const DevOp &op,
+                           const typename CT<R>::T *mats, uint64_t base, double *red, typename CT<R>::T *sm) {
+  using C = typename CT<R>::T;
+  constexpr int DIM = 1 << NQ;
+  constexpr int E = DIAG ? DIM : DIM * DIM;
+  const bool grad = op.param >= 0;
+  const C *m = mats + op.mat;
+  C *gd = sm, *gt = sm + 16, *kk = sm + 32;
+  if (threadIdx.x < E) {
+    const int e = threadIdx.x;
+    const int src = DIAG ? e : (e % DIM) * DIM + e / DIM;     // (r, c) <- (c, r)
+    gd[e] = cconj(m[src]);
+    gt[e] = m[src];
+    if (grad) kk[e] = mats[op.kmat + e];
+  }
+  __syncthreads();
+  double acc = 0.0;
+  if constexpr (DIAG) {
+    for (uint32_t u = threadIdx.x; u < tile_elems; u += blockDim.x) {
+      int idx = 0;
+#pragma unroll
+      for (int j = 0; j < NQ; ++j) {
+        const int p = op.pos[j];
+        const int bit = p >= kFixedBit ? (int)((base >> (p - kFixedBit)) & 1ull) : (int)((u >> p) & 1u);
+        idx = (idx << 1) | bit;
+      }
+      const C x = psi[u], y = mu[u];
+      if (grad) acc += (double)cmul(y, cmul(kk[idx], x)).x;
+      psi[u] = cmul(gd[idx], x);
+      mu[u] = cmul(gt[idx], y);
+    }
+  } else {
+    int lo = op.pos[0], hi = NQ == 2 ? op.pos[1] : 0;
+    if (NQ == 2 && lo > hi) {
+      const int t = lo;
+      lo = hi;
+      hi = t;
+    }
+    for (uint32_t j = threadIdx.x; j < (tile_elems >> NQ); j += blockDim.x) {
+      uint32_t i = insert_zero(j, lo);
+      if (NQ == 2) i = insert_zero(i, hi);
+      uint32_t addr[DIM];
+      C x[DIM], y[DIM];
+#pragma unroll
+      for (int k = 0; k < DIM; ++k) {
+        uint32_t ad = i;
+#pragma unroll
+        for (int q = 0; q < NQ; ++q)
+          if ((k >> (NQ - 1 - q)) & 1) ad |= 1u << op.pos[q];
+        addr[k] = ad;
+        x[k] = psi[ad];
+        y[k] = mu[ad];
+      }
+      if (grad) {
+#pragma unroll
+        for (int r = 0; r < DIM; ++r) {
+          C kp;
+          kp.x = R(0);
+          kp.y = R(0);
+#pragma unroll
+          for (int c = 0; c < DIM; ++c) {
+            const C t = cmul(kk[r * DIM + c], x[c]);
+            kp.x += t.x;
+            kp.y += t.y;
+          }
+          acc += (double)cmul(y[r], kp).x;
+        }
+      }
+#pragma unroll
+      for (int r = 0; r < DIM; ++r) {
+        C np, nm;
+        np.x = np.y = nm.x = nm.y = R(0);
+#pragma unroll
+        for (int c = 0; c < DIM; ++c) {
+          const C a = cmul(gd[r * DIM + c], x[c]), b = cmul(gt[r * DIM + c], y[c]);
+          np.x += a.x;
+          np.y += a.y;
+          nm.x += b.x;
+          nm.y += b.y;
+        }
+        psi[addr[r]] = np;
+        mu[addr[r]] = nm;
+      }
+    }
+  }
+  double tot = 0.0;
+  if (grad) {
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  }
+  __syncthreads();
+  if (grad && threadIdx.x == 0)
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += red[w];
+  return tot;
+}
+
 template <typename R>
-__global__ void __launch_bounds__(256) adjoint_kernel(AdjointArgs a) {
+__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1) adjoint_kernel(AdjointArgs a) {
   using C = typename CT<R>::T;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const uint32_t tile_elems = 1u << a.t;
   C *psi = reinterpret_cast<C *>(smem_raw);
   C *mu = psi + tile_elems;
   __shared__ double red[8];
+  __shared__ C sm[48];                         // the current op's G^dagger, G^T and K
+  const bool contiguous = a.active_mask == ((1ull << a.t) - 1ull);
   const uint64_t full = (1ull << a.h) - 1ull;
   const uint64_t inactive = full & ~a.active_mask;
   const C *mats = reinterpret_cast<const C *>(a.mats);
@@ -170,7 +274,7 @@ __global__ void __launch_bounds__(256) adjoint_kernel(AdjointArgs a) {
     C *gpsi = reinterpret_cast<C *>(a.psi) + (uint64_t)nl * state;
     C *gmu = reinterpret_cast<C *>(a.mu) + (uint64_t)nl * state;
     for (uint32_t u = threadIdx.x; u < tile_elems; u += blockDim.x) {
-      const uint64_t off = base | deposit(u, a.active_mask);
+      const uint64_t off = base | (contiguous ? (uint64_t)u : deposit(u, a.active_mask));
       psi[u] = gpsi[off];
       mu[u] = gmu[off];
     }
@@ -178,15 +282,22 @@ __global__ void __launch_bounds__(256) adjoint_kernel(AdjointArgs a) {
     for (int o = a.num_ops - 1; o >= a.first_op; --o) {
       const DevOp op = a.ops[o];
       const C *m = mats + op.mat;
-      if (op.param >= 0) {
-        const double g = kdot_tile<R>(psi, mu, tile_elems, op, mats + op.kmat, base, red);
-        if (threadIdx.x == 0) atomicAdd(a.grad + op.param, g);
+      double g = 0.0;
+      if (op.nq == 1) {
+        g = op.type == OP_DIAG ? fused_op<R, 1, true>(psi, mu, tile_elems, op, mats, base, red, sm)
+                               : fused_op<R, 1, false>(psi, mu, tile_elems, op, mats, base, red, sm);
+      } else if (op.nq == 2) {
+        g = op.type == OP_DIAG ? fused_op<R, 2, true>(psi, mu, tile_elems, op, mats, base, red, sm)
+                               : fused_op<R, 2, false>(psi, mu, tile_elems, op, mats, base, red, sm);
+      } else {
+        if (op.param >= 0) g = kdot_tile<R>(psi, mu, tile_elems, op, mats + op.kmat, base, red);
+        apply_tile<R>(psi, tile_elems, op, m, 1, base);   // psi <- G^dagger psi
+        apply_tile<R>(mu, tile_elems, op, m, 2, base);    // mu  <- G^T mu
       }
-      apply_tile<R>(psi, tile_elems, op, m, 1, base);   // psi <- G^dagger psi
-      apply_tile<R>(mu, tile_elems, op, m, 2, base);    // mu  <- G^T mu
+      if (op.param >= 0 && threadIdx.x == 0) atomicAdd(a.grad + op.param, g);
     }
     for (uint32_t u = threadIdx.x; u < tile_elems; u += blockDim.x) {
-      const uint64_t off = base | deposit(u, a.active_mask);
+      const uint64_t off = base | (contiguous ? (uint64_t)u : deposit(u, a.active_mask));
       gpsi[off] = psi[u];
       gmu[off] = mu[u];
     }
