@@ -272,6 +272,16 @@ hsf_status hsf_grad(hsf_plan *p, const uint64_t *bits, size_t num, const void *g
       a.parent_lo = parent_lo;
       a.num_nodes = nodes;
       a.tiles_per_node = 1 << (sd.h - ps.t);
+      a.groups = ps.groups.empty() ? nullptr : (const DevGroup *)((unsigned char *)p->dev_gtable + ps.groups_off);
+      a.num_groups = (int32_t)ps.groups.size();
+      a.rbits = p->rbits;
+      const size_t blk = ps.table_end - ps.ops_off;
+      if (!ps.groups.empty() && blk <= (size_t)kMaxStageBytes) {
+        a.stage_src = (unsigned char *)p->dev_gtable + ps.ops_off;
+        a.stage_bytes = (int32_t)((blk + 15) / 16 * 16);
+        a.stage_mats_off = (int32_t)(ps.mats_off - ps.ops_off);
+        a.stage_groups_off = (int32_t)(ps.groups_off - ps.ops_off);
+      }
       CUDA_TRY(launch_sweep(a, p->precision, stm));
       g_launches++;
     }

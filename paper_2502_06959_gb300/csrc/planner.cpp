@@ -1241,7 +1241,9 @@ hsf_status build_programs(hsf_plan &p, bool grad) {
     }
     for (auto &lv : sd.levels) {
       split_passes(lv, sd.h, p.tile_max);
-      if (!grad && !(p.flags & HSF_FLAG_NO_REGISTER_SWEEP))
+      // gradient programs too: the groups only say how the forward sweep holds the ops in
+      // registers; the op list (every rotation its own op) is what the adjoint undoes
+      if (!(p.flags & HSF_FLAG_NO_REGISTER_SWEEP))
         for (auto &ps : lv.passes) build_groups(ps, p.rbits);
     }
   }
