@@ -115,3 +115,17 @@ def test_all_paths_complex128(golden):
     got, desc, _, _, _ = _run(pr, bits, precision="c128")
     err = float(np.max(np.abs(got - ref)))
     assert err <= 1e-12, err
+
+
+@pytest.mark.parametrize("count", [1, 37, 512])
+def test_all_paths_few_bitstrings(golden, count):
+    """Few bitstrings: level 7 then stores only the 16-amplitude segments that those
+    bitstrings' chunks cover (almost none of the state at one bitstring), and the leaf
+    must still see exactly the values it reads.  The first `count` stored bitstrings,
+    all 65536 paths, against the same FP64 amplitudes; the plan is the benchmark's
+    (FP16 level 7 before the factored leaf)."""
+    pr, bits, ref = golden
+    got, desc, _, _, _ = _run(pr, bits[:count].copy())
+    assert "leaf=factored" in desc
+    assert any(l.startswith(" level 7:") and "FP16x3" in l for l in desc.splitlines())
+    _check_c64(got, ref[:count])
