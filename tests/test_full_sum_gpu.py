@@ -128,4 +128,7 @@ def test_all_paths_few_bitstrings(golden, count):
     got, desc, _, _, _ = _run(pr, bits[:count].copy())
     assert "leaf=factored" in desc
     assert any(l.startswith(" level 7:") and "FP16x3" in l for l in desc.splitlines())
-    _check_c64(got, ref[:count])
+    # the same bound as the full set (1e-5 absolute, 1e-4 of the largest of the 4096
+    # reference amplitudes): the error does not depend on which bitstrings are asked
+    err = float(np.max(np.abs(got - ref[:count])))
+    assert err <= 1e-5 and err <= 1e-4 * float(np.max(np.abs(ref))), err
