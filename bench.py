@@ -59,6 +59,8 @@ def parse():
     ap.add_argument("--max-n", type=int, default=0, help="c3 profiling aid: drop circuits above this n")
     ap.add_argument("--largest-only", action="store_true",
                     help="c3 profiling aid: run only the largest circuit once (no graph)")
+    ap.add_argument("--leaf-dots", action="store_true",
+                    help="c2 profiling aid: plan with HSF_FLAG_LEAF_DOTS (level 7 writes the leaf's dots)")
     return ap.parse_args()
 
 
@@ -156,8 +158,8 @@ PROFILED_TRAFFIC = {
     "sweep": {"ratio": 275.1 / 335.5, "source": "paper_2502_06959_gb300/csrc/sweep.cu",
               "kernel": "sweep_reg_kernel", "sha256": "1a9bade5309e94b9",
               "profile": "profiles/sweep_reg_level6_n30.md"},
-    "level_f16": {"ratio": (268.7 + 877.8) / 1342.2, "source": "paper_2502_06959_gb300/csrc/gemm_tc.cu",
-                  "kernel": "level_mma_f16_kernel", "sha256": "b73929fba14e31a5",
+    "level_f16": {"ratio": (268.8 + 878.2) / 1342.2, "source": "paper_2502_06959_gb300/csrc/gemm_tc.cu",
+                  "kernel": "level_mma_f16_kernel", "sha256": "91c1097dc391da30",
                   "profile": "profiles/level_f16_level7_n30.md"},
     "leaf": {"ratio": (1883.1 + 7.0) / 2151.7, "source": "paper_2502_06959_gb300/csrc/accum.cu",
              "kernel": "leaf_contract_fact_kernel", "sha256": "f449d346010749b5",
@@ -667,7 +669,8 @@ def main():
     stream = torch.cuda.current_stream()
 
     # workspace sized once for this circuit
-    plan0 = hsf.Plan.from_problem(pr, precision=args.precision)
+    pflags = hsf.FLAG_LEAF_DOTS if args.leaf_dots else 0
+    plan0 = hsf.Plan.from_problem(pr, precision=args.precision, flags=pflags)
     info = dict(plan0.info)
     free, _ = torch.cuda.mem_get_info()
     budget = int(args.budget_gb * 2 ** 30) if args.budget_gb else int(free * 0.7)
@@ -681,7 +684,8 @@ def main():
 
     def step(plan_each=True):
         if plan_each:
-            h = hsf.hsf_plan_create(pr.n, pr.gates, pr.cut, pr.blocks, precision=args.precision, marshalled=marsh)
+            h = hsf.hsf_plan_create(pr.n, pr.gates, pr.cut, pr.blocks, precision=args.precision, flags=pflags,
+                                       marshalled=marsh)
         else:
             h = plan0.handle
         hsf.hsf_run(h, bits.data_ptr(), S, 0, 0, p_end, out.data_ptr(), ws.data_ptr(), ws_bytes,
@@ -759,7 +763,8 @@ def main():
     e0.record(stream)
     for _ in range(args.steps):
         dbits.copy_(hbits, non_blocking=True)
-        h = hsf.hsf_plan_create(pr.n, pr.gates, pr.cut, pr.blocks, precision=args.precision, marshalled=marsh)
+        h = hsf.hsf_plan_create(pr.n, pr.gates, pr.cut, pr.blocks, precision=args.precision, flags=pflags,
+                                       marshalled=marsh)
         hsf.hsf_run(h, dbits.data_ptr(), S, 0, 0, p_end, out.data_ptr(), ws.data_ptr(), ws_bytes,
                     stream.cuda_stream)
         hout.copy_(out, non_blocking=True)
@@ -881,11 +886,15 @@ def main():
                                    "ref": "tests/golden/c2_n30_amplitudes.json (FP64 Schroedinger oracle)"}
             # the precision forms on the same circuit: the default (tensor-core levels with
             # FP16 / TF32 split operands) against the plain FP32 path (every level swept on
-            # the CUDA cores), each timed over the same steps and checked against FP64
+            # the CUDA cores), each timed over the same steps and checked against FP64; and
+            # the opt-in dot form of the leaf (level 7 writes the leaf's chunk dots instead
+            # of its children: fewer bytes, a slower epilogue)
             line["forms"] = {
                 "default_tc_levels": form_leg(hsf, torch, pr, bits, S, stream, args.steps, 0, gold, budget),
                 "plain_fp32": form_leg(hsf, torch, pr, bits, S, stream, args.steps, hsf.FLAG_NO_TC_LEVEL, gold,
                                        budget),
+                "leaf_dots": form_leg(hsf, torch, pr, bits, S, stream, args.steps, hsf.FLAG_LEAF_DOTS, gold,
+                                      budget),
             }
         else:
             got = plan0.run(bits, path_range=(0, tot)).cpu().numpy()

@@ -133,6 +133,17 @@ typedef struct hsf_plan_opts {
                                         qubits on one side is diagonal on them: CNOT
                                         controls, CZ, RZZ, phases; Sec. IV-D, Example 4)
                                         gets its terms P_z (x) Y_z in closed form */
+#define HSF_FLAG_LEAF_DOTS 256       /* complex64, bitstring output, opt-in: where the
+                                        leaf's operators factor (L_m = S (F_m (x) I) on
+                                        16-amplitude chunks) and the deepest tree level
+                                        runs on the FP16 tensor-core kernel, that level
+                                        writes the leaf's four chunk dots per
+                                        (bitstring, child) instead of its children, and
+                                        the leaf sums their bilinear form (Sec. IV-A;
+                                        the same bits as the default path).  Fewer
+                                        bytes move, but on GB300 the level's epilogue
+                                        is then bound by the dots' shared-memory
+                                        latency and the run is slower              */
 
 typedef struct hsf_plan hsf_plan;
 

@@ -10,6 +10,7 @@
 // * window: full / leading-window output as the rank-P complex product
 //   Out[x_a, x_b] = sum_p L[p, x_a] R[p, x_b] on CUDA cores (FP32 or FP64), folded
 //   into the FP64 output with the same compensation.
+#include <algorithm>
 #include <cstdint>
 
 #include "common.h"
@@ -1406,6 +1407,217 @@ cudaError_t launch_chunk_mask(const uint64_t *ia, const uint64_t *ib, int64_t S,
   if (e == cudaSuccess) e = cudaMemsetAsync(mask_b, 0, bb, st);
   if (e != cudaSuccess) return e;
   chunk_mask_kernel<<<(unsigned)((S + 255) / 256), 256, 0, st>>>(ia, ib, S, c, mask_a, mask_b);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Dot form of the factored leaf (Sec. IV-A, the leaf digits' sum folded into
+// sum_{al,be} G[al][be] d_a[al] d_b[be]).  The deepest tree level's epilogue forms the
+// four dots d[2 i + j] = sum_k S[rr][e_i(k)] x[e_j(k)] of every bitstring's chunk x
+// (e_j(k) puts bit j at the factor's chunk bit) while the child rows are still in
+// registers, so the children never reach memory; the leaf kernel below sums the
+// bilinear form over the parents from those dots.  To find its bitstrings a level
+// epilogue needs them grouped by segment, which the kernels here do once per run.
+// ---------------------------------------------------------------------------
+size_t dot_sort_bytes(int64_t S, int ha, int hb) {
+  auto a256 = [](size_t x) { return (x + 255) / 256 * 256; };
+  size_t t = 0;
+  for (int s = 0; s < 2; ++s) {
+    const size_t nb = (size_t)1 << ((s == 0 ? ha : hb) - 4);
+    t += a256((nb + 1) * 4) + a256(nb * 4) + a256((size_t)S * 4);
+  }
+  return t + 2 * a256((size_t)S * 4) + 2 * a256(256 * 8);
+}
+
+DotSort dot_sort_layout(unsigned char *base, int64_t S, int ha, int hb) {
+  auto a256 = [](size_t x) { return (x + 255) / 256 * 256; };
+  DotSort d{};
+  size_t o = 0;
+  for (int s = 0; s < 2; ++s) {
+    const size_t nb = (size_t)1 << ((s == 0 ? ha : hb) - 4);
+    d.off[s] = reinterpret_cast<uint32_t *>(base + o);
+    o += a256((nb + 1) * 4);
+    d.cur[s] = reinterpret_cast<uint32_t *>(base + o);
+    o += a256(nb * 4);
+    d.list[s] = reinterpret_cast<uint32_t *>(base + o);
+    o += a256((size_t)S * 4);
+  }
+  d.ida = reinterpret_cast<uint32_t *>(base + o);
+  o += a256((size_t)S * 4);
+  d.posb = reinterpret_cast<uint32_t *>(base + o);
+  o += a256((size_t)S * 4);
+  d.T[0] = reinterpret_cast<float2 *>(base + o);
+  o += a256(256 * 8);
+  d.T[1] = reinterpret_cast<float2 *>(base + o);
+  return d;
+}
+
+struct DotSortArgs {
+  const uint64_t *idx[2];
+  int64_t S;
+  int32_t nb[2];
+  int32_t h[2];
+  const float2 *Sm[2];
+  DotSort d;
+};
+// key of storage index ix on a side of 2^h amplitudes: segment within the row, then row
+__device__ __forceinline__ uint32_t dot_key(uint64_t ix, int h) {
+  return (uint32_t)((((ix >> 4) & 3u) << (h - 6)) | (ix >> 6));
+}
+
+// blockIdx.y = side: count the bitstrings of each key into off[key + 1] (off zeroed);
+// the first 256 threads also write the side's S transposed to [e][rr]
+__global__ void dot_count_kernel(DotSortArgs a) {
+  const int side = blockIdx.y;
+  const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s < a.S) atomicAdd(&a.d.off[side][dot_key(a.idx[side][s], a.h[side]) + 1], 1u);
+  if (s < 256) {
+    const int e = (int)(s >> 4), rr = (int)(s & 15);
+    a.d.T[side][s] = a.Sm[side][rr * 16 + e];
+  }
+}
+
+// blockIdx.x = side: inclusive scan of off[1..nb] in place (off[0] = 0), so off[key] is
+// the first position of a key; cur = off[0..nb) as the scatter's cursors
+__global__ void __launch_bounds__(1024) dot_scan_kernel(DotSortArgs a) {
+  __shared__ uint32_t part[1024];
+  const int side = blockIdx.x, t = threadIdx.x;
+  const int nb = a.nb[side];
+  uint32_t *off = a.d.off[side] + 1;
+  const int per = (nb + 1023) / 1024, i0 = min(nb, t * per), i1 = min(nb, i0 + per);
+  uint32_t sum = 0;
+  for (int i = i0; i < i1; ++i) sum += off[i];
+  part[t] = sum;
+  __syncthreads();
+  for (int o = 1; o < 1024; o <<= 1) {
+    const uint32_t x = t >= o ? part[t - o] : 0u;
+    __syncthreads();
+    part[t] += x;
+    __syncthreads();
+  }
+  uint32_t run = part[t] - sum;
+  for (int i = i0; i < i1; ++i) {
+    run += off[i];
+    off[i] = run;
+  }
+  __syncthreads();
+  for (int i = t; i < nb; i += 1024) a.d.cur[side][i] = a.d.off[side][i];
+}
+
+// blockIdx.y = side: each bitstring takes the next position of its key (the order
+// inside a key varies from run to run; every bitstring's dots and sum do not)
+__global__ void dot_scatter_kernel(DotSortArgs a) {
+  const int side = blockIdx.y;
+  const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= a.S) return;
+  const uint64_t ix = a.idx[side][s];
+  const uint32_t pos = atomicAdd(&a.d.cur[side][dot_key(ix, a.h[side])], 1u);
+  a.d.list[side][pos] = (uint32_t)((ix >> 6) << 4) | (uint32_t)(ix & 15);
+  if (side == 0)
+    a.d.ida[pos] = (uint32_t)s;
+  else
+    a.d.posb[s] = pos;
+}
+
+cudaError_t launch_dot_sort(const uint64_t *ia, const uint64_t *ib, int64_t S, int ha, int hb, const void *Sa,
+                            const void *Sb, const DotSort &d, cudaStream_t st) {
+  if (S <= 0) return cudaSuccess;
+  if (ha < 6 || hb < 6 || ha > 24 || hb > 24 || S > ((int64_t)1 << 30)) return cudaErrorInvalidValue;
+  DotSortArgs a{};
+  a.idx[0] = ia;
+  a.idx[1] = ib;
+  a.S = S;
+  a.nb[0] = 1 << (ha - 4);
+  a.nb[1] = 1 << (hb - 4);
+  a.h[0] = ha;
+  a.h[1] = hb;
+  a.Sm[0] = static_cast<const float2 *>(Sa);
+  a.Sm[1] = static_cast<const float2 *>(Sb);
+  a.d = d;
+  for (int s = 0; s < 2; ++s) {
+    cudaError_t e = cudaMemsetAsync(d.off[s], 0, ((size_t)a.nb[s] + 1) * 4, st);
+    if (e != cudaSuccess) return e;
+  }
+  const unsigned gx = (unsigned)((std::max<int64_t>(S, 256) + 255) / 256);
+  dot_count_kernel<<<dim3(gx, 2), 256, 0, st>>>(a);
+  dot_scan_kernel<<<2, 1024, 0, st>>>(a);
+  dot_scatter_kernel<<<dim3((unsigned)((S + 255) / 256), 2), 256, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+// One thread per bitstring, taken in side-a order (its side-a dots are read
+// contiguously, its side-b dots gathered), parents [g ppg, (g + 1) ppg) of the chunk.
+// The arithmetic, and its order, is that of leaf_contract_fact_kernel's two lanes: lane
+// `side` adds d_a[2 side + {0, 1}] (G[2 side + {0, 1}] . d_b) into its own FP32 sum,
+// and the two sums are added at the end.
+__global__ void __launch_bounds__(256) leaf_dots_kernel(LeafArgs a) {
+  using C = float2;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= a.S) return;
+  const int g = blockIdx.y;
+  const uint32_t id = a.dida[t];
+  const int64_t tb = a.dposb[id];
+  const C *Gt = reinterpret_cast<const C *>(a.G);
+  const int r1 = a.r + 1;
+  C gf[4][4];
+  {
+    const C *G = Gt + (size_t)a.r * 16;        // [m0 = 0][m1 = r]
+#pragma unroll
+    for (int al = 0; al < 4; ++al)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) gf[al][b] = G[al * 4 + b];
+  }
+  const float4 *Da = static_cast<const float4 *>(a.Da), *Db = static_cast<const float4 *>(a.Db);
+  const int64_t j0 = (int64_t)g * a.parents_per_group;
+  const int64_t j1 = min(a.num_parents, j0 + a.parents_per_group);
+  float accr[2] = {0.f, 0.f}, acci[2] = {0.f, 0.f};
+#pragma unroll 2
+  for (int64_t j = j0; j < j1; ++j) {
+    const float4 a01 = __ldcs(Da + 2 * (j * a.S + t)), a23 = __ldcs(Da + 2 * (j * a.S + t) + 1);
+    const float4 b01 = __ldcs(Db + 2 * (j * a.S + tb)), b23 = __ldcs(Db + 2 * (j * a.S + tb) + 1);
+    const float ar[4] = {a01.x, a01.z, a23.x, a23.z}, ai[4] = {a01.y, a01.w, a23.y, a23.w};
+    const float br[4] = {b01.x, b01.z, b23.x, b23.z}, bi[4] = {b01.y, b01.w, b23.y, b23.w};
+    C h[4][4];
+#pragma unroll
+    for (int al = 0; al < 4; ++al)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) h[al][b] = gf[al][b];
+    if ((j == 0 && a.m_first > 0) || (j == a.num_parents - 1 && a.m_last < a.r)) {
+      // a parent with only part of its digits in the path range
+      const int m0 = j == 0 ? a.m_first : 0, m1 = j == a.num_parents - 1 ? a.m_last : a.r;
+      const C *G = Gt + ((size_t)m0 * r1 + m1) * 16;
+#pragma unroll
+      for (int al = 0; al < 4; ++al)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) h[al][b] = G[al * 4 + b];
+    }
+#pragma unroll
+    for (int side = 0; side < 2; ++side) {
+      float u0r = 0.f, u0i = 0.f, u1r = 0.f, u1i = 0.f;
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        const C h0 = h[2 * side][b], h1 = h[2 * side + 1][b];
+        u0r = fmaf(h0.x, br[b], fmaf(-h0.y, bi[b], u0r));
+        u0i = fmaf(h0.x, bi[b], fmaf(h0.y, br[b], u0i));
+        u1r = fmaf(h1.x, br[b], fmaf(-h1.y, bi[b], u1r));
+        u1i = fmaf(h1.x, bi[b], fmaf(h1.y, br[b], u1i));
+      }
+      const float a0r = ar[2 * side], a0i = ai[2 * side], a1r = ar[2 * side + 1], a1i = ai[2 * side + 1];
+      accr[side] = fmaf(a0r, u0r, fmaf(-a0i, u0i, accr[side]));
+      acci[side] = fmaf(a0r, u0i, fmaf(a0i, u0r, acci[side]));
+      accr[side] = fmaf(a1r, u1r, fmaf(-a1i, u1i, accr[side]));
+      acci[side] = fmaf(a1r, u1i, fmaf(a1i, u1r, acci[side]));
+    }
+  }
+  double *dst = a.partial + 2 * ((int64_t)g * a.S + id);
+  dst[0] = (double)(accr[0] + accr[1]);
+  dst[1] = (double)(acci[0] + acci[1]);
+}
+
+cudaError_t launch_leaf_dots(const LeafArgs &a, cudaStream_t st) {
+  if (a.S <= 0 || a.num_parents <= 0) return cudaSuccess;
+  if (!a.Da || !a.Db || !a.dida || !a.dposb || !a.G || a.r < 1) return cudaErrorInvalidValue;
+  leaf_dots_kernel<<<dim3((unsigned)((a.S + 255) / 256), (unsigned)a.num_groups), 256, 0, st>>>(a);
   return cudaGetLastError();
 }
 

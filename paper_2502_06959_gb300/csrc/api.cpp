@@ -49,6 +49,9 @@ struct RunLayout {
   size_t off_buf[2][2] = {{0, 0}, {0, 0}};
   size_t off_partial = 0, off_sync = 0, off_comp = 0, off_index = 0, off_gemm = 0, off_sort = 0, total = 0;
   size_t off_mask[2] = {0, 0};   // leaf contraction: segments of the deepest level that bitstrings read
+  bool dots = false;             // leaf in the dot form (use_leaf_dots)
+  size_t off_dots[2] = {0, 0};   // dot form: [nodes of the deepest level][bitstrings] x 32 bytes per side
+  size_t off_dsort = 0;          // dot form: the bitstrings grouped by segment (dot_sort_layout)
   int32_t ppg = 64, groups = 0;
 };
 
@@ -58,23 +61,54 @@ bool use_leaf(const hsf_plan &p, size_t num_bits) {
   return num_bits > 0 && p.leaf_c > 0 && !(p.flags & HSF_FLAG_NO_LEAF_CONTRACT);
 }
 
+// The dot form of the factored leaf (HSF_FLAG_LEAF_DOTS): the deepest level (FP16
+// tensor-core kernel, nothing after its product) writes the leaf's four chunk dots per
+// (child, bitstring) instead of its children, where the operators factor on 16-amplitude
+// chunks (one segment of the kernel's rows) and the dots take no more memory than the
+// children.
+bool use_leaf_dots(const hsf_plan &p, size_t num_bits) {
+  if (!use_leaf(p, num_bits) || !(p.flags & HSF_FLAG_LEAF_DOTS) || p.precision != HSF_PREC_C64) return false;
+  const int B = (int)p.blocks.size(), top = B - 1;
+  if (top < 1 || p.leaf_pf < 0 || p.leaf_pf > 3 || p.leaf_c != 4 || num_bits >= 65536) return false;
+  if (p.radix[B] < 3 || p.radix[B] > 4) return false;     // the factored leaf's digit counts
+  for (int s = 0; s < 2; ++s) {
+    const SideH &sd = p.side[s];
+    if (sd.h < kMmaMinH || sd.h > 24 || (uint64_t)num_bits * 4 > (1ull << sd.h)) return false;
+    const LevelH &lv = sd.levels[top];
+    if (!lv.mma || !lv.post.empty() || !lv.passes.empty()) return false;
+  }
+  return true;
+}
+
 RunLayout layout_for(const hsf_plan &p, size_t num_bits, uint64_t window, uint64_t chunk) {
   RunLayout L;
   L.chunk = chunk;
   L.leaf = use_leaf(p, num_bits);
+  L.dots = use_leaf_dots(p, num_bits);
   const size_t csz = p.precision == HSF_PREC_C64 ? 8 : 16;
   const int B = (int)p.blocks.size();
   const int top = L.leaf ? B - 1 : B;          // deepest level held in memory
+  auto nodes_in_chunk = [&](int k) {           // nodes of level k inside one chunk
+    return std::min<uint64_t>(chunk, (chunk + p.below[k] - 1) / p.below[k] + 1);
+  };
   size_t off = 0;
   for (int s = 0; s < 2; ++s) {
-    uint64_t maxn = 1;                         // nodes of one level inside one chunk
-    for (int k = 0; k <= top; ++k)
-      maxn = std::max<uint64_t>(maxn, std::min<uint64_t>(chunk, (chunk + p.below[k] - 1) / p.below[k] + 1));
+    uint64_t maxn = 1;
+    // (dot form: the deepest level's children are not stored)
+    for (int k = 0; k <= (L.dots ? top - 1 : top); ++k) maxn = std::max<uint64_t>(maxn, nodes_in_chunk(k));
     const size_t sb = ((size_t)1 << p.side[s].h) * csz;
     for (int j = 0; j < 2; ++j) {
       L.off_buf[s][j] = off;
       off += align256(maxn * sb);
     }
+    if (L.dots) {
+      L.off_dots[s] = off;
+      off += align256(nodes_in_chunk(top) * num_bits * 32);
+    }
+  }
+  if (L.dots) {
+    L.off_dsort = off;
+    off += align256(dot_sort_bytes((int64_t)num_bits, p.side[0].h, p.side[1].h));
   }
   if (num_bits > 0) {
     const uint64_t units = L.leaf ? (chunk + p.radix[B] - 1) / p.radix[B] + 1 : chunk;
@@ -89,7 +123,7 @@ RunLayout layout_for(const hsf_plan &p, size_t num_bits, uint64_t window, uint64
     off += align256(num_bits * 16);
     L.off_comp = off;
     off += align256(num_bits * 16);
-    if (L.leaf && p.side[0].h >= 5 && p.side[1].h >= 5 && p.side[0].h <= 28 && p.side[1].h <= 28) {
+    if (L.leaf && !L.dots && p.side[0].h >= 5 && p.side[1].h >= 5 && p.side[0].h <= 28 && p.side[1].h <= 28) {
       for (int s = 0; s < 2; ++s) {
         L.off_mask[s] = off;
         off += align256(std::max<size_t>(4, ((size_t)1 << (p.side[s].h - 4)) / 8));
@@ -514,6 +548,11 @@ hsf_status hsf_run(hsf_plan *p, const uint64_t *bits, size_t num, uint64_t windo
       LAUNCH(HSF_KERNEL_OTHER, 16.0 * num, 0.0,
              launch_chunk_mask(ia, ib, (int64_t)num, p->leaf_c, p->na, p->nb, (uint32_t *)(ws + L.off_mask[0]),
                                (uint32_t *)(ws + L.off_mask[1]), st));
+    if (L.dots)
+      LAUNCH(HSF_KERNEL_OTHER, 40.0 * num, 0.0,
+             launch_dot_sort(ia, ib, (int64_t)num, p->na, p->nb, (unsigned char *)p->dev_table + p->side[0].leaf_s_off,
+                             (unsigned char *)p->dev_table + p->side[1].leaf_s_off,
+                             dot_sort_layout(ws + L.off_dsort, (int64_t)num, p->na, p->nb), st));
   } else {
     ia = (uint64_t *)(ws + L.off_index);
     ib = ia + M;
@@ -569,8 +608,21 @@ hsf_status hsf_run(hsf_plan *p, const uint64_t *bits, size_t num, uint64_t windo
           const double amps = (double)(hi - lo) * (double)(1ull << sd.h);
           const double parents = (double)((hi - 1) / g.radix - lo / g.radix + 1) * (double)(1ull << sd.h);
           // three 128 x 128 x 128 real products (FP16 or TF32 parts) per 128 64-amplitude rows
-          LAUNCH(lv.post.empty() ? HSF_KERNEL_LEVEL_F16 : HSF_KERNEL_LEVEL_MMA, (amps + parents) * csz, 3.0 * 2.0 * 128.0 * 128.0 * (amps / 64.0),
-                 launch_level_mma(g, st));
+          double bytes = (amps + parents) * csz, flops = 3.0 * 2.0 * 128.0 * 128.0 * (amps / 64.0);
+          if (L.dots && k == top) {
+            // dot form: the parents read, 32 bytes of dots written per (child, bitstring);
+            // four dots of 8 complex terms (8 x 32 FLOP) per (child, bitstring)
+            const DotSort ds = dot_sort_layout(ws + L.off_dsort, (int64_t)num, p->na, p->nb);
+            g.dots = (float4 *)(ws + L.off_dots[s]);
+            g.dot_off = ds.off[s];
+            g.dot_list = ds.list[s];
+            g.dot_T = ds.T[s];
+            g.dot_count = (int64_t)num;
+            g.dot_pf = p->leaf_pf;
+            bytes = parents * csz + 32.0 * (double)(hi - lo) * (double)num;
+            flops += 8.0 * 32.0 * (double)(hi - lo) * (double)num;
+          }
+          LAUNCH(lv.post.empty() ? HSF_KERNEL_LEVEL_F16 : HSF_KERNEL_LEVEL_MMA, bytes, flops, launch_level_mma(g, st));
         }
         for (size_t pi = 0; pi < lv.passes.size(); ++pi) {
           const PassH &ps = lv.passes[pi];
@@ -642,6 +694,21 @@ hsf_status hsf_run(hsf_plan *p, const uint64_t *bits, size_t num, uint64_t windo
         la.Sa = (unsigned char *)p->dev_table + p->side[0].leaf_s_off;
         la.Sb = (unsigned char *)p->dev_table + p->side[1].leaf_s_off;
         la.G = (unsigned char *)p->dev_table + p->leaf_g_off;
+      }
+      if (L.dots) {
+        // dot form: the dots the deepest level wrote, read once (64 bytes per (parent,
+        // bitstring)), the 4 x 4 bilinear form (20 complex products) on each
+        const DotSort ds = dot_sort_layout(ws + L.off_dsort, (int64_t)num, p->na, p->nb);
+        la.Da = ws + L.off_dots[0];
+        la.Db = ws + L.off_dots[1];
+        la.dida = ds.ida;
+        la.dposb = ds.posb;
+        const double units = (double)la.num_parents * (double)num;
+        LAUNCH(HSF_KERNEL_LEAF, 64.0 * units + 16.0 * la.num_groups * num, 8.0 * 20.0 * units,
+               launch_leaf_dots(la, st));
+        LAUNCH(HSF_KERNEL_REDUCE, 16.0 * la.num_groups * num + 64.0 * num, 0.0,
+               launch_reduce_partials(la.partial, la.num_groups, la.S, outd, comp, st));
+        continue;
       }
       const bool streams = leaf_streams(la, p->precision);
       if (streams) {

@@ -104,6 +104,11 @@ struct LeafArgs {
   const void *G;         // factored: [(r+1)][(r+1)][4][4], G over digits [m0, m1)
   const void *H;         // chunks of <= 4 amplitudes: [(r+1)][(r+1)][D^2][D][D] or NULL
   const int64_t *perm;   // streaming kernels: bitstring i of ia / ib is output perm[i] (NULL: i)
+  // dot form (launch_leaf_dots): the deepest level wrote, per (parent, bitstring, side),
+  // the four dots d[2 i + j] of the factored leaf instead of the parent states
+  const void *Da, *Db;   // [num_parents][S] x 2 float4, each side in its own bitstring order
+  const uint32_t *dida;  // [S] the bitstring at each position of side a's order
+  const uint32_t *dposb; // [S] position of each bitstring in side b's order
   double *partial;       // [num_groups][S][2]
   uint32_t *sync;        // 2 words of device scratch (grid barrier of the streaming kernel)
   int32_t *err;          // device status word
@@ -219,6 +224,20 @@ struct LevelMmaArgs {
   // segment s of row R is read by some bitstring; other segments are not stored (NULL:
   // every segment is stored)
   const uint32_t *store_mask;
+  // FP16 kernel, deepest level before a factored leaf on 16-amplitude chunks (dot form):
+  // instead of the child rows, the four leaf dots d[2 i + j] = sum_k S[rr][e_i(k)]
+  // x[e_j(k)] of every bitstring's chunk x are written, 32 bytes per (child, bitstring)
+  // (NULL: store the rows)
+  float4 *dots;            // [num_nodes][dot_count] x 2, bitstrings in dot_list order
+  // the bitstrings ordered by key (segment within the row s) << (h - 6) | row R of their
+  // chunk (storage index 64 R + 16 s + rr): dot_off[key] is the first position of a key,
+  // dot_list[pos] = R << 4 | rr
+  const uint32_t *dot_off; // [2^(h-4) + 1]
+  const uint32_t *dot_list;    // [dot_count]
+  const float2 *dot_T;     // [16 e][16 rr] S[rr][e]
+  int64_t dot_count;
+  int32_t dot_pf;          // the factor's chunk bit
+  int32_t pad2;
 };
 // A one- or two-qubit op on storage bits < kMmaPostBits, applied by the tensor-core
 // level's epilogue to each staged 32-row quarter (amplitude bits 0..5, row bits 0..4).
@@ -312,6 +331,23 @@ cudaError_t launch_bitstring_sort(const uint64_t *ia, const uint64_t *ib, int64_
                                   uint64_t *ia_s, uint64_t *ib_s, int64_t *perm, cudaStream_t st);
 // the factored leaf kernel runs for this launch (FP32, factored operators, 3-4 digits)
 bool leaf_factored(const LeafArgs &a, int precision);
+// Dot form of the factored leaf.  launch_dot_sort, once per run: on each side the
+// bitstrings ordered by key (segment s within the 64-amplitude row) << (h - 6) | row R
+// of their chunk, so that the bitstrings of 16 consecutive rows in one segment are one
+// range (off[side] holds the 2^(h-4) + 1 first positions, list[side] R << 4 | rr per
+// position, ida the bitstring at each side-a position, posb the side-b position of each
+// bitstring; cur[side] is scratch of 2^(h-4) words), and S of each side transposed to
+// [e][rr], the table the level epilogue reads.  launch_leaf_dots: the bilinear form
+// summed over the parents from the dots the level wrote.
+struct DotSort {
+  uint32_t *off[2], *cur[2], *list[2], *ida, *posb;
+  float2 *T[2];
+};
+size_t dot_sort_bytes(int64_t S, int ha, int hb);
+DotSort dot_sort_layout(unsigned char *base, int64_t S, int ha, int hb);
+cudaError_t launch_dot_sort(const uint64_t *ia, const uint64_t *ib, int64_t S, int ha, int hb, const void *Sa,
+                            const void *Sb, const DotSort &d, cudaStream_t st);
+cudaError_t launch_leaf_dots(const LeafArgs &a, cudaStream_t st);
 cudaError_t launch_index_prep(const IndexArgs &a, cudaStream_t st);
 // dst[i] = storage index of local index i, i < count.
 cudaError_t launch_range_index(uint64_t *dst, int64_t count, const PermArgs &perm, cudaStream_t st);

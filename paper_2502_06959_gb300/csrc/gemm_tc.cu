@@ -30,6 +30,7 @@
 #include <cstdint>
 #include <cstring>
 #include <mutex>
+#include <type_traits>
 
 #include "common.h"
 
@@ -845,6 +846,17 @@ constexpr int kHThreads = (9 + kHSplit) * 32;   // + 2 x 4 epilogue warps and th
 constexpr uint32_t kHTmemCols = 512;            // W_i hi 128 i + [0,64), lo + [64,128); D 2 x 128 at 256
 constexpr size_t kHSmem = (size_t)kHOps * kHOpBytes + (size_t)kHRaw * kHQuarter + 1024;
 static_assert(kHSmem <= 227 * 1024 - 4096, "FP16 level kernel shared memory");
+// Dot form: each epilogue warp stages 16 rows of its 16-amplitude segment (2 KB) for the
+// lanes that form the leaf dots, and keeps the bitstring entries of its unit's rows
+// (kDotMeta, 1 KB); the CTA keeps S as the [e][rr] table (2 KB).  For that room the raw
+// ring has four stages, the row scales are kept as exponent bytes and the store mask is
+// not used.
+constexpr int kDotRows = 16;
+constexpr int kHRawDots = 4;
+constexpr int kDotMeta = 256;                   // entries per warp held in shared memory
+constexpr size_t kHSmemDots = (size_t)kHOps * kHOpBytes + (size_t)kHRawDots * kHQuarter + 1024;
+static_assert(kHSmemDots + 8 * kDotRows * 128 + 2048 + 8 * kDotMeta * 4 + 4 * 128 + 256 <= 227 * 1024,
+              "FP16 level kernel shared memory (dot form)");
 
 __device__ __forceinline__ void lvl_cp_async16(uint32_t dst, const void *src) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
@@ -878,25 +890,35 @@ __device__ __forceinline__ uint32_t h2_bits(__half2 h) {
 
 constexpr int kHMaskWords = (1 << (17 - 4)) / 32;   // store mask of a half state of up to 2^17 amplitudes
 
+template <int PF>
 __global__ void __launch_bounds__(kHThreads, 1) level_mma_f16_kernel(LevelMmaArgs a) {
+  constexpr bool DOTS = PF >= 0;
+  constexpr int RAW = DOTS ? kHRawDots : kHRaw;   // raw quarters in the ring
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
   uint8_t *sOp = smem;                                  // operand buffer o: sOp + o * kHOpBytes
   uint8_t *sR = sOp + kHOps * kHOpBytes;            // raw quarter r: sR + r * kHQuarter
   __shared__ __align__(8) uint64_t ops_full[kHOps], ops_empty[kHOps],
       sc_full[4], tfull[2], tempty[2], drain;
-  __shared__ float row_inv[4][128];                     // per unit (4 in flight): 1 / row scale
+  // per unit (4 in flight): 1 / row scale (dot form: the scale's exponent byte)
+  __shared__ typename std::conditional<DOTS, uint8_t, float>::type row_inv[4][128];
   __shared__ uint32_t tmem_sh;
   __shared__ volatile int abort_sh, epi_abort[2];
-  __shared__ uint32_t mask_sh[kHMaskWords];             // the store mask, when it fits
+  __shared__ uint32_t mask_sh[DOTS ? 1 : kHMaskWords];  // the store mask, when it fits
+  // dot form: per epilogue warp a row tile and an entry buffer; S as [e][rr]
+  __shared__ __align__(16) float dot_tile[DOTS ? 8 * kDotRows * 32 : 4];
+  __shared__ __align__(16) float2 dot_S[DOTS ? 256 : 1];
+  __shared__ uint32_t dot_meta[DOTS ? 8 * kDotMeta : 1];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t radix = a.radix;
   // 2^(h-4) mask bits; staged in shared memory for h <= 17 (visible after the first
   // __syncthreads below)
-  const bool mask_in_smem = a.store_mask && a.h <= 17;
+  const bool mask_in_smem = !DOTS && a.store_mask && a.h <= 17;
   if (mask_in_smem)
     for (int e = threadIdx.x; e < (1 << (a.h - 4)) / 32; e += blockDim.x) mask_sh[e] = a.store_mask[e];
-  const uint32_t *smask = mask_in_smem ? mask_sh : a.store_mask;
+  const uint32_t *smask = DOTS ? nullptr : mask_in_smem ? mask_sh : a.store_mask;
+  if constexpr (DOTS)
+    for (int e = threadIdx.x; e < 256; e += blockDim.x) dot_S[e] = a.dot_T[e];
   // A CTA serves kHDigits consecutive digits (one when the radix is odd): each parent unit
   // is split once and multiplied by every digit's W.  Units run over the parents with a
   // child in [node_lo, node_lo + num_nodes); children outside are computed, not stored.
@@ -993,7 +1015,7 @@ __global__ void __launch_bounds__(kHThreads, 1) level_mma_f16_kernel(LevelMmaArg
     auto issue = [&](int64_t c) {
       if (c < nquarters) {
         const uint8_t *src = src_of(c);
-        const uint32_t dst = smem_u32(sR + (int)(c % kHRaw) * kHQuarter);
+        const uint32_t dst = smem_u32(sR + (int)(c % RAW) * kHQuarter);
 #pragma unroll
         for (int i = 0; i < kItems; ++i)
 #pragma unroll
@@ -1005,7 +1027,7 @@ __global__ void __launch_bounds__(kHThreads, 1) level_mma_f16_kernel(LevelMmaArg
       lvl_cp_commit();                                   // (empty groups keep the count uniform)
     };
 #pragma unroll
-    for (int c = 0; c < kHRaw - 1; ++c) issue(c);
+    for (int c = 0; c < RAW - 1; ++c) issue(c);
     int64_t it = 0;
     // A split warp stops as a whole: its lanes meet at __syncwarp and full-mask shuffles
     // below, so the abort flag and the result of the bounded wait are combined across
@@ -1020,12 +1042,12 @@ __global__ void __launch_bounds__(kHThreads, 1) level_mma_f16_kernel(LevelMmaArg
         break;
       }
       const uint32_t op = smem_u32(sOp + o * kHOpBytes);
-      float *inv = row_inv[tu & 3];
+      auto *inv = row_inv[tu & 3];
       for (int q = 0; q < 4; ++q, ++it) {
-        issue(it + kHRaw - 1);                         // into the stage read last iteration
-        lvl_cp_wait<kHRaw - 1>();                      // this thread's copies of quarter it
+        issue(it + RAW - 1);                           // into the stage read last iteration
+        lvl_cp_wait<RAW - 1>();                        // this thread's copies of quarter it
         __syncwarp();                                    // ... and the rest of its warp's
-        const uint32_t raw = smem_u32(sR + (int)(it % kHRaw) * kHQuarter);
+        const uint32_t raw = smem_u32(sR + (int)(it % RAW) * kHQuarter);
         float4 xr[kItems][2];
 #pragma unroll
         for (int i = 0; i < kItems; ++i) {
@@ -1065,7 +1087,12 @@ __global__ void __launch_bounds__(kHThreads, 1) level_mma_f16_kernel(LevelMmaArg
           const uint32_t off = (uint32_t)(pc >> 3) * kHAtom + (uint32_t)n * 128 + ((uint32_t)((pc & 7) ^ (n & 7)) << 4);
           sts128(op + off, hb[0], hb[1], hb[2], hb[3]);
           sts128(op + 2 * kHAtom + off, lb[0], lb[1], lb[2], lb[3]);
-          if (pc == 0) inv[n] = __uint_as_float((254u - sb) << 23);
+          if (pc == 0) {
+            if constexpr (DOTS)
+              inv[n] = (uint8_t)sb;
+            else
+              inv[n] = __uint_as_float((254u - sb) << 23);
+          }
         }
       }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -1133,13 +1160,33 @@ __global__ void __launch_bounds__(kHThreads, 1) level_mma_f16_kernel(LevelMmaArg
     const int q4 = warp & 3;
     const int comp = q4 * 32 + lane;
     const float *inv_ws = reinterpret_cast<const float *>(wimg + (size_t)radix * kMmaWDigitBytes) + m0;
+    // dot form: this warp's row tile and entry buffer
+    const int ew = grp * 4 + q4;
+    float *tile = dot_tile + (DOTS ? ew * kDotRows * 32 : 0);
+    uint32_t *meta = dot_meta + (DOTS ? ew * kDotMeta : 0);
     int64_t tu = 0;
     // The four warps of a group meet at named barriers, so they decide to stop together:
     // only they write their epi_abort word, before a barrier, and all read it after.
     for (int64_t u = blockIdx.x; u < units; u += gridDim.x, ++tu) {
-      const float *inv = row_inv[tu & 3];
+      const auto *inv = row_inv[tu & 3];
       const int64_t pu = p_first + (u >> tb);           // the unit's parent
       bool stop = false;
+      // dot form: the bitstring entries of this unit's rows in segment q4 for the group's
+      // two quarters (qr = grp, grp + 2), shared by every digit of the unit.  Sorted by
+      // (segment in row, row), those of 16 consecutive rows are one range of dot_list;
+      // lane 3 qi + b holds boundary b (row 32 qr + 16 b) of quarter qi, and the entries
+      // of quarter 0 then 1 go to meta (up to kDotMeta; the rest are read from dot_list).
+      uint32_t bnd = 0, n0 = 0;
+      if constexpr (DOTS) {
+        const uint32_t kq = ((uint32_t)q4 << (a.h - 6)) + ((uint32_t)(u & ((1 << tb) - 1)) << 7);
+        if (lane < 6) bnd = a.dot_off[kq + 32u * (uint32_t)(grp + 2 * (lane / 3)) + 16u * (uint32_t)(lane % 3)];
+        const uint32_t s0 = __shfl_sync(0xffffffffu, bnd, 0), e0 = __shfl_sync(0xffffffffu, bnd, 2);
+        const uint32_t s1 = __shfl_sync(0xffffffffu, bnd, 3), e1 = __shfl_sync(0xffffffffu, bnd, 5);
+        n0 = e0 - s0;
+        const uint32_t n = min(n0 + (e1 - s1), (uint32_t)kDotMeta);
+        for (uint32_t m = (uint32_t)lane; m < n; m += 32) meta[m] = __ldg(a.dot_list + (m < n0 ? s0 + m : s1 + (m - n0)));
+        __syncwarp();
+      }
       for (int i = 0; i < dpc; ++i) {
         const int64_t oi = tu * dpc + i;
         const int b = (int)(oi & 1);
@@ -1158,40 +1205,131 @@ __global__ void __launch_bounds__(kHThreads, 1) level_mma_f16_kernel(LevelMmaArg
         const bool store = g >= a.node_lo && g < a.node_lo + a.num_nodes;
         const uint64_t dst_off = store ? (((uint64_t)(g - a.node_lo) << a.h) + ((uint64_t)(u & ((1 << tb) - 1)) << 13)) * 2 : 0;
         const float inv_w = inv_ws[i];
-#pragma unroll 1
-        for (int qr = grp; qr < 4; qr += 2) {
-          uint32_t v[32];
-          const uint32_t taddr = tmem + ((uint32_t)(q4 * 32) << 16) + 256u + (uint32_t)(b * 128 + qr * 32);
-          asm volatile(
-              "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-              "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-              : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-                "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
-                "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
-                "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
-              : "r"(taddr));
-          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        if constexpr (DOTS) {
           if (store) {
-            // row j of the quarter goes out from registers, a warp writing its 32
-            // components (128 contiguous bytes: segment q4 of the row) per row; with a
-            // store mask, segments no bitstring reads are skipped (the bit is the same
-            // for the whole warp)
-            float *out = a.child + dst_off + (size_t)qr * 32 * 128 + comp;
-            uint32_t keep = 0xffffffffu;
-            if (smask) {
-              const uint64_t r0 = ((uint64_t)(u & ((1 << tb) - 1)) << 7) + (uint64_t)qr * 32;   // first row
-              const uint32_t *mw = smask + (r0 >> 3);                  // 8 rows (4 bits each) per word
-              keep = 0;
+            // Dot form.  Per half quarter (16 rows), this warp's segment q4 of each row is
+            // staged in its tile (row jj, 16-byte piece p at p ^ (jj % 8)), and each lane
+            // takes one bitstring whose chunk is one of those segments (the range
+            // [hs, he) of dot_list), forms its four dots and writes them at its position.
+            const uint64_t row0 = (uint64_t)(u & ((1 << tb) - 1)) << 7;
+            float4 *dout = a.dots + (uint64_t)(g - a.node_lo) * (uint64_t)a.dot_count * 2u;
+#pragma unroll 1
+            for (int qr = grp; qr < 4; qr += 2) {
+              const int qi = qr >> 1;
+              const uint32_t qs = __shfl_sync(0xffffffffu, bnd, 3 * qi);
 #pragma unroll
-              for (int w4 = 0; w4 < 4; ++w4) {
-                const uint32_t word = mw[w4];
+              for (int hh = 0; hh < 2; ++hh) {
+                const uint32_t hs = __shfl_sync(0xffffffffu, bnd, 3 * qi + hh);
+                const uint32_t he = __shfl_sync(0xffffffffu, bnd, 3 * qi + hh + 1);
+                const uint32_t rbase = (uint32_t)row0 + (uint32_t)(qr * 32 + hh * kDotRows);
+                const uint32_t mbase = (qi ? n0 : 0u) + (hs - qs);
+                uint32_t v[kDotRows];
+                const uint32_t taddr =
+                    tmem + ((uint32_t)(q4 * 32) << 16) + 256u + (uint32_t)(b * 128 + qr * 32 + hh * kDotRows);
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
+                    "[%16];"
+                    : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                      "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
+                      "=r"(v[15])
+                    : "r"(taddr));
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                // the 16 values first, then the 16 stores (interleaving the two ran three
+                // times slower)
+                float xs[kDotRows];
 #pragma unroll
-                for (int jj = 0; jj < 8; ++jj) keep |= ((word >> (4 * jj + q4)) & 1u) << (8 * w4 + jj);
+                for (int jj = 0; jj < kDotRows; ++jj) {
+                  const float sc = __uint_as_float((254u - (uint32_t)inv[qr * 32 + hh * kDotRows + jj]) << 23);
+                  xs[jj] = __uint_as_float(v[jj]) * sc * inv_w;
+                }
+#pragma unroll
+                for (int jj = 0; jj < kDotRows; ++jj) tile[jj * 32 + ((((lane >> 2) ^ (jj & 7)) << 2) | (lane & 3))] = xs[jj];
+                __syncwarp();
+                for (uint32_t t0 = hs; t0 < he; t0 += 32) {
+                  const uint32_t pos = t0 + (uint32_t)lane;
+                  if (pos < he) {
+                    const uint32_t m = mbase + (pos - hs);
+                    const uint32_t ent = m < (uint32_t)kDotMeta ? meta[m] : __ldg(a.dot_list + pos);
+                    const uint32_t j = (ent >> 4) - rbase, rr = ent & 15u;
+                    // amplitude e of row j is float2 e ^ 2 (j % 8) of the row (16-byte
+                    // pieces swizzled); w[e] = S[rr][e] is dot_S[16 e + rr]
+                    const float2 *xrow = reinterpret_cast<const float2 *>(tile) + j * 16;
+                    const uint32_t jx = (j & 7u) << 1;
+                    // the four dots as in the factored leaf kernel: P = sum Re w . x,
+                    // Q = sum Im w . x over (re, im) pairs, w x = (P.x - Q.y, P.y + Q.x)
+                    float2 P[4], Q[4];
+#pragma unroll
+                    for (int al = 0; al < 4; ++al) P[al] = Q[al] = make_float2(0.f, 0.f);
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) {
+                      // the k-th term's amplitudes e_0(k), e_1(k): factor bit 0 / 1 put at
+                      // chunk bit PF
+                      constexpr uint32_t lo = (1u << (DOTS ? PF : 0)) - 1u;
+                      const uint32_t e0 = (((uint32_t)k & ~lo) << 1) | ((uint32_t)k & lo), e1 = e0 | (lo + 1u);
+                      const float2 x0 = xrow[e0 ^ jx], x1 = xrow[e1 ^ jx];
+                      const float2 w0 = dot_S[e0 * 16 + rr], w1 = dot_S[e1 * 16 + rr];
+                      P[0].x = fmaf(w0.x, x0.x, P[0].x);
+                      P[0].y = fmaf(w0.x, x0.y, P[0].y);
+                      Q[0].x = fmaf(w0.y, x0.x, Q[0].x);
+                      Q[0].y = fmaf(w0.y, x0.y, Q[0].y);
+                      P[1].x = fmaf(w0.x, x1.x, P[1].x);
+                      P[1].y = fmaf(w0.x, x1.y, P[1].y);
+                      Q[1].x = fmaf(w0.y, x1.x, Q[1].x);
+                      Q[1].y = fmaf(w0.y, x1.y, Q[1].y);
+                      P[2].x = fmaf(w1.x, x0.x, P[2].x);
+                      P[2].y = fmaf(w1.x, x0.y, P[2].y);
+                      Q[2].x = fmaf(w1.y, x0.x, Q[2].x);
+                      Q[2].y = fmaf(w1.y, x0.y, Q[2].y);
+                      P[3].x = fmaf(w1.x, x1.x, P[3].x);
+                      P[3].y = fmaf(w1.x, x1.y, P[3].y);
+                      Q[3].x = fmaf(w1.y, x1.x, Q[3].x);
+                      Q[3].y = fmaf(w1.y, x1.y, Q[3].y);
+                    }
+                    float4 *dp = dout + 2 * (uint64_t)pos;
+                    dp[0] = make_float4(P[0].x - Q[0].y, P[0].y + Q[0].x, P[1].x - Q[1].y, P[1].y + Q[1].x);
+                    dp[1] = make_float4(P[2].x - Q[2].y, P[2].y + Q[2].x, P[3].x - Q[3].y, P[3].y + Q[3].x);
+                  }
+                }
+                __syncwarp();                                // the tile is read before the next half
               }
             }
-#pragma unroll
-            for (int j = 0; j < 32; ++j)
-              if ((keep >> j) & 1u) out[(size_t)j * 128] = __uint_as_float(v[j]) * inv[qr * 32 + j] * inv_w;
+          }
+        } else {
+  #pragma unroll 1
+          for (int qr = grp; qr < 4; qr += 2) {
+            uint32_t v[32];
+            const uint32_t taddr = tmem + ((uint32_t)(q4 * 32) << 16) + 256u + (uint32_t)(b * 128 + qr * 32);
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                  "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
+                  "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
+                  "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+                : "r"(taddr));
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            if (store) {
+              // row j of the quarter goes out from registers, a warp writing its 32
+              // components (128 contiguous bytes: segment q4 of the row) per row; with a
+              // store mask, segments no bitstring reads are skipped (the bit is the same
+              // for the whole warp)
+              float *out = a.child + dst_off + (size_t)qr * 32 * 128 + comp;
+              uint32_t keep = 0xffffffffu;
+              if (smask) {
+                const uint64_t r0 = ((uint64_t)(u & ((1 << tb) - 1)) << 7) + (uint64_t)qr * 32;   // first row
+                const uint32_t *mw = smask + (r0 >> 3);                  // 8 rows (4 bits each) per word
+                keep = 0;
+  #pragma unroll
+                for (int w4 = 0; w4 < 4; ++w4) {
+                  const uint32_t word = mw[w4];
+  #pragma unroll
+                  for (int jj = 0; jj < 8; ++jj) keep |= ((word >> (4 * jj + q4)) & 1u) << (8 * w4 + jj);
+                }
+              }
+  #pragma unroll
+              for (int j = 0; j < 32; ++j)
+                if ((keep >> j) & 1u) out[(size_t)j * 128] = __uint_as_float(v[j]) * inv[qr * 32 + j] * inv_w;
+            }
           }
         }
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -1413,13 +1551,22 @@ cudaError_t launch_level_mma(const LevelMmaArgs &a, cudaStream_t st) {
     // FP16 split kernel (W image: FP16 parts per digit, then the inverse scales)
     if (a.h < kMmaMinH || (reinterpret_cast<uintptr_t>(a.parent) & 15) || (reinterpret_cast<uintptr_t>(a.child) & 15))
       return cudaErrorInvalidValue;
-    cudaError_t e = cudaFuncSetAttribute(level_mma_f16_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kHSmem);
+    if (a.dots && (!a.dot_off || !a.dot_list || !a.dot_T || a.dot_pf < 0 || a.dot_pf > 3 || a.dot_count <= 0 ||
+                   (reinterpret_cast<uintptr_t>(a.dots) & 15) || (reinterpret_cast<uintptr_t>(a.dot_T) & 15)))
+      return cudaErrorInvalidValue;
+    const size_t smem = a.dots ? kHSmemDots : kHSmem;
+    auto kernel = !a.dots ? level_mma_f16_kernel<-1>
+                  : a.dot_pf == 0 ? level_mma_f16_kernel<0>
+                  : a.dot_pf == 1 ? level_mma_f16_kernel<1>
+                  : a.dot_pf == 2 ? level_mma_f16_kernel<2>
+                                  : level_mma_f16_kernel<3>;
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const int dpc = r % kHDigits == 0 ? kHDigits : 1;
     const int gy = r / dpc;
     const int64_t units = ((a.node_lo + a.num_nodes - 1) / r - a.node_lo / r + 1) << (a.h - kMmaMinH);
     const int64_t gx = std::min<int64_t>(std::max(1, (sms + gy - 1) / gy), std::max<int64_t>(1, units));
-    level_mma_f16_kernel<<<dim3((unsigned)gx, (unsigned)gy), kHThreads, kHSmem, st>>>(a);
+    kernel<<<dim3((unsigned)gx, (unsigned)gy), kHThreads, smem, st>>>(a);
     return cudaGetLastError();
   }
   const size_t smem = kLvlSmem;

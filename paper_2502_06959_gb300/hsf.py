@@ -33,6 +33,7 @@ FLAG_REG5 = 16
 FLAG_REG3 = 32
 FLAG_NO_TC_LEVEL = 64
 FLAG_SVD_BLOCKS = 128
+FLAG_LEAF_DOTS = 256
 
 
 class HsfError(RuntimeError):

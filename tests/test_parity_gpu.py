@@ -477,3 +477,62 @@ def test_c2_leaf_is_factored():
     desc = hsf.hsf_plan_describe(plan.handle)
     plan.close()
     assert "leaf=factored" in desc
+
+
+def _run_profiled(pr, bs, flags=0, path_range=(0, 0), budget=0):
+    """Amplitudes of `bs` and the per-kind launch statistics of that one run."""
+    import torch
+    from paper_2502_06959_gb300 import hsf
+    plan = hsf.Plan.from_problem(pr, precision="c64", flags=flags)
+    dbs = torch.from_numpy(np.asarray(bs, dtype=np.uint64).view(np.int64)).cuda()
+    hsf.hsf_set_profiling(True)
+    try:
+        out = plan.run(dbs, path_range=path_range, budget=budget)
+        torch.cuda.synchronize()
+        stats = hsf.hsf_profile_collect(plan.handle)
+    finally:
+        hsf.hsf_set_profiling(False)
+    res = out.cpu().numpy()
+    plan.close()
+    return res, stats
+
+
+def _took_dot_form(stats_dots, stats_rows):
+    """The leaf's counted FLOP per (parent, bitstring): 8 (4 x 16 + 20) = 672 from stored
+    chunks, 8 x 20 = 160 from the dots; the same units in both runs."""
+    return stats_dots["leaf"]["flops"] * 672.0 == pytest.approx(stats_rows["leaf"]["flops"] * 160.0, rel=1e-12)
+
+
+@pytest.mark.parametrize("count", [1, 37, 4096])
+def test_leaf_dot_form_equals_stored_children(count):
+    """C2 (n = 30, 4^8 paths) at the benchmark's launch sizes: level 7 writing the four
+    leaf dots per (child, bitstring) (HSF_FLAG_LEAF_DOTS) must give the same bits as
+    level 7 storing its children and the factored leaf kernel reading them (the dots are
+    formed from the same FP32 values in the same order, and the bilinear form is summed
+    in the same order), over all paths and over ranges whose first or last parent has
+    only part of its digits."""
+    from paper_2502_06959_gb300 import hsf
+    pr = W.workload_c2()
+    bs = pr.bitstrings[:count]
+    for path_range in ((0, 0), (1, 47), (40001, 40003), (65535, 65536)):
+        a, sa = _run_profiled(pr, bs, hsf.FLAG_LEAF_DOTS, path_range)
+        b, sb = _run_profiled(pr, bs, 0, path_range)
+        assert _took_dot_form(sa, sb), path_range
+        assert np.array_equal(a, b), (path_range, np.max(np.abs(a - b)))
+
+
+def test_leaf_dot_form_over_path_chunks():
+    """A workspace budget that splits the first 4096 C2 paths into four chunks (each
+    chunk's dots overwrite the previous chunk's): the dot form against the oracle's
+    path sum over a range cutting a parent, and against the stored-children run over
+    all 4096 paths."""
+    from paper_2502_06959_gb300 import hsf
+    pr = W.workload_c2()
+    bs = pr.bitstrings[:333]
+    ref, sr = _run_profiled(pr, bs, 0, (0, 4096))
+    got, sg = _run_profiled(pr, bs, hsf.FLAG_LEAF_DOTS, (0, 4096), budget=256 << 20)
+    assert _took_dot_form(sg, sr)
+    check(got, ref, "c64")
+    want, _ = O.hsf_amplitudes(pr.n, pr.gates, pr.cut, pr.blocks, bitstrings=bs, path_range=(1021, 1030))
+    got, _ = _run_profiled(pr, bs, hsf.FLAG_LEAF_DOTS, (1021, 1030), budget=256 << 20)
+    check(got, want, "c64")
