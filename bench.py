@@ -670,6 +670,10 @@ def main():
 
     # workspace sized once for this circuit
     pflags = hsf.FLAG_LEAF_DOTS if args.leaf_dots else 0
+    if args.leaf_dots:
+        # the ncu traffic ratios were taken on the stored-children path
+        for k in ("level_f16", "leaf"):
+            PROFILED_TRAFFIC.pop(k, None)
     plan0 = hsf.Plan.from_problem(pr, precision=args.precision, flags=pflags)
     info = dict(plan0.info)
     free, _ = torch.cuda.mem_get_info()
