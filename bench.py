@@ -159,7 +159,7 @@ PROFILED_TRAFFIC = {
               "kernel": "sweep_reg_kernel", "sha256": "1a9bade5309e94b9",
               "profile": "profiles/sweep_reg_level6_n30.md"},
     "level_f16": {"ratio": (268.8 + 878.2) / 1342.2, "source": "paper_2502_06959_gb300/csrc/gemm_tc.cu",
-                  "kernel": "level_mma_f16_kernel", "sha256": "91c1097dc391da30",
+                  "kernel": "level_mma_f16_kernel", "sha256": "8185c06fa54cecd6",
                   "profile": "profiles/level_f16_level7_n30.md"},
     "leaf": {"ratio": (1883.1 + 7.0) / 2151.7, "source": "paper_2502_06959_gb300/csrc/accum.cu",
              "kernel": "leaf_contract_fact_kernel", "sha256": "f449d346010749b5",

@@ -907,7 +907,7 @@ __global__ void __launch_bounds__(kHThreads, 1) level_mma_f16_kernel(LevelMmaArg
   __shared__ uint32_t mask_sh[DOTS ? 1 : kHMaskWords];  // the store mask, when it fits
   // dot form: per epilogue warp a row tile and an entry buffer; S as [e][rr]
   __shared__ __align__(16) float dot_tile[DOTS ? 8 * kDotRows * 32 : 4];
-  __shared__ __align__(16) float2 dot_S[DOTS ? 256 : 1];
+  __shared__ __align__(16) float2 dot_S[DOTS ? 256 : 1];   // S[rr][e] at [e][rr]
   __shared__ uint32_t dot_meta[DOTS ? 8 * kDotMeta : 1];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t radix = a.radix;
@@ -1164,6 +1164,14 @@ __global__ void __launch_bounds__(kHThreads, 1) level_mma_f16_kernel(LevelMmaArg
     const int ew = grp * 4 + q4;
     float *tile = dot_tile + (DOTS ? ew * kDotRows * 32 : 0);
     uint32_t *meta = dot_meta + (DOTS ? ew * kDotMeta : 0);
+    // dot form: lane 3 qi + b (< 6) loads boundary b (row 32 qr + 16 b, qr = grp + 2 qi)
+    // of the bitstring ranges of unit uu's rows in segment q4, one unit ahead
+    auto load_bnd = [&](int64_t uu) -> uint32_t {
+      if (!DOTS || uu >= units || lane >= 6) return 0u;
+      const uint32_t kq = ((uint32_t)q4 << (a.h - 6)) + ((uint32_t)(uu & ((1 << tb) - 1)) << 7);
+      return a.dot_off[kq + 32u * (uint32_t)(grp + 2 * (lane / 3)) + 16u * (uint32_t)(lane % 3)];
+    };
+    uint32_t bnd_next = load_bnd(blockIdx.x);
     int64_t tu = 0;
     // The four warps of a group meet at named barriers, so they decide to stop together:
     // only they write their epi_abort word, before a barrier, and all read it after.
@@ -1178,8 +1186,8 @@ __global__ void __launch_bounds__(kHThreads, 1) level_mma_f16_kernel(LevelMmaArg
       // of quarter 0 then 1 go to meta (up to kDotMeta; the rest are read from dot_list).
       uint32_t bnd = 0, n0 = 0;
       if constexpr (DOTS) {
-        const uint32_t kq = ((uint32_t)q4 << (a.h - 6)) + ((uint32_t)(u & ((1 << tb) - 1)) << 7);
-        if (lane < 6) bnd = a.dot_off[kq + 32u * (uint32_t)(grp + 2 * (lane / 3)) + 16u * (uint32_t)(lane % 3)];
+        bnd = bnd_next;
+        bnd_next = load_bnd(u + gridDim.x);
         const uint32_t s0 = __shfl_sync(0xffffffffu, bnd, 0), e0 = __shfl_sync(0xffffffffu, bnd, 2);
         const uint32_t s1 = __shfl_sync(0xffffffffu, bnd, 3), e1 = __shfl_sync(0xffffffffu, bnd, 5);
         n0 = e0 - s0;
@@ -1251,12 +1259,25 @@ __global__ void __launch_bounds__(kHThreads, 1) level_mma_f16_kernel(LevelMmaArg
                     const uint32_t m = mbase + (pos - hs);
                     const uint32_t ent = m < (uint32_t)kDotMeta ? meta[m] : __ldg(a.dot_list + pos);
                     const uint32_t j = (ent >> 4) - rbase, rr = ent & 15u;
-                    // amplitude e of row j is float2 e ^ 2 (j % 8) of the row (16-byte
-                    // pieces swizzled); w[e] = S[rr][e] is dot_S[16 e + rr]
-                    const float2 *xrow = reinterpret_cast<const float2 *>(tile) + j * 16;
-                    const uint32_t jx = (j & 7u) << 1;
+                    // the chunk x and the row w = S[rr] into registers first: 16-byte
+                    // piece p (amplitudes 2p, 2p+1) of row j sits at piece p ^ (j % 8);
+                    // w[e] = S[rr][e] is dot_S[16 e + rr] (16 lanes read one 128-byte
+                    // row of the table: no bank conflicts)
+                    const float4 *xq = reinterpret_cast<const float4 *>(tile) + j * 8;
+                    float2 x[16], w[16];
+#pragma unroll
+                    for (int pc = 0; pc < 8; ++pc) {
+                      const float4 q = xq[pc ^ (j & 7u)];
+                      x[2 * pc] = make_float2(q.x, q.y);
+                      x[2 * pc + 1] = make_float2(q.z, q.w);
+                    }
+#pragma unroll
+                    for (int e = 0; e < 16; ++e) w[e] = dot_S[e * 16 + rr];
                     // the four dots as in the factored leaf kernel: P = sum Re w . x,
-                    // Q = sum Im w . x over (re, im) pairs, w x = (P.x - Q.y, P.y + Q.x)
+                    // Q = sum Im w . x over (re, im) pairs, w x = (P.x - Q.y, P.y + Q.x);
+                    // scalar FMAs give the bits of its packed pair FMAs (the broadcast
+                    // pairs those need cost 16-byte table reads, which conflict: 2.5 ms
+                    // per level-7 launch against 2.0)
                     float2 P[4], Q[4];
 #pragma unroll
                     for (int al = 0; al < 4; ++al) P[al] = Q[al] = make_float2(0.f, 0.f);
@@ -1264,10 +1285,9 @@ __global__ void __launch_bounds__(kHThreads, 1) level_mma_f16_kernel(LevelMmaArg
                     for (int k = 0; k < 8; ++k) {
                       // the k-th term's amplitudes e_0(k), e_1(k): factor bit 0 / 1 put at
                       // chunk bit PF
-                      constexpr uint32_t lo = (1u << (DOTS ? PF : 0)) - 1u;
-                      const uint32_t e0 = (((uint32_t)k & ~lo) << 1) | ((uint32_t)k & lo), e1 = e0 | (lo + 1u);
-                      const float2 x0 = xrow[e0 ^ jx], x1 = xrow[e1 ^ jx];
-                      const float2 w0 = dot_S[e0 * 16 + rr], w1 = dot_S[e1 * 16 + rr];
+                      constexpr int lo = (1 << (DOTS ? PF : 0)) - 1;
+                      const int e0 = ((k & ~lo) << 1) | (k & lo), e1 = e0 | (lo + 1);
+                      const float2 x0 = x[e0], x1 = x[e1], w0 = w[e0], w1 = w[e1];
                       P[0].x = fmaf(w0.x, x0.x, P[0].x);
                       P[0].y = fmaf(w0.x, x0.y, P[0].y);
                       Q[0].x = fmaf(w0.y, x0.x, Q[0].x);
