@@ -44,6 +44,16 @@ def test_every_declared_symbol_is_exported(lib):
     assert set(H.SIGNATURES) <= set(names)
 
 
+def test_flag_constants_match_header():
+    """Every HSF_FLAG_* of the header has the same value as the binding's FLAG_*."""
+    text = open(HEADER).read()
+    flags = dict(re.findall(r"#define HSF_FLAG_([A-Z0-9_]+)\s+(\d+)", text))
+    assert "LEAF_DOTS" in flags and "NO_LEAF_CONTRACT" in flags
+    for name, value in flags.items():
+        assert getattr(H, "FLAG_" + name) == int(value), name
+    assert len(set(flags.values())) == len(flags), "flag bits are distinct"
+
+
 def test_struct_layouts_match_header():
     src = r"""
     #include <stdio.h>
